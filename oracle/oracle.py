@@ -1,0 +1,211 @@
+"""ctypes wrapper for the FP64 CPU oracle (oracle/xf_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and bench.py's
+cpu_baseline / reference legs are the only callers.  The CUDA library never
+imports this module and this module never imports the CUDA library.
+
+Packed state layout (shared interface, both sides write their own code for
+it): doubles [s][u][E][n_f*n_f] with s = 0 nu, 1 nubar; per bin the n_f real
+diagonal entries, then (Re, Im) of the upper triangle in row order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "xf_oracle.c")
+_LIB = os.path.join(_HERE, "liborc.so")
+
+_lib = None
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("n_E", ctypes.c_int32), ("n_u", ctypes.c_int32), ("n_f", ctypes.c_int32),
+        ("stepper", ctypes.c_int32), ("geometry", ctypes.c_int32),
+        ("hierarchy", ctypes.c_int32), ("matter", ctypes.c_int32),
+        ("n_threads", ctypes.c_int32),
+        ("R_nu", ctypes.c_double), ("mu0", ctypes.c_double),
+        ("E_min", ctypes.c_double), ("E_max", ctypes.c_double),
+        ("dm2", ctypes.c_double * 2), ("theta", ctypes.c_double * 3),
+        ("ne_ref", ctypes.c_double), ("r_ref", ctypes.c_double), ("ne_power", ctypes.c_double),
+        ("nb0", ctypes.c_double), ("h_ns", ctypes.c_double), ("Ye", ctypes.c_double),
+        ("T", ctypes.c_double * 4), ("eta", ctypes.c_double * 4), ("L", ctypes.c_double * 4),
+        ("eps", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/liborc.so with gcc (no CUDA)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp", "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.POINTER(OrcParams)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.orc_tables.argtypes = [P, dp, dp, dp, dp]
+        L.orc_init_state.argtypes = [P, dp]
+        L.orc_evolve.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                 ctypes.POINTER(ctypes.c_int64)]
+        L.orc_moments.argtypes = [P, dp, ctypes.c_double, dp, dp]
+        L.orc_expm.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp]
+        L.orc_eigh.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.orc_fd_integral.argtypes = [ctypes.c_int, ctypes.c_double]
+        L.orc_fd_integral.restype = ctypes.c_double
+        L.orc_vac_coeff.restype = ctypes.c_double
+        L.orc_matter_coeff.restype = ctypes.c_double
+        L.orc_matter_A.argtypes = [P, ctypes.c_double]
+        L.orc_matter_A.restype = ctypes.c_double
+        _lib = L
+    return _lib
+
+
+def params(p, n_threads: int = 0) -> OrcParams:
+    """Oracle parameter block from an inputs.Problem."""
+    o = OrcParams()
+    o.n_E, o.n_u, o.n_f = p.n_E, p.n_u, p.n_f
+    o.stepper, o.geometry, o.hierarchy, o.matter = p.stepper, p.geometry, p.hierarchy, p.matter
+    o.n_threads = n_threads
+    o.R_nu, o.mu0, o.E_min, o.E_max = p.R_nu, p.mu0, p.E_min, p.E_max
+    o.dm2[:] = list(p.dm2)
+    o.theta[:] = list(p.theta)
+    o.ne_ref, o.r_ref, o.ne_power = p.ne_ref, p.r_ref, p.ne_power
+    o.nb0, o.h_ns, o.Ye = p.nb0, p.h_ns, p.Ye
+    o.T[:] = list(p.T)
+    o.eta[:] = list(p.eta)
+    o.L[:] = list(p.L)
+    o.eps, o.seed = p.eps, p.seed
+    return o
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def state_size(p) -> int:
+    return 2 * p.n_u * p.n_E * p.n_f * p.n_f
+
+
+def tables(p):
+    o = params(p)
+    E = np.zeros(p.n_E)
+    u = np.zeros(p.n_u)
+    phi = np.zeros((4, p.n_E))
+    Hv = np.zeros((p.n_E, p.n_f * p.n_f))
+    rc = lib().orc_tables(ctypes.byref(o), _dp(E), _dp(u), _dp(phi), _dp(Hv))
+    if rc:
+        raise ValueError(f"orc_tables: {rc}")
+    return E, u, phi, Hv
+
+
+def init_state(p) -> np.ndarray:
+    o = params(p)
+    rho = np.zeros(state_size(p))
+    rc = lib().orc_init_state(ctypes.byref(o), _dp(rho))
+    if rc:
+        raise ValueError(f"orc_init_state: {rc}")
+    return rho
+
+
+def evolve(p, rho: np.ndarray, r0: float, h: float, n_steps: int, n_threads: int = 0):
+    """Returns (rho_out, status, steps_done); status 1 = non-finite stop."""
+    o = params(p, n_threads)
+    out = np.ascontiguousarray(rho, dtype=np.float64).copy()
+    done = ctypes.c_int64(0)
+    rc = lib().orc_evolve(ctypes.byref(o), _dp(out), r0, h, int(n_steps), ctypes.byref(done))
+    if rc < 0:
+        raise ValueError(f"orc_evolve: {rc}")
+    return out, rc, done.value
+
+
+def moments(p, rho: np.ndarray, r: float):
+    o = params(p)
+    M0 = np.zeros(p.n_f * p.n_f)
+    M1 = np.zeros(p.n_f * p.n_f)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    lib().orc_moments(ctypes.byref(o), _dp(rho), r, _dp(M0), _dp(M1))
+    return M0, M1
+
+
+def expm(H_packed: np.ndarray, t: float) -> np.ndarray:
+    n = int(round(np.sqrt(H_packed.size)))
+    U = np.zeros(2 * n * n)
+    lib().orc_expm(n, _dp(np.ascontiguousarray(H_packed, dtype=np.float64)), t, _dp(U))
+    return (U[0::2] + 1j * U[1::2]).reshape(n, n)
+
+
+def eigh(H_packed: np.ndarray):
+    n = int(round(np.sqrt(H_packed.size)))
+    w = np.zeros(n)
+    V = np.zeros(2 * n * n)
+    lib().orc_eigh(n, _dp(np.ascontiguousarray(H_packed, dtype=np.float64)), _dp(w), _dp(V))
+    return w, (V[0::2] + 1j * V[1::2]).reshape(n, n)
+
+
+def fd_integral(k: int, eta: float) -> float:
+    return lib().orc_fd_integral(k, eta)
+
+
+def vac_coeff() -> float:
+    return lib().orc_vac_coeff()
+
+
+def matter_coeff() -> float:
+    return lib().orc_matter_coeff()
+
+
+def matter_A(p, r: float) -> float:
+    o = params(p)
+    return lib().orc_matter_A(ctypes.byref(o), r)
+
+
+# ---- packed-layout helpers (plain numpy; interpretation of the layout) ----
+
+def unpack(rho: np.ndarray, n_f: int) -> np.ndarray:
+    """Packed [..., n_f*n_f] -> complex matrices [..., n_f, n_f]."""
+    x = rho.reshape(-1, n_f * n_f)
+    M = np.zeros((x.shape[0], n_f, n_f), dtype=complex)
+    for i in range(n_f):
+        M[:, i, i] = x[:, i]
+    k = n_f
+    for i in range(n_f):
+        for j in range(i + 1, n_f):
+            z = x[:, k] + 1j * x[:, k + 1]
+            M[:, i, j] = z
+            M[:, j, i] = np.conj(z)
+            k += 2
+    return M
+
+
+def pack(M: np.ndarray) -> np.ndarray:
+    n_f = M.shape[-1]
+    M = M.reshape(-1, n_f, n_f)
+    x = np.zeros((M.shape[0], n_f * n_f))
+    for i in range(n_f):
+        x[:, i] = M[:, i, i].real
+    k = n_f
+    for i in range(n_f):
+        for j in range(i + 1, n_f):
+            x[:, k] = M[:, i, j].real
+            x[:, k + 1] = M[:, i, j].imag
+            k += 2
+    return x.reshape(-1)
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(force="--force" in sys.argv))

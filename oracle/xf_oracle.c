@@ -1,0 +1,745 @@
+/*
+ * xf_oracle.c -- plain FP64 CPU oracle for multi-angle collective neutrino
+ * flavor evolution in the neutrino bulb model (XFLAT, arXiv 1907.05560).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file exists to check the CUDA path.  Only
+ * tests/, __graft_entry__.smoke() and the cpu_baseline / reference legs of
+ * bench.py may build, load or call it.  It shares no code, header, table or
+ * constant with the CUDA library: every formula below is written out again
+ * from the paper.
+ *
+ * Representation: every density matrix is a full n_f x n_f complex matrix
+ * (C99 double complex), trace included, exactly as Eq. 3.8-3.9 use it.  Bins
+ * are ordered [s][u][E] with s = 0 for neutrinos and s = 1 for antineutrinos.
+ *
+ * What is computed (section / equation of the paper):
+ *   - vacuum Hamiltonian      Eq. 3.5-3.6 (2 flavors); 3 flavors: the same
+ *                             mass-basis form (1/2E) U diag(0, dm21, dm31) U^T
+ *   - matter potential        Eq. 3.7, profiles Eq. 4.3 (power law) / Eq. 4.4
+ *   - antineutrino rule       A -> -A, B -> -B, B_et -> -B_et*  (after Eq. 3.4)
+ *   - nu-nu potential         Eq. 3.13 with the bulb geometry Eq. 3.14-3.15;
+ *                             single-angle form Eq. 3.16-3.17
+ *   - trajectory length       Eq. 3.3 (l = r cos(theta))
+ *   - spectra                 Eq. 4.1-4.2 (Fermi-Dirac, 1/(exp(E/T-eta)+1))
+ *   - propagator              Eq. 3.10-3.12 (2 flavors); 3 flavors: spectral
+ *                             exponential from a complex Jacobi eigensolver
+ *   - integrators             classic RK4 on d(rho)/dr = -i[H,rho] dl/dr, and
+ *                             the fixed-step coarse predictor-corrector of
+ *                             Sec. 4.2.3 / Listing 5.1 (S1-S3) in rho form
+ *
+ * Readings taken where the paper is silent (each listed in the design doc):
+ *   angle variable u = sin^2(theta_0) on a midpoint grid; energy midpoint grid;
+ *   rho's diagonal carries the number-flux weights phi_a(E) relative to nu_e;
+ *   mu0 absorbs the normalisation of Eq. 3.8; the predictor-corrector averages
+ *   density matrices; the step path length is the exact chord of Eq. 3.3.
+ *
+ * Build: gcc -O2 -std=c11 -fopenmp -ffp-contract=off -fPIC -shared.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+#define NFMAX 3
+
+/* ---- parameters (layout mirrored by oracle/oracle.py) ------------------- */
+enum { ORC_RK4 = 0, ORC_EXPH = 1 };
+enum { ORC_BULB = 0, ORC_MU_R4 = 1, ORC_SINGLE_ANGLE = 2, ORC_CONST = 3 };
+enum { ORC_MATTER_NONE = 0, ORC_MATTER_POWER = 1, ORC_MATTER_EXP = 2 };
+
+typedef struct {
+    int32_t n_E, n_u, n_f, stepper, geometry, hierarchy, matter, n_threads;
+    double R_nu;      /* neutrinosphere radius, km */
+    double mu0;       /* nu-nu coupling, km^-1 */
+    double E_min, E_max; /* MeV */
+    double dm2[2];    /* eV^2, magnitudes: 2 fl dm2[0]; 3 fl dm2_21, dm2_31 */
+    double theta[3];  /* rad: 2 fl theta[0]; 3 fl theta12, theta13, theta23 */
+    double ne_ref, r_ref, ne_power; /* power law n_e = ne_ref (r_ref/r)^p, cm^-3 */
+    double nb0, h_ns, Ye;           /* exponential n_b = nb0 exp(-(r-R)/h_ns) */
+    double T[4], eta[4], L[4];      /* nu_e, nubar_e, nu_x, nubar_x */
+    double eps;       /* off-diagonal seed amplitude */
+    uint64_t seed;
+} orc_params;
+
+/* ---- physical constants, stated here from CODATA 2018 / PDG ------------- */
+static const double HBARC_EV_KM = 1.973269804e-10; /* hbar c in eV km */
+static const double HBARC_EV_CM = 1.973269804e-5;  /* hbar c in eV cm */
+static const double GF_EV2 = 1.1663787e-23;        /* Fermi constant, eV^-2 */
+static const double PI = 3.14159265358979323846;
+
+/* dm^2 [eV^2] / (2 E [MeV]) expressed in km^-1, per unit dm^2/E (Eq. 3.6). */
+double orc_vac_coeff(void) { return 1.0 / (2.0 * 1.0e6 * HBARC_EV_KM); }
+/* sqrt(2) G_F n_e in km^-1 for n_e = 1 cm^-3 (Eq. 3.7). */
+double orc_matter_coeff(void)
+{
+    return sqrt(2.0) * GF_EV2 * HBARC_EV_CM * HBARC_EV_CM * HBARC_EV_CM / HBARC_EV_KM;
+}
+
+/* ---- Fermi-Dirac integral, Eq. 4.2, by composite Simpson quadrature ----- */
+static double fd_quadrature(int k, double eta)
+{
+    double b = (eta > 0 ? eta : 0.0) + 80.0;
+    int n = 400000; /* even */
+    double h = b / n, s = 0.0;
+    for (int i = 0; i <= n; ++i) {
+        double x = i * h, xk = 1.0;
+        for (int q = 0; q < k; ++q) xk *= x;
+        double f = xk / (exp(x - eta) + 1.0);
+        double wgt = (i == 0 || i == n) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+        s += wgt * f;
+    }
+    return s * h / 3.0;
+}
+/* small memo: the same few (k, eta) pairs are asked for on every set-up */
+double orc_fd_integral(int k, double eta)
+{
+    static int nmemo = 0;
+    static int mk[16];
+    static double me[16], mv[16];
+    double v;
+#pragma omp critical(orc_fd_memo)
+    {
+        int hit = -1;
+        for (int i = 0; i < nmemo; ++i)
+            if (mk[i] == k && me[i] == eta) hit = i;
+        if (hit >= 0) v = mv[hit];
+        else {
+            v = fd_quadrature(k, eta);
+            if (nmemo < 16) {
+                mk[nmemo] = k;
+                me[nmemo] = eta;
+                mv[nmemo] = v;
+                ++nmemo;
+            }
+        }
+    }
+    return v;
+}
+
+/* ---- SplitMix64 (Steele, Lea, Flood 2014), i-th output of the stream
+ *      seeded with `seed`, evaluated directly from the counter. ------------ */
+static uint64_t splitmix64_at(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+static double uniform01(uint64_t seed, uint64_t i)
+{
+    return (double)(splitmix64_at(seed, i) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* ---- small dense complex matrix helpers (n <= 3) ------------------------ */
+static void mat_mul(int n, const cplx *A, const cplx *B, cplx *C)
+{
+    cplx T[NFMAX * NFMAX];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            cplx s = 0;
+            for (int k = 0; k < n; ++k) s += A[i * n + k] * B[k * n + j];
+            T[i * n + j] = s;
+        }
+    memcpy(C, T, sizeof(cplx) * n * n);
+}
+static void mat_adjoint(int n, const cplx *A, cplx *B)
+{
+    cplx T[NFMAX * NFMAX];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) T[i * n + j] = conj(A[j * n + i]);
+    memcpy(B, T, sizeof(cplx) * n * n);
+}
+/* rho' = U rho U^dagger */
+static void conjugate_by(int n, const cplx *U, const cplx *rho, cplx *out)
+{
+    cplx Ud[NFMAX * NFMAX], T[NFMAX * NFMAX];
+    mat_adjoint(n, U, Ud);
+    mat_mul(n, U, rho, T);
+    mat_mul(n, T, Ud, out);
+}
+
+/* ---- packed Hermitian <-> full matrix ------------------------------------
+ * packed: n diagonal reals, then (Re, Im) of the upper triangle in row order */
+static void unpack(int n, const double *p, cplx *M)
+{
+    for (int i = 0; i < n; ++i) M[i * n + i] = p[i];
+    int k = n;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            cplx z = p[k] + I * p[k + 1];
+            M[i * n + j] = z;
+            M[j * n + i] = conj(z);
+            k += 2;
+        }
+}
+static void pack(int n, const cplx *M, double *p)
+{
+    for (int i = 0; i < n; ++i) p[i] = creal(M[i * n + i]);
+    int k = n;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            p[k] = creal(M[i * n + j]);
+            p[k + 1] = cimag(M[i * n + j]);
+            k += 2;
+        }
+}
+
+/* ---- complex Hermitian Jacobi eigensolver: A = V diag(w) V^dagger -------- */
+int orc_eigh(int n, const double *Hp, double *w, double *Vri)
+{
+    cplx A[NFMAX * NFMAX], V[NFMAX * NFMAX];
+    unpack(n, Hp, A);
+    for (int i = 0; i < n * n; ++i) V[i] = 0;
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1;
+    double scale = 0;
+    for (int i = 0; i < n * n; ++i) scale += creal(A[i] * conj(A[i]));
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += creal(A[p * n + q] * conj(A[p * n + q]));
+        if (off <= 1e-34 * scale || off == 0.0) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                cplx g = A[p * n + q];
+                double ag = cabs(g);
+                if (ag == 0.0) continue;
+                cplx ph = g / ag; /* e^{i phi} */
+                double app = creal(A[p * n + p]), aqq = creal(A[q * n + q]);
+                double tau = (aqq - app) / (2.0 * ag);
+                double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                /* J = identity except the (p,q) block [[c, s],[-s conj(ph), c conj(ph)]]:
+                 * a phase on column q makes the pivot real, then a real rotation. */
+                cplx J[NFMAX * NFMAX], Jd[NFMAX * NFMAX];
+                for (int i = 0; i < n * n; ++i) J[i] = 0;
+                for (int i = 0; i < n; ++i) J[i * n + i] = 1;
+                J[p * n + p] = c;
+                J[p * n + q] = s;
+                J[q * n + p] = -s * conj(ph);
+                J[q * n + q] = c * conj(ph);
+                mat_adjoint(n, J, Jd);
+                mat_mul(n, Jd, A, A);
+                mat_mul(n, A, J, A);
+                mat_mul(n, V, J, V);
+                A[p * n + q] = 0; /* zero by construction; drop rounding residue */
+                A[q * n + p] = 0;
+            }
+    }
+    for (int i = 0; i < n; ++i) w[i] = creal(A[i * n + i]);
+    for (int i = 0; i < n * n; ++i) {
+        Vri[2 * i] = creal(V[i]);
+        Vri[2 * i + 1] = cimag(V[i]);
+    }
+    return 0;
+}
+
+/* U = exp(-i H t).  2 flavors: the closed form of Eq. 3.10-3.12 applied to
+ * the traceless part of H (the trace is a global phase that cancels in
+ * U rho U^dagger, so it is dropped).  3 flavors: spectral form from the
+ * Jacobi eigensolver. */
+static void expm_minus_iHt(int n, const cplx *H, double t, cplx *U)
+{
+    if (n == 2) {
+        double tr2 = 0.5 * creal(H[0] + H[3]);
+        double h11 = creal(H[0]) - tr2;
+        cplx h12 = H[1];
+        double lam = sqrt(h11 * h11 + creal(h12 * conj(h12)));
+        double cs = cos(lam * t);
+        double sn_over = (lam > 0.0) ? sin(lam * t) / lam : t;
+        U[0] = cs - I * h11 * sn_over;
+        U[1] = -I * h12 * sn_over;
+        U[2] = -I * conj(h12) * sn_over;
+        U[3] = cs + I * h11 * sn_over;
+        return;
+    }
+    double Hp[NFMAX * NFMAX], w[NFMAX], Vri[2 * NFMAX * NFMAX];
+    cplx H0[NFMAX * NFMAX];
+    double trn = 0;
+    for (int i = 0; i < n; ++i) trn += creal(H[i * n + i]) / n;
+    memcpy(H0, H, sizeof(cplx) * n * n);
+    for (int i = 0; i < n; ++i) H0[i * n + i] -= trn;
+    pack(n, H0, Hp);
+    orc_eigh(n, Hp, w, Vri);
+    cplx V[NFMAX * NFMAX], Vd[NFMAX * NFMAX], D[NFMAX * NFMAX];
+    for (int i = 0; i < n * n; ++i) V[i] = Vri[2 * i] + I * Vri[2 * i + 1];
+    mat_adjoint(n, V, Vd);
+    for (int i = 0; i < n * n; ++i) D[i] = 0;
+    for (int k = 0; k < n; ++k) D[k * n + k] = cexp(-I * w[k] * t);
+    mat_mul(n, V, D, U);
+    mat_mul(n, U, Vd, U);
+}
+
+/* exported for tests: U = exp(-i H t), H packed, U as (re, im) pairs */
+int orc_expm(int n, const double *Hp, double t, double *Uri)
+{
+    cplx H[NFMAX * NFMAX], U[NFMAX * NFMAX];
+    unpack(n, Hp, H);
+    expm_minus_iHt(n, H, t, U);
+    for (int i = 0; i < n * n; ++i) {
+        Uri[2 * i] = creal(U[i]);
+        Uri[2 * i + 1] = cimag(U[i]);
+    }
+    return 0;
+}
+
+/* ---- problem set-up -------------------------------------------------------- */
+typedef struct {
+    orc_params p;
+    int n, nE, nu, nbins, m; /* m = n*n */
+    double dE, du;
+    double *E, *u, *phi; /* phi[a*nE + e], a = nu_e, nubar_e, nu_x, nubar_x */
+    cplx *Hvac;          /* [nE][n][n] */
+} orc_ctx;
+
+static int ctx_init(orc_ctx *c, const orc_params *p)
+{
+    memset(c, 0, sizeof(*c));
+    if (p->n_E <= 0 || p->n_u <= 0 || (p->n_f != 2 && p->n_f != 3)) return -1;
+    c->p = *p;
+    c->n = p->n_f;
+    c->m = p->n_f * p->n_f;
+    c->nE = p->n_E;
+    c->nu = p->n_u;
+    c->nbins = 2 * p->n_u * p->n_E;
+    c->dE = (p->E_max - p->E_min) / p->n_E;
+    c->du = 1.0 / p->n_u;
+    c->E = malloc(sizeof(double) * c->nE);
+    c->u = malloc(sizeof(double) * c->nu);
+    c->phi = malloc(sizeof(double) * 4 * c->nE);
+    c->Hvac = malloc(sizeof(cplx) * c->nE * c->m);
+    if (!c->E || !c->u || !c->phi || !c->Hvac) return -2;
+    for (int e = 0; e < c->nE; ++e) c->E[e] = p->E_min + (e + 0.5) * c->dE;
+    for (int j = 0; j < c->nu; ++j) c->u[j] = (j + 0.5) * c->du;
+
+    /* Eq. 4.1-4.2: f_a(E) = E^2 / (F2(eta) T^3 (exp(E/T - eta) + 1)), and the
+     * number flux weight L_a/<E_a> relative to nu_e, <E> = T F3/F2. */
+    double ref = 0;
+    for (int a = 0; a < 4; ++a) {
+        double F2 = orc_fd_integral(2, p->eta[a]);
+        double F3 = orc_fd_integral(3, p->eta[a]);
+        double Tm = p->T[a];
+        double meanE = Tm * F3 / F2;
+        double flux = p->L[a] / meanE;
+        if (a == 0) ref = flux;
+        for (int e = 0; e < c->nE; ++e) {
+            double E = c->E[e];
+            double f = E * E / (F2 * Tm * Tm * Tm * (exp(E / Tm - p->eta[a]) + 1.0));
+            c->phi[a * c->nE + e] = (flux / ref) * f;
+        }
+    }
+
+    /* vacuum Hamiltonian per energy bin, km^-1 */
+    double K = orc_vac_coeff();
+    for (int e = 0; e < c->nE; ++e) {
+        cplx *H = c->Hvac + (size_t)e * c->m;
+        if (c->n == 2) {
+            double dm2 = p->hierarchy * p->dm2[0];
+            double Delta = K * dm2 / c->E[e]; /* Eq. 3.6 */
+            double c2 = cos(2 * p->theta[0]), s2 = sin(2 * p->theta[0]);
+            H[0] = -0.5 * Delta * c2; /* Eq. 3.5 */
+            H[1] = 0.5 * Delta * s2;
+            H[2] = 0.5 * Delta * s2;
+            H[3] = 0.5 * Delta * c2;
+        } else {
+            double s12 = sin(p->theta[0]), c12 = cos(p->theta[0]);
+            double s13 = sin(p->theta[1]), c13 = cos(p->theta[1]);
+            double s23 = sin(p->theta[2]), c23 = cos(p->theta[2]);
+            /* standard mixing matrix with delta_CP = 0 (rows e, mu, tau) */
+            double U[9] = {c12 * c13, s12 * c13, s13,
+                           -s12 * c23 - c12 * s23 * s13, c12 * c23 - s12 * s23 * s13, s23 * c13,
+                           s12 * s23 - c12 * c23 * s13, -c12 * s23 - s12 * c23 * s13, c23 * c13};
+            double m2[3] = {0.0, p->dm2[0], p->hierarchy * p->dm2[1]};
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double s = 0;
+                    for (int k = 0; k < 3; ++k) s += U[i * 3 + k] * m2[k] * U[j * 3 + k];
+                    H[i * 3 + j] = K * s / c->E[e];
+                }
+        }
+    }
+    return 0;
+}
+static void ctx_free(orc_ctx *c)
+{
+    free(c->E);
+    free(c->u);
+    free(c->phi);
+    free(c->Hvac);
+}
+
+/* Eq. 3.7 with the configured n_e(r) */
+static double matter_A(const orc_ctx *c, double r)
+{
+    const orc_params *p = &c->p;
+    double ne = 0;
+    if (p->matter == ORC_MATTER_POWER) ne = p->ne_ref * pow(p->r_ref / r, p->ne_power);
+    else if (p->matter == ORC_MATTER_EXP) ne = p->Ye * p->nb0 * exp(-(r - p->R_nu) / p->h_ns);
+    return orc_matter_coeff() * ne;
+}
+
+/* Per-angle geometry at radius r for the configured mode.
+ *   a[j], b[j]: weights with M0 = dE sum_j a_j S_j, M1 = dE sum_j b_j S_j
+ *   g[j]      : G_j = mu_eff (M0 - g_j M1)
+ *   kap[j]    : dl/dr along trajectory j
+ * BULB: Eq. 3.13-3.15 with u = sin^2(theta_0):  cos(theta') = sqrt(1 - x^2 u),
+ *       d cos(theta') = x^2 du / (2 cos(theta')), and l = r cos(theta) (Eq. 3.3)
+ *       gives dl/dr = 1/cos(theta). */
+static void geometry(const orc_ctx *c, double r, double *a, double *b, double *g, double *kap,
+                     double *mu_eff)
+{
+    const orc_params *p = &c->p;
+    double x = p->R_nu / r, x2 = x * x;
+    for (int j = 0; j < c->nu; ++j) {
+        double cth = sqrt(1.0 - x2 * c->u[j]);
+        switch (p->geometry) {
+        case ORC_BULB:
+            a[j] = x2 * c->du / (2.0 * cth);
+            b[j] = a[j] * cth;
+            g[j] = cth;
+            kap[j] = 1.0 / cth;
+            break;
+        case ORC_MU_R4:
+            a[j] = c->du;
+            b[j] = c->du * cth;
+            g[j] = cth;
+            kap[j] = 1.0 / cth;
+            break;
+        default: /* single-angle and constant-coupling modes: radial, no angle factor */
+            a[j] = c->du;
+            b[j] = 0.0;
+            g[j] = 0.0;
+            kap[j] = 1.0;
+            break;
+        }
+    }
+    if (p->geometry == ORC_MU_R4) *mu_eff = p->mu0 * x2 * x2;
+    else if (p->geometry == ORC_SINGLE_ANGLE) {
+        double t = 1.0 - sqrt(1.0 - x2); /* Eq. 3.17 */
+        *mu_eff = p->mu0 * 0.5 * t * t;
+    } else *mu_eff = p->mu0;
+}
+
+/* Exact path length along trajectory j from r to r+h (Eq. 3.3, l = r cos):
+ * l(r+h) - l(r) = ((r+h)^2 - r^2) / (l(r+h) + l(r)), since l^2 = r^2 - b^2 with
+ * b the impact parameter; written this way it has no cancellation. */
+static double path_length(const orc_ctx *c, int j, double r, double h)
+{
+    if (c->p.geometry != ORC_BULB && c->p.geometry != ORC_MU_R4) return h;
+    double R = c->p.R_nu;
+    double x0 = R / r, x1 = R / (r + h);
+    double l0 = r * sqrt(1.0 - x0 * x0 * c->u[j]);
+    double l1 = (r + h) * sqrt(1.0 - x1 * x1 * c->u[j]);
+    return h * (2.0 * r + h) / (l0 + l1);
+}
+
+/* nu-nu moments (Eq. 3.13): S_j = sum_e (rho_nu - conj(rho_nubar)),
+ * M0 = dE sum_j a_j S_j, M1 = dE sum_j b_j S_j.  Sequential sums in index
+ * order; the angle loop may run in parallel (each S_j is one thread's). */
+static void moments(const orc_ctx *c, const cplx *rho, const double *a, const double *b,
+                    cplx *M0, cplx *M1, cplx *Sbuf)
+{
+    int n = c->n, m = c->m, nE = c->nE, nu = c->nu;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < nu; ++j) {
+        cplx S[NFMAX * NFMAX];
+        for (int k = 0; k < m; ++k) S[k] = 0;
+        for (int e = 0; e < nE; ++e) {
+            const cplx *rn = rho + ((size_t)(0 * nu + j) * nE + e) * m;
+            const cplx *ra = rho + ((size_t)(1 * nu + j) * nE + e) * m;
+            for (int k = 0; k < m; ++k) S[k] += rn[k] - conj(ra[k]);
+        }
+        memcpy(Sbuf + (size_t)j * m, S, sizeof(cplx) * m);
+    }
+    for (int k = 0; k < m; ++k) M0[k] = M1[k] = 0;
+    for (int j = 0; j < nu; ++j)
+        for (int k = 0; k < m; ++k) {
+            M0[k] += a[j] * Sbuf[(size_t)j * m + k];
+            M1[k] += b[j] * Sbuf[(size_t)j * m + k];
+        }
+    for (int k = 0; k < m; ++k) {
+        M0[k] *= c->dE;
+        M1[k] *= c->dE;
+    }
+    (void)n;
+}
+
+/* Hamiltonian of bin (s, j, e):  nu:    H_vac + A P_e + G_j
+ *                                nubar: H_vac - A P_e - conj(G_j) */
+static void hamiltonian(const orc_ctx *c, int s, int e, const cplx *G, double A, cplx *H)
+{
+    int m = c->m, n = c->n;
+    const cplx *Hv = c->Hvac + (size_t)e * m;
+    for (int k = 0; k < m; ++k) H[k] = Hv[k] + (s == 0 ? G[k] : -conj(G[k]));
+    H[0] += (s == 0 ? A : -A);
+    (void)n;
+}
+
+static int all_finite(int m, const cplx *M)
+{
+    for (int k = 0; k < m; ++k)
+        if (!isfinite(creal(M[k])) || !isfinite(cimag(M[k]))) return 0;
+    return 1;
+}
+
+typedef struct {
+    double *a, *b, *g, *kap;
+    cplx *Sbuf;
+} scratch_t;
+
+/* d(rho)/dr = -i [H, rho] dl/dr for every bin; returns 0 if the moments were
+ * not finite. */
+static int rhs(const orc_ctx *c, scratch_t *w, double r, const cplx *rho, cplx *K)
+{
+    int n = c->n, m = c->m, nE = c->nE, nu = c->nu;
+    double mu;
+    geometry(c, r, w->a, w->b, w->g, w->kap, &mu);
+    cplx M0[NFMAX * NFMAX], M1[NFMAX * NFMAX];
+    moments(c, rho, w->a, w->b, M0, M1, w->Sbuf);
+    if (!all_finite(m, M0) || !all_finite(m, M1)) return 0;
+    double A = matter_A(c, r);
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < c->nbins; ++b) {
+        int s = b / (nu * nE), j = (b / nE) % nu, e = b % nE;
+        cplx G[NFMAX * NFMAX], H[NFMAX * NFMAX], X[NFMAX * NFMAX], Y[NFMAX * NFMAX];
+        for (int k = 0; k < m; ++k) G[k] = mu * (M0[k] - w->g[j] * M1[k]);
+        hamiltonian(c, s, e, G, A, H);
+        const cplx *rb = rho + (size_t)b * m;
+        mat_mul(n, H, rb, X);
+        mat_mul(n, rb, H, Y);
+        for (int k = 0; k < m; ++k) K[(size_t)b * m + k] = -I * (X[k] - Y[k]) * w->kap[j];
+    }
+    return 1;
+}
+
+static int step_rk4(const orc_ctx *c, scratch_t *w, cplx *rho, double r, double h, cplx *Y,
+                    cplx *K, cplx *acc)
+{
+    size_t N = (size_t)c->nbins * c->m;
+    /* k1 */
+    if (!rhs(c, w, r, rho, K)) return 0;
+    for (size_t i = 0; i < N; ++i) {
+        acc[i] = K[i];
+        Y[i] = rho[i] + (0.5 * h) * K[i];
+    }
+    /* k2 */
+    if (!rhs(c, w, r + 0.5 * h, Y, K)) return 0;
+    for (size_t i = 0; i < N; ++i) {
+        acc[i] += 2.0 * K[i];
+        Y[i] = rho[i] + (0.5 * h) * K[i];
+    }
+    /* k3 */
+    if (!rhs(c, w, r + 0.5 * h, Y, K)) return 0;
+    for (size_t i = 0; i < N; ++i) {
+        acc[i] += 2.0 * K[i];
+        Y[i] = rho[i] + h * K[i];
+    }
+    /* k4 */
+    if (!rhs(c, w, r + h, Y, K)) return 0;
+    for (size_t i = 0; i < N; ++i) Y[i] = rho[i] + (h / 6.0) * (acc[i] + K[i]);
+    return 1;
+}
+
+/* Coarse predictor-corrector of Sec. 4.2.3 / Listing 5.1 (S1-S3), rho form:
+ *   H0 from rho_n at r;     rho_p = U(H0) rho_n U(H0)^+            (predictor)
+ *   H1 from rho_p at r + h; rho_{n+1} = (rho_p + U(H1) rho_n U(H1)^+) / 2
+ * U(H) = exp(-i H dl_j) with dl_j the path length of trajectory j. */
+static int step_exph(const orc_ctx *c, scratch_t *w, const cplx *rho, double r, double h,
+                     cplx *rp, cplx *out)
+{
+    int n = c->n, m = c->m, nE = c->nE, nu = c->nu;
+    double mu;
+    cplx M0[NFMAX * NFMAX], M1[NFMAX * NFMAX];
+    double *dl = malloc(sizeof(double) * nu);
+    for (int j = 0; j < nu; ++j) dl[j] = path_length(c, j, r, h);
+    for (int pass = 0; pass < 2; ++pass) {
+        double rr = (pass == 0) ? r : r + h;
+        const cplx *src = (pass == 0) ? rho : rp;
+        geometry(c, rr, w->a, w->b, w->g, w->kap, &mu);
+        moments(c, src, w->a, w->b, M0, M1, w->Sbuf);
+        if (!all_finite(m, M0) || !all_finite(m, M1)) {
+            free(dl);
+            return 0;
+        }
+        double A = matter_A(c, rr);
+#pragma omp parallel for schedule(static)
+        for (int b = 0; b < c->nbins; ++b) {
+            int s = b / (nu * nE), j = (b / nE) % nu, e = b % nE;
+            cplx G[NFMAX * NFMAX], H[NFMAX * NFMAX], U[NFMAX * NFMAX], X[NFMAX * NFMAX];
+            for (int k = 0; k < m; ++k) G[k] = mu * (M0[k] - w->g[j] * M1[k]);
+            hamiltonian(c, s, e, G, A, H);
+            expm_minus_iHt(n, H, dl[j], U);
+            conjugate_by(n, U, rho + (size_t)b * m, X);
+            if (pass == 0) memcpy(rp + (size_t)b * m, X, sizeof(cplx) * m);
+            else
+                for (int k = 0; k < m; ++k)
+                    out[(size_t)b * m + k] = 0.5 * (rp[(size_t)b * m + k] + X[k]);
+        }
+    }
+    free(dl);
+    return 1;
+}
+
+/* ---- exported entry points (ctypes) --------------------------------------- */
+
+/* Tables for inspection: E[nE], u[nu], phi[4*nE], Hvac[nE*n*n] packed. */
+int orc_tables(const orc_params *p, double *E, double *u, double *phi, double *Hvac_packed)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, p);
+    if (rc) {
+        ctx_free(&c);
+        return rc;
+    }
+    memcpy(E, c.E, sizeof(double) * c.nE);
+    memcpy(u, c.u, sizeof(double) * c.nu);
+    memcpy(phi, c.phi, sizeof(double) * 4 * c.nE);
+    for (int e = 0; e < c.nE; ++e) pack(c.n, c.Hvac + (size_t)e * c.m, Hvac_packed + (size_t)e * c.m);
+    ctx_free(&c);
+    return 0;
+}
+
+/* Seeded initial state, packed [s][u][E][n*n]:
+ * rho_nu = diag(phi_nue, phi_nux[, phi_nux]), rho_nubar likewise with the
+ * antineutrino spectra; each off-diagonal (i<j) gets
+ * eps sqrt(rho_ii rho_jj) exp(2 pi i U), U the SplitMix64 uniform number with
+ * counter b * n_off + k (k-th upper entry in row order). */
+int orc_init_state(const orc_params *p, double *rho_packed)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, p);
+    if (rc) {
+        ctx_free(&c);
+        return rc;
+    }
+    int n = c.n, m = c.m, noff = n * (n - 1) / 2;
+    for (int b = 0; b < c.nbins; ++b) {
+        int s = b / (c.nu * c.nE), e = b % c.nE;
+        double pe = c.phi[(s == 0 ? 0 : 1) * c.nE + e];
+        double px = c.phi[(s == 0 ? 2 : 3) * c.nE + e];
+        cplx M[NFMAX * NFMAX];
+        for (int k = 0; k < m; ++k) M[k] = 0;
+        M[0] = pe;
+        for (int i = 1; i < n; ++i) M[i * n + i] = px;
+        int k = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                double ph = 2.0 * PI * uniform01(p->seed, (uint64_t)b * noff + k);
+                double amp = p->eps * sqrt(creal(M[i * n + i]) * creal(M[j * n + j]));
+                M[i * n + j] = amp * cexp(I * ph);
+                M[j * n + i] = conj(M[i * n + j]);
+                ++k;
+            }
+        pack(n, M, rho_packed + (size_t)b * m);
+    }
+    ctx_free(&c);
+    return 0;
+}
+
+/* Advance rho (packed, in/out) by n_steps fixed steps of size h from r0.
+ * Returns 0 on success, 1 if a non-finite moment appeared (rho is then left
+ * at the last step whose state was finite; *steps_done tells which), <0 on
+ * argument errors. */
+int orc_evolve(const orc_params *p, double *rho_packed, double r0, double h, int64_t n_steps,
+               int64_t *steps_done)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, p);
+    if (rc) {
+        ctx_free(&c);
+        return rc;
+    }
+#ifdef _OPENMP
+    if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+#endif
+    size_t N = (size_t)c.nbins * c.m;
+    cplx *rho = malloc(sizeof(cplx) * N), *Y = malloc(sizeof(cplx) * N);
+    cplx *K = malloc(sizeof(cplx) * N), *acc = malloc(sizeof(cplx) * N);
+    scratch_t w;
+    w.a = malloc(sizeof(double) * c.nu);
+    w.b = malloc(sizeof(double) * c.nu);
+    w.g = malloc(sizeof(double) * c.nu);
+    w.kap = malloc(sizeof(double) * c.nu);
+    w.Sbuf = malloc(sizeof(cplx) * c.nu * c.m);
+    for (int b = 0; b < c.nbins; ++b) unpack(c.n, rho_packed + (size_t)b * c.m, rho + (size_t)b * c.m);
+    int status = 0;
+    int64_t done = 0;
+    for (int64_t st = 0; st < n_steps; ++st) {
+        double r = r0 + (double)st * h;
+        int ok = (p->stepper == ORC_RK4) ? step_rk4(&c, &w, rho, r, h, Y, K, acc)
+                                         : step_exph(&c, &w, rho, r, h, K, Y);
+        if (ok) {
+            for (size_t i = 0; i < N && ok; ++i)
+                if (!isfinite(creal(Y[i])) || !isfinite(cimag(Y[i]))) ok = 0;
+        }
+        if (!ok) {
+            status = 1;
+            break;
+        }
+        cplx *t = rho;
+        rho = Y;
+        Y = t;
+        ++done;
+    }
+    for (int b = 0; b < c.nbins; ++b) pack(c.n, rho + (size_t)b * c.m, rho_packed + (size_t)b * c.m);
+    if (steps_done) *steps_done = done;
+    free(rho);
+    free(Y);
+    free(K);
+    free(acc);
+    free(w.a);
+    free(w.b);
+    free(w.g);
+    free(w.kap);
+    free(w.Sbuf);
+    ctx_free(&c);
+    return status;
+}
+
+/* Moments of a packed state at radius r (packed Hermitian n*n each). */
+int orc_moments(const orc_params *p, const double *rho_packed, double r, double *M0p, double *M1p)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, p);
+    if (rc) {
+        ctx_free(&c);
+        return rc;
+    }
+    size_t N = (size_t)c.nbins * c.m;
+    cplx *rho = malloc(sizeof(cplx) * N);
+    for (int b = 0; b < c.nbins; ++b) unpack(c.n, rho_packed + (size_t)b * c.m, rho + (size_t)b * c.m);
+    double *a = malloc(sizeof(double) * c.nu), *bb = malloc(sizeof(double) * c.nu);
+    double *g = malloc(sizeof(double) * c.nu), *kap = malloc(sizeof(double) * c.nu);
+    cplx *Sbuf = malloc(sizeof(cplx) * c.nu * c.m);
+    double mu;
+    cplx M0[NFMAX * NFMAX], M1[NFMAX * NFMAX];
+    geometry(&c, r, a, bb, g, kap, &mu);
+    moments(&c, rho, a, bb, M0, M1, Sbuf);
+    pack(c.n, M0, M0p);
+    pack(c.n, M1, M1p);
+    free(rho);
+    free(a);
+    free(bb);
+    free(g);
+    free(kap);
+    free(Sbuf);
+    ctx_free(&c);
+    return 0;
+}
+
+/* Matter potential and single-angle factor at r, for tests. */
+double orc_matter_A(const orc_params *p, double r)
+{
+    orc_ctx c;
+    if (ctx_init(&c, p)) {
+        ctx_free(&c);
+        return NAN;
+    }
+    double A = matter_A(&c, r);
+    ctx_free(&c);
+    return A;
+}

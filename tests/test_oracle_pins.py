@@ -1,0 +1,474 @@
+"""Pins for the FP64 CPU oracle: checks against what the paper and the
+mathematics fix, independent of the oracle's own code.
+
+Each test names the passage it pins.  None of them calls the CUDA library.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1907_05560_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _small(**kw):
+    base = dict(n_E=8, n_u=6, n_f=2, stepper=I.RK4, mu0=0.0, r0=50.0, r1=52.0, n_steps=200,
+                eps=1e-3, seed=7)
+    base.update(kw)
+    return I.Problem(**base)
+
+
+def _trace(rho, n_f):
+    x = rho.reshape(-1, n_f * n_f)
+    return x[:, :n_f].sum(1)
+
+
+# ---------------------------------------------------------------- constants
+
+def test_vacuum_coefficient_matches_pdg_phase(orc):
+    """Eq. 3.6: Delta = dm^2/(2E); Delta*L/2 is the textbook phase
+    1.26693 dm^2[eV^2] L[km] / E[GeV]."""
+    ref = float(dict((r[0], r[1]) for r in _golden("constants.txt"))["osc_phase_per_eV2_km_per_GeV"])
+    # Delta L / 2 per (eV^2 km / MeV) = coeff / 2 ; per GeV: * 1e-3
+    assert orc.vac_coeff() / 2 * 1e-3 == pytest.approx(ref, rel=2e-5)
+
+
+def test_matter_coefficient_matches_pdg(orc):
+    """Eq. 3.7: A = sqrt(2) G_F n_e = 7.63e-14 eV at n_e = N_A cm^-3."""
+    ref = float(dict((r[0], r[1]) for r in _golden("constants.txt"))["matter_potential_eV_per_NA_cm3"])
+    hbarc_ev_km = 1.973269804e-10
+    got_ev = orc.matter_coeff() * 6.02214076e23 * hbarc_ev_km
+    assert got_ev == pytest.approx(ref, rel=1e-3)
+
+
+# ---------------------------------------------------------------- spectra
+
+def test_fd_integrals_closed_form_at_zero(orc):
+    """Eq. 4.2 at eta = 0: F_k(0) = (1 - 2^-k) k! zeta(k+1)."""
+    zeta3, zeta4 = 1.2020569031595942, math.pi ** 4 / 90
+    assert orc.fd_integral(2, 0.0) == pytest.approx(0.75 * 2 * zeta3, rel=1e-12)
+    assert orc.fd_integral(3, 0.0) == pytest.approx(0.875 * 6 * zeta4, rel=1e-12)
+
+
+def test_fd_integrals_match_polylog(orc):
+    """Eq. 4.2: F_k(eta) = -k! Li_{k+1}(-e^eta) (library polylog)."""
+    mpmath = pytest.importorskip("mpmath")
+    for k in (2, 3):
+        for eta in (-1.0, 1.5, 3.0):
+            ref = float(-math.factorial(k) * mpmath.polylog(k + 1, -mpmath.e ** eta))
+            assert orc.fd_integral(k, eta) == pytest.approx(ref, rel=1e-11)
+
+
+def test_fd_temperatures_reproduce_paper(orc):
+    """Sec. 4.5 prints T = 2.76/4.01/6.26 MeV for <E> = 11/16/25 MeV, eta = 3;
+    <E> = T F3/F2 (Eq. 4.1-4.2)."""
+    for name, meanE, eta, T in _golden("fd_temperatures.txt"):
+        ratio = orc.fd_integral(3, float(eta)) / orc.fd_integral(2, float(eta))
+        assert round(float(meanE) / ratio, 2) == pytest.approx(float(T), abs=1e-9), name
+
+
+def test_spectrum_normalised_and_flux_ratios(orc):
+    """Eq. 4.1 is a normalised distribution; the number-flux weight of each
+    species is L/<E> relative to nu_e, i.e. <E_nue>/<E_a> at equal L."""
+    p = I.Problem(n_E=4000, E_min=0.0, E_max=150.0)
+    E, u, phi, Hv = orc.tables(p)
+    dE = E[1] - E[0]
+    ratio = orc.fd_integral(3, 3.0) / orc.fd_integral(2, 3.0)
+    meanE = [T * ratio for T in p.T]
+    for a in range(4):
+        assert phi[a].sum() * dE == pytest.approx(meanE[0] / meanE[a], rel=1e-6)
+
+
+# ---------------------------------------------------------------- eigen / propagator
+
+def _rand_herm(rng, n, degenerate=False):
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    H = A + A.conj().T
+    if degenerate:
+        w, V = np.linalg.eigh(H)
+        w[1] = w[0]
+        H = (V * w) @ V.conj().T
+        H = 0.5 * (H + H.conj().T)
+    return H
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_jacobi_eigh_matches_lapack(orc, n):
+    rng = np.random.default_rng(n)
+    for trial in range(40):
+        H = _rand_herm(rng, n, degenerate=(trial % 5 == 0))
+        w, V = orc.eigh(orc.pack(H[None]))
+        assert np.allclose(np.sort(w), np.linalg.eigvalsh(H), atol=1e-12 * np.abs(H).max())
+        assert np.allclose(V.conj().T @ V, np.eye(n), atol=1e-13)
+        assert np.allclose((V * w) @ V.conj().T, H, atol=1e-12 * np.abs(H).max())
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_propagator_matches_scipy_expm(orc, n):
+    """Eq. 3.10-3.12 (2 flavors) and the spectral form (3 flavors) equal
+    exp(-iHt) up to the global phase of tr(H)."""
+    expm = pytest.importorskip("scipy.linalg").expm
+    rng = np.random.default_rng(10 + n)
+    for trial in range(30):
+        H = _rand_herm(rng, n, degenerate=(trial % 6 == 0))
+        t = rng.uniform(0.01, 3.0)
+        U = orc.expm(orc.pack(H[None]), t)
+        H0 = H - np.trace(H).real / n * np.eye(n)
+        assert np.allclose(U, expm(-1j * H0 * t), atol=1e-12)
+
+
+# ---------------------------------------------------------------- closed forms
+
+def _path_length(p, r):
+    """l(r) - l(r0) with l = r cos(theta) (Eq. 3.3), per angle bin."""
+    u = (np.arange(p.n_u) + 0.5) / p.n_u
+    l = lambda rr: rr * np.sqrt(1.0 - (p.R_nu / rr) ** 2 * u)
+    return l(r) - l(p.r0)
+
+
+@pytest.mark.parametrize("stepper,tol", [(I.RK4, 2e-8), (I.EXPH, 1e-11)])
+def test_vacuum_two_flavor_survival(orc, stepper, tol):
+    """P1: mu = A = 0 gives P_ee = 1 - sin^2(2 theta) sin^2(Delta L / 2) along
+    each trajectory (Eq. 3.5-3.6, Eq. 3.3); ee entry = phi_x + (phi_e - phi_x) P_ee."""
+    p = _small(n_E=12, n_u=5, stepper=stepper, eps=0.0, theta=(0.3, 0, 0), hierarchy=-1,
+               E_min=1.0, E_max=13.0, r0=20.0, r1=30.0, n_steps=1000)
+    E, u, phi, Hv = orc.tables(p)
+    rho = orc.init_state(p)
+    out, st, done = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    assert st == 0 and done == p.n_steps
+    M = orc.unpack(out, 2).reshape(2, p.n_u, p.n_E, 2, 2)
+    Lj = _path_length(p, p.r1)
+    Delta = orc.vac_coeff() * p.hierarchy * p.dm2[0] / E
+    Pee = 1 - np.sin(2 * 0.3) ** 2 * np.sin(np.outer(Lj, Delta) / 2) ** 2
+    for s, (ie, ix) in enumerate([(0, 2), (1, 3)]):
+        want = phi[ix] + (phi[ie] - phi[ix]) * Pee
+        assert np.abs(M[s, :, :, 0, 0].real - want).max() < tol * phi[0].max()
+
+
+@pytest.mark.parametrize("stepper,tol", [(I.RK4, 2e-8), (I.EXPH, 1e-11)])
+def test_constant_matter_msw(orc, stepper, tol):
+    """P2: constant matter.  Textbook two-flavor MSW (Wolfenstein; Mikheyev-
+    Smirnov): Delta_m = sqrt((Delta cos2t -+ A)^2 + (Delta sin2t)^2),
+    sin 2t_m = Delta sin 2t / Delta_m, with -A for antineutrinos."""
+    p = _small(n_E=12, n_u=1, geometry=I.CONST, stepper=stepper, eps=0.0, theta=(0.2, 0, 0),
+               hierarchy=+1, E_min=1.0, E_max=25.0, matter=I.MATTER_POWER, ne_ref=2.0e27,
+               ne_power=0.0, r0=20.0, r1=24.0, n_steps=800)
+    E, u, phi, Hv = orc.tables(p)
+    A = orc.matter_A(p, 22.0)
+    Delta = orc.vac_coeff() * p.dm2[0] / E
+    assert 0.1 < A / Delta.max() and A / Delta.min() < 10  # spans the resonance
+    rho = orc.init_state(p)
+    out, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    M = orc.unpack(out, 2).reshape(2, p.n_E, 2, 2)
+    L = p.r1 - p.r0
+    c2, s2 = math.cos(0.4), math.sin(0.4)
+    for s, sgn, (ie, ix) in [(0, +1, (0, 2)), (1, -1, (1, 3))]:
+        Dm = np.sqrt((Delta * c2 - sgn * A) ** 2 + (Delta * s2) ** 2)
+        sin2m = Delta * s2 / Dm
+        Pee = 1 - sin2m ** 2 * np.sin(Dm * L / 2) ** 2
+        want = phi[ix] + (phi[ie] - phi[ix]) * Pee
+        assert np.abs(M[s, :, 0, 0].real - want).max() < tol * phi[0].max()
+
+
+@pytest.mark.parametrize("stepper,tol", [(I.RK4, 5e-8), (I.EXPH, 1e-11)])
+def test_vacuum_three_flavor(orc, stepper, tol):
+    """P3: three-flavor vacuum oscillation (textbook, delta_CP = 0):
+    P_ab = delta_ab - 4 sum_{j<k} U_aj U_bj U_ak U_bk sin^2(dm2_kj L / 4E)."""
+    p = _small(n_f=3, n_E=10, n_u=3, stepper=stepper, eps=0.0, dm2=(7.5e-5, 2.4e-3),
+               theta=(0.59, 0.15, 0.72), hierarchy=+1, E_min=2.0, E_max=10.0, r0=20.0,
+               r1=30.0, n_steps=4000)
+    E, u, phi, Hv = orc.tables(p)
+    rho = orc.init_state(p)
+    out, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    M = orc.unpack(out, 3).reshape(2, p.n_u, p.n_E, 3, 3)
+    s12, c12 = math.sin(0.59), math.cos(0.59)
+    s13, c13 = math.sin(0.15), math.cos(0.15)
+    s23, c23 = math.sin(0.72), math.cos(0.72)
+    U = np.array([[c12 * c13, s12 * c13, s13],
+                  [-s12 * c23 - c12 * s23 * s13, c12 * c23 - s12 * s23 * s13, s23 * c13],
+                  [s12 * s23 - c12 * c23 * s13, -c12 * s23 - s12 * c23 * s13, c23 * c13]])
+    m2 = np.array([0.0, 7.5e-5, 2.4e-3])
+    K = orc.vac_coeff()
+    Lj = _path_length(p, p.r1)
+    for beta in (0, 1):  # nu_e -> nu_e and nu_e -> nu_mu
+        P = np.full((p.n_u, p.n_E), 1.0 if beta == 0 else 0.0)
+        for j in range(3):
+            for k in range(j + 1, 3):
+                ph = np.outer(Lj, K * (m2[k] - m2[j]) / E) / 2
+                P -= 4 * U[0, j] * U[beta, j] * U[0, k] * U[beta, k] * np.sin(ph) ** 2
+        want = phi[2] + (phi[0] - phi[2]) * P
+        assert np.abs(M[0, :, :, beta, beta].real - want).max() < tol * phi[0].max()
+
+
+def test_bulb_moments_isotropic_closed_form(orc):
+    """Eq. 3.13-3.15 for an angle-independent state: sum_u of the weights
+    gives M0 = dE S (1 - sqrt(1 - x^2)), M1 = dE S x^2 / 2, so that the bulb
+    potential of a radial trajectory, G(cos=1) = mu dE S (M0 - M1)/(dE S),
+    equals the single-angle factor D(r/R) of Eq. 3.17."""
+    p = _small(n_E=3, n_u=20000, eps=1e-2)
+    rho = orc.init_state(p).reshape(2, p.n_u, p.n_E, 4)
+    rho[:, :, :, :] = rho[:, :1, :, :]  # same state on every trajectory
+    for r in (12.0, 30.0, 50.0):
+        x = p.R_nu / r
+        M0, M1 = orc.moments(p, rho.reshape(-1), r)
+        E, u, phi, Hv = orc.tables(p)
+        dE = E[1] - E[0]
+        d = rho[0, 0] - rho[1, 0] * np.array([1, 1, 1, -1])  # rho_nu - conj(rho_nubar), packed
+        S = d.sum(0)
+        f0 = 1 - math.sqrt(1 - x * x)
+        assert np.allclose(M0, dE * S * f0, rtol=2e-5 if r > 12 else 1e-2)
+        assert np.allclose(M1, dE * S * x * x / 2, rtol=1e-9)
+        D = 0.5 * (1 - math.sqrt(1 - x * x)) ** 2
+        assert f0 - x * x / 2 == pytest.approx(D, rel=1e-12)
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("stepper", [I.RK4, I.EXPH])
+@pytest.mark.parametrize("n_f", [2, 3])
+def test_trace_conserved(orc, stepper, n_f):
+    """P4: d(tr rho)/dr = tr(-i[H, rho]) = 0 for every bin."""
+    kw = dict(dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.72)) if n_f == 3 else {}
+    p = _small(n_f=n_f, stepper=stepper, mu0=1e5, r0=50.0, r1=51.0, n_steps=100, **kw)
+    rho = orc.init_state(p)
+    out, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    t0, t1 = _trace(rho, n_f), _trace(out, n_f)
+    assert np.abs(t1 - t0).max() < 1e-13 * np.abs(t0).max()
+
+
+def _purity_like(rho, n_f):
+    M = orc_unpack_cache(rho, n_f)
+    t = np.trace(M, axis1=1, axis2=2).real
+    M0 = M - t[:, None, None] / n_f * np.eye(n_f)
+    return np.einsum("bij,bji->b", M0, M0).real
+
+
+def orc_unpack_cache(rho, n_f):
+    import oracle as O
+    return O.unpack(rho, n_f)
+
+
+@pytest.mark.parametrize("stepper,n_steps,tol", [(I.RK4, 200, 1e-6), (I.EXPH, 800, 1e-5)])
+def test_polarization_length_drift_small(orc, stepper, n_steps, tol):
+    """P4: tr(rho0^2) of the traceless part (|P|^2 / 2 in two flavors) is
+    conserved by the exact flow; the integrators keep it to their truncation
+    order.  Pins that the update is a commutator (a wrong sign or a dropped
+    term changes it at first order)."""
+    p = _small(stepper=stepper, mu0=1e5, r0=50.0, r1=52.0, n_steps=n_steps, eps=1e-2)
+    rho = orc.init_state(p)
+    out, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    a, b = _purity_like(rho, 2), _purity_like(out, 2)
+    assert np.abs(b - a).max() < tol * np.abs(a).max()
+
+
+def _lepton_invariants(orc, p, rho):
+    """I_k = tr(Pi_k F), F = sum_{u,e} du (rho_nu - conj rho_nubar), Pi_k the
+    vacuum mass-basis projectors."""
+    n = p.n_f
+    M = orc.unpack(rho, n).reshape(2, p.n_u, p.n_E, n, n)
+    F = (M[0] - M[1].conj()).sum(axis=(0, 1)) / p.n_u
+    E, u, phi, Hv = orc.tables(p)
+    Hv0 = orc.unpack(Hv[:1].reshape(-1), n)[0]
+    w, V = np.linalg.eigh(Hv0)
+    return np.array([(V[:, k].conj() @ F @ V[:, k]).real for k in range(n)]), np.abs(F).max()
+
+
+@pytest.mark.parametrize("geometry", [I.BULB, I.SINGLE_ANGLE, I.CONST])
+@pytest.mark.parametrize("n_f", [2, 3])
+def test_lepton_number_moment_conserved(orc, geometry, n_f):
+    """P5: with A = 0 the nu-nu terms cancel in d/dr tr(Pi_k F) because
+    sum_u (du/c_u)[M0 - c_u M1, S_u] = [M0, M0] - [M1, M1] = 0 (Eq. 3.13-3.15);
+    RK4 keeps this linear invariant to rounding."""
+    kw = dict(dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.72)) if n_f == 3 else {}
+    n_u = 1 if geometry == I.SINGLE_ANGLE else 6
+    mu0 = 100.0 if geometry == I.CONST else 3e4  # keep mu h inside RK4's stable region
+    p = _small(n_f=n_f, n_u=n_u, geometry=geometry, mu0=mu0, r0=20.0, r1=22.0, n_steps=400,
+               eps=1e-2, **kw)
+    rho = orc.init_state(p)
+    out, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    assert st == 0
+    I0, scale = _lepton_invariants(orc, p, rho)
+    I1, _ = _lepton_invariants(orc, p, out)
+    # the individual bins move at O(1): the invariant must not
+    assert np.abs(orc.unpack(out, n_f) - orc.unpack(rho, n_f)).max() > 1e-4
+    assert np.abs(I1 - I0).max() < 1e-12 * scale
+
+
+def test_bipolar_energy_conserved(orc):
+    """P7: isotropic gas (CONST mode, one angle, A = 0):
+    E = sum_e tr(H_vac,e (rho + conj rho_bar)) + (mu dE / 2) tr(D^2),
+    D = sum_e (rho - conj rho_bar), is conserved by the flow (derived from
+    Eq. 3.4 and the antineutrino rule); RK4 keeps it to O(h^4)."""
+    p = _small(n_E=5, n_u=1, geometry=I.CONST, mu0=50.0, eps=0.05, r0=0.0 + 20, r1=25.0,
+               n_steps=2000, E_min=5.0, E_max=20.0)
+    E, u, phi, Hv = orc.tables(p)
+    Hvm = orc.unpack(Hv.reshape(-1), 2)
+    dE = E[1] - E[0]
+
+    def energy(rho):
+        M = orc.unpack(rho, 2).reshape(2, p.n_E, 2, 2)
+        S = M[0] + M[1].conj()
+        D = (M[0] - M[1].conj()).sum(0)
+        return (np.einsum("eij,eji->", Hvm, S).real + p.mu0 * dE / 2 * np.trace(D @ D).real)
+
+    rho = orc.init_state(p)
+    out, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    moved = np.abs(orc.unpack(out, 2) - orc.unpack(rho, 2)).max()
+    assert moved > 1e-2
+    assert abs(energy(out) - energy(rho)) < 1e-9 * abs(energy(rho))
+
+
+def test_bipolar_instability_only_in_inverted_hierarchy(orc):
+    """Sign of the nu-nu term relative to H_vac: in an isotropic gas with a
+    nu_e excess and mu of the order of the vacuum frequency, the bipolar
+    (pendulum) mode is unstable for the inverted hierarchy only (Hannestad,
+    Raffelt, Sigl, Wong 2006; Duan, Fuller, Carlson, Qian 2006): rho_ee moves
+    at O(10%) in IH and only at the vacuum amplitude sin^2(2 theta) in NH."""
+    def max_change(hier):
+        p = _small(n_E=1, n_u=1, geometry=I.CONST, mu0=20.0, eps=1e-6, theta=(0.01, 0, 0),
+                   hierarchy=hier, E_min=9.0, E_max=11.0, r0=20.0, r1=120.0, n_steps=20000)
+        rho = orc.init_state(p)
+        ee0 = orc.unpack(rho, 2)[:, 0, 0].real
+        r, worst = p.r0, 0.0
+        for _ in range(20):
+            rho, st, _ = orc.evolve(p, rho, r, p.h, 1000)
+            r += 1000 * p.h
+            worst = max(worst, np.abs(orc.unpack(rho, 2)[:, 0, 0].real - ee0).max() / ee0[0])
+        return worst
+    assert max_change(-1) > 0.1
+    assert max_change(+1) < 2 * math.sin(0.02) ** 2
+
+
+def test_nu_nubar_symmetric_in_vacuum(orc):
+    """P9: with A = mu = 0 the antineutrino Hamiltonian equals H_vac (after
+    Eq. 3.4), so equal initial states stay equal."""
+    p = _small(mu0=0.0, eps=1e-2, r0=20.0, r1=30.0, n_steps=300)
+    rho = orc.init_state(p).reshape(2, -1)
+    rho[1] = rho[0]
+    for stepper in (I.RK4, I.EXPH):
+        out, st, _ = orc.evolve(p.replace(stepper=stepper), rho.reshape(-1), p.r0, p.h, p.n_steps)
+        out = out.reshape(2, -1)
+        assert np.array_equal(out[0], out[1])
+
+
+# ---------------------------------------------------------------- independent SA integrator
+
+def _sa_bloch_rk4(orc, p, rho):
+    """Single-angle model (Eq. 3.16-3.17) written independently in
+    polarization-vector form: rho = (P0 + P.sigma)/2, H = (h0 + h.sigma)/2,
+    dP/dr = h x P.  h_vac = Delta (sin2t, 0, -cos2t) (Eq. 3.5), matter
+    (0, 0, A) (Eq. 3.7), nu-nu mu D(x) dE sum_e (P - P_bar*), with
+    P* = (Px, -Py, Pz) the Bloch vector of the complex conjugate."""
+    E, u, phi, Hv = orc.tables(p)
+    dE = E[1] - E[0]
+    Delta = orc.vac_coeff() * p.hierarchy * p.dm2[0] / E
+    th = p.theta[0]
+    hv = np.stack([Delta * math.sin(2 * th), 0 * Delta, -Delta * math.cos(2 * th)], 1)
+    x = rho.reshape(2, p.n_E, 4)
+    P = np.stack([2 * x[:, :, 2], -2 * x[:, :, 3], x[:, :, 0] - x[:, :, 1]], 2)  # [s][e][3]
+    P0 = x[:, :, 0] + x[:, :, 1]
+    cj = np.array([1.0, -1.0, 1.0])
+
+    def f(r, P):
+        xx = p.R_nu / r
+        mu = p.mu0 * 0.5 * (1 - math.sqrt(1 - xx * xx)) ** 2
+        hG = mu * dE * (P[0] - P[1] * cj).sum(0)
+        h_nu = hv + hG
+        h_nb = hv - hG * cj
+        return np.stack([np.cross(h_nu, P[0]), np.cross(h_nb, P[1])])
+
+    h = p.h
+    for n in range(p.n_steps):
+        r = p.r0 + n * h
+        k1 = f(r, P)
+        k2 = f(r + h / 2, P + h / 2 * k1)
+        k3 = f(r + h / 2, P + h / 2 * k2)
+        k4 = f(r + h, P + h * k3)
+        P = P + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    out = np.stack([(P0 + P[:, :, 2]) / 2, (P0 - P[:, :, 2]) / 2, P[:, :, 0] / 2, -P[:, :, 1] / 2], 2)
+    return out.reshape(-1)
+
+
+def test_single_angle_matches_bloch_brute_force(orc):
+    """P6: the oracle's multi-angle integrator in single-angle mode with one
+    angle bin equals an independently written Bloch-vector integrator."""
+    p = _small(n_E=9, n_u=1, geometry=I.SINGLE_ANGLE, mu0=1e5, eps=1e-2, r0=40.0, r1=42.0,
+               n_steps=400)
+    rho = orc.init_state(p)
+    out, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    assert st == 0
+    ref = _sa_bloch_rk4(orc, p, rho)
+    assert np.abs(orc.unpack(out, 2) - orc.unpack(rho, 2)).max() > 1e-3
+    assert np.abs(out - ref).max() < 1e-12 * np.abs(rho).max()
+
+
+# ---------------------------------------------------------------- convergence
+
+def test_convergence_orders(orc):
+    """P8: halving h cuts the RK4 error ~16x and the predictor-corrector
+    error ~4x (second order, Sec. 4.2.3)."""
+    base = _small(n_E=6, n_u=4, mu0=1e5, eps=1e-2, r0=50.0, r1=51.0)
+    rho = orc.init_state(base)
+    ref, _, _ = orc.evolve(base, rho, 50.0, 1.0 / 3200, 3200)
+
+    def err(stepper, n):
+        out, _, _ = orc.evolve(base.replace(stepper=stepper), rho, 50.0, 1.0 / n, n)
+        return np.abs(out - ref).max()
+
+    e = [err(I.RK4, n) for n in (25, 50, 100)]
+    assert 12 < e[0] / e[1] < 20 and 12 < e[1] / e[2] < 20
+    e = [err(I.EXPH, n) for n in (50, 100, 200)]
+    assert 3.2 < e[0] / e[1] < 4.8 and 3.2 < e[1] / e[2] < 4.8
+
+
+# ---------------------------------------------------------------- state / status
+
+def test_initial_state_structure(orc):
+    """Seeded start: flavor-diagonal phi_a(E) with |rho_ij| = eps sqrt(rho_ii rho_jj)."""
+    p = _small(n_f=3, eps=1e-6, seed=3)
+    rho = orc.init_state(p)
+    M = orc.unpack(rho, 3).reshape(2, p.n_u, p.n_E, 3, 3)
+    E, u, phi, Hv = orc.tables(p)
+    assert np.allclose(M[0, :, :, 0, 0].real, phi[0][None])
+    assert np.allclose(M[1, :, :, 2, 2].real, phi[3][None])
+    amp = np.abs(M[0, :, :, 0, 1])
+    assert np.allclose(amp, 1e-6 * np.sqrt(phi[0] * phi[2])[None], rtol=1e-12)
+    ph = np.angle(M[:, :, :, 0, 1]).ravel()
+    assert ph.std() > 1.0  # phases spread over the circle
+    assert not np.array_equal(orc.init_state(p.replace(seed=4)), rho)
+
+
+def test_literal_rk4_config_reports_nonfinite(orc):
+    """Explicit RK4 at h = 0.095 km from 10 km (mu0 = 1e5) is far outside its
+    stability region; the oracle reports it and keeps the last finite state."""
+    p = I.c1().replace(stepper=I.RK4)
+    rho = orc.init_state(p)
+    out, st, done = orc.evolve(p, rho, p.r0, p.h, 400)
+    assert st == 1 and done < 400
+    assert np.isfinite(out).all()
+
+
+def test_literal_mu_r4_breaks_lepton_number(orc):
+    """The literal reading (r-independent angle weights, mu0 (R/r)^4) loses the
+    cancellation of P5: its weights lack the 1/cos factor of Eq. 3.15 that
+    matches the path factor dl/dr = 1/cos of Eq. 3.3.  This is why the bulb
+    geometry is the default mode."""
+    p = _small(n_u=6, geometry=I.MU_R4, mu0=3e4, r0=20.0, r1=22.0, n_steps=400, eps=1e-2)
+    rho = orc.init_state(p)
+    out, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    I0, scale = _lepton_invariants(orc, p, rho)
+    I1, _ = _lepton_invariants(orc, p, out)
+    assert np.abs(I1 - I0).max() > 1e-6 * scale
