@@ -85,13 +85,17 @@ static double fd_quadrature(int k, double eta)
 {
     double b = (eta > 0 ? eta : 0.0) + 80.0;
     int n = 400000; /* even */
-    double h = b / n, s = 0.0;
+    double h = b / n, s = 0.0, comp = 0.0;
     for (int i = 0; i <= n; ++i) {
         double x = i * h, xk = 1.0;
         for (int q = 0; q < k; ++q) xk *= x;
         double f = xk / (exp(x - eta) + 1.0);
         double wgt = (i == 0 || i == n) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
-        s += wgt * f;
+        /* compensated (Kahan) summation: 4e5 terms would otherwise lose ~1e-13 */
+        double y = wgt * f - comp;
+        double t = s + y;
+        comp = (t - s) - y;
+        s = t;
     }
     return s * h / 3.0;
 }

@@ -59,8 +59,8 @@ def test_matter_coefficient_matches_pdg(orc):
 def test_fd_integrals_closed_form_at_zero(orc):
     """Eq. 4.2 at eta = 0: F_k(0) = (1 - 2^-k) k! zeta(k+1)."""
     zeta3, zeta4 = 1.2020569031595942, math.pi ** 4 / 90
-    assert orc.fd_integral(2, 0.0) == pytest.approx(0.75 * 2 * zeta3, rel=1e-12)
-    assert orc.fd_integral(3, 0.0) == pytest.approx(0.875 * 6 * zeta4, rel=1e-12)
+    assert orc.fd_integral(2, 0.0) == pytest.approx(0.75 * 2 * zeta3, rel=1e-14)
+    assert orc.fd_integral(3, 0.0) == pytest.approx(0.875 * 6 * zeta4, rel=1e-14)
 
 
 def test_fd_integrals_match_polylog(orc):
@@ -69,7 +69,7 @@ def test_fd_integrals_match_polylog(orc):
     for k in (2, 3):
         for eta in (-1.0, 1.5, 3.0):
             ref = float(-math.factorial(k) * mpmath.polylog(k + 1, -mpmath.e ** eta))
-            assert orc.fd_integral(k, eta) == pytest.approx(ref, rel=1e-11)
+            assert orc.fd_integral(k, eta) == pytest.approx(ref, rel=1e-14)
 
 
 def test_fd_temperatures_reproduce_paper(orc):
