@@ -1,0 +1,334 @@
+"""Throughput benchmark of the flavor-evolution hot path on GB300.
+
+Workload (the three-flavor bulb run): 1000 angle bins x 200 energy bins x
+{nu, nubar} = 400,000 3x3 density matrices, matter n_e = 1e33 (10 km/r)^3
+cm^-3, mu0 = 1e5 km^-1, the paper's predictor-corrector with the exact
+propagator, 20000 steps from 10 to 1000 km (h = 0.0495 km), FP64.
+
+One bench "step" = one chunk of --chunk radial steps (default 100) of the
+whole problem, i.e. one persistent launch.  L2 (129 MB) is flushed between
+timed chunks by writing a 512 MB buffer; the flush is outside the CUDA-event
+brackets.  Metric: bin-steps/s = 400,000 x radial steps / second (one bin =
+one n_f x n_f density matrix at one (angle, energy) for nu or nubar).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xf|reference]
+
+N > 1 runs N independent replicas (one per GPU, seeds differ, no data-path
+communication: "scaling": "weak"); rank 0 prints the JSON line with the
+whole-job value and the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bin-steps/s FP32-batched vs FP64 plain at <=1e-3 P_surv err; serve p50/p99"
+UNIT = "bin-steps/s"
+WORKLOAD = "bulb 3-flavor 1000 angles x 200 energies x nu/nubar, matter r^-3, mu0 1e5, EXPH, 10->1000 km"
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.file.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- algorithmic work
+
+# FP64 floating-point operations per bin-step of the predictor-corrector in
+# three flavors (two propagator applications per step), counted from the
+# per-bin formulas (+ - * / sqrt each 1, FMA 2, sincos not counted); the
+# Jacobi eigensolver is counted at the sweep number measured on this
+# workload.  Derivation in DESIGN.md ("Algorithmic work").
+FLOPS_PER_BIN_STEP = {("exph", 3): 2846, ("rk4", 3): 684, ("exph", 2): 120, ("rk4", 2): 172}
+
+
+def oracle_sample(problem, n_steps, threads):
+    """Time the CPU oracle (as it stands) on n_steps of the full problem."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    O.build()
+    rho = O.init_state(problem)
+    t0 = time.perf_counter()
+    O.evolve(problem, rho, problem.r0, problem.h, n_steps, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return problem.n_bins * n_steps / dt, dt
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1907_05560_gb300 import inputs as I
+    p = I.c2()
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(p, 1, threads)
+    times = []
+    for _ in range(args.steps):
+        v, dt = oracle_sample(p, 1, threads)
+        times.append(dt)
+    total = sum(times)
+    value = p.n_bins * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "bins": p.n_bins, "radial_steps_per_step": 1,
+                   "note": "FP64 CPU oracle on all host cores, one radial step of the full problem per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} radial steps of the full 400,000-bin problem from 10 km"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_xf(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1907_05560_gb300 import build as B
+    B.build()
+    from paper_1907_05560_gb300 import inputs as I
+    from paper_1907_05560_gb300 import xf
+
+    stream = torch.cuda.current_stream()
+    chunk = args.chunk
+    p = I.c2().replace(seed=2 + rank)
+    if args.precision == "fp32":
+        p = p.replace(precision=I.FP32_M64)
+
+    ctx = xf.Context(p, stream=stream)
+    ctx.init_state(p.r0)
+    ctas, threads, bars = ctx.launch_info()
+    flush = torch.empty(max(1, args.flush_mb) * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(args.warmup):
+        ctx.step_async(chunk, p.h)
+    ctx.sync()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        ctx.step_async(chunk, p.h)
+        ends[k].record(stream)
+    ctx.sync()
+    barrier()
+    clk = clocks.stop()
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms per chunk (one launch)
+    t_sum = sum(per) * 1e-3
+    if world > 1:
+        t = torch.tensor([t_sum], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_sum = float(t.item())
+    bin_steps = p.n_bins * chunk * args.steps
+    value = bin_steps * world / t_sum
+
+    # FP32 variant on the same input (same workload, same launch pattern)
+    fp32 = None
+    if args.precision == "fp64" and not args.skip_fp32:
+        q = p.replace(precision=I.FP32_M64)
+        c32 = xf.Context(q, stream=stream)
+        c32.init_state(q.r0)
+        for _ in range(args.warmup):
+            c32.step_async(chunk, q.h)
+        c32.sync()
+        s32 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        e32 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        barrier()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            s32[k].record(stream)
+            c32.step_async(chunk, q.h)
+            e32[k].record(stream)
+        c32.sync()
+        barrier()
+        t32 = sum(s.elapsed_time(e) for s, e in zip(s32, e32)) * 1e-3
+        fp32 = {"value": q.n_bins * chunk * args.steps * world / t32, "unit": UNIT,
+                "ms_per_step": 1e3 * t32 / args.steps, "precision": "FP32 bins, FP64 moments/radius/phase"}
+        c32.close()
+
+    # end to end through the C ABI with host buffers: set_state (H2D) + step + get_state (D2H)
+    host = torch.empty(ctx.n_doubles, dtype=torch.float64).pin_memory().numpy()
+    rho, _, _ = ctx.get_state(host)
+    e2e_times = []
+    barrier()
+    for k in range(max(1, args.e2e_steps)):
+        t0 = time.perf_counter()
+        ctx.set_state(host, p.r0 + 0.0)
+        ctx.step(chunk, p.h)
+        ctx.get_state(host)
+        e2e_times.append(time.perf_counter() - t0)
+    barrier()
+    e2e_t = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = p.n_bins * chunk * len(e2e_times) * world / e2e_t
+    nbytes = ctx.n_doubles * 8
+
+    # roofline of the dominant kernel (the persistent integrator, one launch per chunk)
+    avg_launch_s = t_sum / args.steps
+    kind = ("exph" if p.stepper == I.EXPH else "rk4", p.n_f)
+    flops = FLOPS_PER_BIN_STEP[kind] * p.n_bins * chunk
+    achieved = flops / avg_launch_s / 1e12
+    peak_meas = xf.peak(xf.PEAK_FP64_FMA if args.precision == "fp64" else xf.PEAK_FP32_FMA) / 1e12
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    # derived ALU peak: 152 SMs x (FP64: 2 FMA, FP32: 128 FMA) per clock x 2 flop x max clock
+    per_clk = 2 if args.precision == "fp64" else 128
+    peak_nom = 152 * per_clk * 2 * sm_max * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_nom, "unit": "TFLOP/s",
+                "frac": achieved / peak_nom, "traffic": None,
+                "kernel": "xf_run_kernel<3,EXPH,%s>" % ("double" if args.precision == "fp64" else "float"),
+                "peak_source": "derived: 152 SMs x %d FMA/clk x 2 x %.0f MHz (recipe FP64 1.25 TFLOP/s)" % (per_clk, sm_max),
+                "peak_measured_fma": peak_meas}
+
+    # CPU baseline: the oracle on the host cores, bounded sample
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        threads_cpu = os.cpu_count() or 1
+        v, dt = oracle_sample(I.c2(), args.cpu_steps, threads_cpu)
+        cpu = {"value": v, "unit": UNIT, "cores": threads_cpu, "kind": "oracle",
+               "sample": f"{args.cpu_steps} radial steps of the full 400,000-bin problem from 10 km ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_sum / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic (seeded initial state, paper's spectra)",
+            "config": {"workload": WORKLOAD, "bins": p.n_bins, "n_u": p.n_u, "n_E": p.n_E, "n_f": p.n_f,
+                       "radial_steps_per_step": chunk, "h_km": p.h, "ctas": ctas, "threads": threads,
+                       "barriers_per_radial_step": bars, "l2": f"flushed ({args.flush_mb} MB write) between timed steps",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "fp32_m64": fp32, "clocks": clk, "gpu_launches": args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="xf", choices=["xf", "reference"])
+    ap.add_argument("--chunk", type=int, default=100, help="radial steps per bench step")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
+    ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("need --steps >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_xf(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,231 @@
+/*
+ * xf.h -- C ABI of the GB300 flavor-evolution library (libxf.so).
+ *
+ * The library integrates the nonlinear mean-field flavor equations of the
+ * neutrino bulb model (XFLAT, arXiv 1907.05560, Sec. 3.1-3.2): for every
+ * angle bin u and energy bin E it evolves the neutrino and antineutrino
+ * density matrices rho(E,u) (2 or 3 flavors) in radius r,
+ *     d rho / dr = -i [H, rho] dl/dr,                     (Eq. 3.2, Eq. 3.4)
+ *     H_nu    = H_vac(E) + A(r) P_e + G_u,                 (Eq. 3.5-3.7)
+ *     H_nubar = H_vac(E) - A(r) P_e - conj(G_u),           (rule after Eq. 3.4)
+ *     G_u     = mu (M0 - cos(theta_u) M1),                 (Eq. 3.13-3.15)
+ * where M0 and M1 are reductions over every bin of rho_nu - conj(rho_nubar).
+ * Each integrator stage is one fused GPU pass (moment reduction + per-bin
+ * update) inside a persistent kernel with a grid-wide barrier.
+ *
+ * Conventions for every entry point:
+ *   - Return value: XF_OK (0) or a negative XF_E_* code.  No function throws,
+ *     aborts or exits; xf_last_error(ctx) describes the last failure.
+ *   - Handles are opaque and owned by the caller until xf_destroy.
+ *   - Every pointer argument is caller-owned; the library copies what it needs
+ *     before returning and keeps no pointer after return (except the
+ *     allocator callbacks and the stream handle, which must outlive the ctx).
+ *   - Host arrays use the packed layout below.  Device memory is allocated by
+ *     the library (cudaMalloc, or the allocator given to xf_create_ex).
+ *   - Calls on one ctx are not thread-safe; distinct ctxs are independent.
+ *
+ * Packed host layout of a state (n_doubles = 2 * n_u * n_E * n_f * n_f):
+ *   rho[((s * n_u + j) * n_E + e) * n_f*n_f + k], s = 0 neutrino, 1 antineutrino,
+ *   j = angle bin, e = energy bin; per bin k runs over the n_f real diagonal
+ *   entries, then (Re, Im) of the upper-triangle entries in row order:
+ *   2 flavors (rho11, rho22, Re rho12, Im rho12); 3 flavors (rho11, rho22,
+ *   rho33, Re/Im rho12, Re/Im rho13, Re/Im rho23).  Flavor order e, x (2 fl)
+ *   or e, mu, tau (3 fl).
+ * Grids: E_e = E_min + (e + 1/2) dE, dE = (E_max - E_min)/n_E; angle variable
+ *   u_j = (j + 1/2)/n_u with u = sin^2(theta_0) at the neutrinosphere (Eq. 3.14).
+ */
+#ifndef XF_H
+#define XF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define XF_OK 0
+#define XF_PENDING 1              /* xf_poll: job not finished yet */
+#define XF_E_ARG (-1)             /* bad argument: null, size, enum, range */
+#define XF_E_STATE (-2)           /* state values not finite / not Hermitian-packable */
+#define XF_E_NOMEM (-3)           /* device or host allocation failed */
+#define XF_E_CUDA (-4)            /* CUDA runtime error (message in xf_last_error) */
+#define XF_E_NONFINITE (-5)       /* integration produced a non-finite moment; state
+                                     is left at the last finite step */
+#define XF_E_BARRIER_TIMEOUT (-6) /* a grid barrier wait exceeded its time limit */
+#define XF_E_UNSTABLE (-7)        /* strict mode: RK4 step outside its stable region */
+#define XF_E_BUSY (-8)            /* serving: queue full */
+#define XF_E_TOO_BIG (-9)         /* serving: job larger than the memory budget */
+#define XF_E_NOTFOUND (-10)       /* serving: unknown job id */
+#define XF_E_TIMEOUT (-11)        /* serving: job exceeded its time limit */
+#define XF_E_UNSUPPORTED (-12)    /* combination not built */
+
+/* ---- enums -------------------------------------------------------------- */
+enum xf_stepper {
+    XF_RK4 = 0,  /* classic fixed-step RK4 on d rho/dr = -i[H,rho] dl/dr: 4 fused stages */
+    XF_EXPH = 1  /* the paper's coarse predictor-corrector (Sec. 4.2.3, Listing 5.1 S1-S3)
+                    with the exact propagator exp(-i H dl) (Eq. 3.10-3.12): 2 stages */
+};
+enum xf_precision {
+    XF_FP64 = 0,        /* FP64 everywhere */
+    XF_FP32_M64 = 1,    /* FP32 per-bin arithmetic and storage; FP64 moments, radius, phase */
+    XF_FP32_COMP = 2,   /* as FP32_M64 but moments summed in compensated FP32 (TwoSum) */
+    XF_FP32_M64_RENORM = 3 /* FP32_M64 plus per-step restoration of |P| (2 fl) / tr rho0^2 */
+};
+enum xf_geometry {
+    XF_GEOM_BULB = 0,         /* Eq. 3.13-3.15: w_u = x^2 du/(2 cos_u), x = R/r; dl/dr = 1/cos_u */
+    XF_GEOM_MU_R4 = 1,        /* literal mu0 (R/r)^4 with r-independent weights du; dl/dr = 1/cos_u */
+    XF_GEOM_SINGLE_ANGLE = 2, /* Eq. 3.16-3.17: G = mu0 D(r/R) dE sum(rho - conj rho_bar), dl = dr */
+    XF_GEOM_CONST = 3         /* isotropic, constant mu0: G = mu0 dE du sum(...), dl = dr */
+};
+enum xf_matter {
+    XF_MATTER_NONE = 0,
+    XF_MATTER_POWER = 1, /* n_e = ne_ref (r_ref/r)^ne_power   (Eq. 4.3 shape) */
+    XF_MATTER_EXP = 2    /* n_e = Ye nb0 exp(-(r - R)/h_ns)      (Eq. 4.4) */
+};
+
+#define XF_PARAMS_VERSION 1u
+
+/* Problem parameters.  Fill with xf_params_default, then set fields.
+ * Keyword names of the paper's configuration file (App. A.3) in brackets. */
+typedef struct xf_params {
+    uint32_t size;      /* = sizeof(xf_params) */
+    uint32_t version;   /* = XF_PARAMS_VERSION */
+    int32_t stepper;    /* enum xf_stepper */
+    int32_t precision;  /* enum xf_precision */
+    int32_t geometry;   /* enum xf_geometry */
+    int32_t hierarchy;  /* +1 normal, -1 inverted: sign of dm2 (2 fl) / dm2_31 (3 fl) */
+    int32_t matter;     /* enum xf_matter */
+    int32_t strict;     /* 1: RK4 returns XF_E_UNSTABLE before a step it cannot take stably */
+    double R_nu_km;     /* neutrinosphere radius [R0 is the start radius; R_nu is Eq. 3.14's R] */
+    double mu0_per_km;  /* nu-nu coupling, absorbs the normalisation of Eq. 3.8 */
+    double E_min_MeV, E_max_MeV; /* [E0, E1] */
+    double dm2_eV2[2];  /* magnitudes; 2 fl: dm2[0] [dm2]; 3 fl: dm2_21, dm2_31 */
+    double theta[3];    /* 2 fl: theta[0] [theta]; 3 fl: theta12, theta13, theta23 (delta_CP = 0) */
+    double ne_ref_cm3, r_ref_km, ne_power; /* XF_MATTER_POWER */
+    double nb0_cm3, h_ns_km, Ye;           /* XF_MATTER_EXP [nb0, hNS, Ye] */
+    double T_MeV[4];    /* temperatures nu_e, nubar_e, nu_x, nubar_x [T*] */
+    double eta[4];      /* degeneracy parameters [eta*] */
+    double L[4];        /* luminosities, any common unit [L*] */
+    double eps_perturb; /* seeded off-diagonal amplitude (fraction of sqrt(rho_ii rho_jj)) */
+    uint64_t seed;      /* seed of the SplitMix64 phases of the perturbation */
+} xf_params;
+
+typedef struct xf_ctx xf_ctx;
+
+/* Device allocator hook: alloc(bytes, user) returns a device pointer or NULL;
+ * free(ptr, user) releases it.  Must stay valid until xf_destroy. */
+typedef struct xf_allocator {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *user;
+} xf_allocator;
+
+/* Default parameters: the bulb-model values of Sec. 4.5 (eta = 3,
+ * T = 2.76/4.01/6.26 MeV, equal L, R = 10 km, theta = 0.1), RK4, FP64, BULB,
+ * no matter, dm2 = 2.4e-3 eV^2 inverted, mu0 = 1e5 km^-1, eps = 1e-6, seed 1.
+ * p must be non-null. */
+void xf_params_default(xf_params *p);
+
+/* Create a context for one problem of n_u angle bins x n_E energy bins x
+ * {nu, nubar}, n_flavor in {2, 3}.  Validates p (XF_E_ARG on bad sizes,
+ * enums, non-finite or non-positive physical values), builds the per-energy
+ * tables on the host in FP64 and allocates the device state.  On success
+ * *out owns the context; on failure *out is NULL.  The state is undefined
+ * until xf_set_state or xf_init_state. */
+int xf_create(int n_E, int n_u, int n_flavor, const xf_params *p, xf_ctx **out);
+/* As xf_create, with device memory taken from `alloc` (NULL: cudaMalloc). */
+int xf_create_ex(int n_E, int n_u, int n_flavor, const xf_params *p, const xf_allocator *alloc,
+                 xf_ctx **out);
+/* Release the context and its device memory.  NULL is accepted (no-op). */
+int xf_destroy(xf_ctx *ctx);
+
+/* Use `stream` (a cudaStream_t) for all later work on this ctx; NULL = the
+ * legacy default stream.  The stream must outlive its use by the ctx. */
+int xf_set_stream(xf_ctx *ctx, void *stream);
+
+/* Copy a packed host state (layout above, n_doubles exact) to the device and
+ * set the radius to r_km (>= R_nu).  XF_E_STATE if any value is non-finite.  The trace
+ * of every bin is kept in FP64 and never changes (d tr rho/dr = 0). */
+int xf_set_state(xf_ctx *ctx, const double *rho, size_t n_doubles, double r_km);
+
+/* Seeded initial state at radius r_km (>= R_nu): rho_nu(u,E) = diag(phi_nue(E),
+ * phi_nux(E)[, phi_nux(E)]), rho_nubar likewise with the antineutrino spectra
+ * (Eq. 4.1-4.2; phi_a = (L_a/<E_a>) f_a(E) relative to nu_e), and each upper
+ * entry (i<j) = eps sqrt(rho_ii rho_jj) exp(2 pi i U), U the SplitMix64 uniform
+ * number at counter b * n_f(n_f-1)/2 + k for bin b = (s n_u + j) n_E + e. */
+int xf_init_state(xf_ctx *ctx, double r_km);
+
+/* Advance n_steps >= 0 fixed steps of dr_km > 0 from the current radius.
+ * Synchronous: returns when the work has finished on the ctx stream.
+ * XF_E_NONFINITE: the state is left at the last step whose moments were
+ * finite (xf_get_state reports how many steps were taken).
+ * XF_E_BARRIER_TIMEOUT: a grid barrier did not complete within its limit; the
+ * kernel returned without hanging and the state is undefined. */
+int xf_step(xf_ctx *ctx, int64_t n_steps, double dr_km);
+/* As xf_step but returns after enqueuing (no host synchronisation); errors
+ * from the device are reported by the next synchronous call on the ctx. */
+int xf_step_async(xf_ctx *ctx, int64_t n_steps, double dr_km);
+/* Wait for enqueued work; returns its device status. */
+int xf_sync(xf_ctx *ctx);
+
+/* Copy the current state to a packed host array (n_doubles exact); r_km and
+ * steps_done (total steps since the last set/init) may be NULL. */
+int xf_get_state(xf_ctx *ctx, double *rho, size_t n_doubles, double *r_km, int64_t *steps_done);
+
+/* nu-nu moments of the current state at the current radius (Eq. 3.13-3.15
+ * for the ctx geometry), packed Hermitian n_f*n_f doubles each (layout of one
+ * bin above), trace included, computed on the device in FP64:
+ *   M0 = dE sum_{u,E} a_u (rho_nu - conj rho_nubar),  M1 = dE sum b_u (...),
+ *   BULB: a_u = x^2 du / (2 cos_u), b_u = a_u cos_u. */
+int xf_moments(xf_ctx *ctx, double *M0, double *M1, size_t n_doubles);
+
+/* Per-bin outputs of the current state (Sec. 4.5 survival probability), each
+ * array n_bins = 2 n_u n_E doubles in [s][u][E] order, any may be NULL:
+ *   p_surv: (rho_ee - phi_x)/(phi_e - phi_x) with phi the initial diagonal
+ *           weights of that species and energy (NaN where phi_e == phi_x);
+ *   trace:  tr rho;   purity: tr(rho0^2), rho0 the traceless part
+ *           (= |P|^2/2 in two flavors). */
+int xf_outputs(xf_ctx *ctx, double *p_surv, double *trace, double *purity, size_t n_bins);
+
+/* Host copies of the per-energy tables, for inspection: E[n_E] (MeV),
+ * phi[4 * n_E] (nu_e, nubar_e, nu_x, nubar_x).  Any pointer may be NULL. */
+int xf_tables(xf_ctx *ctx, double *E, double *phi);
+
+/* Number of grid barriers per integrator step of this ctx's stepper
+ * (RK4: 4, EXPH: 2) and the device grid size used. */
+int xf_launch_info(xf_ctx *ctx, int *ctas, int *threads, int *barriers_per_step);
+
+/* Options (xf_set_option), for tuning and testing:
+ *   XF_OPT_GRID: persistent grid size in CTAs; 0 = automatic (default).  The
+ *     value is clamped to the co-resident maximum and to the pair count.
+ *     The reduction tree follows the grid, so results can differ from the
+ *     automatic shape by rounding.
+ *   XF_OPT_BARRIER_TIMEOUT_NS: time limit of one grid-barrier wait
+ *     (default 2e9 ns).  On expiry every CTA leaves and the call returns
+ *     XF_E_BARRIER_TIMEOUT.
+ *   XF_OPT_TEST_SKIP_ARRIVAL: test hook; CTA `value` (>= 0) leaves the kernel
+ *     at its first grid barrier without arriving, so the other CTAs' bounded
+ *     wait runs out.  -1 (default) disables it.  Exercises the timeout path
+ *     without faulting or hanging the GPU. */
+enum xf_option { XF_OPT_GRID = 1, XF_OPT_BARRIER_TIMEOUT_NS = 2, XF_OPT_TEST_SKIP_ARRIVAL = 3 };
+int xf_set_option(xf_ctx *ctx, int option, int64_t value);
+
+/* Measured ALU peaks of the current device, for roofline denominators:
+ * XF_PEAK_FP64_FMA / XF_PEAK_FP32_FMA write the FMA throughput in FLOP/s
+ * (an FMA counts 2) of a register-resident FMA loop over 8 CTAs per SM,
+ * best of 5 timed launches (CUDA events).  Not part of the integration. */
+enum xf_peak_kind { XF_PEAK_FP64_FMA = 0, XF_PEAK_FP32_FMA = 1 };
+int xf_peak(int which, double *value);
+
+/* Human-readable name of a status code (static storage). */
+const char *xf_status_str(int status);
+/* Message of the last failure on ctx (static per-ctx storage; "" if none).
+ * With ctx == NULL: the last failure of xf_create in this thread. */
+const char *xf_last_error(const xf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XF_H */

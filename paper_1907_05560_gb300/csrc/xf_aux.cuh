@@ -1,0 +1,277 @@
+// xf_aux.cuh -- non-hot-path device kernels: seeded initial state, packed <->
+// component-major layout conversion, full moments, per-bin outputs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xf_math.cuh"
+
+namespace xf {
+
+// SplitMix64 (Steele, Lea & Flood 2014): the i-th output of the stream
+// seeded with `seed`, computed from the counter alone.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct LayoutArgs {
+    int n_E, n_u, n_pairs, npad;
+    const double *phi;  // [4][n_E] number-flux weights (nu_e, nubar_e, nu_x, nubar_x)
+    double eps;
+    uint64_t seed;
+    int *bad;           // set to 1 if an input value is not finite
+};
+
+// Bin b = (s n_u + j) n_E + e  <->  species s, pair p = j n_E + e.
+__device__ __forceinline__ void bin_split(const LayoutArgs &a, long long b, int *s, int *p)
+{
+    long long per = (long long)a.n_u * a.n_E;
+    *s = (int)(b / per);
+    *p = (int)(b - (long long)(*s) * per);
+}
+
+// Seeded initial state (one thread per bin): rho = diag(phi_e, phi_x[, phi_x])
+// plus eps sqrt(rho_ii rho_jj) exp(2 pi i U) on each upper entry.
+template <int NF, typename Real>
+__global__ void init_state_kernel(LayoutArgs a, Real *state, double *trace)
+{
+    constexpr int S = Comp<NF>::S, NOFF = NF * (NF - 1) / 2;
+    const long long nb = 2ll * a.n_pairs;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        int s, p;
+        bin_split(a, b, &s, &p);
+        const int e = p % a.n_E;
+        const double pe = a.phi[(s == 0 ? 0 : 1) * a.n_E + e];
+        const double px = a.phi[(s == 0 ? 2 : 3) * a.n_E + e];
+        double dg[3] = {pe, px, px};
+        double tr = pe + (NF - 1) * px;
+        double t[S];
+        if constexpr (NF == 2) {
+            t[0] = 0.5 * (pe - px);
+        } else {
+            double tau = tr / 3.0;
+            t[0] = pe - tau;
+            t[1] = px - tau;
+        }
+        int k = 0;
+        for (int i = 0; i < NF; ++i)
+            for (int j = i + 1; j < NF; ++j) {
+                uint64_t z = splitmix64(a.seed, (uint64_t)b * NOFF + k);
+                double U = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+                double sn, cs;
+                sincos(6.283185307179586476925286766559 * U, &sn, &cs);
+                double amp = a.eps * sqrt(dg[i] * dg[j]);
+                t[NF - 1 + 2 * k] = amp * cs;
+                t[NF + 2 * k] = amp * sn;
+                ++k;
+            }
+#pragma unroll
+        for (int c = 0; c < S; ++c) state[(size_t)(c * 2 + s) * a.npad + p] = (Real)t[c];
+        trace[(size_t)s * a.npad + p] = tr;
+    }
+}
+
+// packed host layout -> traceless components + trace
+template <int NF, typename Real>
+__global__ void pack_to_state_kernel(LayoutArgs a, const double *packed, Real *state, double *trace)
+{
+    constexpr int S = Comp<NF>::S, M = NF * NF;
+    const long long nb = 2ll * a.n_pairs;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        int s, p;
+        bin_split(a, b, &s, &p);
+        const double *x = packed + (size_t)b * M;
+        bool ok = true;
+        for (int c = 0; c < M; ++c) ok = ok && isfinite(x[c]);
+        if (!ok) *a.bad = 1;
+        double t[S], tr;
+        if constexpr (NF == 2) {
+            tr = x[0] + x[1];
+            t[0] = 0.5 * (x[0] - x[1]);
+            t[1] = x[2];
+            t[2] = x[3];
+        } else {
+            tr = x[0] + x[1] + x[2];
+            double tau = tr / 3.0;
+            t[0] = x[0] - tau;
+            t[1] = x[1] - tau;
+            for (int c = 0; c < 6; ++c) t[2 + c] = x[3 + c];
+        }
+#pragma unroll
+        for (int c = 0; c < S; ++c) state[(size_t)(c * 2 + s) * a.npad + p] = (Real)t[c];
+        trace[(size_t)s * a.npad + p] = tr;
+    }
+}
+
+// traceless components + trace -> packed host layout
+template <int NF, typename Real>
+__global__ void state_to_pack_kernel(LayoutArgs a, const Real *state, const double *trace, double *packed)
+{
+    constexpr int S = Comp<NF>::S, M = NF * NF;
+    const long long nb = 2ll * a.n_pairs;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        int s, p;
+        bin_split(a, b, &s, &p);
+        double t[S];
+#pragma unroll
+        for (int c = 0; c < S; ++c) t[c] = (double)state[(size_t)(c * 2 + s) * a.npad + p];
+        const double tr = trace[(size_t)s * a.npad + p];
+        double *x = packed + (size_t)b * M;
+        if constexpr (NF == 2) {
+            const double tau = 0.5 * tr;
+            x[0] = tau + t[0];
+            x[1] = tau - t[0];
+            x[2] = t[1];
+            x[3] = t[2];
+        } else {
+            const double tau = tr / 3.0;
+            x[0] = tau + t[0];
+            x[1] = tau + t[1];
+            x[2] = tau - t[0] - t[1];
+            for (int c = 0; c < 6; ++c) x[3 + c] = t[2 + c];
+        }
+    }
+}
+
+// Per-bin outputs: survival probability, trace, tr(T^2) of the traceless part.
+template <int NF, typename Real>
+__global__ void outputs_kernel(LayoutArgs a, const Real *state, const double *trace, double *p_surv,
+                               double *trace_out, double *purity)
+{
+    constexpr int S = Comp<NF>::S;
+    const long long nb = 2ll * a.n_pairs;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        int s, p;
+        bin_split(a, b, &s, &p);
+        const int e = p % a.n_E;
+        double t[S];
+#pragma unroll
+        for (int c = 0; c < S; ++c) t[c] = (double)state[(size_t)(c * 2 + s) * a.npad + p];
+        const double tr = trace[(size_t)s * a.npad + p];
+        double ree, pur;
+        if constexpr (NF == 2) {
+            ree = 0.5 * tr + t[0];
+            pur = 2.0 * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        } else {
+            ree = tr / 3.0 + t[0];
+            const double t3 = -(t[0] + t[1]);
+            pur = t[0] * t[0] + t[1] * t[1] + t3 * t3;
+            for (int c = 2; c < 8; ++c) pur += 2.0 * t[c] * t[c];
+        }
+        const double pe = a.phi[(s == 0 ? 0 : 1) * a.n_E + e];
+        const double px = a.phi[(s == 0 ? 2 : 3) * a.n_E + e];
+        if (p_surv) p_surv[b] = (pe != px) ? (ree - px) / (pe - px) : (double)NAN;
+        if (trace_out) trace_out[b] = tr;
+        if (purity) purity[b] = pur;
+    }
+}
+
+// Full nu-nu moments of a state at radius r (fixed-order, two kernels):
+// CTA b sums pairs [b * chunk, (b+1) * chunk) -> part[b][NV + 2], where the
+// last two entries carry the trace sums (trace of rho_nu - rho_nubar) for the
+// a- and b-weights; a single CTA then sums the partials in order and writes
+// the packed Hermitian M0, M1 (trace restored on the diagonal).
+struct MomArgs {
+    int n_E, n_u, n_pairs, npad, geometry, chunk;
+    double R, du, dE, r;
+};
+
+__device__ __forceinline__ void mom_weights(const MomArgs &m, int j, double *wa, double *wb)
+{
+    *wa = m.du;
+    *wb = 0.0;
+    if (m.geometry == 0 || m.geometry == 1) {
+        double x = m.R / m.r, x2 = x * x;
+        double c = sqrt(1.0 - x2 * ((j + 0.5) * m.du));
+        if (m.geometry == 0) {
+            *wa = x2 * m.du / (2.0 * c);
+            *wb = *wa * c;
+        } else {
+            *wb = m.du * c;
+        }
+    }
+}
+
+template <int NF, typename Real, int NT>
+__global__ void __launch_bounds__(NT) moments_partial_kernel(MomArgs m, const Real *state,
+                                                             const double *trace, double *part)
+{
+    constexpr int S = Comp<NF>::S, NV = 2 * S + 2;
+    __shared__ double s_w[NT / 32][NV];
+    double acc[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) acc[c] = 0.0;
+    const int p0 = blockIdx.x * m.chunk, p1 = min(p0 + m.chunk, m.n_pairs);
+    for (int p = p0 + threadIdx.x; p < p1; p += NT) {
+        const int j = p / m.n_E;
+        double wa, wb;
+        mom_weights(m, j, &wa, &wb);
+        Real tn[S], tb[S], d[S];
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            tn[c] = state[(size_t)(c * 2 + 0) * m.npad + p];
+            tb[c] = state[(size_t)(c * 2 + 1) * m.npad + p];
+        }
+        nu_minus_conj_nubar<NF, Real>(tn, tb, d);
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            acc[c] += wa * (double)d[c];
+            acc[S + c] += wb * (double)d[c];
+        }
+        const double dtr = trace[p] - trace[(size_t)m.npad + p];
+        acc[2 * S] += wa * dtr;
+        acc[2 * S + 1] += wb * dtr;
+    }
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+        double v = acc[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int q = 0; q < NT / 32; ++q) s += s_w[q][threadIdx.x];
+        part[(size_t)blockIdx.x * NV + threadIdx.x] = s;
+    }
+}
+
+template <int NF>
+__global__ void moments_final_kernel(const double *part, int G, double dE, double *M0, double *M1)
+{
+    constexpr int S = Comp<NF>::S, NV = 2 * S + 2, M = NF * NF;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double tot[NV];
+    for (int c = 0; c < NV; ++c) tot[c] = 0.0;
+    for (int g = 0; g < G; ++g)
+        for (int c = 0; c < NV; ++c) tot[c] += part[(size_t)g * NV + c];
+    for (int w = 0; w < 2; ++w) {
+        const double *t = tot + w * S;
+        const double tau = tot[2 * S + w] / NF * dE;
+        double *x = (w == 0) ? M0 : M1;
+        if constexpr (NF == 2) {
+            x[0] = tau + t[0] * dE;
+            x[1] = tau - t[0] * dE;
+            x[2] = t[1] * dE;
+            x[3] = t[2] * dE;
+        } else {
+            x[0] = tau + t[0] * dE;
+            x[1] = tau + t[1] * dE;
+            x[2] = tau - (t[0] + t[1]) * dE;
+            for (int c = 0; c < 6; ++c) x[3 + c] = t[2 + c] * dE;
+        }
+        (void)M;
+    }
+}
+
+} // namespace xf

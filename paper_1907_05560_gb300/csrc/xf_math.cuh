@@ -1,0 +1,343 @@
+// xf_math.cuh -- per-bin arithmetic of the flavor-evolution path on packed,
+// traceless Hermitian components (device side).
+//
+// A density matrix or Hamiltonian is stored as its traceless part; the trace
+// of rho is constant (d tr rho/dr = tr(-i[H,rho]) = 0) and the trace of H
+// drops out of every commutator and of U rho U^dagger.
+//
+//   2 flavors, S = 3:  T = [[a, x + i y], [x - i y, -a]]
+//                      comps (a, x, y)
+//   3 flavors, S = 8:  T = [[t1, z12, z13], [., t2, z23], [., ., -t1-t2]]
+//                      comps (t1, t2, Re z12, Im z12, Re z13, Im z13, Re z23, Im z23)
+//
+// Equations: d rho/dl = -i [H, rho] (Eq. 3.2/3.4 written for rho); the
+// propagator exp(-i H dl) of Eq. 3.10-3.12.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace xf {
+
+template <int NF> struct Comp;
+template <> struct Comp<2> { static constexpr int S = 3; };
+template <> struct Comp<3> { static constexpr int S = 8; };
+
+// ---------------------------------------------------------------- helpers
+__host__ __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
+__host__ __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
+__host__ __device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+__host__ __device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+
+// Phase phi = lam * dl, evaluated in FP64; returns (sin, cos) in Real.  For
+// FP32 the FP64 phase is reduced to [-pi, pi] in FP64 before sincosf, so a
+// long step does not lose the phase to FP32 rounding of its argument.
+template <typename Real>
+__host__ __device__ __forceinline__ void phase_sincos(double phi, Real *s, Real *c);
+template <>
+__host__ __device__ __forceinline__ void phase_sincos<double>(double phi, double *s, double *c)
+{
+    sincos(phi, s, c);
+}
+template <>
+__host__ __device__ __forceinline__ void phase_sincos<float>(double phi, float *s, float *c)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double k = rint(phi * (1.0 / two_pi));
+    float red = (float)fma(-k, two_pi, phi);
+    sincosf(red, s, c);
+}
+
+// ---------------------------------------------------------------- 2 flavors
+// -i[H, T] for traceless 2x2 H = (hz, hx, hy), T = (a, x, y):
+//   da = 2 (hy x - hx y),  dx = 2 (hz y - a hy),  dy = 2 (a hx - hz x)
+template <typename Real>
+__host__ __device__ __forceinline__ void comm2(const Real *h, const Real *t, Real *d)
+{
+    d[0] = Real(2) * (h[2] * t[1] - h[1] * t[2]);
+    d[1] = Real(2) * (h[0] * t[2] - t[0] * h[2]);
+    d[2] = Real(2) * (t[0] * h[1] - h[0] * t[1]);
+}
+
+// T' = U T U^dagger with U = exp(-i H dl) (Eq. 3.11): a rotation of the Bloch
+// vector of T about the Bloch vector of H by the angle 2 lam dl,
+// lam = sqrt(h11^2 + |h12|^2) (Eq. 3.12).  With W = (1/2)(-i[H,T]) and
+// Q the same map applied to W (Rodrigues' formula):
+//   T' = T + 2 sigma C W + 2 sigma^2 Q,  sigma = sin(lam dl)/lam, C = cos(lam dl)
+template <typename Real>
+__host__ __device__ __forceinline__ void prop2(const Real *h, double dl, const Real *t, Real *out)
+{
+    Real lam2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+    Real lam = sqrt_r(lam2);
+    Real sn, cs;
+    phase_sincos<Real>((double)lam * dl, &sn, &cs);
+    Real sig = (lam > Real(0)) ? sn / lam : (Real)dl;
+    Real w[3], q[3];
+    w[0] = h[2] * t[1] - h[1] * t[2];
+    w[1] = h[0] * t[2] - t[0] * h[2];
+    w[2] = t[0] * h[1] - h[0] * t[1];
+    q[0] = h[2] * w[1] - h[1] * w[2];
+    q[1] = h[0] * w[2] - w[0] * h[2];
+    q[2] = w[0] * h[1] - h[0] * w[1];
+    Real c1 = Real(2) * sig * cs, c2 = Real(2) * sig * sig;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[k] = t[k] + c1 * w[k] + c2 * q[k];
+}
+
+// ---------------------------------------------------------------- 3 flavors
+template <typename Real> struct cx {
+    Real r, i;
+};
+template <typename Real> __host__ __device__ __forceinline__ cx<Real> mk(Real r, Real i) { return {r, i}; }
+template <typename Real> __host__ __device__ __forceinline__ cx<Real> operator+(cx<Real> a, cx<Real> b)
+{
+    return {a.r + b.r, a.i + b.i};
+}
+template <typename Real> __host__ __device__ __forceinline__ cx<Real> operator-(cx<Real> a, cx<Real> b)
+{
+    return {a.r - b.r, a.i - b.i};
+}
+template <typename Real> __host__ __device__ __forceinline__ cx<Real> operator*(cx<Real> a, cx<Real> b)
+{
+    return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r};
+}
+template <typename Real> __host__ __device__ __forceinline__ cx<Real> operator*(Real a, cx<Real> b)
+{
+    return {a * b.r, a * b.i};
+}
+template <typename Real> __host__ __device__ __forceinline__ cx<Real> cj(cx<Real> a) { return {a.r, -a.i}; }
+// a * conj(b)
+template <typename Real> __host__ __device__ __forceinline__ cx<Real> mulc(cx<Real> a, cx<Real> b)
+{
+    return {a.r * b.r + a.i * b.i, a.i * b.r - a.r * b.i};
+}
+
+// -i[H, T] for traceless Hermitian 3x3 (comps layout above).  With X = H T:
+//   D_kk = 2 Im X_kk,   D_jk = -i (X_jk - conj(X_kj))  (j < k)
+// written out so that real diagonal entries never multiply zero imaginary parts.
+template <typename Real>
+__host__ __device__ __forceinline__ void comm3(const Real *h, const Real *t, Real *d)
+{
+    const Real h1 = h[0], h2 = h[1], h3 = -(h[0] + h[1]);
+    const Real r1 = t[0], r2 = t[1], r3 = -(t[0] + t[1]);
+    const cx<Real> h12 = mk(h[2], h[3]), h13 = mk(h[4], h[5]), h23 = mk(h[6], h[7]);
+    const cx<Real> r12 = mk(t[2], t[3]), r13 = mk(t[4], t[5]), r23 = mk(t[6], t[7]);
+    // Im(a conj b) = a.i b.r - a.r b.i
+    Real d11 = Real(2) * ((h12.i * r12.r - h12.r * r12.i) + (h13.i * r13.r - h13.r * r13.i));
+    Real d22 = Real(2) * ((h12.r * r12.i - h12.i * r12.r) + (h23.i * r23.r - h23.r * r23.i));
+    // Z12 = (h1 - h2) r12 - (r1 - r2) h12 + h13 conj(r23) - conj(h23) r13
+    cx<Real> z12 = (h1 - h2) * r12 - (r1 - r2) * h12 + mulc(h13, r23) - mulc(r13, h23);
+    // Z13 = (h1 - h3) r13 - (r1 - r3) h13 + h12 r23 - h23 r12
+    cx<Real> z13 = (h1 - h3) * r13 - (r1 - r3) * h13 + h12 * r23 - h23 * r12;
+    // Z23 = (h2 - h3) r23 - (r2 - r3) h23 + conj(h12) r13 - h13 conj(r12)
+    cx<Real> z23 = (h2 - h3) * r23 - (r2 - r3) * h23 + mulc(r13, h12) - mulc(h13, r12);
+    d[0] = d11;
+    d[1] = d22;
+    // -i Z = (Z.i, -Z.r)
+    d[2] = z12.i;
+    d[3] = -z12.r;
+    d[4] = z13.i;
+    d[5] = -z13.r;
+    d[6] = z23.i;
+    d[7] = -z23.r;
+}
+
+// index of the stored upper entry (a, b), a < b: (0,1) -> 0, (0,2) -> 1, (1,2) -> 2
+__host__ __device__ constexpr int oidx(int a, int b) { return a == 0 ? b - 1 : 2; }
+
+// One Jacobi rotation on pivot (P, Q) of the Hermitian matrix held as diag
+// dg[3] and upper entries o[3], accumulating V <- V J with
+// J = [[c, s e^{i phi}], [-s e^{-i phi}, c]] on rows/cols (P, Q),
+// e^{i phi} = A_PQ / |A_PQ|, t = tan(theta) the smaller root of
+// t^2 + 2 tau t - 1 = 0, tau = (A_QQ - A_PP) / (2 |A_PQ|).  J^dagger A J has
+// a zero (P, Q) entry, A_PP -> A_PP - t |A_PQ|, A_QQ -> A_QQ + t |A_PQ|.
+template <typename Real, int P, int Q>
+__host__ __device__ __forceinline__ void jacobi_rot(Real *dg, cx<Real> *o, cx<Real> (*V)[3])
+{
+    constexpr int R = 3 - P - Q;
+    cx<Real> g = o[oidx(P, Q)];
+    Real ag2 = g.r * g.r + g.i * g.i;
+    if (!(ag2 > Real(0))) return;
+    Real ag = sqrt_r(ag2);
+    Real er = g.r / ag, ei = g.i / ag; // e^{i phi}
+    Real tau = (dg[Q] - dg[P]) / (Real(2) * ag);
+    Real t = (tau >= Real(0) ? Real(1) : Real(-1)) / (fabs(tau) + sqrt_r(Real(1) + tau * tau));
+    Real c = Real(1) / sqrt_r(Real(1) + t * t);
+    Real s = t * c;
+    dg[P] -= t * ag;
+    dg[Q] += t * ag;
+    o[oidx(P, Q)] = mk(Real(0), Real(0));
+    // A_RP and A_RQ: stored when R is the row of an upper entry, else conjugated
+    cx<Real> aRP = (R < P) ? o[oidx(R, P)] : cj(o[oidx(P, R)]);
+    cx<Real> aRQ = (R < Q) ? o[oidx(R, Q)] : cj(o[oidx(Q, R)]);
+    const cx<Real> e = mk(er, ei), ec = mk(er, -ei);
+    // (J^dagger A J)_RP = c A_RP - s e^{-i phi} A_RQ,  (.)_RQ = s e^{i phi} A_RP + c A_RQ
+    cx<Real> nRP = c * aRP - s * (ec * aRQ);
+    cx<Real> nRQ = s * (e * aRP) + c * aRQ;
+    if (R < P) o[oidx(R, P)] = nRP;
+    else o[oidx(P, R)] = cj(nRP);
+    if (R < Q) o[oidx(R, Q)] = nRQ;
+    else o[oidx(Q, R)] = cj(nRQ);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        cx<Real> vp = V[k][P], vq = V[k][Q];
+        V[k][P] = c * vp - s * (ec * vq);
+        V[k][Q] = s * (e * vp) + c * vq;
+    }
+}
+
+template <typename Real> struct JacobiTol;
+template <> struct JacobiTol<double> {
+    static constexpr double rel2 = 1e-34;
+    static constexpr int sweeps = 8;
+};
+template <> struct JacobiTol<float> {
+    static constexpr float rel2 = 1e-15f;
+    static constexpr int sweeps = 6;
+};
+
+// T' = U T U^dagger with U = exp(-i H dl), H traceless Hermitian 3x3:
+// H = V diag(lam) V^dagger by cyclic Jacobi, then
+// T' = V (E o (V^dagger T V)) V^dagger with E_jk = exp(-i (lam_j - lam_k) dl).
+template <typename Real>
+__host__ __device__ __forceinline__ void prop3(const Real *h, double dl, const Real *t, Real *out)
+{
+    Real dg[3] = {h[0], h[1], -(h[0] + h[1])};
+    cx<Real> o[3] = {mk(h[2], h[3]), mk(h[4], h[5]), mk(h[6], h[7])};
+    cx<Real> V[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) V[a][b] = mk(Real(a == b ? 1 : 0), Real(0));
+    const Real scale2 = dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2] +
+                        Real(2) * (o[0].r * o[0].r + o[0].i * o[0].i + o[1].r * o[1].r +
+                                   o[1].i * o[1].i + o[2].r * o[2].r + o[2].i * o[2].i);
+    for (int sweep = 0; sweep < JacobiTol<Real>::sweeps; ++sweep) {
+        Real off2 = o[0].r * o[0].r + o[0].i * o[0].i + o[1].r * o[1].r + o[1].i * o[1].i +
+                    o[2].r * o[2].r + o[2].i * o[2].i;
+        if (!(off2 > JacobiTol<Real>::rel2 * scale2)) break;
+        jacobi_rot<Real, 0, 1>(dg, o, V);
+        jacobi_rot<Real, 0, 2>(dg, o, V);
+        jacobi_rot<Real, 1, 2>(dg, o, V);
+    }
+    // T as a full Hermitian matrix
+    const Real t3 = -(t[0] + t[1]);
+    const cx<Real> T[3][3] = {{mk(t[0], Real(0)), mk(t[2], t[3]), mk(t[4], t[5])},
+                              {mk(t[2], -t[3]), mk(t[1], Real(0)), mk(t[6], t[7])},
+                              {mk(t[4], -t[5]), mk(t[6], -t[7]), mk(t3, Real(0))}};
+    // W = T V
+    cx<Real> W[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) W[a][k] = T[a][0] * V[0][k] + T[a][1] * V[1][k] + T[a][2] * V[2][k];
+    // R = V^dagger W (Hermitian): diag real, upper entries
+    Real Rd[3];
+    cx<Real> Ro[3]; // (0,1), (0,2), (1,2)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        Rd[j] = V[0][j].r * W[0][j].r + V[0][j].i * W[0][j].i + V[1][j].r * W[1][j].r +
+                V[1][j].i * W[1][j].i + V[2][j].r * W[2][j].r + V[2][j].i * W[2][j].i;
+    Ro[0] = mulc(W[0][1], V[0][0]) + mulc(W[1][1], V[1][0]) + mulc(W[2][1], V[2][0]);
+    Ro[1] = mulc(W[0][2], V[0][0]) + mulc(W[1][2], V[1][0]) + mulc(W[2][2], V[2][0]);
+    Ro[2] = mulc(W[0][2], V[0][1]) + mulc(W[1][2], V[1][1]) + mulc(W[2][2], V[2][1]);
+    // phases exp(-i (lam_j - lam_k) dl) on the upper entries
+    {
+        Real s, c;
+        phase_sincos<Real>((double)(dg[0] - dg[1]) * dl, &s, &c);
+        Ro[0] = Ro[0] * mk(c, -s);
+        phase_sincos<Real>((double)(dg[0] - dg[2]) * dl, &s, &c);
+        Ro[1] = Ro[1] * mk(c, -s);
+        phase_sincos<Real>((double)(dg[1] - dg[2]) * dl, &s, &c);
+        Ro[2] = Ro[2] * mk(c, -s);
+    }
+    const cx<Real> Rm[3][3] = {{mk(Rd[0], Real(0)), Ro[0], Ro[1]},
+                               {cj(Ro[0]), mk(Rd[1], Real(0)), Ro[2]},
+                               {cj(Ro[1]), cj(Ro[2]), mk(Rd[2], Real(0))}};
+    // Z = V R', T' = Z V^dagger
+    cx<Real> Z[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Z[a][k] = V[a][0] * Rm[0][k] + V[a][1] * Rm[1][k] + V[a][2] * Rm[2][k];
+    Real o00 = Z[0][0].r * V[0][0].r + Z[0][0].i * V[0][0].i + Z[0][1].r * V[0][1].r +
+               Z[0][1].i * V[0][1].i + Z[0][2].r * V[0][2].r + Z[0][2].i * V[0][2].i;
+    Real o11 = Z[1][0].r * V[1][0].r + Z[1][0].i * V[1][0].i + Z[1][1].r * V[1][1].r +
+               Z[1][1].i * V[1][1].i + Z[1][2].r * V[1][2].r + Z[1][2].i * V[1][2].i;
+    cx<Real> o01 = mulc(Z[0][0], V[1][0]) + mulc(Z[0][1], V[1][1]) + mulc(Z[0][2], V[1][2]);
+    cx<Real> o02 = mulc(Z[0][0], V[2][0]) + mulc(Z[0][1], V[2][1]) + mulc(Z[0][2], V[2][2]);
+    cx<Real> o12 = mulc(Z[1][0], V[2][0]) + mulc(Z[1][1], V[2][1]) + mulc(Z[1][2], V[2][2]);
+    // keep the result exactly traceless in the packed form: t3 is implied
+    out[0] = o00;
+    out[1] = o11;
+    out[2] = o01.r;
+    out[3] = o01.i;
+    out[4] = o02.r;
+    out[5] = o02.i;
+    out[6] = o12.r;
+    out[7] = o12.i;
+}
+
+// ---------------------------------------------------------------- dispatch
+template <int NF, typename Real>
+__host__ __device__ __forceinline__ void comm(const Real *h, const Real *t, Real *d)
+{
+    if constexpr (NF == 2) comm2<Real>(h, t, d);
+    else comm3<Real>(h, t, d);
+}
+template <int NF, typename Real>
+__host__ __device__ __forceinline__ void prop(const Real *h, double dl, const Real *t, Real *out)
+{
+    if constexpr (NF == 2) prop2<Real>(h, dl, t, out);
+    else prop3<Real>(h, dl, t, out);
+}
+
+// Traceless components of rho_nu - conj(rho_nubar): conjugation flips the
+// sign of every imaginary part.
+template <int NF, typename Real>
+__host__ __device__ __forceinline__ void nu_minus_conj_nubar(const Real *tn, const Real *tb, Real *d)
+{
+    if constexpr (NF == 2) {
+        d[0] = tn[0] - tb[0];
+        d[1] = tn[1] - tb[1];
+        d[2] = tn[2] + tb[2];
+    } else {
+        d[0] = tn[0] - tb[0];
+        d[1] = tn[1] - tb[1];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            d[2 + 2 * k] = tn[2 + 2 * k] - tb[2 + 2 * k];
+            d[3 + 2 * k] = tn[3 + 2 * k] + tb[3 + 2 * k];
+        }
+    }
+}
+
+// Hamiltonians of the two species of one (u, E) pair (traceless comps):
+//   H_nu = H_vac + A P_e + G,   H_nubar = H_vac - A P_e - conj(G)
+// P_e = diag(1, 0[, 0]) has traceless part (1/2)(1,-1) or (2/3, -1/3, -1/3).
+template <int NF, typename Real>
+__host__ __device__ __forceinline__ void hamiltonians(const Real *hv, Real A, const Real *g, Real *hn, Real *hb)
+{
+    constexpr int S = Comp<NF>::S;
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        hn[k] = hv[k] + g[k];
+        hb[k] = hv[k] - g[k];
+    }
+    if constexpr (NF == 2) {
+        hb[2] = hv[2] + g[2];
+        hn[0] += Real(0.5) * A;
+        hb[0] -= Real(0.5) * A;
+    } else {
+        hb[3] = hv[3] + g[3];
+        hb[5] = hv[5] + g[5];
+        hb[7] = hv[7] + g[7];
+        const Real a1 = A * Real(2) / Real(3), a2 = A / Real(3);
+        hn[0] += a1;
+        hn[1] -= a2;
+        hb[0] -= a1;
+        hb[1] += a2;
+    }
+}
+
+} // namespace xf

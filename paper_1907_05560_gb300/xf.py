@@ -1,0 +1,263 @@
+"""Thin ctypes binding of libxf.so (include/xf.h): argument marshalling only.
+
+Every step of the integration runs in the library's CUDA kernels.  PyTorch is
+used only for device memory (its caching allocator, through the allocator
+hook) and streams.  Loading fails loudly if libxf.so has not been built or no
+GPU is usable: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs as I
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libxf.so")
+
+XF_OK = 0
+XF_PENDING = 1
+STATUS = {0: "XF_OK", 1: "XF_PENDING", -1: "XF_E_ARG", -2: "XF_E_STATE", -3: "XF_E_NOMEM",
+          -4: "XF_E_CUDA", -5: "XF_E_NONFINITE", -6: "XF_E_BARRIER_TIMEOUT", -7: "XF_E_UNSTABLE",
+          -8: "XF_E_BUSY", -9: "XF_E_TOO_BIG", -10: "XF_E_NOTFOUND", -11: "XF_E_TIMEOUT",
+          -12: "XF_E_UNSUPPORTED"}
+STATUS_CODE = {v: k for k, v in STATUS.items()}
+
+
+class XFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+class XFParams(ctypes.Structure):
+    _fields_ = [
+        ("size", ctypes.c_uint32), ("version", ctypes.c_uint32),
+        ("stepper", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("geometry", ctypes.c_int32), ("hierarchy", ctypes.c_int32),
+        ("matter", ctypes.c_int32), ("strict", ctypes.c_int32),
+        ("R_nu_km", ctypes.c_double), ("mu0_per_km", ctypes.c_double),
+        ("E_min_MeV", ctypes.c_double), ("E_max_MeV", ctypes.c_double),
+        ("dm2_eV2", ctypes.c_double * 2), ("theta", ctypes.c_double * 3),
+        ("ne_ref_cm3", ctypes.c_double), ("r_ref_km", ctypes.c_double), ("ne_power", ctypes.c_double),
+        ("nb0_cm3", ctypes.c_double), ("h_ns_km", ctypes.c_double), ("Ye", ctypes.c_double),
+        ("T_MeV", ctypes.c_double * 4), ("eta", ctypes.c_double * 4), ("L", ctypes.c_double * 4),
+        ("eps_perturb", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class XFAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
+
+
+# every symbol include/xf.h declares, with its ctypes signature
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "xf_params_default": (None, [ctypes.POINTER(XFParams)]),
+    "xf_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(XFParams),
+                                 ctypes.POINTER(_P)]),
+    "xf_create_ex": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(XFParams),
+                                    ctypes.POINTER(XFAllocator), ctypes.POINTER(_P)]),
+    "xf_destroy": (ctypes.c_int, [_P]),
+    "xf_set_stream": (ctypes.c_int, [_P, _P]),
+    "xf_set_state": (ctypes.c_int, [_P, _D, ctypes.c_size_t, ctypes.c_double]),
+    "xf_init_state": (ctypes.c_int, [_P, ctypes.c_double]),
+    "xf_step": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double]),
+    "xf_step_async": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double]),
+    "xf_sync": (ctypes.c_int, [_P]),
+    "xf_get_state": (ctypes.c_int, [_P, _D, ctypes.c_size_t, _D, ctypes.POINTER(ctypes.c_int64)]),
+    "xf_moments": (ctypes.c_int, [_P, _D, _D, ctypes.c_size_t]),
+    "xf_outputs": (ctypes.c_int, [_P, _D, _D, _D, ctypes.c_size_t]),
+    "xf_tables": (ctypes.c_int, [_P, _D, _D]),
+    "xf_launch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "xf_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
+    "xf_peak": (ctypes.c_int, [ctypes.c_int, _D]),
+    "xf_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "xf_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libxf.so and bind every entry point (no GPU needed to load)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(nvcc for sm_103a); there is no CPU fallback")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def params_from(p: I.Problem) -> XFParams:
+    L = load()
+    x = XFParams()
+    L.xf_params_default(ctypes.byref(x))
+    x.stepper, x.precision, x.geometry = p.stepper, p.precision, p.geometry
+    x.hierarchy, x.matter = p.hierarchy, p.matter
+    x.R_nu_km, x.mu0_per_km, x.E_min_MeV, x.E_max_MeV = p.R_nu, p.mu0, p.E_min, p.E_max
+    x.dm2_eV2[:] = list(p.dm2)
+    x.theta[:] = list(p.theta)
+    x.ne_ref_cm3, x.r_ref_km, x.ne_power = p.ne_ref, p.r_ref, p.ne_power
+    x.nb0_cm3, x.h_ns_km, x.Ye = p.nb0, p.h_ns, p.Ye
+    x.T_MeV[:] = list(p.T)
+    x.eta[:] = list(p.eta)
+    x.L[:] = list(p.L)
+    x.eps_perturb, x.seed = p.eps, p.seed
+    return x
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations to PyTorch's caching allocator."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.dev = torch.cuda.current_device()
+        self._alloc = ALLOC_FN(self._a)
+        self._free = FREE_FN(self._f)
+        self.struct = XFAllocator(self._alloc, self._free, None)
+
+    def _a(self, nbytes, user):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.dev)
+        except Exception:
+            return None
+
+    def _f(self, ptr, user):
+        self.torch.cuda.caching_allocator_delete(ptr)
+
+
+class Context:
+    """One flavor-evolution problem resident on the GPU (xf_ctx)."""
+
+    def __init__(self, problem: I.Problem, allocator: str = "torch", stream=None):
+        self.L = load()
+        self.problem = problem
+        self.n_f = problem.n_f
+        self.n_bins = 2 * problem.n_u * problem.n_E
+        self.n_doubles = self.n_bins * self.n_f * self.n_f
+        prm = params_from(problem)
+        h = _P()
+        self._allocator = None
+        if allocator == "torch":
+            self._allocator = _TorchAllocator()
+            rc = self.L.xf_create_ex(problem.n_E, problem.n_u, problem.n_f, ctypes.byref(prm),
+                                     ctypes.byref(self._allocator.struct), ctypes.byref(h))
+        else:
+            rc = self.L.xf_create(problem.n_E, problem.n_u, problem.n_f, ctypes.byref(prm),
+                                  ctypes.byref(h))
+        if rc != XF_OK:
+            raise XFError(rc, self.L.xf_last_error(None).decode())
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- helpers
+    def _check(self, rc: int):
+        if rc != XF_OK:
+            raise XFError(rc, self.L.xf_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.xf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- API
+    def set_stream(self, stream):
+        ptr = stream if isinstance(stream, int) else int(getattr(stream, "cuda_stream", 0))
+        return self._check(self.L.xf_set_stream(self.h, _P(ptr)))
+
+    def set_state(self, rho: np.ndarray, r_km: float):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        return self._check(self.L.xf_set_state(self.h, _dp(rho), rho.size, float(r_km)))
+
+    def init_state(self, r_km: float):
+        return self._check(self.L.xf_init_state(self.h, float(r_km)))
+
+    def step(self, n_steps: int, dr_km: float):
+        return self._check(self.L.xf_step(self.h, int(n_steps), float(dr_km)))
+
+    def step_async(self, n_steps: int, dr_km: float):
+        return self._check(self.L.xf_step_async(self.h, int(n_steps), float(dr_km)))
+
+    def sync(self):
+        return self._check(self.L.xf_sync(self.h))
+
+    def get_state(self, out: np.ndarray | None = None):
+        rho = out if out is not None else np.empty(self.n_doubles)
+        r = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        self._check(self.L.xf_get_state(self.h, _dp(rho), rho.size, ctypes.byref(r), ctypes.byref(n)))
+        return rho, r.value, n.value
+
+    def moments(self):
+        m = self.n_f * self.n_f
+        M0, M1 = np.empty(m), np.empty(m)
+        self._check(self.L.xf_moments(self.h, _dp(M0), _dp(M1), m))
+        return M0, M1
+
+    def outputs(self):
+        p, t, q = np.empty(self.n_bins), np.empty(self.n_bins), np.empty(self.n_bins)
+        self._check(self.L.xf_outputs(self.h, _dp(p), _dp(t), _dp(q), self.n_bins))
+        return p, t, q
+
+    def tables(self):
+        E = np.empty(self.problem.n_E)
+        phi = np.empty(4 * self.problem.n_E)
+        self._check(self.L.xf_tables(self.h, _dp(E), _dp(phi)))
+        return E, phi.reshape(4, -1)
+
+    def set_option(self, option: int, value: int):
+        return self._check(self.L.xf_set_option(self.h, int(option), int(value)))
+
+    def launch_info(self):
+        g, t, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.L.xf_launch_info(self.h, ctypes.byref(g), ctypes.byref(t), ctypes.byref(b)))
+        return g.value, t.value, b.value
+
+
+OPT_GRID, OPT_BARRIER_TIMEOUT_NS, OPT_TEST_SKIP_ARRIVAL = 1, 2, 3
+
+
+PEAK_FP64_FMA, PEAK_FP32_FMA = 0, 1
+
+
+def peak(which: int) -> float:
+    """Measured FMA throughput (FLOP/s) of the current device."""
+    v = ctypes.c_double(0.0)
+    rc = load().xf_peak(int(which), ctypes.byref(v))
+    if rc != XF_OK:
+        raise XFError(rc, "xf_peak failed")
+    return v.value
+
+
+def status_str(code: int) -> str:
+    return load().xf_status_str(code).decode()
