@@ -219,6 +219,41 @@ int xf_set_option(xf_ctx *ctx, int option, int64_t value);
 enum xf_peak_kind { XF_PEAK_FP64_FMA = 0, XF_PEAK_FP32_FMA = 1 };
 int xf_peak(int which, double *value);
 
+/* ---- stepping without allocation -----------------------------------------
+ * Some callers cannot allocate device memory when they want to step a
+ * problem: code that runs inside a memory pool owning the whole device
+ * budget, plug-ins whose host application forbids allocation on its hot
+ * path, and latency-bound loops where cudaMalloc's implicit synchronisation
+ * is not acceptable.  xf_step_noalloc serves them.  It has no counterpart in
+ * the paper: it is the xf_step integration (same kernels, same equations),
+ * packaged so that the call allocates nothing.
+ *
+ * The caller passes the state in its own device memory: rho_dev holds
+ * 2 * n_u * n_E * n_flavor^2 doubles in the packed layout above, is read as
+ * the state at radius r_km (>= R_nu) and overwritten with the state after
+ * n_steps steps of dr_km (on XF_E_NONFINITE: the last finite state).  All
+ * working memory (component-major state buffers, the per-energy table, the
+ * CTA partial moments, the barrier, error and step words) lives in one
+ * file-scope device array of XF_NOALLOC_SCRATCH_BYTES that every GPU loading
+ * libxf.so holds until the process exits.  The call makes no cudaMalloc,
+ * cudaFree or other allocating call.  Precisions XF_FP64 and XF_FP32_M64.
+ *
+ *   - XF_E_TOO_BIG: the problem's working set (about 2(n_f^2-1) x 3 x
+ *     sizeof(Real) + 16 bytes per (angle, energy) pair, plus small tables)
+ *     exceeds XF_NOALLOC_SCRATCH_BYTES; nothing was run.
+ *   - The call is synchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).
+ *   - Every call shares the array and it keeps the previous call's contents;
+ *     each call clears the words that must start at zero and rewrites the
+ *     state buffers from rho_dev.  Calls whose GPU work overlaps (several
+ *     host threads or streams at once) race on the array: serialise them.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture. */
+#define XF_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int xf_step_noalloc(int n_E, int n_u, int n_flavor, const xf_params *p, double *rho_dev, double r_km,
+                    int64_t n_steps, double dr_km, void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *xf_status_str(int status);
 /* Message of the last failure on ctx (static per-ctx storage; "" if none).

@@ -81,6 +81,8 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_int)]),
     "xf_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     "xf_peak": (ctypes.c_int, [ctypes.c_int, _D]),
+    "xf_step_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(XFParams),
+                                       _P, ctypes.c_double, ctypes.c_int64, ctypes.c_double, _P]),
     "xf_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "xf_last_error": (ctypes.c_char_p, [_P]),
 }
