@@ -197,11 +197,48 @@ int xf_tables(xf_ctx *ctx, double *E, double *phi);
  * (RK4: 4, EXPH: 2) and the device grid size used. */
 int xf_launch_info(xf_ctx *ctx, int *ctas, int *threads, int *barriers_per_step);
 
+/* ---- batches: many problems in one persistent launch ----------------------
+ * A batch ctx holds several independent problems (sizes, flavors, couplings,
+ * hierarchies and spectra may all differ; stepper and precision are shared)
+ * and advances them together: one cooperative launch per call tiles every
+ * problem into runs of (angle, energy) pairs, and each problem's moments are
+ * summed from its own tiles only, so a problem's result does not depend on
+ * what it is packed with (bitwise, for equal tile size and precision).
+ * The single-problem calls above act on problem 0 of a batch. */
+typedef struct xf_problem {
+    int32_t n_E, n_u, n_flavor, reserved; /* reserved: set to 0 */
+    xf_params params;
+} xf_problem;
+
+/* Create a batch of n_problems >= 1 problems (validated as xf_create does;
+ * XF_E_ARG if steppers or precisions differ).  All states start undefined. */
+int xf_create_batch(int n_problems, const xf_problem *problems, const xf_allocator *alloc, xf_ctx **out);
+int xf_batch_size(xf_ctx *ctx, int *n_problems);
+/* Per-problem state I/O (layouts and rules as the single-problem calls);
+ * xf_batch_init_state with inst = -1 initialises every problem. */
+int xf_batch_set_state(xf_ctx *ctx, int inst, const double *rho, size_t n_doubles, double r_km);
+int xf_batch_init_state(xf_ctx *ctx, int inst, double r_km);
+int xf_batch_get_state(xf_ctx *ctx, int inst, double *rho, size_t n_doubles, double *r_km, int64_t *steps_done);
+int xf_batch_outputs(xf_ctx *ctx, int inst, double *p_surv, double *trace, double *purity, size_t n_bins);
+/* Advance every problem by n_steps steps; dr_km holds one step size per
+ * problem (NULL: each keeps its previous one).  Synchronous.  A problem whose
+ * moments turn non-finite stops at its last finite state while the others
+ * continue: xf_batch_status tells which (status XF_OK / XF_E_NONFINITE /
+ * XF_E_STATE), how many steps each took and its radius. */
+int xf_batch_step(xf_ctx *ctx, int64_t n_steps, const double *dr_km);
+int xf_batch_status(xf_ctx *ctx, int inst, int *status, int64_t *steps_done, double *r_km);
+
 /* Options (xf_set_option), for tuning and testing:
  *   XF_OPT_GRID: persistent grid size in CTAs; 0 = automatic (default).  The
- *     value is clamped to the co-resident maximum and to the pair count.
- *     The reduction tree follows the grid, so results can differ from the
- *     automatic shape by rounding.
+ *     value is clamped to the co-resident maximum and to the tile count.
+ *   XF_OPT_TILE_PAIRS: tile size in (angle, energy) pairs, rounded up to a
+ *     multiple of 32; 0 = automatic (one problem: one tile per co-resident
+ *     CTA slot; several problems: about 8 tiles per slot).  Each problem's
+ *     reduction tree follows its tiles, so a different tile size can change
+ *     results by rounding; equal tile sizes give bitwise equal results.
+ *   XF_OPT_GRAPH: 1 = capture the launch sequence of a step call into a CUDA
+ *     graph on first use and replay it afterwards (re-captured when the
+ *     step count per launch or the tiling changes); 0 = plain launches.
  *   XF_OPT_BARRIER_TIMEOUT_NS: time limit of one grid-barrier wait
  *     (default 2e9 ns).  On expiry every CTA leaves and the call returns
  *     XF_E_BARRIER_TIMEOUT.
@@ -209,7 +246,13 @@ int xf_launch_info(xf_ctx *ctx, int *ctas, int *threads, int *barriers_per_step)
  *     at its first grid barrier without arriving, so the other CTAs' bounded
  *     wait runs out.  -1 (default) disables it.  Exercises the timeout path
  *     without faulting or hanging the GPU. */
-enum xf_option { XF_OPT_GRID = 1, XF_OPT_BARRIER_TIMEOUT_NS = 2, XF_OPT_TEST_SKIP_ARRIVAL = 3 };
+enum xf_option {
+    XF_OPT_GRID = 1,
+    XF_OPT_BARRIER_TIMEOUT_NS = 2,
+    XF_OPT_TEST_SKIP_ARRIVAL = 3,
+    XF_OPT_TILE_PAIRS = 4,
+    XF_OPT_GRAPH = 5
+};
 int xf_set_option(xf_ctx *ctx, int option, int64_t value);
 
 /* Measured ALU peaks of the current device, for roofline denominators:

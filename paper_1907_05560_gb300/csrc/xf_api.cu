@@ -1,6 +1,7 @@
 // xf_api.cu -- host side of the C ABI declared in include/xf.h: argument
 // validation, per-energy tables (FP64, on the host), device memory, layout
-// conversion and the launches of the persistent integrator.
+// conversion, tiling of one or many problems onto the persistent grid, and
+// the launches of the integrator (optionally replayed from a CUDA graph).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,58 +61,67 @@ double fermi_dirac(int k, double eta)
 
 thread_local std::string g_create_error;
 
-// One enqueued launch: steps k0 .. k0 + n - 1 of the run r0 + k h.
-struct Pending {
-    double r0, h;
-    long long k0, n;
+// Host record of one problem of a pack.
+struct InstHost {
+    int n_E = 0, n_u = 0, nf = 0, S = 0, n_pairs = 0, npad = 0;
+    long long n_bins = 0;
+    xf_params p{};
+    std::vector<double> E, phi, hvac; // tables: E[n_E], phi[4][n_E], hvac[n_E][S]
+    long long state_off = 0;          // Real elements into the state arenas
+    long long trace_off = 0;          // doubles into the trace arena (2 npad)
+    long long phi_off = 0;            // doubles into the phi arena (4 n_E)
+    int hvac_off = 0;                 // Real elements into the table arena
+    int tile_begin = 0, tile_end = 0;
+    // position (host view, valid after a sync): r = r0 + k0 h
+    bool state_valid = false;
+    double r0 = 0.0, h = 0.0;
+    long long k0 = 0, steps = 0;
+    int cur = 0, err = 0;
 };
 
 } // namespace
 
 struct xf_ctx {
-    int n_E = 0, n_u = 0, nf = 0, S = 0, n_pairs = 0, npad = 0;
-    long long n_bins = 0;
-    xf_params p{};
-    int real_bytes = 8;
+    std::vector<InstHost> in;
+    int real_bytes = 8, stepper = XF_RK4, nfm = 2;
     cudaStream_t stream = nullptr;
     xf_allocator alloc{};
     bool has_alloc = false;
     int device = 0, num_sms = 0;
 
-    std::vector<double> E, phi, hvac; // host tables (phi [4][n_E], hvac [n_E][S])
-
-    // device memory
+    // arenas
     void *rho[2] = {nullptr, nullptr};
-    void *aux = nullptr;
-    void *hvac_d = nullptr;
+    void *aux = nullptr, *hvac_d = nullptr;
     double *trace = nullptr, *phi_d = nullptr, *staging = nullptr;
-    double *partials = nullptr, *mom_out = nullptr, *mom_part = nullptr, *mom_full = nullptr;
-    unsigned *bar = nullptr;
-    int *err = nullptr, *bad = nullptr;
-    unsigned long long *steps = nullptr;
+    size_t staging_doubles = 0;
     std::vector<void *> owned;
 
-    // launch shape
+    // tiling and launch shape
     RunKernel kern{nullptr, 0};
-    int G = 1, pairs_per_cta = 0, span_max = 1;
+    std::vector<Tile> tiles;
+    std::vector<int> cta_tiles;
+    int G = 1, tile_pairs = 0, span_max = 1, max_tiles = 0;
     size_t smem = 0;
-    int mom_G = 1, mom_chunk = 0;
+    Tile *tiles_d = nullptr;
+    int *cta_tiles_d = nullptr;
+    Inst *inst_d = nullptr;
+    InstPos *pos_d = nullptr;
+    double *partials = nullptr, *mom_out = nullptr, *mom_part = nullptr, *mom_full = nullptr;
+    int mom_part_slots = 0;
+    unsigned *bar = nullptr;
+    int *err = nullptr, *bad = nullptr;
 
-    // run state.  Radii follow r = r_base + k h with k counted from the last
-    // change of h, so a run split into several calls takes the same radii as
-    // one call.  The "pred" fields anticipate the enqueued launches.
-    bool state_valid = false;
-    int cur = 0;                   // buffer of the current state (after sync)
-    double r = 0.0;                // radius of the current state (after sync)
-    long long steps_total = 0;
-    double r_base = 0.0, h_base = 0.0;
-    long long k_base = 0;
-    int pred_cur = 0;
-    double pred_r_base = 0.0, pred_h = 0.0;
-    long long pred_k_base = 0;
-    std::vector<Pending> pending;
+    // options
+    int grid_request = 0, tile_request = 0, skip_cta = -1, use_graph = 0;
     unsigned long long timeout_ns = 2000000000ull;
-    int grid_request = 0, skip_cta = -1;
+
+    // launches since the last sync; graph of one step launch, captured and
+    // replayed on a private stream ordered after / before the ctx stream
+    int pending = 0;
+    cudaGraphExec_t graph = nullptr;
+    long long graph_steps = 0;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
     std::string last_error;
 };
@@ -132,7 +142,7 @@ int fail(xf_ctx *c, int code, const char *fmt, ...)
 
 int cuda_fail(xf_ctx *c, cudaError_t e, const char *what)
 {
-    cudaGetLastError(); // clear the sticky-free error state
+    cudaGetLastError(); // clear the non-sticky error state
     if (e == cudaErrorMemoryAllocation) return fail(c, XF_E_NOMEM, "%s: %s", what, cudaGetErrorString(e));
     return fail(c, XF_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
@@ -159,6 +169,13 @@ void *dev_alloc(xf_ctx *c, size_t bytes)
 
 void free_all(xf_ctx *c)
 {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    c->gstream = nullptr;
+    c->ev_in = c->ev_out = nullptr;
     for (void *p : c->owned) {
         if (c->has_alloc) c->alloc.free(p, c->alloc.user);
         else cudaFree(p);
@@ -168,74 +185,72 @@ void free_all(xf_ctx *c)
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
-int validate(const xf_params *p, int n_E, int n_u, int nf)
+int validate(xf_ctx *c, const xf_params *p, int n_E, int n_u, int nf)
 {
-    if (!p) return fail(nullptr, XF_E_ARG, "params is NULL");
-    if (p->size != sizeof(xf_params)) return fail(nullptr, XF_E_ARG, "params.size %u != %zu", p->size, sizeof(xf_params));
-    if (p->version != XF_PARAMS_VERSION) return fail(nullptr, XF_E_ARG, "params.version %u unsupported", p->version);
-    if (n_E <= 0 || n_u <= 0) return fail(nullptr, XF_E_ARG, "n_E and n_u must be positive (got %d, %d)", n_E, n_u);
-    if (nf != 2 && nf != 3) return fail(nullptr, XF_E_ARG, "n_flavor must be 2 or 3 (got %d)", nf);
-    if ((long long)n_E * n_u > (long long)(INT_MAX / 16)) return fail(nullptr, XF_E_ARG, "n_E * n_u too large");
-    if (p->stepper != XF_RK4 && p->stepper != XF_EXPH) return fail(nullptr, XF_E_ARG, "bad stepper %d", p->stepper);
+    if (!p) return fail(c, XF_E_ARG, "params is NULL");
+    if (p->size != sizeof(xf_params)) return fail(c, XF_E_ARG, "params.size %u != %zu", p->size, sizeof(xf_params));
+    if (p->version != XF_PARAMS_VERSION) return fail(c, XF_E_ARG, "params.version %u unsupported", p->version);
+    if (n_E <= 0 || n_u <= 0) return fail(c, XF_E_ARG, "n_E and n_u must be positive (got %d, %d)", n_E, n_u);
+    if (nf != 2 && nf != 3) return fail(c, XF_E_ARG, "n_flavor must be 2 or 3 (got %d)", nf);
+    if ((long long)n_E * n_u > (long long)(INT_MAX / 16)) return fail(c, XF_E_ARG, "n_E * n_u too large");
+    if (p->stepper != XF_RK4 && p->stepper != XF_EXPH) return fail(c, XF_E_ARG, "bad stepper %d", p->stepper);
     if (p->precision < XF_FP64 || p->precision > XF_FP32_M64_RENORM)
-        return fail(nullptr, XF_E_ARG, "bad precision %d", p->precision);
+        return fail(c, XF_E_ARG, "bad precision %d", p->precision);
     if (p->precision == XF_FP32_COMP || p->precision == XF_FP32_M64_RENORM)
-        return fail(nullptr, XF_E_UNSUPPORTED, "precision %d not built", p->precision);
-    if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CONST)
-        return fail(nullptr, XF_E_ARG, "bad geometry %d", p->geometry);
-    if (p->geometry == XF_GEOM_SINGLE_ANGLE && n_u != 1)
-        return fail(nullptr, XF_E_ARG, "single-angle geometry needs n_u == 1");
-    if (p->hierarchy != 1 && p->hierarchy != -1) return fail(nullptr, XF_E_ARG, "hierarchy must be +1 or -1");
-    if (p->matter < XF_MATTER_NONE || p->matter > XF_MATTER_EXP) return fail(nullptr, XF_E_ARG, "bad matter %d", p->matter);
-    if (!finite_pos(p->R_nu_km)) return fail(nullptr, XF_E_ARG, "R_nu_km must be finite and > 0");
-    if (!std::isfinite(p->mu0_per_km) || p->mu0_per_km < 0) return fail(nullptr, XF_E_ARG, "mu0 must be finite and >= 0");
+        return fail(c, XF_E_UNSUPPORTED, "precision %d not built", p->precision);
+    if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CONST) return fail(c, XF_E_ARG, "bad geometry %d", p->geometry);
+    if (p->geometry == XF_GEOM_SINGLE_ANGLE && n_u != 1) return fail(c, XF_E_ARG, "single-angle geometry needs n_u == 1");
+    if (p->hierarchy != 1 && p->hierarchy != -1) return fail(c, XF_E_ARG, "hierarchy must be +1 or -1");
+    if (p->matter < XF_MATTER_NONE || p->matter > XF_MATTER_EXP) return fail(c, XF_E_ARG, "bad matter %d", p->matter);
+    if (!finite_pos(p->R_nu_km)) return fail(c, XF_E_ARG, "R_nu_km must be finite and > 0");
+    if (!std::isfinite(p->mu0_per_km) || p->mu0_per_km < 0) return fail(c, XF_E_ARG, "mu0 must be finite and >= 0");
     if (!std::isfinite(p->E_min_MeV) || p->E_min_MeV < 0 || !std::isfinite(p->E_max_MeV) || p->E_max_MeV <= p->E_min_MeV)
-        return fail(nullptr, XF_E_ARG, "need 0 <= E_min < E_max, finite");
+        return fail(c, XF_E_ARG, "need 0 <= E_min < E_max, finite");
     for (int i = 0; i < 2; ++i)
-        if (!std::isfinite(p->dm2_eV2[i])) return fail(nullptr, XF_E_ARG, "dm2 not finite");
+        if (!std::isfinite(p->dm2_eV2[i])) return fail(c, XF_E_ARG, "dm2 not finite");
     for (int i = 0; i < 3; ++i)
-        if (!std::isfinite(p->theta[i])) return fail(nullptr, XF_E_ARG, "theta not finite");
+        if (!std::isfinite(p->theta[i])) return fail(c, XF_E_ARG, "theta not finite");
     for (int a = 0; a < 4; ++a)
         if (!finite_pos(p->T_MeV[a]) || !std::isfinite(p->eta[a]) || !finite_pos(p->L[a]))
-            return fail(nullptr, XF_E_ARG, "spectrum parameters of species %d invalid", a);
-    if (!std::isfinite(p->eps_perturb) || p->eps_perturb < 0) return fail(nullptr, XF_E_ARG, "eps must be finite and >= 0");
+            return fail(c, XF_E_ARG, "spectrum parameters of species %d invalid", a);
+    if (!std::isfinite(p->eps_perturb) || p->eps_perturb < 0) return fail(c, XF_E_ARG, "eps must be finite and >= 0");
     if (p->matter == XF_MATTER_POWER &&
         (!std::isfinite(p->ne_ref_cm3) || p->ne_ref_cm3 < 0 || !finite_pos(p->r_ref_km) || !std::isfinite(p->ne_power)))
-        return fail(nullptr, XF_E_ARG, "power-law matter parameters invalid");
+        return fail(c, XF_E_ARG, "power-law matter parameters invalid");
     if (p->matter == XF_MATTER_EXP &&
         (!std::isfinite(p->nb0_cm3) || p->nb0_cm3 < 0 || !finite_pos(p->h_ns_km) || !std::isfinite(p->Ye)))
-        return fail(nullptr, XF_E_ARG, "exponential matter parameters invalid");
+        return fail(c, XF_E_ARG, "exponential matter parameters invalid");
     return XF_OK;
 }
 
 // Host tables: energy grid, number-flux weights phi_a(E) (Eq. 4.1-4.2),
 // traceless vacuum Hamiltonian per energy bin (Eq. 3.5-3.6; 3 flavors in the
 // mass basis with the standard mixing matrix, delta_CP = 0).
-void build_tables(xf_ctx *c)
+void build_tables(InstHost &c)
 {
-    const xf_params &p = c->p;
-    const double dE = (p.E_max_MeV - p.E_min_MeV) / c->n_E;
-    c->E.resize(c->n_E);
-    for (int e = 0; e < c->n_E; ++e) c->E[e] = p.E_min_MeV + (e + 0.5) * dE;
-    c->phi.assign(4 * (size_t)c->n_E, 0.0);
+    const xf_params &p = c.p;
+    const double dE = (p.E_max_MeV - p.E_min_MeV) / c.n_E;
+    c.E.resize(c.n_E);
+    for (int e = 0; e < c.n_E; ++e) c.E[e] = p.E_min_MeV + (e + 0.5) * dE;
+    c.phi.assign(4 * (size_t)c.n_E, 0.0);
     double flux_ref = 0.0;
     for (int a = 0; a < 4; ++a) {
         const double F2 = fermi_dirac(2, p.eta[a]), F3 = fermi_dirac(3, p.eta[a]);
         const double T = p.T_MeV[a];
         const double flux = p.L[a] / (T * F3 / F2); // L / <E>
         if (a == 0) flux_ref = flux;
-        for (int e = 0; e < c->n_E; ++e) {
-            const double E = c->E[e];
+        for (int e = 0; e < c.n_E; ++e) {
+            const double E = c.E[e];
             const double f = E * E / (F2 * T * T * T * (std::exp(E / T - p.eta[a]) + 1.0));
-            c->phi[(size_t)a * c->n_E + e] = flux / flux_ref * f;
+            c.phi[(size_t)a * c.n_E + e] = flux / flux_ref * f;
         }
     }
     const double K = vac_coefficient();
-    c->hvac.assign((size_t)c->n_E * c->S, 0.0);
-    for (int e = 0; e < c->n_E; ++e) {
-        double *h = &c->hvac[(size_t)e * c->S];
-        if (c->nf == 2) {
-            const double Delta = K * p.hierarchy * p.dm2_eV2[0] / c->E[e];
+    c.hvac.assign((size_t)c.n_E * c.S, 0.0);
+    for (int e = 0; e < c.n_E; ++e) {
+        double *h = &c.hvac[(size_t)e * c.S];
+        if (c.nf == 2) {
+            const double Delta = K * p.hierarchy * p.dm2_eV2[0] / c.E[e];
             h[0] = -0.5 * Delta * std::cos(2.0 * p.theta[0]);
             h[1] = 0.5 * Delta * std::sin(2.0 * p.theta[0]);
             h[2] = 0.0;
@@ -252,7 +267,7 @@ void build_tables(xf_ctx *c)
                 for (int j = 0; j < 3; ++j) {
                     double s = 0.0;
                     for (int k = 0; k < 3; ++k) s += U[i][k] * m2[k] * U[j][k];
-                    H[i][j] = K / c->E[e] * s;
+                    H[i][j] = K / c.E[e] * s;
                 }
             const double tau = (H[0][0] + H[1][1] + H[2][2]) / 3.0;
             h[0] = H[0][0] - tau;
@@ -267,187 +282,613 @@ void build_tables(xf_ctx *c)
     }
 }
 
-LayoutArgs layout_args(xf_ctx *c)
+LayoutArgs layout_args(xf_ctx *c, const InstHost &in)
 {
     LayoutArgs a;
-    a.n_E = c->n_E;
-    a.n_u = c->n_u;
-    a.n_pairs = c->n_pairs;
-    a.npad = c->npad;
-    a.phi = c->phi_d;
-    a.eps = c->p.eps_perturb;
-    a.seed = c->p.seed;
+    a.n_E = in.n_E;
+    a.n_u = in.n_u;
+    a.n_pairs = in.n_pairs;
+    a.npad = in.npad;
+    a.phi = c->phi_d + in.phi_off;
+    a.eps = in.p.eps_perturb;
+    a.seed = in.p.seed;
     a.bad = c->bad;
     return a;
 }
 
-int elementwise_grid(xf_ctx *c)
+int elementwise_grid(xf_ctx *c, const InstHost &in)
 {
-    long long nb = c->n_bins;
-    long long g = (nb + 255) / 256;
-    return (int)std::min<long long>(g, (long long)c->num_sms * 16);
+    long long g = (in.n_bins + 255) / 256;
+    return (int)std::max<long long>(1, std::min<long long>(g, (long long)c->num_sms * 16));
 }
 
-// Choose the persistent launch shape: CTAs co-resident (cooperative launch),
-// contiguous pair chunks per CTA, angle-table span for the dynamic smem.
+// Cost weight of a pair (relative work per stage): three flavors ~10x two.
+double pair_cost(const InstHost &in) { return in.nf == 3 ? 10.0 : 1.0; }
+
+// Tile every instance into runs of at most TP pairs, then give
+// each CTA a contiguous run of tiles of about equal cost.
 int plan_launch(xf_ctx *c)
 {
     const int nt = c->kern.nt;
-    auto span_for = [&](int chunk) {
-        // a chunk of `chunk` consecutive pairs touches at most this many angles
-        return std::min(c->n_u, (chunk + c->n_E - 1) / c->n_E + 1);
-    };
-    int occ = 0;
-    int G = 1;
-    for (int iter = 0; iter < 4; ++iter) {
-        int chunk = (c->n_pairs + G - 1) / G;
-        int span = span_for(chunk);
-        size_t smem = 5 * sizeof(double) * (size_t)std::max(span, 1);
-        if (smem > 48 * 1024) {
-            if (cudaFuncSetAttribute(c->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(c, XF_E_UNSUPPORTED, "angle table needs %zu bytes of shared memory", smem);
-            }
-        }
-        XF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->kern.fn, nt, smem), "occupancy");
-        if (occ < 1) return fail(c, XF_E_UNSUPPORTED, "kernel cannot be resident (smem %zu)", smem);
-        int gmax = occ * c->num_sms;
-        int want = (c->n_pairs + nt - 1) / nt;
-        if (c->n_pairs <= 8 * nt) want = 1; // small problems: one CTA, no grid barrier
-        if (c->grid_request > 0) want = std::min(c->grid_request, c->n_pairs);
-        int newG = std::max(1, std::min(gmax, want));
-        c->G = newG;
-        c->pairs_per_cta = (c->n_pairs + newG - 1) / newG;
-        c->span_max = span_for(c->pairs_per_cta);
-        c->smem = 5 * sizeof(double) * (size_t)std::max(c->span_max, 1);
-        if (newG == G && iter > 0) break;
-        G = newG;
+    int occ_free = 0;
+    XF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_free, c->kern.fn, nt, 0), "occupancy");
+    if (occ_free < 1) return fail(c, XF_E_UNSUPPORTED, "integrator kernel cannot be resident");
+    long long total_pairs = 0;
+    double total_cost = 0.0;
+    for (const InstHost &in : c->in) {
+        total_pairs += in.n_pairs;
+        total_cost += pair_cost(in) * in.n_pairs;
     }
-    // recheck residency with the final smem
-    XF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->kern.fn, nt, c->smem), "occupancy");
-    if (occ * c->num_sms < c->G) return fail(c, XF_E_UNSUPPORTED, "grid of %d CTAs not co-resident", c->G);
+    // tile size: one problem -> one tile per co-resident CTA slot (every CTA
+    // gets the same work); several problems -> about 8 tiles per slot, so that
+    // runs of unequal tiles balance.  A multiple of 32 (whole warps).
+    const long long slots = (long long)occ_free * c->num_sms;
+    long long tp = c->tile_request;
+    if (tp <= 0) {
+        const long long per = (c->in.size() == 1) ? slots : 8 * slots;
+        tp = (total_pairs + per - 1) / per;
+    }
+    tp = std::min<long long>(std::max<long long>((tp + 31) / 32 * 32, 32), 1 << 20);
+    const int TP = (int)tp;
+    c->tiles.clear();
+    for (size_t i = 0; i < c->in.size(); ++i) {
+        InstHost &in = c->in[i];
+        in.tile_begin = (int)c->tiles.size();
+        for (int p0 = 0; p0 < in.n_pairs; p0 += TP) c->tiles.push_back({(int)i, p0, std::min(TP, in.n_pairs - p0), 0});
+        in.tile_end = (int)c->tiles.size();
+    }
+    const int T = (int)c->tiles.size();
+    int span = 1;
+    for (const Tile &t : c->tiles) {
+        const InstHost &in = c->in[t.inst];
+        span = std::max(span, (t.p0 + t.np - 1) / in.n_E - t.p0 / in.n_E + 1);
+    }
+    // per-angle tables: 5 FP64 slots, or 6 FP32 slots (step length as hi + lo)
+    size_t smem = (c->real_bytes == 8 ? 5 * sizeof(double) : 6 * sizeof(float)) * (size_t)span;
+    smem = (smem + 15) & ~size_t(15);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(c->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, XF_E_UNSUPPORTED, "angle table needs %zu bytes of shared memory", smem);
+    }
+    int occ = 0;
+    XF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->kern.fn, nt, smem), "occupancy");
+    if (occ < 1) return fail(c, XF_E_UNSUPPORTED, "kernel cannot be resident (smem %zu)", smem);
+    int G = std::min(T, occ * c->num_sms);
+    if (c->grid_request > 0) G = std::min(G, c->grid_request);
+    G = std::max(G, 1);
+    // contiguous runs of tiles with about total_cost / G each, at least one
+    // tile per CTA
+    std::vector<int> ct(G + 1, T);
+    ct[0] = 0;
+    double acc = 0.0;
+    int cta = 1;
+    for (int t = 0; t < T && cta < G; ++t) {
+        const InstHost &in = c->in[c->tiles[t].inst];
+        acc += pair_cost(in) * c->tiles[t].np;
+        const bool must_cut = (T - (t + 1)) == (G - cta); // one tile left per remaining CTA
+        if ((acc >= total_cost * cta / G || must_cut) && T - (t + 1) >= G - cta) ct[cta++] = t + 1;
+    }
+    for (; cta < G; ++cta) ct[cta] = std::max(ct[cta - 1] + 1, T - (G - cta));
+    c->G = G;
+    c->tile_pairs = TP;
+    c->span_max = span;
+    c->smem = smem;
+    c->cta_tiles = ct;
+    // device copies (the tile buffers are sized for the most tiles seen)
+    if (T > c->max_tiles) {
+        c->partials = (double *)dev_alloc(c, sizeof(double) * 2 * (size_t)T * NVMAX);
+        c->tiles_d = (Tile *)dev_alloc(c, sizeof(Tile) * (size_t)T);
+        c->cta_tiles_d = (int *)dev_alloc(c, sizeof(int) * (size_t)(T + 1));
+        if (!c->partials || !c->tiles_d || !c->cta_tiles_d)
+            return fail(c, XF_E_NOMEM, "device allocation of the tile tables failed");
+        c->max_tiles = T;
+    }
+    XF_CUDA(c, cudaMemcpy(c->tiles_d, c->tiles.data(), sizeof(Tile) * T, cudaMemcpyHostToDevice), "copy tiles");
+    XF_CUDA(c, cudaMemcpy(c->cta_tiles_d, ct.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice), "copy tiling");
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
     return XF_OK;
 }
 
-double radius_of(double r_base, long long k, double h) { return h != 0.0 ? r_base + (double)k * h : r_base; }
-
-void reset_position(xf_ctx *c, double r_km)
+// Device copy of the instance table (static fields and the current r0, h).
+int upload_instances(xf_ctx *c)
 {
-    c->cur = c->pred_cur = 0;
-    c->r = r_km;
-    c->steps_total = 0;
-    c->r_base = c->pred_r_base = r_km;
-    c->h_base = c->pred_h = 0.0;
-    c->k_base = c->pred_k_base = 0;
-    c->pending.clear();
+    std::vector<Inst> v(c->in.size());
+    const double gf = matter_coefficient();
+    for (size_t i = 0; i < c->in.size(); ++i) {
+        const InstHost &h = c->in[i];
+        Inst &d = v[i];
+        std::memset(&d, 0, sizeof d);
+        d.n_E = h.n_E;
+        d.n_u = h.n_u;
+        d.nf = h.nf;
+        d.geometry = h.p.geometry;
+        d.matter = h.p.matter;
+        d.n_pairs = h.n_pairs;
+        d.npad = h.npad;
+        d.hvac_off = h.hvac_off;
+        d.state_off = h.state_off;
+        d.R = h.p.R_nu_km;
+        d.mu0 = h.p.mu0_per_km;
+        d.du = 1.0 / h.n_u;
+        d.dE = (h.p.E_max_MeV - h.p.E_min_MeV) / h.n_E;
+        d.ne_ref = h.p.ne_ref_cm3;
+        d.r_ref = h.p.r_ref_km;
+        d.ne_power = h.p.ne_power;
+        d.nb0 = h.p.nb0_cm3;
+        d.h_ns = h.p.h_ns_km;
+        d.Ye = h.p.Ye;
+        d.gf = gf;
+        d.r0 = h.r0;
+        d.h = h.h;
+        d.tile_begin = h.tile_begin;
+        d.tile_end = h.tile_end;
+    }
+    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    XF_CUDA(c, cudaMemcpy(c->inst_d, v.data(), sizeof(Inst) * v.size(), cudaMemcpyHostToDevice), "copy instances");
+    return XF_OK;
 }
 
+__global__ void set_requests_kernel(InstPos *pos, int n, long long steps, int only)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (only < 0 || i == only) && pos[i].err == 0) pos[i].remaining = steps;
+}
+// Restart instance i's step count at k0 (keeping its step total when `keep`).
+__global__ void reset_pos_kernel(InstPos *pos, int i, int cur, int keep)
+{
+    pos[i].k0 = 0;
+    pos[i].remaining = 0;
+    if (!keep) {
+        pos[i].steps = 0;
+        pos[i].cur = cur;
+        pos[i].err = 0;
+    }
+}
+
+// Read the device progress of every instance into the host view.
 int sync_status(xf_ctx *c)
 {
     XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    std::vector<InstPos> ps(c->in.size());
     int err = 0;
-    unsigned long long done = 0;
+    XF_CUDA(c, cudaMemcpy(ps.data(), c->pos_d, sizeof(InstPos) * ps.size(), cudaMemcpyDeviceToHost), "read progress");
     XF_CUDA(c, cudaMemcpy(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
-    XF_CUDA(c, cudaMemcpy(&done, c->steps, sizeof(done), cudaMemcpyDeviceToHost), "read step count");
-    // walk the enqueued launches with the number of steps actually taken
-    long long left = (long long)done;
-    for (const Pending &q : c->pending) {
-        long long n = std::min(left, q.n);
-        c->r_base = q.r0;
-        c->h_base = q.h;
-        c->k_base = q.k0 + n;
-        left -= n;
-        if (n < q.n) break;
+    for (size_t i = 0; i < c->in.size(); ++i) {
+        InstHost &h = c->in[i];
+        h.k0 = ps[i].k0;
+        h.cur = ps[i].cur;
+        h.steps = (long long)ps[i].steps;
+        h.err = ps[i].err;
     }
-    c->pending.clear();
-    c->steps_total += (long long)done;
-    c->cur = (c->cur + (int)(done & 1ull)) & 1;
-    c->r = radius_of(c->r_base, c->k_base, c->h_base);
-    c->pred_cur = c->cur;
-    c->pred_r_base = c->r_base;
-    c->pred_h = c->h_base;
-    c->pred_k_base = c->k_base;
-    XF_CUDA(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "reset error word");
-    XF_CUDA(c, cudaMemsetAsync(c->steps, 0, sizeof(unsigned long long), c->stream), "reset step count");
-    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
-    if (err & ERR_BARRIER) return fail(c, XF_E_BARRIER_TIMEOUT, "grid barrier timed out; state undefined");
-    if (err & ERR_NONFINITE)
-        return fail(c, XF_E_NONFINITE, "non-finite moments; state kept at step %lld", c->steps_total);
+    c->pending = 0;
+    if (err) {
+        XF_CUDA(c, cudaMemset(c->err, 0, sizeof(int)), "reset error word");
+        for (InstHost &h : c->in) h.state_valid = false;
+        return fail(c, XF_E_BARRIER_TIMEOUT, "grid barrier timed out; state undefined");
+    }
     return XF_OK;
 }
 
-int launch_steps(xf_ctx *c, long long n, double dr)
+double radius(const InstHost &h) { return h.h != 0.0 ? h.r0 + (double)h.k0 * h.h : h.r0; }
+
+// Enqueue one integrator launch of n steps (every instance with remaining > 0).
+int enqueue_run(xf_ctx *c, long long n, cudaStream_t stream)
+{
+    RunArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.inst = c->inst_d;
+    a.tiles = c->tiles_d;
+    a.cta_tiles = c->cta_tiles_d;
+    a.n_inst = (int)c->in.size();
+    a.n_tiles = (int)c->tiles.size();
+    a.span_max = c->span_max;
+    a.n_steps = n;
+    a.hvac = c->hvac_d;
+    a.rho0 = c->rho[0];
+    a.rho1 = c->rho[1];
+    a.aux = c->aux;
+    a.partials = c->partials;
+    a.mom_out = c->mom_out;
+    a.pos = c->pos_d;
+    a.bar = c->bar;
+    a.err = c->err;
+    a.timeout_ns = c->timeout_ns;
+    a.skip_cta = c->skip_cta;
+    XF_CUDA(c, cudaMemsetAsync(c->bar, 0, sizeof(unsigned), stream), "reset barrier");
+    void *args[] = {&a};
+    cudaError_t e;
+    if (c->G > 1)
+        e = cudaLaunchCooperativeKernel(c->kern.fn, dim3(c->G), dim3(c->kern.nt), args, c->smem, stream);
+    else
+        e = cudaLaunchKernel(c->kern.fn, dim3(1), dim3(c->kern.nt), args, c->smem, stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "launch of the integrator kernel");
+    return XF_OK;
+}
+
+// Enqueue n steps for instance `only` (or all with only < 0): request, launch.
+// With the graph option the (request, reset, launch) sequence of a given n is
+// captured once and replayed.
+int enqueue_steps(xf_ctx *c, long long n, int only)
 {
     const long long kChunk = 1ll << 16;
-    if (dr != c->pred_h) { // new step size: restart the step count at the current radius
-        c->pred_r_base = radius_of(c->pred_r_base, c->pred_k_base, c->pred_h);
-        c->pred_k_base = 0;
-        c->pred_h = dr;
-    }
+    const int ni = (int)c->in.size();
     while (n > 0) {
-        long long m = std::min(n, kChunk);
-        RunArgs a;
-        std::memset(&a, 0, sizeof a);
-        a.n_E = c->n_E;
-        a.n_u = c->n_u;
-        a.n_pairs = c->n_pairs;
-        a.npad = c->npad;
-        a.geometry = c->p.geometry;
-        a.matter = c->p.matter;
-        a.pairs_per_cta = c->pairs_per_cta;
-        a.span_max = c->span_max;
-        a.R = c->p.R_nu_km;
-        a.mu0 = c->p.mu0_per_km;
-        a.du = 1.0 / c->n_u;
-        a.dE = (c->p.E_max_MeV - c->p.E_min_MeV) / c->n_E;
-        a.ne_ref = c->p.ne_ref_cm3;
-        a.r_ref = c->p.r_ref_km;
-        a.ne_power = c->p.ne_power;
-        a.nb0 = c->p.nb0_cm3;
-        a.h_ns = c->p.h_ns_km;
-        a.Ye = c->p.Ye;
-        a.gf = matter_coefficient();
-        a.r0 = c->pred_r_base;
-        a.h = dr;
-        a.k0 = c->pred_k_base;
-        a.n_steps = m;
-        a.cur = c->pred_cur;
-        a.hvac = c->hvac_d;
-        a.rho0 = c->rho[0];
-        a.rho1 = c->rho[1];
-        a.aux = c->aux;
-        a.partials = c->partials;
-        a.mom_out = c->mom_out;
-        a.bar = c->bar;
-        a.err = c->err;
-        a.steps_done = c->steps;
-        a.timeout_ns = c->timeout_ns;
-        a.skip_cta = c->skip_cta;
-        XF_CUDA(c, cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream), "reset barrier");
-        void *args[] = {&a};
-        cudaError_t e;
-        if (c->G > 1)
-            e = cudaLaunchCooperativeKernel(c->kern.fn, dim3(c->G), dim3(c->kern.nt), args, c->smem, c->stream);
-        else
-            e = cudaLaunchKernel(c->kern.fn, dim3(1), dim3(c->kern.nt), args, c->smem, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "launch of the integrator kernel");
-        c->pending.push_back({c->pred_r_base, dr, c->pred_k_base, m});
-        c->pred_k_base += m;
-        c->pred_cur = (c->pred_cur + (int)(m & 1)) & 1;
+        const long long m = std::min(n, kChunk);
+        if (c->use_graph && only < 0) {
+            if (!c->gstream) {
+                XF_CUDA(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking), "graph stream");
+                XF_CUDA(c, cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming), "graph event");
+                XF_CUDA(c, cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming), "graph event");
+            }
+            if (!c->graph || c->graph_steps != m) {
+                if (c->graph) cudaGraphExecDestroy(c->graph);
+                c->graph = nullptr;
+                cudaGraph_t g = nullptr;
+                XF_CUDA(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal), "begin capture");
+                set_requests_kernel<<<(ni + 127) / 128, 128, 0, c->gstream>>>(c->pos_d, ni, m, -1);
+                int rc = enqueue_run(c, m, c->gstream);
+                cudaError_t e = cudaStreamEndCapture(c->gstream, &g);
+                if (rc) {
+                    if (g) cudaGraphDestroy(g);
+                    return rc;
+                }
+                if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+                e = cudaGraphInstantiate(&c->graph, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+                c->graph_steps = m;
+            }
+            XF_CUDA(c, cudaEventRecord(c->ev_in, c->stream), "order graph after stream");
+            XF_CUDA(c, cudaStreamWaitEvent(c->gstream, c->ev_in, 0), "order graph after stream");
+            XF_CUDA(c, cudaGraphLaunch(c->graph, c->gstream), "graph launch");
+            XF_CUDA(c, cudaEventRecord(c->ev_out, c->gstream), "order stream after graph");
+            XF_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_out, 0), "order stream after graph");
+        } else {
+            set_requests_kernel<<<(ni + 127) / 128, 128, 0, c->stream>>>(c->pos_d, ni, m, only);
+            XF_CUDA(c, cudaGetLastError(), "request kernel");
+            int rc = enqueue_run(c, m, c->stream);
+            if (rc) return rc;
+        }
+        ++c->pending;
         n -= m;
     }
     return XF_OK;
 }
 
 template <typename F>
-int dispatch_layout(xf_ctx *c, F &&f)
+int dispatch_layout(xf_ctx *c, const InstHost &in, F &&f)
 {
-    if (c->nf == 2) {
+    if (in.nf == 2) {
         if (c->real_bytes == 8) return f(std::integral_constant<int, 2>(), (double *)nullptr);
         return f(std::integral_constant<int, 2>(), (float *)nullptr);
     }
     if (c->real_bytes == 8) return f(std::integral_constant<int, 3>(), (double *)nullptr);
     return f(std::integral_constant<int, 3>(), (float *)nullptr);
+}
+
+InstHost *instance(xf_ctx *c, int i)
+{
+    if (!c || i < 0 || i >= (int)c->in.size()) return nullptr;
+    return &c->in[i];
+}
+
+// Set instance i's step size: a new h restarts the step count at the current
+// radius (the caller uploads the instance table afterwards).
+int set_step_size(xf_ctx *c, int i, double dr)
+{
+    InstHost &h = c->in[i];
+    if (dr == h.h) return XF_OK;
+    if (c->pending) {
+        int rc = sync_status(c);
+        if (rc) return rc;
+    }
+    h.r0 = radius(h);
+    h.k0 = 0;
+    h.h = dr;
+    reset_pos_kernel<<<1, 1, 0, c->stream>>>(c->pos_d, i, h.cur, 1);
+    XF_CUDA(c, cudaGetLastError(), "position kernel");
+    return XF_OK;
+}
+
+int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ctx **out)
+{
+    g_create_error.clear();
+    if (!out) return fail(nullptr, XF_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (n <= 0 || !probs) return fail(nullptr, XF_E_ARG, "need at least one problem");
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, XF_E_ARG, "allocator callbacks missing");
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(nullptr, &probs[i].params, probs[i].n_E, probs[i].n_u, probs[i].n_flavor);
+        if (rc) {
+            if (n > 1) g_create_error = "problem " + std::to_string(i) + ": " + g_create_error;
+            return rc;
+        }
+        if (probs[i].params.stepper != probs[0].params.stepper || probs[i].params.precision != probs[0].params.precision)
+            return fail(nullptr, XF_E_ARG, "all problems of a pack need the same stepper and precision");
+    }
+    xf_ctx *c = new (std::nothrow) xf_ctx();
+    if (!c) return fail(nullptr, XF_E_NOMEM, "host allocation failed");
+    if (alloc) {
+        c->alloc = *alloc;
+        c->has_alloc = true;
+    }
+    c->real_bytes = (probs[0].params.precision == XF_FP64) ? 8 : 4;
+    c->stepper = probs[0].params.stepper;
+    auto bail = [&](int code) {
+        free_all(c);
+        g_create_error = c->last_error;
+        delete c;
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "no usable CUDA device"));
+
+    c->in.resize(n);
+    long long state_elems = 0, trace_d = 0, phi_d = 0;
+    long long hv = 0;
+    bool has2 = false, has3 = false;
+    for (int i = 0; i < n; ++i) {
+        InstHost &h = c->in[i];
+        h.n_E = probs[i].n_E;
+        h.n_u = probs[i].n_u;
+        h.nf = probs[i].n_flavor;
+        h.S = h.nf * h.nf - 1;
+        h.n_pairs = h.n_E * h.n_u;
+        h.npad = (h.n_pairs + 63) & ~63;
+        h.n_bins = 2ll * h.n_pairs;
+        h.p = probs[i].params;
+        build_tables(h);
+        h.state_off = state_elems;
+        state_elems += (long long)2 * h.S * h.npad;
+        h.trace_off = trace_d;
+        trace_d += 2ll * h.npad;
+        h.phi_off = phi_d;
+        phi_d += 4ll * h.n_E;
+        h.hvac_off = (int)hv;
+        hv += (long long)h.n_E * h.S;
+        c->staging_doubles = std::max(c->staging_doubles, (size_t)h.n_bins * h.nf * h.nf);
+        (h.nf == 2 ? has2 : has3) = true;
+    }
+    if (hv > INT_MAX) return bail(fail(c, XF_E_ARG, "tables too large"));
+    c->nfm = (has2 && has3) ? 0 : (has3 ? 3 : 2);
+    const int st = (c->stepper == XF_RK4) ? STEP_RK4 : STEP_EXPH;
+    c->kern = (c->real_bytes == 8) ? run_kernel_fp64(c->nfm, st) : run_kernel_fp32(c->nfm, st);
+    if (!c->kern.fn) return bail(fail(c, XF_E_UNSUPPORTED, "kernel variant not built"));
+
+    const size_t plane = (size_t)state_elems * c->real_bytes;
+    c->rho[0] = dev_alloc(c, plane);
+    c->rho[1] = dev_alloc(c, plane);
+    c->aux = dev_alloc(c, plane);
+    c->trace = (double *)dev_alloc(c, sizeof(double) * (size_t)trace_d);
+    c->hvac_d = dev_alloc(c, (size_t)hv * c->real_bytes);
+    c->phi_d = (double *)dev_alloc(c, sizeof(double) * (size_t)phi_d);
+    c->staging = (double *)dev_alloc(c, sizeof(double) * c->staging_doubles);
+    c->inst_d = (Inst *)dev_alloc(c, sizeof(Inst) * n);
+    c->pos_d = (InstPos *)dev_alloc(c, sizeof(InstPos) * n);
+    c->mom_out = (double *)dev_alloc(c, sizeof(double) * NVMAX * n);
+    c->mom_full = (double *)dev_alloc(c, sizeof(double) * 18);
+    c->bar = (unsigned *)dev_alloc(c, 64);
+    c->err = (int *)dev_alloc(c, 64);
+    c->bad = (int *)dev_alloc(c, 64);
+    for (void *q : {c->rho[0], c->rho[1], c->aux, (void *)c->trace, c->hvac_d, (void *)c->phi_d, (void *)c->staging,
+                    (void *)c->inst_d, (void *)c->pos_d, (void *)c->mom_out, (void *)c->mom_full, (void *)c->bar,
+                    (void *)c->err, (void *)c->bad})
+        if (!q) return bail(fail(c, XF_E_NOMEM, "device allocation failed"));
+
+    // tables to the device (Real copy of H_vac)
+    std::vector<double> phi_all;
+    std::vector<double> hv64;
+    for (const InstHost &h : c->in) {
+        phi_all.insert(phi_all.end(), h.phi.begin(), h.phi.end());
+        hv64.insert(hv64.end(), h.hvac.begin(), h.hvac.end());
+    }
+    if (c->real_bytes == 8) e = cudaMemcpy(c->hvac_d, hv64.data(), sizeof(double) * hv64.size(), cudaMemcpyHostToDevice);
+    else {
+        std::vector<float> hf(hv64.begin(), hv64.end());
+        e = cudaMemcpy(c->hvac_d, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(c->phi_d, phi_all.data(), sizeof(double) * phi_all.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->err, 0, 64);
+    if (e == cudaSuccess) e = cudaMemset(c->bar, 0, 64);
+    if (e == cudaSuccess) e = cudaMemset(c->pos_d, 0, sizeof(InstPos) * n);
+    if (e == cudaSuccess) e = cudaMemset(c->rho[0], 0, plane);
+    if (e == cudaSuccess) e = cudaMemset(c->rho[1], 0, plane);
+    if (e == cudaSuccess) e = cudaMemset(c->aux, 0, plane);
+    if (e == cudaSuccess) e = cudaMemset(c->trace, 0, sizeof(double) * (size_t)trace_d);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "device set-up"));
+    int rc = plan_launch(c);
+    if (rc) return bail(rc);
+    rc = upload_instances(c);
+    if (rc) return bail(rc);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "device set-up"));
+    *out = c;
+    return XF_OK;
+}
+
+int check_r(xf_ctx *c, const InstHost &h, double r_km)
+{
+    if (!std::isfinite(r_km) || r_km < h.p.R_nu_km) return fail(c, XF_E_ARG, "r_km must be finite and >= R_nu");
+    return XF_OK;
+}
+
+// Instance i now holds a fresh state in buffer 0 at radius r_km.
+int reset_instance(xf_ctx *c, int i, double r_km, bool valid)
+{
+    InstHost &h = c->in[i];
+    h.r0 = r_km;
+    h.h = 0.0;
+    h.k0 = 0;
+    h.steps = 0;
+    h.cur = 0;
+    h.err = 0;
+    h.state_valid = valid;
+    reset_pos_kernel<<<1, 1, 0, c->stream>>>(c->pos_d, i, 0, 0);
+    XF_CUDA(c, cudaGetLastError(), "position kernel");
+    return upload_instances(c);
+}
+
+int set_state_impl(xf_ctx *c, int i, const double *rho, size_t n_doubles, double r_km)
+{
+    InstHost *hp = instance(c, i);
+    if (!hp) return c ? fail(c, XF_E_ARG, "bad instance index %d", i) : XF_E_ARG;
+    InstHost &h = *hp;
+    if (!rho) return fail(c, XF_E_ARG, "rho is NULL");
+    if (n_doubles != (size_t)h.n_bins * h.nf * h.nf)
+        return fail(c, XF_E_ARG, "n_doubles %zu != %lld", n_doubles, h.n_bins * h.nf * h.nf);
+    int rc = check_r(c, h, r_km);
+    if (rc) return rc;
+    if (c->pending) sync_status(c);
+    XF_CUDA(c, cudaMemcpyAsync(c->staging, rho, sizeof(double) * n_doubles, cudaMemcpyHostToDevice, c->stream),
+            "copy state to device");
+    XF_CUDA(c, cudaMemsetAsync(c->bad, 0, sizeof(int), c->stream), "reset flag");
+    LayoutArgs la = layout_args(c, h);
+    const int grid = elementwise_grid(c, h);
+    rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
+        constexpr int NF = decltype(nfc)::value;
+        using Real = std::remove_pointer_t<decltype(realp)>;
+        pack_to_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, c->staging, (Real *)c->rho[0] + h.state_off,
+                                                                    c->trace + h.trace_off);
+        return (int)cudaGetLastError();
+    });
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "layout kernel");
+    int bad = 0;
+    XF_CUDA(c, cudaMemcpyAsync(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read flag");
+    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    rc = reset_instance(c, i, r_km, !bad);
+    if (rc) return rc;
+    if (bad) return fail(c, XF_E_STATE, "state contains non-finite values");
+    return XF_OK;
+}
+
+int init_state_impl(xf_ctx *c, int i, double r_km)
+{
+    InstHost *hp = instance(c, i);
+    if (!hp) return c ? fail(c, XF_E_ARG, "bad instance index %d", i) : XF_E_ARG;
+    InstHost &h = *hp;
+    int rc = check_r(c, h, r_km);
+    if (rc) return rc;
+    if (c->pending) sync_status(c);
+    LayoutArgs la = layout_args(c, h);
+    const int grid = elementwise_grid(c, h);
+    rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
+        constexpr int NF = decltype(nfc)::value;
+        using Real = std::remove_pointer_t<decltype(realp)>;
+        init_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (Real *)c->rho[0] + h.state_off,
+                                                                 c->trace + h.trace_off);
+        return (int)cudaGetLastError();
+    });
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "init kernel");
+    return reset_instance(c, i, r_km, true);
+}
+
+int get_state_impl(xf_ctx *c, int i, double *rho, size_t n_doubles, double *r_km, int64_t *steps_done)
+{
+    InstHost *hp = instance(c, i);
+    if (!hp) return c ? fail(c, XF_E_ARG, "bad instance index %d", i) : XF_E_ARG;
+    InstHost &h = *hp;
+    if (!rho) return fail(c, XF_E_ARG, "rho is NULL");
+    if (n_doubles != (size_t)h.n_bins * h.nf * h.nf)
+        return fail(c, XF_E_ARG, "n_doubles %zu != %lld", n_doubles, h.n_bins * h.nf * h.nf);
+    if (c->pending) sync_status(c);
+    if (!h.state_valid) return fail(c, XF_E_STATE, "no valid state");
+    LayoutArgs la = layout_args(c, h);
+    const int grid = elementwise_grid(c, h);
+    int rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
+        constexpr int NF = decltype(nfc)::value;
+        using Real = std::remove_pointer_t<decltype(realp)>;
+        state_to_pack_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(
+            la, (const Real *)c->rho[h.cur] + h.state_off, c->trace + h.trace_off, c->staging);
+        return (int)cudaGetLastError();
+    });
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "layout kernel");
+    XF_CUDA(c, cudaMemcpyAsync(rho, c->staging, sizeof(double) * n_doubles, cudaMemcpyDeviceToHost, c->stream),
+            "copy state to host");
+    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (r_km) *r_km = radius(h);
+    if (steps_done) *steps_done = h.steps;
+    return XF_OK;
+}
+
+int outputs_impl(xf_ctx *c, int i, double *p_surv, double *trace, double *purity, size_t n_bins)
+{
+    InstHost *hp = instance(c, i);
+    if (!hp) return c ? fail(c, XF_E_ARG, "bad instance index %d", i) : XF_E_ARG;
+    InstHost &h = *hp;
+    if (n_bins != (size_t)h.n_bins) return fail(c, XF_E_ARG, "n_bins %zu != %lld", n_bins, h.n_bins);
+    if (c->pending) sync_status(c);
+    if (!h.state_valid) return fail(c, XF_E_STATE, "no valid state");
+    double *outs[3] = {p_surv, trace, purity};
+    double *dev[3] = {nullptr, nullptr, nullptr};
+    // staging holds n_bins * n_f^2 >= 4 n_bins doubles: room for three outputs
+    for (int k = 0; k < 3; ++k)
+        if (outs[k]) dev[k] = c->staging + (size_t)k * h.n_bins;
+    LayoutArgs la = layout_args(c, h);
+    const int grid = elementwise_grid(c, h);
+    int rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
+        constexpr int NF = decltype(nfc)::value;
+        using Real = std::remove_pointer_t<decltype(realp)>;
+        outputs_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (const Real *)c->rho[h.cur] + h.state_off,
+                                                              c->trace + h.trace_off, dev[0], dev[1], dev[2]);
+        return (int)cudaGetLastError();
+    });
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "outputs kernel");
+    for (int k = 0; k < 3; ++k)
+        if (outs[k])
+            XF_CUDA(c, cudaMemcpyAsync(outs[k], dev[k], sizeof(double) * n_bins, cudaMemcpyDeviceToHost, c->stream),
+                    "copy outputs");
+    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    return XF_OK;
+}
+
+int moments_impl(xf_ctx *c, int i, double *M0, double *M1, size_t n_doubles)
+{
+    InstHost *hp = instance(c, i);
+    if (!hp) return c ? fail(c, XF_E_ARG, "bad instance index %d", i) : XF_E_ARG;
+    InstHost &h = *hp;
+    if (!M0 || !M1) return fail(c, XF_E_ARG, "M0/M1 NULL");
+    if (n_doubles != (size_t)h.nf * h.nf) return fail(c, XF_E_ARG, "n_doubles must be n_f*n_f");
+    if (c->pending) sync_status(c);
+    if (!h.state_valid) return fail(c, XF_E_STATE, "no valid state");
+    MomArgs m;
+    m.n_E = h.n_E;
+    m.n_u = h.n_u;
+    m.n_pairs = h.n_pairs;
+    m.npad = h.npad;
+    m.geometry = h.p.geometry;
+    m.chunk = std::max(256, (h.n_pairs + c->num_sms * 4 - 1) / (c->num_sms * 4));
+    m.R = h.p.R_nu_km;
+    m.du = 1.0 / h.n_u;
+    m.dE = (h.p.E_max_MeV - h.p.E_min_MeV) / h.n_E;
+    m.r = radius(h);
+    const int G = (h.n_pairs + m.chunk - 1) / m.chunk;
+    if (G > c->mom_part_slots) {
+        c->mom_part = (double *)dev_alloc(c, sizeof(double) * (size_t)G * (NVMAX + 2));
+        if (!c->mom_part) return fail(c, XF_E_NOMEM, "device allocation failed");
+        c->mom_part_slots = G;
+    }
+    const double dE = m.dE;
+    int rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
+        constexpr int NF = decltype(nfc)::value;
+        using Real = std::remove_pointer_t<decltype(realp)>;
+        moments_partial_kernel<NF, Real, 256><<<G, 256, 0, c->stream>>>(
+            m, (const Real *)c->rho[h.cur] + h.state_off, c->trace + h.trace_off, c->mom_part);
+        moments_final_kernel<NF><<<1, 32, 0, c->stream>>>(c->mom_part, G, dE, c->mom_full, c->mom_full + NF * NF);
+        return (int)cudaGetLastError();
+    });
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "moments kernel");
+    double host[18];
+    XF_CUDA(c, cudaMemcpyAsync(host, c->mom_full, sizeof(double) * 2 * n_doubles, cudaMemcpyDeviceToHost, c->stream),
+            "copy moments");
+    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    std::memcpy(M0, host, sizeof(double) * n_doubles);
+    std::memcpy(M1, host + n_doubles, sizeof(double) * n_doubles);
+    return XF_OK;
 }
 
 } // namespace
@@ -493,94 +934,21 @@ int xf_create(int n_E, int n_u, int n_flavor, const xf_params *p, xf_ctx **out)
 
 int xf_create_ex(int n_E, int n_u, int n_flavor, const xf_params *p, const xf_allocator *alloc, xf_ctx **out)
 {
-    g_create_error.clear();
     if (!out) return fail(nullptr, XF_E_ARG, "out is NULL");
     *out = nullptr;
-    int rc = validate(p, n_E, n_u, n_flavor);
-    if (rc) return rc;
-    if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, XF_E_ARG, "allocator callbacks missing");
+    if (!p) return fail(nullptr, XF_E_ARG, "params is NULL");
+    xf_problem prob;
+    std::memset(&prob, 0, sizeof prob);
+    prob.n_E = n_E;
+    prob.n_u = n_u;
+    prob.n_flavor = n_flavor;
+    prob.params = *p;
+    return create_pack(1, &prob, alloc, out);
+}
 
-    xf_ctx *c = new (std::nothrow) xf_ctx();
-    if (!c) return fail(nullptr, XF_E_NOMEM, "host allocation failed");
-    c->n_E = n_E;
-    c->n_u = n_u;
-    c->nf = n_flavor;
-    c->S = n_flavor * n_flavor - 1;
-    c->n_pairs = n_E * n_u;
-    c->npad = (c->n_pairs + 63) & ~63;
-    c->n_bins = 2ll * c->n_pairs;
-    c->p = *p;
-    c->real_bytes = (p->precision == XF_FP64) ? 8 : 4;
-    if (alloc) {
-        c->alloc = *alloc;
-        c->has_alloc = true;
-    }
-    auto bail = [&](int code) {
-        free_all(c);
-        g_create_error = c->last_error;
-        delete c;
-        return code;
-    };
-    cudaError_t e = cudaGetDevice(&c->device);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
-    if (e != cudaSuccess) return bail(cuda_fail(c, e, "no usable CUDA device"));
-
-    build_tables(c);
-    const int st = (p->stepper == XF_RK4) ? STEP_RK4 : STEP_EXPH;
-    c->kern = (c->real_bytes == 8) ? run_kernel_fp64(c->nf, st) : run_kernel_fp32(c->nf, st);
-    if (!c->kern.fn) return bail(fail(c, XF_E_UNSUPPORTED, "kernel variant not built"));
-    rc = plan_launch(c);
-    if (rc) return bail(rc);
-
-    const size_t plane = (size_t)2 * c->S * c->npad * c->real_bytes;
-    const int NV = 2 * c->S;
-    c->mom_chunk = std::max(256, (c->n_pairs + c->num_sms * 4 - 1) / (c->num_sms * 4));
-    c->mom_G = (c->n_pairs + c->mom_chunk - 1) / c->mom_chunk;
-    c->rho[0] = dev_alloc(c, plane);
-    c->rho[1] = dev_alloc(c, plane);
-    c->aux = dev_alloc(c, plane);
-    c->trace = (double *)dev_alloc(c, sizeof(double) * 2 * (size_t)c->npad);
-    c->hvac_d = dev_alloc(c, (size_t)c->n_E * c->S * c->real_bytes);
-    c->phi_d = (double *)dev_alloc(c, sizeof(double) * 4 * (size_t)c->n_E);
-    c->staging = (double *)dev_alloc(c, sizeof(double) * (size_t)c->n_bins * c->nf * c->nf);
-    int occ_max = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_max, c->kern.fn, c->kern.nt, 0) != cudaSuccess) {
-        cudaGetLastError();
-        occ_max = 32;
-    }
-    c->partials = (double *)dev_alloc(c, sizeof(double) * 2 * (size_t)std::max(c->G, occ_max * c->num_sms) * NV);
-    c->mom_out = (double *)dev_alloc(c, sizeof(double) * NV);
-    c->mom_part = (double *)dev_alloc(c, sizeof(double) * (size_t)c->mom_G * (NV + 2));
-    c->mom_full = (double *)dev_alloc(c, sizeof(double) * 2 * c->nf * c->nf);
-    c->bar = (unsigned *)dev_alloc(c, 64);
-    c->err = (int *)dev_alloc(c, 64);
-    c->bad = (int *)dev_alloc(c, 64);
-    c->steps = (unsigned long long *)dev_alloc(c, 64);
-    for (void *q : {c->rho[0], c->rho[1], c->aux, (void *)c->trace, c->hvac_d, (void *)c->phi_d,
-                    (void *)c->staging, (void *)c->partials, (void *)c->mom_out, (void *)c->mom_part,
-                    (void *)c->mom_full, (void *)c->bar, (void *)c->err, (void *)c->bad, (void *)c->steps})
-        if (!q) return bail(fail(c, XF_E_NOMEM, "device allocation failed"));
-
-    // tables to the device (Real copy of H_vac)
-    if (c->real_bytes == 8) {
-        e = cudaMemcpy(c->hvac_d, c->hvac.data(), sizeof(double) * c->hvac.size(), cudaMemcpyHostToDevice);
-    } else {
-        std::vector<float> hf(c->hvac.begin(), c->hvac.end());
-        e = cudaMemcpy(c->hvac_d, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice);
-    }
-    if (e == cudaSuccess)
-        e = cudaMemcpy(c->phi_d, c->phi.data(), sizeof(double) * c->phi.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(c->err, 0, 64);
-    if (e == cudaSuccess) e = cudaMemset(c->steps, 0, 64);
-    if (e == cudaSuccess) e = cudaMemset(c->bar, 0, 64);
-    if (e == cudaSuccess) e = cudaMemset(c->rho[0], 0, plane);
-    if (e == cudaSuccess) e = cudaMemset(c->rho[1], 0, plane);
-    if (e == cudaSuccess) e = cudaMemset(c->aux, 0, plane);
-    if (e == cudaSuccess) e = cudaMemset(c->trace, 0, sizeof(double) * 2 * (size_t)c->npad);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return bail(cuda_fail(c, e, "device set-up"));
-    *out = c;
-    return XF_OK;
+int xf_create_batch(int n_problems, const xf_problem *problems, const xf_allocator *alloc, xf_ctx **out)
+{
+    return create_pack(n_problems, problems, alloc, out);
 }
 
 int xf_destroy(xf_ctx *c)
@@ -596,60 +964,42 @@ int xf_destroy(xf_ctx *c)
 int xf_set_stream(xf_ctx *c, void *stream)
 {
     if (!c) return XF_E_ARG;
-    if (!c->pending.empty()) {
+    if (c->pending) {
         int rc = sync_status(c);
         if (rc) return rc;
     }
     c->stream = (cudaStream_t)stream;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
     return XF_OK;
 }
 
 int xf_set_state(xf_ctx *c, const double *rho, size_t n_doubles, double r_km)
 {
     if (!c) return XF_E_ARG;
-    if (!rho) return fail(c, XF_E_ARG, "rho is NULL");
-    if (n_doubles != (size_t)c->n_bins * c->nf * c->nf)
-        return fail(c, XF_E_ARG, "n_doubles %zu != %lld", n_doubles, c->n_bins * c->nf * c->nf);
-    if (!std::isfinite(r_km) || r_km < c->p.R_nu_km) return fail(c, XF_E_ARG, "r_km must be finite and >= R_nu");
-    if (!c->pending.empty()) sync_status(c);
-    XF_CUDA(c, cudaMemcpyAsync(c->staging, rho, sizeof(double) * n_doubles, cudaMemcpyHostToDevice, c->stream),
-            "copy state to device");
-    XF_CUDA(c, cudaMemsetAsync(c->bad, 0, sizeof(int), c->stream), "reset flag");
-    LayoutArgs la = layout_args(c);
-    const int grid = elementwise_grid(c);
-    int rc = dispatch_layout(c, [&](auto nfc, auto *realp) {
-        constexpr int NF = decltype(nfc)::value;
-        using Real = std::remove_pointer_t<decltype(realp)>;
-        pack_to_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, c->staging, (Real *)c->rho[0], c->trace);
-        return (int)cudaGetLastError();
-    });
-    if (rc) return cuda_fail(c, (cudaError_t)rc, "layout kernel");
-    int bad = 0;
-    XF_CUDA(c, cudaMemcpyAsync(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read flag");
-    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
-    reset_position(c, r_km);
-    c->state_valid = !bad;
-    if (bad) return fail(c, XF_E_STATE, "state contains non-finite values");
-    return XF_OK;
+    return set_state_impl(c, 0, rho, n_doubles, r_km);
+}
+int xf_batch_set_state(xf_ctx *c, int inst, const double *rho, size_t n_doubles, double r_km)
+{
+    if (!c) return XF_E_ARG;
+    return set_state_impl(c, inst, rho, n_doubles, r_km);
 }
 
 int xf_init_state(xf_ctx *c, double r_km)
 {
     if (!c) return XF_E_ARG;
-    if (!std::isfinite(r_km) || r_km < c->p.R_nu_km) return fail(c, XF_E_ARG, "r_km must be finite and >= R_nu");
-    if (!c->pending.empty()) sync_status(c);
-    LayoutArgs la = layout_args(c);
-    const int grid = elementwise_grid(c);
-    int rc = dispatch_layout(c, [&](auto nfc, auto *realp) {
-        constexpr int NF = decltype(nfc)::value;
-        using Real = std::remove_pointer_t<decltype(realp)>;
-        init_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (Real *)c->rho[0], c->trace);
-        return (int)cudaGetLastError();
-    });
-    if (rc) return cuda_fail(c, (cudaError_t)rc, "init kernel");
-    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
-    reset_position(c, r_km);
-    c->state_valid = true;
+    return init_state_impl(c, 0, r_km);
+}
+int xf_batch_init_state(xf_ctx *c, int inst, double r_km)
+{
+    if (!c) return XF_E_ARG;
+    if (inst >= 0) return init_state_impl(c, inst, r_km);
+    for (int i = 0; i < (int)c->in.size(); ++i) {
+        int rc = init_state_impl(c, i, r_km);
+        if (rc) return rc;
+    }
     return XF_OK;
 }
 
@@ -658,17 +1008,26 @@ int xf_step_async(xf_ctx *c, int64_t n_steps, double dr_km)
     if (!c) return XF_E_ARG;
     if (n_steps < 0) return fail(c, XF_E_ARG, "n_steps must be >= 0");
     if (!std::isfinite(dr_km) || dr_km <= 0) return fail(c, XF_E_ARG, "dr_km must be finite and > 0");
-    if (!c->state_valid) return fail(c, XF_E_STATE, "no valid state (call xf_set_state or xf_init_state)");
+    InstHost &h = c->in[0];
+    if (!h.state_valid) return fail(c, XF_E_STATE, "no valid state (call xf_set_state or xf_init_state)");
     if (n_steps == 0) return XF_OK;
-    return launch_steps(c, n_steps, dr_km);
+    if (dr_km != h.h) {
+        int rc = set_step_size(c, 0, dr_km);
+        if (rc) return rc;
+        rc = upload_instances(c);
+        if (rc) return rc;
+    }
+    return enqueue_steps(c, n_steps, c->in.size() == 1 ? -1 : 0);
 }
 
 int xf_sync(xf_ctx *c)
 {
     if (!c) return XF_E_ARG;
     int rc = sync_status(c);
-    if (rc == XF_E_BARRIER_TIMEOUT) c->state_valid = false;
-    return rc;
+    if (rc) return rc;
+    if (c->in[0].err & ERR_NONFINITE)
+        return fail(c, XF_E_NONFINITE, "non-finite moments; state kept at step %lld", c->in[0].steps);
+    return XF_OK;
 }
 
 int xf_step(xf_ctx *c, int64_t n_steps, double dr_km)
@@ -678,115 +1037,103 @@ int xf_step(xf_ctx *c, int64_t n_steps, double dr_km)
     return xf_sync(c);
 }
 
+int xf_batch_step(xf_ctx *c, int64_t n_steps, const double *dr_km)
+{
+    if (!c) return XF_E_ARG;
+    if (n_steps < 0) return fail(c, XF_E_ARG, "n_steps must be >= 0");
+    bool changed = false;
+    for (size_t i = 0; i < c->in.size(); ++i) {
+        InstHost &h = c->in[i];
+        if (!h.state_valid) return fail(c, XF_E_STATE, "problem %zu has no valid state", i);
+        const double dr = dr_km ? dr_km[i] : h.h;
+        if (!std::isfinite(dr) || dr <= 0) return fail(c, XF_E_ARG, "step size of problem %zu invalid", i);
+        if (dr != h.h) {
+            int rc = set_step_size(c, (int)i, dr);
+            if (rc) return rc;
+            changed = true;
+        }
+    }
+    if (changed) {
+        int rc = upload_instances(c);
+        if (rc) return rc;
+    }
+    if (n_steps == 0) return XF_OK;
+    int rc = enqueue_steps(c, n_steps, -1);
+    if (rc) return rc;
+    return sync_status(c);
+}
+
+int xf_batch_get_state(xf_ctx *c, int inst, double *rho, size_t n_doubles, double *r_km, int64_t *steps_done)
+{
+    if (!c) return XF_E_ARG;
+    return get_state_impl(c, inst, rho, n_doubles, r_km, steps_done);
+}
+
+int xf_batch_status(xf_ctx *c, int inst, int *status, int64_t *steps_done, double *r_km)
+{
+    InstHost *h = instance(c, inst);
+    if (!h) return c ? fail(c, XF_E_ARG, "bad instance index %d", inst) : XF_E_ARG;
+    if (c->pending) {
+        int rc = sync_status(c);
+        if (rc) return rc;
+    }
+    if (status) *status = !h->state_valid ? XF_E_STATE : (h->err & ERR_NONFINITE) ? XF_E_NONFINITE : XF_OK;
+    if (steps_done) *steps_done = h->steps;
+    if (r_km) *r_km = radius(*h);
+    return XF_OK;
+}
+
+int xf_batch_outputs(xf_ctx *c, int inst, double *p_surv, double *trace, double *purity, size_t n_bins)
+{
+    if (!c) return XF_E_ARG;
+    return outputs_impl(c, inst, p_surv, trace, purity, n_bins);
+}
+
+int xf_batch_size(xf_ctx *c, int *n_problems)
+{
+    if (!c || !n_problems) return XF_E_ARG;
+    *n_problems = (int)c->in.size();
+    return XF_OK;
+}
+
 int xf_get_state(xf_ctx *c, double *rho, size_t n_doubles, double *r_km, int64_t *steps_done)
 {
     if (!c) return XF_E_ARG;
-    if (!rho) return fail(c, XF_E_ARG, "rho is NULL");
-    if (n_doubles != (size_t)c->n_bins * c->nf * c->nf)
-        return fail(c, XF_E_ARG, "n_doubles %zu != %lld", n_doubles, c->n_bins * c->nf * c->nf);
-    if (!c->pending.empty()) sync_status(c);
-    if (!c->state_valid) return fail(c, XF_E_STATE, "no valid state");
-    LayoutArgs la = layout_args(c);
-    const int grid = elementwise_grid(c);
-    int rc = dispatch_layout(c, [&](auto nfc, auto *realp) {
-        constexpr int NF = decltype(nfc)::value;
-        using Real = std::remove_pointer_t<decltype(realp)>;
-        state_to_pack_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (const Real *)c->rho[c->cur], c->trace,
-                                                                    c->staging);
-        return (int)cudaGetLastError();
-    });
-    if (rc) return cuda_fail(c, (cudaError_t)rc, "layout kernel");
-    XF_CUDA(c, cudaMemcpyAsync(rho, c->staging, sizeof(double) * n_doubles, cudaMemcpyDeviceToHost, c->stream),
-            "copy state to host");
-    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
-    if (r_km) *r_km = c->r;
-    if (steps_done) *steps_done = c->steps_total;
-    return XF_OK;
+    return get_state_impl(c, 0, rho, n_doubles, r_km, steps_done);
 }
 
 int xf_moments(xf_ctx *c, double *M0, double *M1, size_t n_doubles)
 {
     if (!c) return XF_E_ARG;
-    if (!M0 || !M1) return fail(c, XF_E_ARG, "M0/M1 NULL");
-    if (n_doubles != (size_t)c->nf * c->nf) return fail(c, XF_E_ARG, "n_doubles must be n_f*n_f");
-    if (!c->pending.empty()) sync_status(c);
-    if (!c->state_valid) return fail(c, XF_E_STATE, "no valid state");
-    MomArgs m;
-    m.n_E = c->n_E;
-    m.n_u = c->n_u;
-    m.n_pairs = c->n_pairs;
-    m.npad = c->npad;
-    m.geometry = c->p.geometry;
-    m.chunk = c->mom_chunk;
-    m.R = c->p.R_nu_km;
-    m.du = 1.0 / c->n_u;
-    m.dE = (c->p.E_max_MeV - c->p.E_min_MeV) / c->n_E;
-    m.r = c->r;
-    const double dE = m.dE;
-    int rc = dispatch_layout(c, [&](auto nfc, auto *realp) {
-        constexpr int NF = decltype(nfc)::value;
-        using Real = std::remove_pointer_t<decltype(realp)>;
-        moments_partial_kernel<NF, Real, 256><<<c->mom_G, 256, 0, c->stream>>>(m, (const Real *)c->rho[c->cur],
-                                                                             c->trace, c->mom_part);
-        moments_final_kernel<NF><<<1, 32, 0, c->stream>>>(c->mom_part, c->mom_G, dE, c->mom_full,
-                                                        c->mom_full + NF * NF);
-        return (int)cudaGetLastError();
-    });
-    if (rc) return cuda_fail(c, (cudaError_t)rc, "moments kernel");
-    double host[18];
-    XF_CUDA(c, cudaMemcpyAsync(host, c->mom_full, sizeof(double) * 2 * n_doubles, cudaMemcpyDeviceToHost, c->stream),
-            "copy moments");
-    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
-    std::memcpy(M0, host, sizeof(double) * n_doubles);
-    std::memcpy(M1, host + n_doubles, sizeof(double) * n_doubles);
-    return XF_OK;
+    return moments_impl(c, 0, M0, M1, n_doubles);
 }
 
 int xf_outputs(xf_ctx *c, double *p_surv, double *trace, double *purity, size_t n_bins)
 {
     if (!c) return XF_E_ARG;
-    if (n_bins != (size_t)c->n_bins) return fail(c, XF_E_ARG, "n_bins %zu != %lld", n_bins, c->n_bins);
-    if (!c->pending.empty()) sync_status(c);
-    if (!c->state_valid) return fail(c, XF_E_STATE, "no valid state");
-    double *outs[3] = {p_surv, trace, purity};
-    double *dev[3] = {nullptr, nullptr, nullptr};
-    // staging holds n_bins * n_f^2 >= 4 n_bins doubles: room for three outputs
-    for (int i = 0; i < 3; ++i)
-        if (outs[i]) dev[i] = c->staging + (size_t)i * c->n_bins;
-    LayoutArgs la = layout_args(c);
-    const int grid = elementwise_grid(c);
-    int rc = dispatch_layout(c, [&](auto nfc, auto *realp) {
-        constexpr int NF = decltype(nfc)::value;
-        using Real = std::remove_pointer_t<decltype(realp)>;
-        outputs_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (const Real *)c->rho[c->cur], c->trace, dev[0],
-                                                              dev[1], dev[2]);
-        return (int)cudaGetLastError();
-    });
-    if (rc) return cuda_fail(c, (cudaError_t)rc, "outputs kernel");
-    for (int i = 0; i < 3; ++i)
-        if (outs[i])
-            XF_CUDA(c, cudaMemcpyAsync(outs[i], dev[i], sizeof(double) * n_bins, cudaMemcpyDeviceToHost, c->stream),
-                    "copy outputs");
-    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
-    return XF_OK;
+    return outputs_impl(c, 0, p_surv, trace, purity, n_bins);
 }
 
 int xf_set_option(xf_ctx *c, int option, int64_t value)
 {
     if (!c) return XF_E_ARG;
-    if (!c->pending.empty()) {
+    if (c->pending) {
         int rc = sync_status(c);
         if (rc) return rc;
     }
     switch (option) {
-    case XF_OPT_GRID: {
-        if (value < 0 || value > INT_MAX) return fail(c, XF_E_ARG, "grid must be >= 0");
-        int old = c->grid_request;
-        c->grid_request = (int)value;
+    case XF_OPT_GRID:
+    case XF_OPT_TILE_PAIRS: {
+        if (value < 0 || value > (1 << 20)) return fail(c, XF_E_ARG, "value must be in [0, 2^20]");
+        int &slot = (option == XF_OPT_GRID) ? c->grid_request : c->tile_request;
+        int old = slot;
+        slot = (int)value;
         int rc = plan_launch(c);
+        if (!rc) rc = upload_instances(c);
         if (rc) {
-            c->grid_request = old;
+            slot = old;
             plan_launch(c);
+            upload_instances(c);
         }
         return rc;
     }
@@ -798,6 +1145,10 @@ int xf_set_option(xf_ctx *c, int option, int64_t value)
         if (value < -1 || value > INT_MAX) return fail(c, XF_E_ARG, "bad CTA index");
         c->skip_cta = (int)value;
         return XF_OK;
+    case XF_OPT_GRAPH:
+        if (value != 0 && value != 1) return fail(c, XF_E_ARG, "graph option is 0 or 1");
+        c->use_graph = (int)value;
+        return XF_OK;
     default: return fail(c, XF_E_ARG, "unknown option %d", option);
     }
 }
@@ -805,8 +1156,8 @@ int xf_set_option(xf_ctx *c, int option, int64_t value)
 int xf_tables(xf_ctx *c, double *E, double *phi)
 {
     if (!c) return XF_E_ARG;
-    if (E) std::memcpy(E, c->E.data(), sizeof(double) * c->E.size());
-    if (phi) std::memcpy(phi, c->phi.data(), sizeof(double) * c->phi.size());
+    if (E) std::memcpy(E, c->in[0].E.data(), sizeof(double) * c->in[0].E.size());
+    if (phi) std::memcpy(phi, c->in[0].phi.data(), sizeof(double) * c->in[0].phi.size());
     return XF_OK;
 }
 
@@ -815,7 +1166,7 @@ int xf_launch_info(xf_ctx *c, int *ctas, int *threads, int *barriers_per_step)
     if (!c) return XF_E_ARG;
     if (ctas) *ctas = c->G;
     if (threads) *threads = c->kern.nt;
-    if (barriers_per_step) *barriers_per_step = (c->p.stepper == XF_RK4) ? 4 : 2;
+    if (barriers_per_step) *barriers_per_step = (c->stepper == XF_RK4) ? 4 : 2;
     return XF_OK;
 }
 

@@ -3,12 +3,17 @@
 
 namespace xf {
 
-RunKernel run_kernel_fp64(int nf, int stepper)
+RunKernel run_kernel_fp64(int nfm, int stepper)
 {
-    if (nf == 2 && stepper == STEP_RK4) return {(const void *)xf_run_kernel<2, STEP_RK4, double, 256>, 256};
-    if (nf == 2 && stepper == STEP_EXPH) return {(const void *)xf_run_kernel<2, STEP_EXPH, double, 256>, 256};
-    if (nf == 3 && stepper == STEP_RK4) return {(const void *)xf_run_kernel<3, STEP_RK4, double, 128>, 128};
-    if (nf == 3 && stepper == STEP_EXPH) return {(const void *)xf_run_kernel<3, STEP_EXPH, double, 128>, 128};
+    if (stepper == STEP_RK4) {
+        if (nfm == 2) return {(const void *)xf_run_kernel<2, STEP_RK4, double, 256>, 256};
+        if (nfm == 3) return {(const void *)xf_run_kernel<3, STEP_RK4, double, 128>, 128};
+        if (nfm == 0) return {(const void *)xf_run_kernel<0, STEP_RK4, double, 128>, 128};
+    } else if (stepper == STEP_EXPH) {
+        if (nfm == 2) return {(const void *)xf_run_kernel<2, STEP_EXPH, double, 256>, 256};
+        if (nfm == 3) return {(const void *)xf_run_kernel<3, STEP_EXPH, double, 128>, 128};
+        if (nfm == 0) return {(const void *)xf_run_kernel<0, STEP_EXPH, double, 128>, 128};
+    }
     return {nullptr, 0};
 }
 

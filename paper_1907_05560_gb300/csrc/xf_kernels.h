@@ -11,8 +11,9 @@ struct RunKernel {
     int nt;         // threads per CTA it was compiled for
 };
 
-// nf in {2, 3}, stepper STEP_RK4 / STEP_EXPH; fn == nullptr if not built.
-RunKernel run_kernel_fp64(int nf, int stepper);
-RunKernel run_kernel_fp32(int nf, int stepper);
+// nfm: 2 or 3 (all instances of the pack have that many flavors) or 0
+// (mixed pack); stepper STEP_RK4 / STEP_EXPH.  fn == nullptr if not built.
+RunKernel run_kernel_fp64(int nfm, int stepper);
+RunKernel run_kernel_fp32(int nfm, int stepper);
 
 } // namespace xf

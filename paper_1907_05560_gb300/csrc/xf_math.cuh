@@ -29,22 +29,55 @@ __host__ __device__ __forceinline__ void sincos_r(float x, float *s, float *c) {
 __host__ __device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
 __host__ __device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
 
-// Phase phi = lam * dl, evaluated in FP64; returns (sin, cos) in Real.  For
-// FP32 the FP64 phase is reduced to [-pi, pi] in FP64 before sincosf, so a
-// long step does not lose the phase to FP32 rounding of its argument.
-template <typename Real>
-__host__ __device__ __forceinline__ void phase_sincos(double phi, Real *s, Real *c);
-template <>
-__host__ __device__ __forceinline__ void phase_sincos<double>(double phi, double *s, double *c)
+// Step path length in the precision of the phase arithmetic: FP64 for the
+// FP64 path; for FP32 an unevaluated sum hi + lo of two floats (about 48
+// significant bits), so that the phase lam * dl of a long step keeps FP64-like
+// accuracy without FP64 instructions (a warp-wide FP64 instruction occupies
+// this GPU's FP64 pipe for 16 cycles).
+template <typename Real> struct StepLen;
+template <> struct StepLen<double> {
+    double v;
+};
+template <> struct StepLen<float> {
+    float hi, lo;
+};
+__host__ __device__ __forceinline__ StepLen<double> make_step_len(double dl, double *) { return {dl}; }
+__host__ __device__ __forceinline__ StepLen<float> make_step_len(double dl, float *)
 {
-    sincos(phi, s, c);
+    float hi = (float)dl;
+    return {hi, (float)(dl - (double)hi)};
 }
-template <>
-__host__ __device__ __forceinline__ void phase_sincos<float>(double phi, float *s, float *c)
+__host__ __device__ __forceinline__ double step_len_value(StepLen<double> d) { return d.v; }
+__host__ __device__ __forceinline__ float step_len_value(StepLen<float> d) { return d.hi; }
+
+// (sin, cos) of the phase lam * dl.
+//  FP64: directly.
+//  FP32: the product in float-float (exact product by FMA, plus lam * lo),
+//  reduced modulo 2 pi with a three-part split of 2 pi (6.28125 has 8
+//  significant bits, so k * 6.28125 is exact for |k| < 2^16), then sincosf of
+//  the reduced float.  Phases beyond 2^14 rad take an FP64 reduction.
+__host__ __device__ __forceinline__ void phase_sincos(double lam, StepLen<double> d, double *s, double *c)
 {
-    const double two_pi = 6.283185307179586476925286766559;
-    double k = rint(phi * (1.0 / two_pi));
-    float red = (float)fma(-k, two_pi, phi);
+    sincos(lam * d.v, s, c);
+}
+__host__ __device__ __forceinline__ void phase_sincos(float lam, StepLen<float> d, float *s, float *c)
+{
+    const float p = lam * d.hi;
+    float e = fmaf(lam, d.hi, -p); // rounding error of the product, exact
+    e = fmaf(lam, d.lo, e);
+    float red;
+    if (fabsf(p) < 16384.0f) {
+        const float k = rintf(p * 0.15915494309189535f);
+        red = fmaf(-k, 6.28125f, p);
+        red = fmaf(-k, 1.9353071693331003e-3f, red); // float((2 pi) - 6.28125)
+        red = fmaf(-k, 1.0253131677018246e-11f, red); // (2 pi) - 6.28125 - that float
+        red += e;
+    } else {
+        const double two_pi = 6.283185307179586476925286766559;
+        const double ph = (double)p + (double)e;
+        const double k = rint(ph * (1.0 / two_pi));
+        red = (float)fma(-k, two_pi, ph);
+    }
     sincosf(red, s, c);
 }
 
@@ -65,13 +98,13 @@ __host__ __device__ __forceinline__ void comm2(const Real *h, const Real *t, Rea
 // Q the same map applied to W (Rodrigues' formula):
 //   T' = T + 2 sigma C W + 2 sigma^2 Q,  sigma = sin(lam dl)/lam, C = cos(lam dl)
 template <typename Real>
-__host__ __device__ __forceinline__ void prop2(const Real *h, double dl, const Real *t, Real *out)
+__host__ __device__ __forceinline__ void prop2(const Real *h, StepLen<Real> dl, const Real *t, Real *out)
 {
     Real lam2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
     Real lam = sqrt_r(lam2);
     Real sn, cs;
-    phase_sincos<Real>((double)lam * dl, &sn, &cs);
-    Real sig = (lam > Real(0)) ? sn / lam : (Real)dl;
+    phase_sincos(lam, dl, &sn, &cs);
+    Real sig = (lam > Real(0)) ? sn / lam : step_len_value(dl);
     Real w[3], q[3];
     w[0] = h[2] * t[1] - h[1] * t[2];
     w[1] = h[0] * t[2] - t[0] * h[2];
@@ -200,7 +233,7 @@ template <> struct JacobiTol<float> {
 // H = V diag(lam) V^dagger by cyclic Jacobi, then
 // T' = V (E o (V^dagger T V)) V^dagger with E_jk = exp(-i (lam_j - lam_k) dl).
 template <typename Real>
-__host__ __device__ __forceinline__ void prop3(const Real *h, double dl, const Real *t, Real *out)
+__host__ __device__ __forceinline__ void prop3(const Real *h, StepLen<Real> dl, const Real *t, Real *out)
 {
     Real dg[3] = {h[0], h[1], -(h[0] + h[1])};
     cx<Real> o[3] = {mk(h[2], h[3]), mk(h[4], h[5]), mk(h[6], h[7])};
@@ -244,11 +277,11 @@ __host__ __device__ __forceinline__ void prop3(const Real *h, double dl, const R
     // phases exp(-i (lam_j - lam_k) dl) on the upper entries
     {
         Real s, c;
-        phase_sincos<Real>((double)(dg[0] - dg[1]) * dl, &s, &c);
+        phase_sincos(dg[0] - dg[1], dl, &s, &c);
         Ro[0] = Ro[0] * mk(c, -s);
-        phase_sincos<Real>((double)(dg[0] - dg[2]) * dl, &s, &c);
+        phase_sincos(dg[0] - dg[2], dl, &s, &c);
         Ro[1] = Ro[1] * mk(c, -s);
-        phase_sincos<Real>((double)(dg[1] - dg[2]) * dl, &s, &c);
+        phase_sincos(dg[1] - dg[2], dl, &s, &c);
         Ro[2] = Ro[2] * mk(c, -s);
     }
     const cx<Real> Rm[3][3] = {{mk(Rd[0], Real(0)), Ro[0], Ro[1]},
@@ -286,7 +319,7 @@ __host__ __device__ __forceinline__ void comm(const Real *h, const Real *t, Real
     else comm3<Real>(h, t, d);
 }
 template <int NF, typename Real>
-__host__ __device__ __forceinline__ void prop(const Real *h, double dl, const Real *t, Real *out)
+__host__ __device__ __forceinline__ void prop(const Real *h, StepLen<Real> dl, const Real *t, Real *out)
 {
     if constexpr (NF == 2) prop2<Real>(h, dl, t, out);
     else prop3<Real>(h, dl, t, out);

@@ -115,11 +115,32 @@ __global__ void vacuum_table_kernel(Real *hv, int n_E, double E_min, double dE, 
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Tiles of TP pairs over one problem, and contiguous runs of tiles per CTA
+// (computed on the device so that no host array is needed).
+__global__ void noalloc_plan_kernel(Tile *tiles, int *cta_tiles, int T, int TP, int n_pairs, int G)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        const int p0 = t * TP;
+        tiles[t] = Tile{0, p0, min(TP, n_pairs - p0), 0};
+    }
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= G; c += gridDim.x * blockDim.x)
+        cta_tiles[c] = (int)(((long long)c * T) / G);
+}
+
+__global__ void noalloc_pos_kernel(InstPos *pos, long long n_steps)
+{
+    pos->k0 = 0;
+    pos->remaining = n_steps;
+    pos->steps = 0;
+    pos->cur = 0;
+    pos->err = 0;
+}
+
 template <int NF, typename Real>
 int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_km, int64_t n_steps,
                 double dr_km, cudaStream_t stream, unsigned char *base)
 {
-    constexpr int S = Comp<NF>::S, NV = 2 * S;
+    constexpr int S = Comp<NF>::S;
     const int n_pairs = n_E * n_u;
     const int npad = (n_pairs + 63) & ~63;
     const int st = (p->stepper == XF_RK4) ? STEP_RK4 : STEP_EXPH;
@@ -131,32 +152,31 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
         cudaGetLastError();
         return noalloc_fail(XF_E_CUDA, "device query failed");
     }
-    // launch shape: as many co-resident CTAs as the pairs need (one CTA for
-    // small problems), contiguous pair chunks, angle tables in shared memory
-    int G = (n_pairs <= 8 * kern.nt) ? 1 : (n_pairs + kern.nt - 1) / kern.nt;
-    size_t smem = 0;
-    int chunk = 0, span = 0;
-    for (int iter = 0; iter < 4; ++iter) {
-        chunk = (n_pairs + G - 1) / G;
-        span = std::min(n_u, (chunk + n_E - 1) / n_E + 1);
-        smem = 5 * sizeof(double) * (size_t)std::max(span, 1);
-        if (smem > 48 * 1024 &&
-            cudaFuncSetAttribute(kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-            cudaGetLastError();
-            return noalloc_fail(XF_E_UNSUPPORTED, "angle table too large for shared memory");
-        }
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern.fn, kern.nt, smem) != cudaSuccess || occ < 1) {
-            cudaGetLastError();
-            return noalloc_fail(XF_E_UNSUPPORTED, "integrator kernel cannot be resident");
-        }
-        const int gmax = occ * sms;
-        if (G <= gmax) break;
-        G = gmax;
+    // launch shape: at most one tile per co-resident CTA
+    int occ0 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, kern.fn, kern.nt, 0) != cudaSuccess || occ0 < 1) {
+        cudaGetLastError();
+        return noalloc_fail(XF_E_UNSUPPORTED, "integrator kernel cannot be resident");
     }
-    chunk = (n_pairs + G - 1) / G;
-    span = std::min(n_u, (chunk + n_E - 1) / n_E + 1);
-    smem = 5 * sizeof(double) * (size_t)std::max(span, 1);
+    // one tile per co-resident CTA slot, a multiple of 32 pairs
+    const long long slots = (long long)occ0 * sms;
+    const int TP = (int)std::min<long long>(
+        1 << 20, std::max<long long>(32, ((n_pairs + slots - 1) / slots + 31) / 32 * 32));
+    const int T = (n_pairs + TP - 1) / TP;
+    const int span = std::min(n_u, (TP + n_E - 1) / n_E + 1);
+    size_t smem = (sizeof(Real) == 8 ? 5 * sizeof(double) : 6 * sizeof(float)) * (size_t)std::max(span, 1);
+    smem = (smem + 15) & ~size_t(15);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(XF_E_UNSUPPORTED, "angle table too large for shared memory");
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern.fn, kern.nt, smem) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return noalloc_fail(XF_E_UNSUPPORTED, "integrator kernel cannot be resident");
+    }
+    const int G = std::max(1, std::min(T, occ * sms));
 
     // carve the scratch array
     const size_t plane = align256((size_t)2 * S * npad * sizeof(Real));
@@ -172,17 +192,24 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
     Real *hvac = (Real *)(base + off);
     off += align256(sizeof(Real) * (size_t)n_E * S);
     double *partials = (double *)(base + off);
-    off += align256(sizeof(double) * 2 * (size_t)G * NV);
+    off += align256(sizeof(double) * 2 * (size_t)T * NVMAX);
+    Tile *tiles = (Tile *)(base + off);
+    off += align256(sizeof(Tile) * (size_t)T);
+    int *cta_tiles = (int *)(base + off);
+    off += align256(sizeof(int) * (size_t)(G + 1));
+    Inst *inst = (Inst *)(base + off);
+    off += align256(sizeof(Inst));
+    InstPos *pos = (InstPos *)(base + off);
+    off += align256(sizeof(InstPos));
     double *mom_out = (double *)(base + off);
-    off += align256(sizeof(double) * NV);
-    unsigned char *ctrl = base + off; // bar | err | bad | steps
+    off += align256(sizeof(double) * NVMAX);
+    unsigned char *ctrl = base + off; // bar | err | bad
     off += 256;
     if (off > (size_t)XF_NOALLOC_SCRATCH_BYTES)
         return noalloc_fail(XF_E_TOO_BIG, "working set larger than XF_NOALLOC_SCRATCH_BYTES");
     unsigned *bar = (unsigned *)ctrl;
     int *err = (int *)(ctrl + 64);
     int *bad = (int *)(ctrl + 128);
-    unsigned long long *steps = (unsigned long long *)(ctrl + 192);
 
 #define NA_CUDA(call, what)                                                                         \
     do {                                                                                            \
@@ -215,6 +242,37 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
         hvac, n_E, p->E_min_MeV, dE, K, dm2a, dm2b, std::cos(2.0 * p->theta[0]), std::sin(2.0 * p->theta[0]),
         u[0], u[1], u[2], u[3], u[4], u[5], u[6], u[7], u[8]);
     NA_CUDA(cudaGetLastError(), "table kernel");
+    noalloc_plan_kernel<<<(std::max(T, G + 1) + 127) / 128, 128, 0, stream>>>(tiles, cta_tiles, T, TP, n_pairs, G);
+    NA_CUDA(cudaGetLastError(), "plan kernel");
+    noalloc_pos_kernel<<<1, 1, 0, stream>>>(pos, n_steps);
+    NA_CUDA(cudaGetLastError(), "position kernel");
+
+    // the problem's descriptor (a stack value; the copy is staged before return)
+    Inst d;
+    std::memset(&d, 0, sizeof d);
+    d.n_E = n_E;
+    d.n_u = n_u;
+    d.nf = NF;
+    d.geometry = p->geometry;
+    d.matter = p->matter;
+    d.n_pairs = n_pairs;
+    d.npad = npad;
+    d.R = p->R_nu_km;
+    d.mu0 = p->mu0_per_km;
+    d.du = 1.0 / n_u;
+    d.dE = dE;
+    d.ne_ref = p->ne_ref_cm3;
+    d.r_ref = p->r_ref_km;
+    d.ne_power = p->ne_power;
+    d.nb0 = p->nb0_cm3;
+    d.h_ns = p->h_ns_km;
+    d.Ye = p->Ye;
+    d.gf = std::sqrt(2.0) * 1.1663787e-23 * std::pow(1.973269804e-5, 3) / 1.973269804e-10; // Eq. 3.7
+    d.r0 = r_km;
+    d.h = dr_km;
+    d.tile_begin = 0;
+    d.tile_end = T;
+    NA_CUDA(cudaMemcpyAsync(inst, &d, sizeof d, cudaMemcpyHostToDevice, stream), "copy descriptor");
 
     // caller's packed state -> component-major working buffers
     LayoutArgs la;
@@ -230,45 +288,26 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
 
     // the persistent integrator, in launches of at most 65536 steps
     const long long kChunk = 1ll << 16;
-    long long k0 = 0;
-    int cur = 0;
-    while (k0 < n_steps) {
-        const long long m = std::min<long long>(n_steps - k0, kChunk);
+    for (long long done = 0; done < n_steps;) {
+        const long long m = std::min<long long>(n_steps - done, kChunk);
         RunArgs a;
         std::memset(&a, 0, sizeof a);
-        a.n_E = n_E;
-        a.n_u = n_u;
-        a.n_pairs = n_pairs;
-        a.npad = npad;
-        a.geometry = p->geometry;
-        a.matter = p->matter;
-        a.pairs_per_cta = chunk;
+        a.inst = inst;
+        a.tiles = tiles;
+        a.cta_tiles = cta_tiles;
+        a.n_inst = 1;
+        a.n_tiles = T;
         a.span_max = span;
-        a.R = p->R_nu_km;
-        a.mu0 = p->mu0_per_km;
-        a.du = 1.0 / n_u;
-        a.dE = dE;
-        a.ne_ref = p->ne_ref_cm3;
-        a.r_ref = p->r_ref_km;
-        a.ne_power = p->ne_power;
-        a.nb0 = p->nb0_cm3;
-        a.h_ns = p->h_ns_km;
-        a.Ye = p->Ye;
-        a.gf = std::sqrt(2.0) * 1.1663787e-23 * std::pow(1.973269804e-5, 3) / 1.973269804e-10; // Eq. 3.7
-        a.r0 = r_km;
-        a.h = dr_km;
-        a.k0 = k0;
         a.n_steps = m;
-        a.cur = cur;
         a.hvac = hvac;
         a.rho0 = rho0;
         a.rho1 = rho1;
         a.aux = aux;
         a.partials = partials;
         a.mom_out = mom_out;
+        a.pos = pos;
         a.bar = bar;
         a.err = err;
-        a.steps_done = steps;
         a.timeout_ns = 2000000000ull;
         a.skip_cta = -1;
         NA_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), stream), "clear barrier");
@@ -276,25 +315,24 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
         cudaError_t e = (G > 1) ? cudaLaunchCooperativeKernel(kern.fn, dim3(G), dim3(kern.nt), args, smem, stream)
                                 : cudaLaunchKernel(kern.fn, dim3(1), dim3(kern.nt), args, smem, stream);
         NA_CUDA(e, "launch of the integrator kernel");
-        k0 += m;
-        cur ^= (int)(m & 1);
+        done += m;
     }
 
     int h_err = 0, h_bad = 0;
-    unsigned long long h_steps = 0;
+    InstPos h_pos;
     NA_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, stream), "read error word");
     NA_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, stream), "read flag");
-    NA_CUDA(cudaMemcpyAsync(&h_steps, steps, sizeof(h_steps), cudaMemcpyDeviceToHost, stream), "read step count");
+    NA_CUDA(cudaMemcpyAsync(&h_pos, pos, sizeof(InstPos), cudaMemcpyDeviceToHost, stream), "read progress");
     NA_CUDA(cudaStreamSynchronize(stream), "stream synchronize");
     if (h_bad) return noalloc_fail(XF_E_STATE, "input state contains non-finite values");
     if (h_err & ERR_BARRIER) return noalloc_fail(XF_E_BARRIER_TIMEOUT, "grid barrier timed out; output not written");
 
     // working buffers -> caller's packed state (the buffer of the last step taken)
-    Real *last = (h_steps & 1ull) ? rho1 : rho0;
+    Real *last = h_pos.cur ? rho1 : rho0;
     state_to_pack_kernel<NF, Real><<<egrid, 256, 0, stream>>>(la, last, trace, rho_dev);
     NA_CUDA(cudaGetLastError(), "layout kernel");
     NA_CUDA(cudaStreamSynchronize(stream), "stream synchronize");
-    if (h_err & ERR_NONFINITE)
+    if (h_pos.err & ERR_NONFINITE)
         return noalloc_fail(XF_E_NONFINITE, "non-finite moments; output holds the last finite state");
 #undef NA_CUDA
     return XF_OK;

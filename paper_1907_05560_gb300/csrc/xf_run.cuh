@@ -1,22 +1,26 @@
-// xf_run.cuh -- the persistent fused integrator kernel.
+// xf_run.cuh -- the persistent fused integrator kernel (one or many problems).
 //
-// One cooperative launch advances one problem by n_steps fixed radial steps.
-// Every integrator stage is one pass over the CTA's (u, E) pairs (both species
-// of a pair are handled by the same thread):
+// One cooperative launch advances every active problem ("instance") of a
+// pack by up to n_steps fixed radial steps.  Each instance is cut into tiles
+// of at most TP (angle, energy) pairs (a multiple of 32); the CTAs of the grid take
+// contiguous runs of tiles.  Every integrator stage is one pass over the tiles:
 //
-//   1. each thread updates its pairs (Hamiltonian assembly + RK4 stage or
-//      exact propagator) from the moments M0, M1 of the stage input, and
-//      accumulates the weighted nu-nu sums of the stage output (Eq. 3.13)
-//   2. fixed-order reduction: per thread (pairs in index order) -> warp
-//      shuffle tree -> CTA (warps in order) -> one partial per CTA in global
-//   3. grid barrier (bounded spin on a global counter; times out with an
-//      error flag instead of hanging)
-//   4. every CTA sums all CTA partials in the same fixed order, so every CTA
-//      holds bitwise identical M0, M1 for the next stage
+//   1. for each of its tiles a CTA sums the partials of all tiles of the
+//      tile's instance in tile order (the moments M0, M1 of the stage input,
+//      Eq. 3.13), builds the per-angle tables of the tile (weights, cos theta,
+//      dl/dr, path length) and updates every pair (both species); each thread
+//      accumulates the weighted nu-nu sums of the stage output
+//   2. the tile's sums are reduced in fixed order (thread, warp shuffle tree,
+//      warps in order) into one partial per tile in global memory
+//   3. grid barrier (bounded spin; times out with an error flag, never hangs)
 //
+// An instance's moments depend only on its own tiles: not on the grid size and
+// not on the other instances packed with it, so a problem gives bitwise the
+// same result alone and inside a batch (same tile size, threads and precision).
 // RK4 needs 4 stages per step, the predictor-corrector (Sec. 4.2.3, Listing
-// 5.1 S1-S3) needs 2.  The reduction tree depends only on the launch shape,
-// so results are deterministic run to run.
+// 5.1 S1-S3) needs 2.  FP32 variants accumulate a warp's sums in FP32 and
+// everything above the warp in FP64 (a warp-wide FP64 instruction occupies the
+// SM's FP64 pipe for 16 cycles on this GPU).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -30,27 +34,49 @@ enum { GEOM_BULB = 0, GEOM_MU_R4 = 1, GEOM_SA = 2, GEOM_CONST = 3 };
 enum { MAT_NONE = 0, MAT_POWER = 1, MAT_EXP = 2 };
 enum { STEP_RK4 = 0, STEP_EXPH = 1 };
 enum { ERR_NONFINITE = 1, ERR_BARRIER = 2 };
+constexpr int NVMAX = 16; // 2 (n_f^2 - 1) for three flavors
 
-// Kernel arguments (one problem).  State planes are component-major:
-// element (c, s, p) of a state buffer is at ((c * 2 + s) * npad + p).
-struct RunArgs {
-    int n_E, n_u, n_pairs, npad;
-    int geometry, matter;
-    int pairs_per_cta, span_max;
+// One problem of a pack.  Its state buffers are component-major planes:
+// element (c, s, p) at state_off + (c * 2 + s) * npad + p.
+struct Inst {
+    int n_E, n_u, nf, geometry;
+    int matter, n_pairs, npad, hvac_off;
+    long long state_off;
     double R, mu0, du, dE;
-    double ne_ref, r_ref, ne_power, nb0, h_ns, Ye, gf; // gf = sqrt(2) G_F in km^-1 cm^3
-    double r0, h;             // step k of this launch starts at r0 + (k0 + k) h
-    long long k0, n_steps;
-    int cur;                  // buffer (0/1) holding the input state
-    const void *hvac;         // Real [n_E][S]
-    void *rho0, *rho1, *aux;  // Real state buffers
-    double *partials;         // [2][grid][2S]
-    double *mom_out;          // [2S] M0 | M1 of the final state (dE applied)
-    unsigned *bar;            // barrier counter, zero at launch
-    int *err;                 // error bits
-    unsigned long long *steps_done; // running total, incremented by CTA 0 at exit
+    double ne_ref, r_ref, ne_power, nb0, h_ns, Ye, gf;
+    double r0, h;           // step k of the run starts at r0 + k h
+    int tile_begin, tile_end;
+};
+
+// Progress of an instance, kept on the device and advanced by the kernel, so
+// that a launch can be replayed (CUDA graph) without host updates.
+struct InstPos {
+    long long k0;           // steps taken since (r0, h) were set
+    long long remaining;    // steps still requested
+    unsigned long long steps; // steps taken in total (reported to the host)
+    int cur;                // buffer (0/1) holding the current state
+    int err;                // ERR_NONFINITE once the instance stopped
+};
+
+struct Tile {
+    int inst, p0, np, pad_;
+};
+
+struct RunArgs {
+    const Inst *inst;
+    const Tile *tiles;
+    const int *cta_tiles;   // [grid + 1]: CTA c processes tiles [cta_tiles[c], cta_tiles[c+1])
+    int n_inst, n_tiles, span_max, pad_;
+    long long n_steps;      // max over instances
+    const void *hvac;       // Real tables, instance i at hvac_off
+    void *rho0, *rho1, *aux; // Real state arenas
+    double *partials;       // [2][n_tiles][NVMAX]
+    double *mom_out;        // [n_inst][NVMAX] M0 | M1 of each instance's final state (dE applied)
+    InstPos *pos;           // [n_inst] progress (read and advanced by the kernel)
+    unsigned *bar;          // barrier counter, zero at launch
+    int *err;               // launch-wide error bits (barrier)
     unsigned long long timeout_ns;
-    int skip_cta;             // test hook: this CTA leaves at its first barrier (-1: none)
+    int skip_cta;           // test hook: this CTA leaves at its first barrier (-1: none)
 };
 
 __device__ __forceinline__ unsigned long long gtimer()
@@ -109,14 +135,14 @@ __device__ __forceinline__ bool grid_barrier(const RunArgs &a, unsigned k, int *
     return *s_flag != 0;
 }
 
-__device__ __forceinline__ double matter_A(const RunArgs &a, double r)
+__device__ __forceinline__ double matter_A(const Inst &a, double r)
 {
     if (a.matter == MAT_POWER) return a.gf * a.ne_ref * pow(a.r_ref / r, a.ne_power);
     if (a.matter == MAT_EXP) return a.gf * a.Ye * a.nb0 * exp(-(r - a.R) / a.h_ns);
     return 0.0;
 }
 
-__device__ __forceinline__ double mu_eff(const RunArgs &a, double r)
+__device__ __forceinline__ double mu_eff(const Inst &a, double r)
 {
     double x = a.R / r, x2 = x * x;
     if (a.geometry == GEOM_MU_R4) return a.mu0 * x2 * x2;
@@ -128,15 +154,36 @@ __device__ __forceinline__ double mu_eff(const RunArgs &a, double r)
 }
 
 // cos(theta) of trajectory j at radius r (Eq. 3.14), u_j = (j + 1/2) du.
-__device__ __forceinline__ double cos_u(const RunArgs &a, int j, double r)
+__device__ __forceinline__ double cos_u(const Inst &a, int j, double r)
 {
     double x = a.R / r;
     return sqrt(1.0 - x * x * ((j + 0.5) * a.du));
 }
 
-// Table slots (each span_max doubles): 0 gamma (G = mu (M0 - gamma M1)),
-// 1 kappa = dl/dr, 2 weight a (M0), 3 weight b (M1), 4 dl (step path length).
-__device__ inline void build_rhs_table(const RunArgs &a, double *tb, int j_lo, int span, double r)
+// Per-tile tables in shared memory, each slot span_max entries of Real,
+// computed in FP64 and stored in the kernel's precision: 0 gamma
+// (G = mu (M0 - gamma M1)), 1 kappa = dl/dr, 2 weight a (M0), 3 weight b (M1),
+// 4 dl (path length of the step; FP32 kernels keep dl as hi in slot 4 and lo
+// in slot 5, see StepLen).
+template <typename Real> struct TabSlots;
+template <> struct TabSlots<double> { static constexpr int n = 5; };
+template <> struct TabSlots<float> { static constexpr int n = 6; };
+
+__device__ __forceinline__ void store_dl(double *tb, int smax, int q, double dl) { tb[4 * smax + q] = dl; }
+__device__ __forceinline__ void store_dl(float *tb, int smax, int q, double dl)
+{
+    const StepLen<float> d = make_step_len(dl, (float *)nullptr);
+    tb[4 * smax + q] = d.hi;
+    tb[5 * smax + q] = d.lo;
+}
+__device__ __forceinline__ StepLen<double> load_dl(const double *tb, int smax, int q) { return {tb[4 * smax + q]}; }
+__device__ __forceinline__ StepLen<float> load_dl(const float *tb, int smax, int q)
+{
+    return {tb[4 * smax + q], tb[5 * smax + q]};
+}
+
+template <typename Real>
+__device__ inline void build_rhs_table(const Inst &a, Real *tb, int smax, int j_lo, int span, double r)
 {
     for (int q = threadIdx.x; q < span; q += blockDim.x) {
         int j = j_lo + q;
@@ -146,12 +193,13 @@ __device__ inline void build_rhs_table(const RunArgs &a, double *tb, int j_lo, i
             g = c;
             k = 1.0 / c;
         }
-        tb[0 * a.span_max + q] = g;
-        tb[1 * a.span_max + q] = k;
+        tb[0 * smax + q] = (Real)g;
+        tb[1 * smax + q] = (Real)k;
     }
 }
 // weights of the nu-nu sums at radius r (Eq. 3.13-3.15)
-__device__ inline void build_weight_table(const RunArgs &a, double *tb, int j_lo, int span, double r)
+template <typename Real>
+__device__ inline void build_weight_table(const Inst &a, Real *tb, int smax, int j_lo, int span, double r)
 {
     for (int q = threadIdx.x; q < span; q += blockDim.x) {
         int j = j_lo + q;
@@ -164,13 +212,14 @@ __device__ inline void build_weight_table(const RunArgs &a, double *tb, int j_lo
         } else if (a.geometry == GEOM_MU_R4) {
             wb = a.du * cos_u(a, j, r);
         }
-        tb[2 * a.span_max + q] = wa;
-        tb[3 * a.span_max + q] = wb;
+        tb[2 * smax + q] = (Real)wa;
+        tb[3 * smax + q] = (Real)wb;
     }
 }
 // exact path length from r to r + h along trajectory j (Eq. 3.3, l = r cos):
 // l(r+h) - l(r) = h (2r + h) / (l(r) + l(r+h)), free of cancellation.
-__device__ inline void build_dl_table(const RunArgs &a, double *tb, int j_lo, int span, double r, double h)
+template <typename Real>
+__device__ inline void build_dl_table(const Inst &a, Real *tb, int smax, int j_lo, int span, double r, double h)
 {
     for (int q = threadIdx.x; q < span; q += blockDim.x) {
         int j = j_lo + q;
@@ -179,18 +228,27 @@ __device__ inline void build_dl_table(const RunArgs &a, double *tb, int j_lo, in
             double l0 = r * cos_u(a, j, r), l1 = (r + h) * cos_u(a, j, r + h);
             dl = h * (2.0 * r + h) / (l0 + l1);
         }
-        tb[4 * a.span_max + q] = dl;
+        store_dl(tb, smax, q, dl);
     }
 }
 
-// Reduce per-thread partial sums m[NV] over the CTA in fixed order and write
-// the CTA partial to part[blockIdx.x * NV + c].
-template <int NV, int NT>
-__device__ __forceinline__ void cta_partial(double *m, double (*s_w)[NV], double *part)
+// Shared per-CTA scratch of the kernel.
+struct Shared {
+    double M[NVMAX];        // moments (dE applied) of the current tile's instance
+    double scr[256];        // reduction scratch (>= NT)
+    double w[8][NVMAX];     // per-warp sums (NT <= 256)
+    double A, mu;           // stage scalars of the current tile's instance
+    int flag, m_inst;       // barrier flag; instance whose moments sit in M
+};
+
+// Reduce per-thread partial sums over the CTA in fixed order: warp shuffle
+// tree in Acc precision, warps in order in FP64; writes NV doubles to part.
+template <int NV, int NT, typename Acc>
+__device__ __forceinline__ void cta_partial(Acc *m, Shared &sh, double *part)
 {
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
-        double v = m[c];
+        Acc v = m[c];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
         m[c] = v;
@@ -198,43 +256,36 @@ __device__ __forceinline__ void cta_partial(double *m, double (*s_w)[NV], double
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0)
 #pragma unroll
-        for (int c = 0; c < NV; ++c) s_w[w][c] = m[c];
+        for (int c = 0; c < NV; ++c) sh.w[w][c] = (double)m[c];
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
 #pragma unroll
-        for (int q = 0; q < NT / 32; ++q) s += s_w[q][threadIdx.x];
-        __stcg(part + (size_t)blockIdx.x * NV + threadIdx.x, s);
+        for (int q = 0; q < NT / 32; ++q) s += sh.w[q][threadIdx.x];
+        __stcg(part + threadIdx.x, s);
     }
+    __syncthreads();
 }
 
-// Sum the CTA partials of all CTAs in fixed order; result (times dE) in s_M.
-template <int NV, int NT>
-__device__ __forceinline__ void grid_total(const double *part, int G, double dE, double *s_M,
-                                           double *s_scr)
+// Moments of an instance: the partials of its tiles [t0, t1) summed in tile
+// order (times dE), written to sh.M.
+template <int NT>
+__device__ __forceinline__ void instance_total(const double *part, int t0, int t1, int nv, double dE, Shared &sh)
 {
-    constexpr int LG = NT / NV; // threads per component
+    constexpr int LG = NT / NVMAX; // threads per component
     const int t = threadIdx.x, c = t / LG, k = t % LG;
     double acc = 0.0;
-    if (c < NV)
-        for (int g = k; g < G; g += LG) acc += __ldcg(part + (size_t)g * NV + c);
-    s_scr[t] = acc;
+    if (c < nv)
+        for (int g = t0 + k; g < t1; g += LG) acc += __ldcg(part + (size_t)g * NVMAX + c);
+    sh.scr[t] = acc;
     __syncthreads();
-    if (t < NV) {
+    if (t < nv) {
         double s = 0.0;
-        for (int q = 0; q < LG; ++q) s += s_scr[t * LG + q];
-        s_M[t] = s * dE;
+#pragma unroll
+        for (int q = 0; q < LG; ++q) s += sh.scr[t * LG + q];
+        sh.M[t] = s * dE;
     }
     __syncthreads();
-}
-
-template <int NV>
-__device__ __forceinline__ bool all_finite(const double *s_M)
-{
-    bool ok = true;
-#pragma unroll
-    for (int c = 0; c < NV; ++c) ok = ok && isfinite(s_M[c]);
-    return ok;
 }
 
 template <typename Real, int S>
@@ -251,192 +302,329 @@ __device__ __forceinline__ void store_state(Real *buf, int npad, int s, int p, c
 }
 
 // Accumulate the weighted nu-nu sums of one pair's stage output.
-template <int NF, typename Real>
-__device__ __forceinline__ void accum(const Real *tn, const Real *tb, double wa, double wb, double *m)
+template <int NF, typename Real, typename Acc>
+__device__ __forceinline__ void accum(const Real *tn, const Real *tb, Acc wa, Acc wb, Acc *m)
 {
     constexpr int S = Comp<NF>::S;
     Real d[S];
     nu_minus_conj_nubar<NF, Real>(tn, tb, d);
 #pragma unroll
     for (int c = 0; c < S; ++c) {
-        double dc = (double)d[c];
+        Acc dc = (Acc)d[c];
         m[c] += wa * dc;
         m[S + c] += wb * dc;
     }
 }
 
+// The fields of an instance a tile's inner loop needs, held in registers.
+template <typename Real>
+struct TileView {
+    const Real *cur, *hvac;
+    Real *nxt, *aux;
+    int n_E, npad, p0, p1, j_lo;
+    double h;
+};
+
+// One stage of one tile: update every pair, accumulate and reduce the sums.
 template <int NF, int STEP, typename Real, int NT>
-__global__ void __launch_bounds__(NT) xf_run_kernel(RunArgs a)
+__device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int st, const Real *tb, Shared &sh,
+                                           double *part_out)
 {
     constexpr int S = Comp<NF>::S, NV = 2 * S;
-    extern __shared__ double s_tab[];
-    __shared__ double s_M[NV];
-    __shared__ double s_scr[NT];
-    __shared__ double s_w[NT / 32][NV];
-    __shared__ int s_flag;
-
-    const int G = gridDim.x;
-    const int p_begin = blockIdx.x * a.pairs_per_cta;
-    const int p_end = min(p_begin + a.pairs_per_cta, a.n_pairs);
-    const int j_lo = (p_begin < a.n_pairs) ? p_begin / a.n_E : 0;
-    const int span = (p_begin < p_end) ? (p_end - 1) / a.n_E - j_lo + 1 : 0;
-    const Real *hvac = (const Real *)a.hvac;
-    Real *const buf0 = (Real *)a.rho0, *const buf1 = (Real *)a.rho1;
-    Real *aux = (Real *)a.aux;
-    unsigned nbar = 0;
-
-    // an earlier launch on this ctx failed: leave the state untouched
-    if (threadIdx.x == 0) s_flag = *(volatile int *)a.err;
-    __syncthreads();
-    if (s_flag) return;
-
-    // ---- prologue: moments of the input state at r0
-    {
-        build_weight_table(a, s_tab, j_lo, span, a.r0 + (double)a.k0 * a.h);
-        __syncthreads();
-        double m[NV];
+    using Acc = Real; // warp-level accumulation precision
+    const double h = v.h;
+    const double mu = sh.mu;
+    const Real A = (Real)sh.A;
+    Real M0[S], M1[S];
 #pragma unroll
-        for (int c = 0; c < NV; ++c) m[c] = 0.0;
-        const Real *in = a.cur ? buf1 : buf0;
-        for (int p = p_begin + threadIdx.x; p < p_end; p += NT) {
-            const int q = p / a.n_E - j_lo;
-            Real tn[S], tb[S];
-            load_state<Real, S>(in, a.npad, 0, p, tn);
-            load_state<Real, S>(in, a.npad, 1, p, tb);
-            accum<NF, Real>(tn, tb, s_tab[2 * a.span_max + q], s_tab[3 * a.span_max + q], m);
+    for (int c = 0; c < S; ++c) {
+        M0[c] = (Real)(mu * sh.M[c]);
+        M1[c] = (Real)(mu * sh.M[S + c]);
+    }
+    Acc m[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) m[c] = Acc(0);
+
+    for (int p = v.p0 + threadIdx.x; p < v.p1; p += NT) {
+        const int j = p / v.n_E, e = p - j * v.n_E, q = j - v.j_lo;
+        const Real gam = tb[q];
+        Real g[S], hv[S], hn[S], hb[S];
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            g[c] = M0[c] - gam * M1[c];
+            hv[c] = v.hvac[(size_t)e * S + c];
         }
-        cta_partial<NV, NT>(m, s_w, a.partials);
-        if (!grid_barrier(a, ++nbar, &s_flag)) return;
-        grid_total<NV, NT>(a.partials, G, a.dE, s_M, s_scr);
-        if (!all_finite<NV>(s_M)) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.err, ERR_NONFINITE);
-            return;
+        hamiltonians<NF, Real>(hv, A, g, hn, hb);
+        Real on[S], ob[S]; // stage outputs (nu, nubar)
+        if constexpr (STEP == STEP_RK4) {
+            const Real kap = tb[smax + q];
+            const Real cy = (Real)((st == 2) ? h : 0.5 * h);
+            const Real cb = (Real)((st == 0 || st == 3) ? h / 6.0 : h / 3.0);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                Real y[S], kk[S], rn[S], bb[S];
+                if (st == 0) load_state<Real, S>(v.cur, v.npad, s, p, y);
+                else load_state<Real, S>(v.aux, v.npad, s, p, y);
+                comm<NF, Real>(s == 0 ? hn : hb, y, kk);
+#pragma unroll
+                for (int c = 0; c < S; ++c) kk[c] *= kap;
+                if (st == 0) {
+#pragma unroll
+                    for (int c = 0; c < S; ++c) rn[c] = y[c];
+                } else if (st < 3) {
+                    load_state<Real, S>(v.cur, v.npad, s, p, rn);
+                }
+                if (st == 0) {
+#pragma unroll
+                    for (int c = 0; c < S; ++c) bb[c] = rn[c] + cb * kk[c];
+                } else {
+                    load_state<Real, S>(v.nxt, v.npad, s, p, bb);
+#pragma unroll
+                    for (int c = 0; c < S; ++c) bb[c] += cb * kk[c];
+                }
+                store_state<Real, S>(v.nxt, v.npad, s, p, bb);
+                Real *o = (s == 0) ? on : ob;
+                if (st < 3) {
+#pragma unroll
+                    for (int c = 0; c < S; ++c) o[c] = rn[c] + cy * kk[c];
+                    store_state<Real, S>(v.aux, v.npad, s, p, o);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < S; ++c) o[c] = bb[c];
+                }
+            }
+        } else {
+            const StepLen<Real> dl = load_dl(tb, smax, q);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                Real rn[S], pr[S];
+                load_state<Real, S>(v.cur, v.npad, s, p, rn);
+                prop<NF, Real>(s == 0 ? hn : hb, dl, rn, pr);
+                Real *o = (s == 0) ? on : ob;
+                if (st == 0) {
+#pragma unroll
+                    for (int c = 0; c < S; ++c) o[c] = pr[c];
+                    store_state<Real, S>(v.aux, v.npad, s, p, o);
+                } else {
+                    Real pp[S];
+                    load_state<Real, S>(v.aux, v.npad, s, p, pp);
+#pragma unroll
+                    for (int c = 0; c < S; ++c) o[c] = Real(0.5) * (pp[c] + pr[c]);
+                    store_state<Real, S>(v.nxt, v.npad, s, p, o);
+                }
+            }
+        }
+        accum<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], m);
+    }
+    cta_partial<NV, NT, Acc>(m, sh, part_out);
+}
+
+// Prologue for one tile: weighted sums of the input state.
+template <int NF, typename Real, int NT>
+__device__ __forceinline__ void prologue_tile(const TileView<Real> v, int smax, const Real *tb, Shared &sh,
+                                              double *part_out)
+{
+    constexpr int S = Comp<NF>::S, NV = 2 * S;
+    using Acc = Real;
+    Acc m[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) m[c] = Acc(0);
+    for (int p = v.p0 + threadIdx.x; p < v.p1; p += NT) {
+        const int q = p / v.n_E - v.j_lo;
+        Real tn[S], tb_[S];
+        load_state<Real, S>(v.cur, v.npad, 0, p, tn);
+        load_state<Real, S>(v.cur, v.npad, 1, p, tb_);
+        accum<NF, Real, Acc>(tn, tb_, tb[2 * smax + q], tb[3 * smax + q], m);
+    }
+    cta_partial<NV, NT, Acc>(m, sh, part_out);
+}
+
+__device__ __forceinline__ bool moments_finite(const double *M, int nv)
+{
+    bool ok = true;
+    for (int c = 0; c < nv; ++c) ok = ok && isfinite(M[c]);
+    return ok;
+}
+
+// Steps instance i takes in this launch (read at each visit; once the owner
+// of its first tile advances the record, later visits see 0 and skip it).
+__device__ __forceinline__ long long launch_steps(const RunArgs &a, const InstPos &ps)
+{
+    if (ps.err) return 0;
+    return ps.remaining < a.n_steps ? ps.remaining : a.n_steps;
+}
+
+template <typename Real>
+__device__ __forceinline__ TileView<Real> make_view(const RunArgs &a, const Inst &in, const InstPos &ps,
+                                                    const Tile &tl, long long k)
+{
+    TileView<Real> v;
+    Real *const b0 = (Real *)a.rho0 + in.state_off, *const b1 = (Real *)a.rho1 + in.state_off;
+    const bool odd = ((ps.cur + (int)(k & 1)) & 1) != 0;
+    v.cur = odd ? b1 : b0;
+    v.nxt = odd ? b0 : b1;
+    v.aux = (Real *)a.aux + in.state_off;
+    v.hvac = (const Real *)a.hvac + in.hvac_off;
+    v.n_E = in.n_E;
+    v.npad = in.npad;
+    v.p0 = tl.p0;
+    v.p1 = tl.p0 + tl.np;
+    v.j_lo = tl.p0 / in.n_E;
+    v.h = in.h;
+    return v;
+}
+
+// Record the step count and final moments of an instance whose last step
+// has just completed (part_in holds the partials of its final state).
+// Advance an instance's progress record by `done` steps (called once per
+// instance and launch, by the CTA that owns its first tile).
+__device__ __forceinline__ void advance(InstPos *pp, long long done, int err)
+{
+    pp->k0 += done;
+    pp->remaining -= done;
+    pp->steps += (unsigned long long)done;
+    pp->cur ^= (int)(done & 1);
+    if (err) {
+        pp->err = err;
+        pp->remaining = 0;
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void finish_instance(const RunArgs &a, const Inst &in, int inst, long long n,
+                                                const double *part_in, int nv, Shared &sh)
+{
+    __syncthreads();
+    instance_total<NT>(part_in, in.tile_begin, in.tile_end, nv, in.dE, sh);
+    if (threadIdx.x == 0) {
+        sh.m_inst = -1;
+        if (moments_finite(sh.M, nv)) {
+            for (int c = 0; c < nv; ++c) a.mom_out[(size_t)inst * NVMAX + c] = sh.M[c];
+            advance(a.pos + inst, n, 0);
+        } else {
+            // the last step's output is not finite: its input is the last finite state
+            advance(a.pos + inst, n - 1, ERR_NONFINITE);
         }
     }
+    __syncthreads();
+}
+
+// NFM: 2 or 3 (every instance has that many flavors) or 0 (mixed pack).
+template <int NFM, int STEP, typename Real, int NT>
+__global__ void __launch_bounds__(NT) xf_run_kernel(RunArgs a)
+{
+    extern __shared__ double s_dyn[];
+    Real *const s_tab = (Real *)s_dyn;
+    __shared__ Shared sh;
+    const int t_begin = a.cta_tiles[blockIdx.x], t_end = a.cta_tiles[blockIdx.x + 1];
+    const int smax = a.span_max;
+    unsigned nbar = 0;
+
+    // an earlier launch on these buffers failed at a barrier: touch nothing
+    if (threadIdx.x == 0) sh.flag = *(volatile int *)a.err;
+    __syncthreads();
+    if (sh.flag) return;
+
+    // ---- prologue: weighted sums of every tile's input state at its start radius
+    for (int t = t_begin; t < t_end; ++t) {
+        const Tile tl = a.tiles[t];
+        const Inst &in = a.inst[tl.inst];
+        const InstPos ps = a.pos[tl.inst];
+        if (launch_steps(a, ps) <= 0) continue;
+        const int nf = NFM ? NFM : in.nf;
+        const TileView<Real> v = make_view<Real>(a, in, ps, tl, 0);
+        const int span = (v.p1 - 1) / in.n_E - v.j_lo + 1;
+        __syncthreads();
+        build_weight_table(in, s_tab, smax, v.j_lo, span, in.r0 + (double)ps.k0 * in.h);
+        __syncthreads();
+        double *out = a.partials + (size_t)t * NVMAX;
+        if (nf == 2) {
+            if constexpr (NFM != 3) prologue_tile<2, Real, NT>(v, smax, s_tab, sh, out);
+        } else {
+            if constexpr (NFM != 2) prologue_tile<3, Real, NT>(v, smax, s_tab, sh, out);
+        }
+    }
+    if (!grid_barrier(a, ++nbar, &sh.flag)) return;
 
     constexpr int NSTAGE = (STEP == STEP_RK4) ? 4 : 2;
     for (long long k = 0; k < a.n_steps; ++k) {
-        // radii from the global step index, so that a run split over several
-        // launches evaluates the same radii as one launch
-        const double kk = (double)(a.k0 + k), h = a.h;
-        const double r = a.r0 + kk * h, r_half = a.r0 + (kk + 0.5) * h, r_next = a.r0 + (kk + 1.0) * h;
-        const bool odd = ((a.cur + (int)(k & 1)) & 1) != 0;
-        const Real *cur = odd ? buf1 : buf0;
-        Real *nxt = odd ? buf0 : buf1;
 #pragma unroll 1
         for (int st = 0; st < NSTAGE; ++st) {
-            // radius of the right-hand side and of the stage output
-            double r_rhs, r_out;
-            if constexpr (STEP == STEP_RK4) {
-                r_rhs = (st == 0) ? r : (st == 3 ? r_next : r_half);
-                r_out = (st <= 1) ? r_half : r_next;
-            } else {
-                r_rhs = (st == 0) ? r : r_next;
-                r_out = r_next;
-            }
-            __syncthreads();
-            build_rhs_table(a, s_tab, j_lo, span, r_rhs);
-            build_weight_table(a, s_tab, j_lo, span, r_out);
-            if (STEP == STEP_EXPH && st == 0) build_dl_table(a, s_tab, j_lo, span, r, h);
-            const double mu = mu_eff(a, r_rhs);
-            const Real A = (Real)matter_A(a, r_rhs);
-            __syncthreads();
-            Real M0[S], M1[S];
-#pragma unroll
-            for (int c = 0; c < S; ++c) {
-                M0[c] = (Real)(mu * s_M[c]);
-                M1[c] = (Real)(mu * s_M[S + c]);
-            }
-            double m[NV];
-#pragma unroll
-            for (int c = 0; c < NV; ++c) m[c] = 0.0;
-
-            for (int p = p_begin + threadIdx.x; p < p_end; p += NT) {
-                const int j = p / a.n_E, e = p - j * a.n_E, q = j - j_lo;
-                const Real gam = (Real)s_tab[q];
-                Real g[S], hv[S], hn[S], hb[S];
-#pragma unroll
-                for (int c = 0; c < S; ++c) {
-                    g[c] = M0[c] - gam * M1[c];
-                    hv[c] = hvac[(size_t)e * S + c];
+            const double *part_in = a.partials + (size_t)((nbar - 1) & 1) * a.n_tiles * NVMAX;
+            double *part_out = a.partials + (size_t)(nbar & 1) * a.n_tiles * NVMAX;
+            if (threadIdx.x == 0) sh.m_inst = -1;
+            for (int t = t_begin; t < t_end; ++t) {
+                const Tile tl = a.tiles[t];
+                const Inst &in = a.inst[tl.inst];
+                const InstPos ps = a.pos[tl.inst];
+                const long long n_i = launch_steps(a, ps);
+                if (n_i <= 0 || k > n_i) continue;
+                const int nf = NFM ? NFM : in.nf, nv = 2 * (nf * nf - 1);
+                if (k == n_i) { // the instance's last step of this launch just completed
+                    if (st == 0 && t == in.tile_begin) finish_instance<NT>(a, in, tl.inst, n_i, part_in, nv, sh);
+                    continue;
                 }
-                hamiltonians<NF, Real>(hv, A, g, hn, hb);
-                Real on[S], ob[S]; // stage outputs (nu, nubar)
+                double *out = part_out + (size_t)t * NVMAX;
+                // moments of the stage input of this tile's instance (once per instance)
+                __syncthreads();
+                if (sh.m_inst != tl.inst) {
+                    instance_total<NT>(part_in, in.tile_begin, in.tile_end, nv, in.dE, sh);
+                    if (threadIdx.x == 0) sh.m_inst = tl.inst;
+                }
+                __syncthreads();
+                if (!moments_finite(sh.M, nv)) {
+                    // The instance stops.  Stage 0 checks the output of the
+                    // previous step: the last finite state is then step k-1's
+                    // input; later stages check intermediates of step k.
+                    // Non-finite partials keep every later stage skipping it.
+                    if (threadIdx.x < NVMAX) __stcg(out + threadIdx.x, (double)NAN);
+                    if (threadIdx.x == 0 && t == in.tile_begin) {
+                        const long long done = (st == 0) ? (k > 0 ? k - 1 : 0) : k;
+                        advance(a.pos + tl.inst, done, ERR_NONFINITE);
+                    }
+                    continue;
+                }
+                const double kk = (double)(ps.k0 + k), h = in.h;
+                const double r = in.r0 + kk * h, r_half = in.r0 + (kk + 0.5) * h, r_next = in.r0 + (kk + 1.0) * h;
+                double r_rhs, r_out;
                 if constexpr (STEP == STEP_RK4) {
-                    const Real kap = (Real)s_tab[a.span_max + q];
-                    const Real cy = (Real)((st == 2) ? h : 0.5 * h);
-                    const Real cb = (Real)((st == 0 || st == 3) ? h / 6.0 : h / 3.0);
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        Real y[S], kk[S], rn[S], bb[S];
-                        if (st == 0) load_state<Real, S>(cur, a.npad, s, p, y);
-                        else load_state<Real, S>(aux, a.npad, s, p, y);
-                        comm<NF, Real>(s == 0 ? hn : hb, y, kk);
-#pragma unroll
-                        for (int c = 0; c < S; ++c) kk[c] *= kap;
-                        if (st == 0) {
-#pragma unroll
-                            for (int c = 0; c < S; ++c) rn[c] = y[c];
-                        } else if (st < 3) {
-                            load_state<Real, S>(cur, a.npad, s, p, rn);
-                        }
-                        if (st == 0) {
-#pragma unroll
-                            for (int c = 0; c < S; ++c) bb[c] = rn[c] + cb * kk[c];
-                        } else {
-                            load_state<Real, S>(nxt, a.npad, s, p, bb);
-#pragma unroll
-                            for (int c = 0; c < S; ++c) bb[c] += cb * kk[c];
-                        }
-                        store_state<Real, S>(nxt, a.npad, s, p, bb);
-                        Real *o = (s == 0) ? on : ob;
-                        if (st < 3) {
-#pragma unroll
-                            for (int c = 0; c < S; ++c) o[c] = rn[c] + cy * kk[c];
-                            store_state<Real, S>(aux, a.npad, s, p, o);
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < S; ++c) o[c] = bb[c];
-                        }
-                    }
+                    r_rhs = (st == 0) ? r : (st == 3 ? r_next : r_half);
+                    r_out = (st <= 1) ? r_half : r_next;
                 } else {
-                    const double dl = s_tab[4 * a.span_max + q];
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        Real rn[S], pr[S];
-                        load_state<Real, S>(cur, a.npad, s, p, rn);
-                        prop<NF, Real>(s == 0 ? hn : hb, dl, rn, pr);
-                        Real *o = (s == 0) ? on : ob;
-                        if (st == 0) {
-#pragma unroll
-                            for (int c = 0; c < S; ++c) o[c] = pr[c];
-                            store_state<Real, S>(aux, a.npad, s, p, o);
-                        } else {
-                            Real pp[S];
-                            load_state<Real, S>(aux, a.npad, s, p, pp);
-#pragma unroll
-                            for (int c = 0; c < S; ++c) o[c] = Real(0.5) * (pp[c] + pr[c]);
-                            store_state<Real, S>(nxt, a.npad, s, p, o);
-                        }
-                    }
+                    r_rhs = (st == 0) ? r : r_next;
+                    r_out = r_next;
                 }
-                accum<NF, Real>(on, ob, s_tab[2 * a.span_max + q], s_tab[3 * a.span_max + q], m);
-            }
-            cta_partial<NV, NT>(m, s_w, a.partials + (size_t)(nbar & 1) * G * NV);
-            if (!grid_barrier(a, ++nbar, &s_flag)) return;
-            grid_total<NV, NT>(a.partials + (size_t)((nbar - 1) & 1) * G * NV, G, a.dE, s_M, s_scr);
-            if (!all_finite<NV>(s_M)) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) {
-                    atomicOr(a.err, ERR_NONFINITE);
-                    atomicAdd(a.steps_done, (unsigned long long)k);
+                const TileView<Real> v = make_view<Real>(a, in, ps, tl, k);
+                const int span = (v.p1 - 1) / in.n_E - v.j_lo + 1;
+                build_rhs_table(in, s_tab, smax, v.j_lo, span, r_rhs);
+                build_weight_table(in, s_tab, smax, v.j_lo, span, r_out);
+                // the step's path lengths serve both stages; a CTA holding several
+                // tiles rebuilds them for every tile
+                if (STEP == STEP_EXPH) build_dl_table(in, s_tab, smax, v.j_lo, span, r, h);
+                if (threadIdx.x == 0) {
+                    sh.mu = mu_eff(in, r_rhs);
+                    sh.A = matter_A(in, r_rhs);
                 }
-                return;
+                __syncthreads();
+                if (nf == 2) {
+                    if constexpr (NFM != 3) stage_tile<2, STEP, Real, NT>(v, smax, st, s_tab, sh, out);
+                } else {
+                    if constexpr (NFM != 2) stage_tile<3, STEP, Real, NT>(v, smax, st, s_tab, sh, out);
+                }
             }
+            if (!grid_barrier(a, ++nbar, &sh.flag)) return;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        atomicAdd(a.steps_done, (unsigned long long)a.n_steps);
-        for (int c = 0; c < NV; ++c) a.mom_out[c] = s_M[c];
+    // instances that ran to the end of the launch
+    const double *part_in = a.partials + (size_t)((nbar - 1) & 1) * a.n_tiles * NVMAX;
+    for (int t = t_begin; t < t_end; ++t) {
+        const Tile tl = a.tiles[t];
+        const Inst &in = a.inst[tl.inst];
+        if (t != in.tile_begin) continue;
+        const long long n_i = launch_steps(a, a.pos[tl.inst]);
+        if (n_i != a.n_steps || n_i <= 0) continue;
+        const int nf = NFM ? NFM : in.nf;
+        finish_instance<NT>(a, in, tl.inst, n_i, part_in, 2 * (nf * nf - 1), sh);
     }
 }
 

@@ -49,6 +49,11 @@ class XFParams(ctypes.Structure):
     ]
 
 
+class XFProblem(ctypes.Structure):
+    _fields_ = [("n_E", ctypes.c_int32), ("n_u", ctypes.c_int32), ("n_flavor", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("params", XFParams)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -80,6 +85,17 @@ SIGNATURES = {
     "xf_launch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
     "xf_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
+    "xf_create_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(XFProblem), ctypes.POINTER(XFAllocator),
+                                       ctypes.POINTER(_P)]),
+    "xf_batch_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "xf_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.c_size_t, ctypes.c_double]),
+    "xf_batch_init_state": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
+    "xf_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.c_size_t, _D,
+                                          ctypes.POINTER(ctypes.c_int64)]),
+    "xf_batch_outputs": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, ctypes.c_size_t]),
+    "xf_batch_step": (ctypes.c_int, [_P, ctypes.c_int64, _D]),
+    "xf_batch_status": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int64), _D]),
     "xf_peak": (ctypes.c_int, [ctypes.c_int, _D]),
     "xf_step_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(XFParams),
                                        _P, ctypes.c_double, ctypes.c_int64, ctypes.c_double, _P]),
@@ -246,7 +262,72 @@ class Context:
         return g.value, t.value, b.value
 
 
-OPT_GRID, OPT_BARRIER_TIMEOUT_NS, OPT_TEST_SKIP_ARRIVAL = 1, 2, 3
+OPT_GRID, OPT_BARRIER_TIMEOUT_NS, OPT_TEST_SKIP_ARRIVAL, OPT_TILE_PAIRS, OPT_GRAPH = 1, 2, 3, 4, 5
+
+
+class Batch(Context):
+    """Several problems advanced together in one persistent launch (a batch
+    xf_ctx).  Problems may differ in size, flavors and physics; stepper and
+    precision are shared."""
+
+    def __init__(self, problems, allocator: str = "torch", stream=None):  # noqa: D401
+        self.L = load()
+        self.problems = list(problems)
+        self.problem = self.problems[0]
+        arr = (XFProblem * len(self.problems))()
+        for k, p in enumerate(self.problems):
+            arr[k].n_E, arr[k].n_u, arr[k].n_flavor, arr[k].reserved = p.n_E, p.n_u, p.n_f, 0
+            arr[k].params = params_from(p)
+        h = _P()
+        self._allocator = _TorchAllocator() if allocator == "torch" else None
+        alloc = ctypes.byref(self._allocator.struct) if self._allocator else None
+        rc = self.L.xf_create_batch(len(self.problems), arr, alloc, ctypes.byref(h))
+        if rc != XF_OK:
+            raise XFError(rc, self.L.xf_last_error(None).decode())
+        self.h = h
+        self.n_f = self.problem.n_f
+        self.n_bins = 2 * self.problem.n_u * self.problem.n_E
+        self.n_doubles = self.n_bins * self.n_f * self.n_f
+        if stream is not None:
+            self.set_stream(stream)
+
+    def __len__(self):
+        return len(self.problems)
+
+    def _size(self, i):
+        p = self.problems[i]
+        return 2 * p.n_u * p.n_E * p.n_f * p.n_f
+
+    def set_state_i(self, i: int, rho: np.ndarray, r_km: float):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        return self._check(self.L.xf_batch_set_state(self.h, i, _dp(rho), rho.size, float(r_km)))
+
+    def init_state_i(self, i: int, r_km: float):
+        return self._check(self.L.xf_batch_init_state(self.h, i, float(r_km)))
+
+    def get_state_i(self, i: int, out: np.ndarray | None = None):
+        rho = out if out is not None else np.empty(self._size(i))
+        r = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        self._check(self.L.xf_batch_get_state(self.h, i, _dp(rho), rho.size, ctypes.byref(r), ctypes.byref(n)))
+        return rho, r.value, n.value
+
+    def outputs_i(self, i: int):
+        p = self.problems[i]
+        nb = 2 * p.n_u * p.n_E
+        a, b, c = np.empty(nb), np.empty(nb), np.empty(nb)
+        self._check(self.L.xf_batch_outputs(self.h, i, _dp(a), _dp(b), _dp(c), nb))
+        return a, b, c
+
+    def step_all(self, n_steps: int, dr_km=None):
+        dr = None if dr_km is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(dr_km, dtype=np.float64), (len(self.problems),)))
+        return self._check(self.L.xf_batch_step(self.h, int(n_steps), _dp(dr) if dr is not None else None))
+
+    def status_i(self, i: int):
+        st, n, r = ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_double(0.0)
+        self._check(self.L.xf_batch_status(self.h, i, ctypes.byref(st), ctypes.byref(n), ctypes.byref(r)))
+        return STATUS.get(st.value, st.value), n.value, r.value
 
 
 PEAK_FP64_FMA, PEAK_FP32_FMA = 0, 1
