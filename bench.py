@@ -248,6 +248,10 @@ def run_xf(args):
     if args.precision == "fp64" and not args.skip_batch:
         batched = run_batched(args, xf, I, torch, stream, flush, barrier, world)
 
+    serving = None
+    if args.precision == "fp64" and not args.skip_serve and rank == 0:
+        serving = run_serving(args, xf, I, torch)
+
     # end to end through the C ABI with host buffers: set_state (H2D) + step + get_state (D2H)
     host = torch.empty(ctx.n_doubles, dtype=torch.float64).pin_memory().numpy()
     rho, _, _ = ctx.get_state(host)
@@ -305,7 +309,7 @@ def run_xf(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "fp32_m64": fp32, "batched": batched, "clocks": clk, "gpu_launches": args.steps,
+            "fp32_m64": fp32, "batched": batched, "serving": serving, "clocks": clk, "gpu_launches": args.steps,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -359,6 +363,67 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
             "achieved_tflops_fp32": flops / avg / 1e12}
 
 
+def run_serving(args, xf, I, torch):
+    """The served job stream: Poisson arrivals of two-flavor jobs with the
+    batched ensemble's size distribution (n_u 64-1024, n_E 32-256), 1000-20000
+    steps of h = 0.01 km from 50 km, FP32 bins with FP64 moments; continuous
+    batching in a server with up to 256 resident jobs and a memory budget of
+    up to 150 GB.  Latency = finish - arrival.  Reported at a rate the GPU
+    sustains and, briefly, at the overloaded rate of 200 jobs/s."""
+    import threading
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(150e9, 0.5 * free))
+    out = {}
+    for label, rate, window in (("sustained", args.serve_rate, args.serve_window), ("rate_200", 200.0, 1.0)):
+        arrivals = I.c5_arrivals(rate_per_s=rate, window_s=window, seed=5)
+        srv = xf.Server(max_jobs=256, mem_budget_bytes=budget, chunk_steps=args.serve_chunk)
+        ids, t_sub = [], []
+        t0 = time.perf_counter()
+
+        def feeder():
+            for t_arr, p in arrivals:
+                d = t0 + t_arr - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                ids.append(srv.submit(p))
+                t_sub.append(time.perf_counter())
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        srv.drain(timeout_s=600.0)
+        t_end = time.perf_counter()
+        lat, work = [], 0.0
+        for j, (t_arr, p) in zip(ids, arrivals):
+            meta, _ = srv.poll(j)
+            lat.append(meta["t_done"] - meta["t_submit"])
+            work += p.n_bins * p.n_steps
+        st = srv.stats()
+        srv.close()
+        lat.sort()
+        q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+        out[label] = {"rate_jobs_per_s": rate, "window_s": window, "jobs": len(ids), "p50_s": q(0.50),
+                      "p99_s": q(0.99), "value": work / (t_end - t0), "unit": UNIT,
+                      "gpu_busy_value": st["bin_steps"] / max(st["busy_s"], 1e-9),
+                      "max_resident": st["max_resident"], "epochs": st["epochs"]}
+    # the same kind of jobs, each alone in FP64 (sample of 3)
+    sample = [p for _, p in I.c5_arrivals(rate_per_s=200.0, window_s=1.0, seed=6)][:3]
+    work, t = 0.0, 0.0
+    for p in sample:
+        q = p.replace(precision=I.FP64)
+        c = xf.Context(q)
+        c.init_state(q.r0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        c.step(q.n_steps, q.h)
+        t += time.perf_counter() - t1
+        work += q.n_bins * q.n_steps
+        c.close()
+    out["alone_fp64"] = {"value": work / t, "unit": UNIT, "jobs": len(sample)}
+    out["budget_bytes"] = budget
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,6 +439,10 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--batch-chunk", type=int, default=10, help="radial steps per batched bench step")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=10.0, help="sustained arrival rate, jobs/s")
+    ap.add_argument("--serve-window", type=float, default=5.0, help="arrival window at the sustained rate, s")
+    ap.add_argument("--serve-chunk", type=int, default=200, help="radial steps per serving epoch")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")

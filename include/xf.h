@@ -228,6 +228,74 @@ int xf_batch_outputs(xf_ctx *ctx, int inst, double *p_surv, double *trace, doubl
 int xf_batch_step(xf_ctx *ctx, int64_t n_steps, const double *dr_km);
 int xf_batch_status(xf_ctx *ctx, int inst, int *status, int64_t *steps_done, double *r_km);
 
+/* ---- serving: a continuous-batching job server ---------------------------
+ * A server owns one pack of `max_jobs` slots and a device arena of
+ * `mem_budget_bytes`, and a scheduler thread that repeats epochs:
+ *   1. admit queued jobs (first come, first served) while a slot is free
+ *      and their state fits the memory budget;
+ *   2. advance every resident job by min(its remaining steps, chunk_steps)
+ *      in one persistent launch;
+ *   3. retire finished jobs (state copied to host if kept), freeing slots
+ *      and memory for the next admissions.
+ * Jobs that arrive while others run are thus admitted between launches and
+ * share the GPU with them.  The server uses a fixed tile size, so a job's
+ * result is the same (bitwise, for equal tile size, stepper and precision)
+ * alone and in any mix.  Timestamps are seconds since xf_server_create. */
+typedef struct xf_server xf_server;
+typedef struct xf_server_cfg {
+    uint32_t size;            /* = sizeof(xf_server_cfg) */
+    int32_t max_jobs;         /* resident slots, >= 1 */
+    int64_t mem_budget_bytes; /* device memory for resident jobs (their blocks) */
+    int64_t chunk_steps;      /* radial steps per epoch, >= 1 */
+    int32_t queue_cap;        /* queued jobs beyond which xf_submit returns XF_E_BUSY */
+    int32_t stepper;          /* shared by all jobs */
+    int32_t precision;        /* shared by all jobs */
+    int32_t n_flavor;         /* 2 or 3 (every job), or 0 (mixed) */
+    int32_t tile_pairs;       /* tile size in pairs (0: 1024) */
+    int32_t reserved;         /* set to 0 */
+} xf_server_cfg;
+typedef struct xf_job {
+    xf_problem problem;       /* its params.stepper / precision must match the server's */
+    double r0_km, dr_km;      /* start radius (>= R_nu) and step size */
+    int64_t n_steps;          /* steps to take, >= 1 */
+    const double *rho0;       /* packed host state at r0_km (copied at submit), or NULL
+                                 for the seeded initial state of xf_init_state */
+    int32_t keep_state;       /* 1: keep the final state for xf_poll */
+    int32_t reserved;         /* set to 0 */
+} xf_job;
+typedef struct xf_job_result {
+    int32_t status;           /* XF_OK, or XF_E_NONFINITE (state = last finite step) */
+    int32_t reserved;
+    int64_t steps_done;
+    double r_km;              /* radius of the final state */
+    double t_submit, t_start, t_done; /* queued, admitted, finished (s) */
+} xf_job_result;
+typedef struct xf_server_stats {
+    int64_t submitted, completed, queued, resident, max_resident;
+    int64_t epochs;
+    double bin_steps;         /* sum over launches of bins x steps taken */
+    double busy_s;            /* time spent in launches */
+    int64_t mem_used_bytes, mem_peak_bytes;
+} xf_server_stats;
+
+/* Create a server (XF_E_ARG on bad configuration); the scheduler thread
+ * starts at once and uses the device current in the calling thread. */
+int xf_server_create(const xf_server_cfg *cfg, xf_server **out);
+/* Queue a job; *job_id identifies it.  XF_E_ARG: invalid job; XF_E_TOO_BIG:
+ * its block exceeds the memory budget; XF_E_BUSY: the queue is full. */
+int xf_submit(xf_server *srv, const xf_job *job, uint64_t *job_id);
+/* XF_PENDING while the job is queued or running.  When finished: XF_OK,
+ * *res filled, the final state copied to rho_out (n_doubles exact; if the job
+ * kept it and rho_out is non-NULL) and the job forgotten.  XF_E_NOTFOUND for
+ * an unknown (or already collected) id. */
+int xf_poll(xf_server *srv, uint64_t job_id, xf_job_result *res, double *rho_out, size_t n_doubles);
+/* Wait until every submitted job has finished, at most timeout_s seconds
+ * (XF_E_TIMEOUT when it runs out). */
+int xf_server_drain(xf_server *srv, double timeout_s);
+int xf_server_get_stats(xf_server *srv, xf_server_stats *st);
+/* Stop the scheduler, drop queued and resident jobs, free everything. */
+int xf_server_destroy(xf_server *srv);
+
 /* Options (xf_set_option), for tuning and testing:
  *   XF_OPT_GRID: persistent grid size in CTAs; 0 = automatic (default).  The
  *     value is clamped to the co-resident maximum and to the tile count.

@@ -17,10 +17,11 @@
 #include "../../include/xf.h"
 #include "xf_aux.cuh"
 #include "xf_kernels.h"
+#include "xf_pack.h"
 
 using namespace xf;
 
-namespace {
+namespace xfp {
 
 // ---- physical constants (CODATA 2018 / PDG), stated for this library -----
 constexpr double kHbarcEvKm = 1.973269804e-10; // hbar c, eV km
@@ -61,72 +62,10 @@ double fermi_dirac(int k, double eta)
 
 thread_local std::string g_create_error;
 
-// Host record of one problem of a pack.
-struct InstHost {
-    int n_E = 0, n_u = 0, nf = 0, S = 0, n_pairs = 0, npad = 0;
-    long long n_bins = 0;
-    xf_params p{};
-    std::vector<double> E, phi, hvac; // tables: E[n_E], phi[4][n_E], hvac[n_E][S]
-    long long state_off = 0;          // Real elements into the state arenas
-    long long trace_off = 0;          // doubles into the trace arena (2 npad)
-    long long phi_off = 0;            // doubles into the phi arena (4 n_E)
-    int hvac_off = 0;                 // Real elements into the table arena
-    int tile_begin = 0, tile_end = 0;
-    // position (host view, valid after a sync): r = r0 + k0 h
-    bool state_valid = false;
-    double r0 = 0.0, h = 0.0;
-    long long k0 = 0, steps = 0;
-    int cur = 0, err = 0;
-};
+} // namespace xfp
 
-} // namespace
 
-struct xf_ctx {
-    std::vector<InstHost> in;
-    int real_bytes = 8, stepper = XF_RK4, nfm = 2;
-    cudaStream_t stream = nullptr;
-    xf_allocator alloc{};
-    bool has_alloc = false;
-    int device = 0, num_sms = 0;
-
-    // arenas
-    void *rho[2] = {nullptr, nullptr};
-    void *aux = nullptr, *hvac_d = nullptr;
-    double *trace = nullptr, *phi_d = nullptr, *staging = nullptr;
-    size_t staging_doubles = 0;
-    std::vector<void *> owned;
-
-    // tiling and launch shape
-    RunKernel kern{nullptr, 0};
-    std::vector<Tile> tiles;
-    std::vector<int> cta_tiles;
-    int G = 1, tile_pairs = 0, span_max = 1, max_tiles = 0;
-    size_t smem = 0;
-    Tile *tiles_d = nullptr;
-    int *cta_tiles_d = nullptr;
-    Inst *inst_d = nullptr;
-    InstPos *pos_d = nullptr;
-    double *partials = nullptr, *mom_out = nullptr, *mom_part = nullptr, *mom_full = nullptr;
-    int mom_part_slots = 0;
-    unsigned *bar = nullptr;
-    int *err = nullptr, *bad = nullptr;
-
-    // options
-    int grid_request = 0, tile_request = 0, skip_cta = -1, use_graph = 0;
-    unsigned long long timeout_ns = 2000000000ull;
-
-    // launches since the last sync; graph of one step launch, captured and
-    // replayed on a private stream ordered after / before the ctx stream
-    int pending = 0;
-    cudaGraphExec_t graph = nullptr;
-    long long graph_steps = 0;
-    cudaStream_t gstream = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-
-    std::string last_error;
-};
-
-namespace {
+namespace xfp {
 
 int fail(xf_ctx *c, int code, const char *fmt, ...)
 {
@@ -289,7 +228,7 @@ LayoutArgs layout_args(xf_ctx *c, const InstHost &in)
     a.n_u = in.n_u;
     a.n_pairs = in.n_pairs;
     a.npad = in.npad;
-    a.phi = c->phi_d + in.phi_off;
+    a.phi = (const double *)c->arena + in.phi_off;
     a.eps = in.p.eps_perturb;
     a.seed = in.p.seed;
     a.bad = c->bad;
@@ -315,9 +254,12 @@ int plan_launch(xf_ctx *c)
     if (occ_free < 1) return fail(c, XF_E_UNSUPPORTED, "integrator kernel cannot be resident");
     long long total_pairs = 0;
     double total_cost = 0.0;
+    int n_active = 0;
     for (const InstHost &in : c->in) {
+        if (!in.active) continue;
         total_pairs += in.n_pairs;
         total_cost += pair_cost(in) * in.n_pairs;
+        ++n_active;
     }
     // tile size: one problem -> one tile per co-resident CTA slot (every CTA
     // gets the same work); several problems -> about 8 tiles per slot, so that
@@ -325,7 +267,7 @@ int plan_launch(xf_ctx *c)
     const long long slots = (long long)occ_free * c->num_sms;
     long long tp = c->tile_request;
     if (tp <= 0) {
-        const long long per = (c->in.size() == 1) ? slots : 8 * slots;
+        const long long per = (n_active <= 1) ? slots : 8 * slots;
         tp = (total_pairs + per - 1) / per;
     }
     tp = std::min<long long>(std::max<long long>((tp + 31) / 32 * 32, 32), 1 << 20);
@@ -334,10 +276,19 @@ int plan_launch(xf_ctx *c)
     for (size_t i = 0; i < c->in.size(); ++i) {
         InstHost &in = c->in[i];
         in.tile_begin = (int)c->tiles.size();
-        for (int p0 = 0; p0 < in.n_pairs; p0 += TP) c->tiles.push_back({(int)i, p0, std::min(TP, in.n_pairs - p0), 0});
+        if (in.active)
+            for (int p0 = 0; p0 < in.n_pairs; p0 += TP)
+                c->tiles.push_back({(int)i, p0, std::min(TP, in.n_pairs - p0), 0});
         in.tile_end = (int)c->tiles.size();
     }
     const int T = (int)c->tiles.size();
+    c->dirty = false;
+    if (T == 0) { // nothing to run
+        c->G = 0;
+        c->tile_pairs = TP;
+        c->cta_tiles.assign(1, 0);
+        return XF_OK;
+    }
     int span = 1;
     for (const Tile &t : c->tiles) {
         const InstHost &in = c->in[t.inst];
@@ -410,7 +361,7 @@ int upload_instances(xf_ctx *c)
         d.n_pairs = h.n_pairs;
         d.npad = h.npad;
         d.hvac_off = h.hvac_off;
-        d.state_off = h.state_off;
+        for (int b = 0; b < 3; ++b) d.off[b] = h.off[b];
         d.R = h.p.R_nu_km;
         d.mu0 = h.p.mu0_per_km;
         d.du = 1.0 / h.n_u;
@@ -487,10 +438,7 @@ int enqueue_run(xf_ctx *c, long long n, cudaStream_t stream)
     a.n_tiles = (int)c->tiles.size();
     a.span_max = c->span_max;
     a.n_steps = n;
-    a.hvac = c->hvac_d;
-    a.rho0 = c->rho[0];
-    a.rho1 = c->rho[1];
-    a.aux = c->aux;
+    a.arena = c->arena;
     a.partials = c->partials;
     a.mom_out = c->mom_out;
     a.pos = c->pos_d;
@@ -498,6 +446,7 @@ int enqueue_run(xf_ctx *c, long long n, cudaStream_t stream)
     a.err = c->err;
     a.timeout_ns = c->timeout_ns;
     a.skip_cta = c->skip_cta;
+    if (c->G == 0) return XF_OK;
     XF_CUDA(c, cudaMemsetAsync(c->bar, 0, sizeof(unsigned), stream), "reset barrier");
     void *args[] = {&a};
     cudaError_t e;
@@ -559,6 +508,32 @@ int enqueue_steps(xf_ctx *c, long long n, int only)
     return XF_OK;
 }
 
+__global__ void set_request_array_kernel(InstPos *pos, int n, const long long *req)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && pos[i].err == 0) pos[i].remaining = req[i];
+}
+
+// One launch of up to n steps in which problem i takes req[i] <= n steps
+// (0: idle); re-tiles first if problems were added or removed.
+int enqueue_requests(xf_ctx *c, long long n, const std::vector<long long> &req)
+{
+    if (c->dirty) {
+        int rc = plan_launch(c);
+        if (!rc) rc = upload_instances(c);
+        if (rc) return rc;
+    }
+    const int ni = (int)c->in.size();
+    if ((int)req.size() != ni || n <= 0) return fail(c, XF_E_ARG, "request vector size mismatch");
+    XF_CUDA(c, cudaMemcpy(c->staging, req.data(), sizeof(long long) * ni, cudaMemcpyHostToDevice), "copy requests");
+    set_request_array_kernel<<<(ni + 127) / 128, 128, 0, c->stream>>>(c->pos_d, ni, (const long long *)c->staging);
+    XF_CUDA(c, cudaGetLastError(), "request kernel");
+    int rc = enqueue_run(c, n, c->stream);
+    if (rc) return rc;
+    ++c->pending;
+    return XF_OK;
+}
+
 template <typename F>
 int dispatch_layout(xf_ctx *c, const InstHost &in, F &&f)
 {
@@ -594,30 +569,81 @@ int set_step_size(xf_ctx *c, int i, double dr)
     return XF_OK;
 }
 
-int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ctx **out)
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Bytes of a problem's block: three state buffers, trace, vacuum table, weights.
+long long block_bytes(int n_E, int n_u, int nf, int real_bytes)
 {
-    g_create_error.clear();
-    if (!out) return fail(nullptr, XF_E_ARG, "out is NULL");
-    *out = nullptr;
-    if (n <= 0 || !probs) return fail(nullptr, XF_E_ARG, "need at least one problem");
-    if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, XF_E_ARG, "allocator callbacks missing");
-    for (int i = 0; i < n; ++i) {
-        int rc = validate(nullptr, &probs[i].params, probs[i].n_E, probs[i].n_u, probs[i].n_flavor);
-        if (rc) {
-            if (n > 1) g_create_error = "problem " + std::to_string(i) + ": " + g_create_error;
-            return rc;
-        }
-        if (probs[i].params.stepper != probs[0].params.stepper || probs[i].params.precision != probs[0].params.precision)
-            return fail(nullptr, XF_E_ARG, "all problems of a pack need the same stepper and precision");
+    const long long S = nf * nf - 1, n_pairs = (long long)n_E * n_u, npad = (n_pairs + 63) & ~63ll;
+    return 3 * (long long)align256(2 * S * npad * real_bytes) + (long long)align256(2 * npad * 8) +
+           (long long)align256((size_t)n_E * S * real_bytes) + (long long)align256((size_t)4 * n_E * 8);
+}
+
+// Fill slot i with a problem: tables on the host, a block of the arena, the
+// tables copied into it, state buffers zeroed.  The slot becomes active; the
+// launch is re-tiled before the next step.
+int setup_problem(xf_ctx *c, int i, const xf_problem &prob)
+{
+    InstHost &h = c->in[i];
+    h = InstHost();
+    h.n_E = prob.n_E;
+    h.n_u = prob.n_u;
+    h.nf = prob.n_flavor;
+    h.S = h.nf * h.nf - 1;
+    h.n_pairs = h.n_E * h.n_u;
+    h.npad = (h.n_pairs + 63) & ~63;
+    h.n_bins = 2ll * h.n_pairs;
+    h.p = prob.params;
+    const int rb = c->real_bytes;
+    h.block_bytes = block_bytes(h.n_E, h.n_u, h.nf, rb);
+    h.block = c->blocks.alloc(h.block_bytes);
+    if (h.block < 0) return fail(c, XF_E_NOMEM, "no room for the problem in the arena");
+    const long long plane = (long long)align256((size_t)2 * h.S * h.npad * rb);
+    const long long tr = (long long)align256((size_t)2 * h.npad * 8);
+    const long long hv = (long long)align256((size_t)h.n_E * h.S * rb);
+    for (int b = 0; b < 3; ++b) h.off[b] = (h.block + b * plane) / rb;
+    h.trace_off = (h.block + 3 * plane) / 8;
+    h.hvac_off = (h.block + 3 * plane + tr) / rb;
+    h.phi_off = (h.block + 3 * plane + tr + hv) / 8;
+    build_tables(h);
+    const size_t need = (size_t)h.n_bins * h.nf * h.nf;
+    if (need > c->staging_doubles) {
+        double *st = (double *)dev_alloc(c, sizeof(double) * std::max(need, (size_t)c->in.size()));
+        if (!st) return fail(c, XF_E_NOMEM, "device allocation of the staging buffer failed");
+        c->staging = st;
+        c->staging_doubles = std::max(need, (size_t)c->in.size());
     }
+    cudaError_t e;
+    if (rb == 8) {
+        e = cudaMemcpy((double *)c->arena + h.hvac_off, h.hvac.data(), sizeof(double) * h.hvac.size(),
+                       cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> hf(h.hvac.begin(), h.hvac.end());
+        e = cudaMemcpy((float *)c->arena + h.hvac_off, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy((double *)c->arena + h.phi_off, h.phi.data(), sizeof(double) * h.phi.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->arena + h.block, 0, 3 * plane + tr, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "problem set-up");
+    h.active = true;
+    c->dirty = true;
+    return XF_OK;
+}
+
+// A ctx with its control buffers and an arena of arena_bytes, no problem yet.
+int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, int nfm, const xf_allocator *alloc,
+               xf_ctx **out)
+{
     xf_ctx *c = new (std::nothrow) xf_ctx();
     if (!c) return fail(nullptr, XF_E_NOMEM, "host allocation failed");
     if (alloc) {
         c->alloc = *alloc;
         c->has_alloc = true;
     }
-    c->real_bytes = (probs[0].params.precision == XF_FP64) ? 8 : 4;
-    c->stepper = probs[0].params.stepper;
+    c->real_bytes = (precision == XF_FP64) ? 8 : 4;
+    c->stepper = stepper;
+    c->nfm = nfm;
     auto bail = [&](int code) {
         free_all(c);
         g_create_error = c->last_error;
@@ -627,87 +653,134 @@ int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ct
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "no usable CUDA device"));
-
-    c->in.resize(n);
-    long long state_elems = 0, trace_d = 0, phi_d = 0;
-    long long hv = 0;
-    bool has2 = false, has3 = false;
-    for (int i = 0; i < n; ++i) {
-        InstHost &h = c->in[i];
-        h.n_E = probs[i].n_E;
-        h.n_u = probs[i].n_u;
-        h.nf = probs[i].n_flavor;
-        h.S = h.nf * h.nf - 1;
-        h.n_pairs = h.n_E * h.n_u;
-        h.npad = (h.n_pairs + 63) & ~63;
-        h.n_bins = 2ll * h.n_pairs;
-        h.p = probs[i].params;
-        build_tables(h);
-        h.state_off = state_elems;
-        state_elems += (long long)2 * h.S * h.npad;
-        h.trace_off = trace_d;
-        trace_d += 2ll * h.npad;
-        h.phi_off = phi_d;
-        phi_d += 4ll * h.n_E;
-        h.hvac_off = (int)hv;
-        hv += (long long)h.n_E * h.S;
-        c->staging_doubles = std::max(c->staging_doubles, (size_t)h.n_bins * h.nf * h.nf);
-        (h.nf == 2 ? has2 : has3) = true;
-    }
-    if (hv > INT_MAX) return bail(fail(c, XF_E_ARG, "tables too large"));
-    c->nfm = (has2 && has3) ? 0 : (has3 ? 3 : 2);
-    const int st = (c->stepper == XF_RK4) ? STEP_RK4 : STEP_EXPH;
-    c->kern = (c->real_bytes == 8) ? run_kernel_fp64(c->nfm, st) : run_kernel_fp32(c->nfm, st);
+    const int st = (stepper == XF_RK4) ? STEP_RK4 : STEP_EXPH;
+    c->kern = (c->real_bytes == 8) ? run_kernel_fp64(nfm, st) : run_kernel_fp32(nfm, st);
     if (!c->kern.fn) return bail(fail(c, XF_E_UNSUPPORTED, "kernel variant not built"));
-
-    const size_t plane = (size_t)state_elems * c->real_bytes;
-    c->rho[0] = dev_alloc(c, plane);
-    c->rho[1] = dev_alloc(c, plane);
-    c->aux = dev_alloc(c, plane);
-    c->trace = (double *)dev_alloc(c, sizeof(double) * (size_t)trace_d);
-    c->hvac_d = dev_alloc(c, (size_t)hv * c->real_bytes);
-    c->phi_d = (double *)dev_alloc(c, sizeof(double) * (size_t)phi_d);
+    c->in.resize(n_slots);
+    c->arena = (unsigned char *)dev_alloc(c, (size_t)std::max(arena_bytes, 256ll));
+    c->blocks.reset(arena_bytes);
+    c->staging_doubles = (size_t)n_slots;
     c->staging = (double *)dev_alloc(c, sizeof(double) * c->staging_doubles);
-    c->inst_d = (Inst *)dev_alloc(c, sizeof(Inst) * n);
-    c->pos_d = (InstPos *)dev_alloc(c, sizeof(InstPos) * n);
-    c->mom_out = (double *)dev_alloc(c, sizeof(double) * NVMAX * n);
+    c->inst_d = (Inst *)dev_alloc(c, sizeof(Inst) * n_slots);
+    c->pos_d = (InstPos *)dev_alloc(c, sizeof(InstPos) * n_slots);
+    c->mom_out = (double *)dev_alloc(c, sizeof(double) * NVMAX * n_slots);
     c->mom_full = (double *)dev_alloc(c, sizeof(double) * 18);
     c->bar = (unsigned *)dev_alloc(c, 64);
     c->err = (int *)dev_alloc(c, 64);
     c->bad = (int *)dev_alloc(c, 64);
-    for (void *q : {c->rho[0], c->rho[1], c->aux, (void *)c->trace, c->hvac_d, (void *)c->phi_d, (void *)c->staging,
-                    (void *)c->inst_d, (void *)c->pos_d, (void *)c->mom_out, (void *)c->mom_full, (void *)c->bar,
-                    (void *)c->err, (void *)c->bad})
+    for (void *q : {(void *)c->arena, (void *)c->staging, (void *)c->inst_d, (void *)c->pos_d, (void *)c->mom_out,
+                    (void *)c->mom_full, (void *)c->bar, (void *)c->err, (void *)c->bad})
         if (!q) return bail(fail(c, XF_E_NOMEM, "device allocation failed"));
-
-    // tables to the device (Real copy of H_vac)
-    std::vector<double> phi_all;
-    std::vector<double> hv64;
-    for (const InstHost &h : c->in) {
-        phi_all.insert(phi_all.end(), h.phi.begin(), h.phi.end());
-        hv64.insert(hv64.end(), h.hvac.begin(), h.hvac.end());
-    }
-    if (c->real_bytes == 8) e = cudaMemcpy(c->hvac_d, hv64.data(), sizeof(double) * hv64.size(), cudaMemcpyHostToDevice);
-    else {
-        std::vector<float> hf(hv64.begin(), hv64.end());
-        e = cudaMemcpy(c->hvac_d, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice);
-    }
-    if (e == cudaSuccess) e = cudaMemcpy(c->phi_d, phi_all.data(), sizeof(double) * phi_all.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(c->err, 0, 64);
+    e = cudaMemset(c->err, 0, 64);
     if (e == cudaSuccess) e = cudaMemset(c->bar, 0, 64);
-    if (e == cudaSuccess) e = cudaMemset(c->pos_d, 0, sizeof(InstPos) * n);
-    if (e == cudaSuccess) e = cudaMemset(c->rho[0], 0, plane);
-    if (e == cudaSuccess) e = cudaMemset(c->rho[1], 0, plane);
-    if (e == cudaSuccess) e = cudaMemset(c->aux, 0, plane);
-    if (e == cudaSuccess) e = cudaMemset(c->trace, 0, sizeof(double) * (size_t)trace_d);
-    if (e != cudaSuccess) return bail(cuda_fail(c, e, "device set-up"));
-    int rc = plan_launch(c);
-    if (rc) return bail(rc);
-    rc = upload_instances(c);
-    if (rc) return bail(rc);
-    e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemset(c->pos_d, 0, sizeof(InstPos) * n_slots);
+    if (e == cudaSuccess) e = cudaMemset(c->inst_d, 0, sizeof(Inst) * n_slots);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "device set-up"));
     *out = c;
+    return XF_OK;
+}
+
+void destroy_pack(xf_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+}
+
+int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ctx **out)
+{
+    g_create_error.clear();
+    if (!out) return fail(nullptr, XF_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (n <= 0 || !probs) return fail(nullptr, XF_E_ARG, "need at least one problem");
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, XF_E_ARG, "allocator callbacks missing");
+    bool has2 = false, has3 = false;
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(nullptr, &probs[i].params, probs[i].n_E, probs[i].n_u, probs[i].n_flavor);
+        if (rc) {
+            if (n > 1) g_create_error = "problem " + std::to_string(i) + ": " + g_create_error;
+            return rc;
+        }
+        if (probs[i].params.stepper != probs[0].params.stepper || probs[i].params.precision != probs[0].params.precision)
+            return fail(nullptr, XF_E_ARG, "all problems of a pack need the same stepper and precision");
+        (probs[i].n_flavor == 2 ? has2 : has3) = true;
+    }
+    const int rb = probs[0].params.precision == XF_FP64 ? 8 : 4;
+    long long bytes = 0;
+    for (int i = 0; i < n; ++i) bytes += block_bytes(probs[i].n_E, probs[i].n_u, probs[i].n_flavor, rb);
+    xf_ctx *c = nullptr;
+    int rc = create_ctx(n, bytes, probs[0].params.stepper, probs[0].params.precision,
+                        (has2 && has3) ? 0 : (has3 ? 3 : 2), alloc, &c);
+    if (rc) return rc;
+    for (int i = 0; i < n && !rc; ++i) rc = setup_problem(c, i, probs[i]);
+    if (!rc) rc = plan_launch(c);
+    if (!rc) rc = upload_instances(c);
+    if (!rc) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "device set-up");
+    }
+    if (rc) {
+        g_create_error = c->last_error;
+        destroy_pack(c);
+        return rc;
+    }
+    *out = c;
+    return XF_OK;
+}
+
+// A pack of n_slots empty slots sharing an arena of arena_bytes (serving).
+int create_slots(int n_slots, long long arena_bytes, int stepper, int precision, int nfm, xf_ctx **out)
+{
+    return create_ctx(n_slots, arena_bytes, stepper, precision, nfm, nullptr, out);
+}
+
+int add_problem(xf_ctx *c, const xf_problem &prob, const double *rho, double r_km, double dr_km, int *slot)
+{
+    int rc = validate(c, &prob.params, prob.n_E, prob.n_u, prob.n_flavor);
+    if (rc) return rc;
+    if (prob.params.stepper != c->stepper || (prob.params.precision == XF_FP64) != (c->real_bytes == 8))
+        return fail(c, XF_E_ARG, "stepper or precision differs from the pack's");
+    if (c->nfm && prob.n_flavor != c->nfm) return fail(c, XF_E_ARG, "flavor count differs from the pack's");
+    if (!std::isfinite(dr_km) || dr_km <= 0) return fail(c, XF_E_ARG, "dr_km must be finite and > 0");
+    int i = -1;
+    for (int k = 0; k < (int)c->in.size(); ++k)
+        if (!c->in[k].active) {
+            i = k;
+            break;
+        }
+    if (i < 0) return fail(c, XF_E_BUSY, "no free slot");
+    if (c->pending) {
+        rc = sync_status(c);
+        if (rc) return rc;
+    }
+    rc = setup_problem(c, i, prob);
+    if (rc) {
+        c->in[i].active = false;
+        return rc == XF_E_NOMEM ? XF_E_BUSY : rc;
+    }
+    const size_t n = (size_t)c->in[i].n_bins * prob.n_flavor * prob.n_flavor;
+    rc = rho ? set_state_impl(c, i, rho, n, r_km) : init_state_impl(c, i, r_km);
+    if (rc) {
+        remove_problem(c, i);
+        return rc;
+    }
+    c->in[i].h = dr_km; // start the step count at r_km with this step size
+    c->dirty = true;
+    *slot = i;
+    return XF_OK;
+}
+
+int remove_problem(xf_ctx *c, int slot)
+{
+    if (!c || slot < 0 || slot >= (int)c->in.size() || !c->in[slot].active) return XF_E_ARG;
+    InstHost &h = c->in[slot];
+    c->blocks.release(h.block);
+    h.active = false;
+    h.state_valid = false;
+    h.block = -1;
+    c->dirty = true;
     return XF_OK;
 }
 
@@ -752,8 +825,8 @@ int set_state_impl(xf_ctx *c, int i, const double *rho, size_t n_doubles, double
     rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
-        pack_to_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, c->staging, (Real *)c->rho[0] + h.state_off,
-                                                                    c->trace + h.trace_off);
+        pack_to_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, c->staging, (Real *)c->arena + h.off[0],
+                                                                    (double *)c->arena + h.trace_off);
         return (int)cudaGetLastError();
     });
     if (rc) return cuda_fail(c, (cudaError_t)rc, "layout kernel");
@@ -779,8 +852,8 @@ int init_state_impl(xf_ctx *c, int i, double r_km)
     rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
-        init_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (Real *)c->rho[0] + h.state_off,
-                                                                 c->trace + h.trace_off);
+        init_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (Real *)c->arena + h.off[0],
+                                                                 (double *)c->arena + h.trace_off);
         return (int)cudaGetLastError();
     });
     if (rc) return cuda_fail(c, (cudaError_t)rc, "init kernel");
@@ -803,7 +876,7 @@ int get_state_impl(xf_ctx *c, int i, double *rho, size_t n_doubles, double *r_km
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
         state_to_pack_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(
-            la, (const Real *)c->rho[h.cur] + h.state_off, c->trace + h.trace_off, c->staging);
+            la, (const Real *)c->arena + h.off[h.cur], (const double *)c->arena + h.trace_off, c->staging);
         return (int)cudaGetLastError();
     });
     if (rc) return cuda_fail(c, (cudaError_t)rc, "layout kernel");
@@ -833,8 +906,9 @@ int outputs_impl(xf_ctx *c, int i, double *p_surv, double *trace, double *purity
     int rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
-        outputs_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (const Real *)c->rho[h.cur] + h.state_off,
-                                                              c->trace + h.trace_off, dev[0], dev[1], dev[2]);
+        outputs_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (const Real *)c->arena + h.off[h.cur],
+                                                              (const double *)c->arena + h.trace_off, dev[0],
+                                                              dev[1], dev[2]);
         return (int)cudaGetLastError();
     });
     if (rc) return cuda_fail(c, (cudaError_t)rc, "outputs kernel");
@@ -877,7 +951,7 @@ int moments_impl(xf_ctx *c, int i, double *M0, double *M1, size_t n_doubles)
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
         moments_partial_kernel<NF, Real, 256><<<G, 256, 0, c->stream>>>(
-            m, (const Real *)c->rho[h.cur] + h.state_off, c->trace + h.trace_off, c->mom_part);
+            m, (const Real *)c->arena + h.off[h.cur], (const double *)c->arena + h.trace_off, c->mom_part);
         moments_final_kernel<NF><<<1, 32, 0, c->stream>>>(c->mom_part, G, dE, c->mom_full, c->mom_full + NF * NF);
         return (int)cudaGetLastError();
     });
@@ -891,7 +965,9 @@ int moments_impl(xf_ctx *c, int i, double *M0, double *M1, size_t n_doubles)
     return XF_OK;
 }
 
-} // namespace
+} // namespace xfp
+
+using namespace xfp;
 
 // ============================================================== C ABI
 extern "C" {
@@ -953,11 +1029,7 @@ int xf_create_batch(int n_problems, const xf_problem *problems, const xf_allocat
 
 int xf_destroy(xf_ctx *c)
 {
-    if (!c) return XF_OK;
-    cudaStreamSynchronize(c->stream);
-    cudaGetLastError();
-    free_all(c);
-    delete c;
+    destroy_pack(c);
     return XF_OK;
 }
 

@@ -257,6 +257,10 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
     d.matter = p->matter;
     d.n_pairs = n_pairs;
     d.npad = npad;
+    d.off[0] = rho0 - (Real *)base;
+    d.off[1] = rho1 - (Real *)base;
+    d.off[2] = aux - (Real *)base;
+    d.hvac_off = hvac - (Real *)base;
     d.R = p->R_nu_km;
     d.mu0 = p->mu0_per_km;
     d.du = 1.0 / n_u;
@@ -299,10 +303,7 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
         a.n_tiles = T;
         a.span_max = span;
         a.n_steps = m;
-        a.hvac = hvac;
-        a.rho0 = rho0;
-        a.rho1 = rho1;
-        a.aux = aux;
+        a.arena = base;
         a.partials = partials;
         a.mom_out = mom_out;
         a.pos = pos;

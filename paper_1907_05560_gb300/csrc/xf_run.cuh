@@ -36,12 +36,14 @@ enum { STEP_RK4 = 0, STEP_EXPH = 1 };
 enum { ERR_NONFINITE = 1, ERR_BARRIER = 2 };
 constexpr int NVMAX = 16; // 2 (n_f^2 - 1) for three flavors
 
-// One problem of a pack.  Its state buffers are component-major planes:
-// element (c, s, p) at state_off + (c * 2 + s) * npad + p.
+// One problem of a pack.  Its three state buffers (the two ping-pong copies
+// of rho and the auxiliary stage buffer) are component-major planes at Real
+// offsets off[0..2] from the arena base: element (c, s, p) at
+// off[b] + (c * 2 + s) * npad + p.  Its vacuum table is at Real offset hvac_off.
 struct Inst {
     int n_E, n_u, nf, geometry;
-    int matter, n_pairs, npad, hvac_off;
-    long long state_off;
+    int matter, n_pairs, npad, pad0_;
+    long long off[3], hvac_off;
     double R, mu0, du, dE;
     double ne_ref, r_ref, ne_power, nb0, h_ns, Ye, gf;
     double r0, h;           // step k of the run starts at r0 + k h
@@ -68,8 +70,7 @@ struct RunArgs {
     const int *cta_tiles;   // [grid + 1]: CTA c processes tiles [cta_tiles[c], cta_tiles[c+1])
     int n_inst, n_tiles, span_max, pad_;
     long long n_steps;      // max over instances
-    const void *hvac;       // Real tables, instance i at hvac_off
-    void *rho0, *rho1, *aux; // Real state arenas
+    void *arena;            // base of the problems' state buffers and tables
     double *partials;       // [2][n_tiles][NVMAX]
     double *mom_out;        // [n_inst][NVMAX] M0 | M1 of each instance's final state (dE applied)
     InstPos *pos;           // [n_inst] progress (read and advanced by the kernel)
@@ -459,12 +460,13 @@ __device__ __forceinline__ TileView<Real> make_view(const RunArgs &a, const Inst
                                                     const Tile &tl, long long k)
 {
     TileView<Real> v;
-    Real *const b0 = (Real *)a.rho0 + in.state_off, *const b1 = (Real *)a.rho1 + in.state_off;
+    Real *const base = (Real *)a.arena;
+    Real *const b0 = base + in.off[0], *const b1 = base + in.off[1];
     const bool odd = ((ps.cur + (int)(k & 1)) & 1) != 0;
     v.cur = odd ? b1 : b0;
     v.nxt = odd ? b0 : b1;
-    v.aux = (Real *)a.aux + in.state_off;
-    v.hvac = (const Real *)a.hvac + in.hvac_off;
+    v.aux = base + in.off[2];
+    v.hvac = base + in.hvac_off;
     v.n_E = in.n_E;
     v.npad = in.npad;
     v.p0 = tl.p0;

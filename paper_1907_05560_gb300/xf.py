@@ -54,6 +54,32 @@ class XFProblem(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("params", XFParams)]
 
 
+class XFServerCfg(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_uint32), ("max_jobs", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64),
+                ("chunk_steps", ctypes.c_int64), ("queue_cap", ctypes.c_int32), ("stepper", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("n_flavor", ctypes.c_int32), ("tile_pairs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class XFJob(ctypes.Structure):
+    _fields_ = [("problem", XFProblem), ("r0_km", ctypes.c_double), ("dr_km", ctypes.c_double),
+                ("n_steps", ctypes.c_int64), ("rho0", ctypes.POINTER(ctypes.c_double)),
+                ("keep_state", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class XFJobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("steps_done", ctypes.c_int64),
+                ("r_km", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class XFServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("resident", ctypes.c_int64), ("max_resident", ctypes.c_int64), ("epochs", ctypes.c_int64),
+                ("bin_steps", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("mem_used_bytes", ctypes.c_int64), ("mem_peak_bytes", ctypes.c_int64)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -96,6 +122,12 @@ SIGNATURES = {
     "xf_batch_step": (ctypes.c_int, [_P, ctypes.c_int64, _D]),
     "xf_batch_status": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int64), _D]),
+    "xf_server_create": (ctypes.c_int, [ctypes.POINTER(XFServerCfg), ctypes.POINTER(_P)]),
+    "xf_submit": (ctypes.c_int, [_P, ctypes.POINTER(XFJob), ctypes.POINTER(ctypes.c_uint64)]),
+    "xf_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(XFJobResult), _D, ctypes.c_size_t]),
+    "xf_server_drain": (ctypes.c_int, [_P, ctypes.c_double]),
+    "xf_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(XFServerStats)]),
+    "xf_server_destroy": (ctypes.c_int, [_P]),
     "xf_peak": (ctypes.c_int, [ctypes.c_int, _D]),
     "xf_step_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(XFParams),
                                        _P, ctypes.c_double, ctypes.c_int64, ctypes.c_double, _P]),
@@ -344,3 +376,78 @@ def peak(which: int) -> float:
 
 def status_str(code: int) -> str:
     return load().xf_status_str(code).decode()
+
+
+class Server:
+    """Continuous-batching job server (xf_server_*): jobs are admitted into
+    GPU slots as slots and memory free up and advance together in chunks."""
+
+    def __init__(self, max_jobs: int, mem_budget_bytes: int, chunk_steps: int, *, stepper=I.EXPH,
+                 precision=I.FP32_M64, n_flavor: int = 2, queue_cap: int = 100000, tile_pairs: int = 0):
+        self.L = load()
+        cfg = XFServerCfg()
+        cfg.size = ctypes.sizeof(XFServerCfg)
+        cfg.max_jobs, cfg.mem_budget_bytes, cfg.chunk_steps = max_jobs, int(mem_budget_bytes), chunk_steps
+        cfg.queue_cap, cfg.stepper, cfg.precision, cfg.n_flavor = queue_cap, stepper, precision, n_flavor
+        cfg.tile_pairs = tile_pairs
+        h = _P()
+        rc = self.L.xf_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != XF_OK:
+            raise XFError(rc, "xf_server_create failed")
+        self.h = h
+        self._sizes = {}
+
+    def submit(self, p: I.Problem, rho0: np.ndarray | None = None, keep_state: bool = False,
+               r0: float | None = None, dr: float | None = None, n_steps: int | None = None) -> int:
+        job = XFJob()
+        job.problem.n_E, job.problem.n_u, job.problem.n_flavor, job.problem.reserved = p.n_E, p.n_u, p.n_f, 0
+        job.problem.params = params_from(p)
+        job.r0_km = p.r0 if r0 is None else r0
+        job.dr_km = p.h if dr is None else dr
+        job.n_steps = p.n_steps if n_steps is None else n_steps
+        keep = None
+        if rho0 is not None:
+            keep = np.ascontiguousarray(rho0, dtype=np.float64)
+            job.rho0 = _dp(keep)
+        job.keep_state = 1 if keep_state else 0
+        jid = ctypes.c_uint64(0)
+        rc = self.L.xf_submit(self.h, ctypes.byref(job), ctypes.byref(jid))
+        if rc != XF_OK:
+            raise XFError(rc, "xf_submit")
+        self._sizes[jid.value] = 2 * p.n_u * p.n_E * p.n_f * p.n_f
+        return jid.value
+
+    def poll(self, job_id: int, want_state: bool = False):
+        """None while pending, else (result dict, state or None)."""
+        res = XFJobResult()
+        out = np.empty(self._sizes.get(job_id, 0)) if want_state else None
+        rc = self.L.xf_poll(self.h, job_id, ctypes.byref(res), _dp(out) if out is not None else None,
+                            out.size if out is not None else 0)
+        if rc == XF_PENDING:
+            return None
+        if rc != XF_OK:
+            raise XFError(rc, "xf_poll")
+        self._sizes.pop(job_id, None)
+        return ({"status": STATUS.get(res.status, res.status), "steps": res.steps_done, "r": res.r_km,
+                 "t_submit": res.t_submit, "t_start": res.t_start, "t_done": res.t_done}, out)
+
+    def drain(self, timeout_s: float = 600.0):
+        rc = self.L.xf_server_drain(self.h, float(timeout_s))
+        if rc != XF_OK:
+            raise XFError(rc, "xf_server_drain")
+
+    def stats(self) -> dict:
+        st = XFServerStats()
+        self.L.xf_server_get_stats(self.h, ctypes.byref(st))
+        return {k: getattr(st, k) for k, _ in XFServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.xf_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
