@@ -219,10 +219,9 @@ def run_xf(args):
     bin_steps = p.n_bins * chunk * args.steps
     value = bin_steps * world / t_sum
 
-    # FP32 variant on the same input (same workload, same launch pattern)
-    fp32 = None
-    if args.precision == "fp64" and not args.skip_fp32:
-        q = p.replace(precision=I.FP32_M64)
+    # FP32 variants on the same input (same workload, same launch pattern)
+    def time_precision(prec):
+        q = p.replace(precision=prec)
         c32 = xf.Context(q, stream=stream)
         c32.init_state(q.r0)
         for _ in range(args.warmup):
@@ -239,9 +238,18 @@ def run_xf(args):
         c32.sync()
         barrier()
         t32 = sum(s.elapsed_time(e) for s, e in zip(s32, e32)) * 1e-3
-        fp32 = {"value": q.n_bins * chunk * args.steps * world / t32, "unit": UNIT,
-                "ms_per_step": 1e3 * t32 / args.steps, "precision": "FP32 bins, FP64 moments/radius/phase"}
         c32.close()
+        return {"value": q.n_bins * chunk * args.steps * world / t32, "unit": UNIT,
+                "ms_per_step": 1e3 * t32 / args.steps}
+
+    fp32 = None
+    variants = None
+    if args.precision == "fp64" and not args.skip_fp32:
+        fp32 = time_precision(I.FP32_M64)
+        fp32["precision"] = "FP32 bins, FP64 moments/radius/phase"
+        variants = {"fp32_comp": time_precision(I.FP32_COMP), "fp32_m64_renorm": time_precision(I.FP32_M64_RENORM)}
+        variants["fp32_comp"]["precision"] = "FP32 bins, compensated FP32 moment sums to the warp"
+        variants["fp32_m64_renorm"]["precision"] = "FP32_M64 plus per-step restoration of tr(T^2)"
 
     # batched ensemble: 256 seeded problems (~40 M bins) in one persistent launch per call
     batched = None
@@ -309,7 +317,7 @@ def run_xf(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "fp32_m64": fp32, "batched": batched, "serving": serving, "clocks": clk, "gpu_launches": args.steps,
+            "fp32_m64": fp32, "fp32_variants": variants, "batched": batched, "serving": serving, "clocks": clk, "gpu_launches": args.steps,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -433,7 +441,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=100, help="radial steps per bench step")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--cpu-steps", type=int, default=250)
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")

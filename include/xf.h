@@ -70,8 +70,13 @@ enum xf_stepper {
 enum xf_precision {
     XF_FP64 = 0,        /* FP64 everywhere */
     XF_FP32_M64 = 1,    /* FP32 per-bin arithmetic and storage; FP64 moments, radius, phase */
-    XF_FP32_COMP = 2,   /* as FP32_M64 but moments summed in compensated FP32 (TwoSum) */
-    XF_FP32_M64_RENORM = 3 /* FP32_M64 plus per-step restoration of |P| (2 fl) / tr rho0^2 */
+    XF_FP32_COMP = 2,   /* as FP32_M64, but each thread's and each warp's moment sums are
+                           compensated FP32 (TwoSum, error carried beside the sum) before the
+                           FP64 sum over warps and tiles */
+    XF_FP32_M64_RENORM = 3 /* FP32_M64 plus, after every step, each bin's traceless part scaled
+                              back to its initial tr(T^2) (|P| in 2 flavors, tr rho^2 in 3; both
+                              are constants of the exact flow, Eq. 3.10).  The trace is exact in
+                              every variant (kept per bin in FP64, never updated) */
 };
 enum xf_geometry {
     XF_GEOM_BULB = 0,         /* Eq. 3.13-3.15: w_u = x^2 du/(2 cos_u), x = R/r; dl/dr = 1/cos_u */
@@ -227,6 +232,18 @@ int xf_batch_outputs(xf_ctx *ctx, int inst, double *p_surv, double *trace, doubl
  * XF_E_STATE), how many steps each took and its radius. */
 int xf_batch_step(xf_ctx *ctx, int64_t n_steps, const double *dr_km);
 int xf_batch_status(xf_ctx *ctx, int inst, int *status, int64_t *steps_done, double *r_km);
+/* The moments M0, M1 (Eq. 3.13, host arrays of n_f*n_f doubles each, packed
+ * like a bin) of problem `inst`'s current state as the integrator's own
+ * in-launch reduction summed them, i.e. in the precision variant's
+ * arithmetic (FP32 terms and warp sums, compensated for XF_FP32_COMP, FP64
+ * above the warp).  Traceless part only: the trace part of nu - conj(nubar)
+ * adds a multiple of the identity to H, which the flow ignores, so the
+ * integrator never forms it (the diagonal entries sum to zero).  Compare with
+ * xf_moments / the batch's FP64 moments of the same state to see the
+ * summation error.  Valid after a step call that advanced the problem;
+ * XF_E_STATE before that (and after a state reset or a non-finite stop).
+ * Also accepts a single-problem context with inst = 0. */
+int xf_batch_run_moments(xf_ctx *ctx, int inst, double *M0, double *M1, size_t n_doubles);
 
 /* ---- serving: a continuous-batching job server ---------------------------
  * A server owns one pack of `max_jobs` slots and a device arena of

@@ -135,8 +135,6 @@ int validate(xf_ctx *c, const xf_params *p, int n_E, int n_u, int nf)
     if (p->stepper != XF_RK4 && p->stepper != XF_EXPH) return fail(c, XF_E_ARG, "bad stepper %d", p->stepper);
     if (p->precision < XF_FP64 || p->precision > XF_FP32_M64_RENORM)
         return fail(c, XF_E_ARG, "bad precision %d", p->precision);
-    if (p->precision == XF_FP32_COMP || p->precision == XF_FP32_M64_RENORM)
-        return fail(c, XF_E_UNSUPPORTED, "precision %d not built", p->precision);
     if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CONST) return fail(c, XF_E_ARG, "bad geometry %d", p->geometry);
     if (p->geometry == XF_GEOM_SINGLE_ANGLE && n_u != 1) return fail(c, XF_E_ARG, "single-angle geometry needs n_u == 1");
     if (p->hierarchy != 1 && p->hierarchy != -1) return fail(c, XF_E_ARG, "hierarchy must be +1 or -1");
@@ -361,6 +359,7 @@ int upload_instances(xf_ctx *c)
         d.n_pairs = h.n_pairs;
         d.npad = h.npad;
         d.hvac_off = h.hvac_off;
+        d.ref_off = h.ref_off;
         for (int b = 0; b < 3; ++b) d.off[b] = h.off[b];
         d.R = h.p.R_nu_km;
         d.mu0 = h.p.mu0_per_km;
@@ -571,12 +570,15 @@ int set_step_size(xf_ctx *c, int i, double dr)
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Bytes of a problem's block: three state buffers, trace, vacuum table, weights.
-long long block_bytes(int n_E, int n_u, int nf, int real_bytes)
+// Bytes of a problem's block: three state buffers, trace, vacuum table,
+// weights, and for the renormalising variant the initial tr(T^2) per bin.
+long long block_bytes(int n_E, int n_u, int nf, int precision)
 {
+    const long long rb = precision == XF_FP64 ? 8 : 4;
     const long long S = nf * nf - 1, n_pairs = (long long)n_E * n_u, npad = (n_pairs + 63) & ~63ll;
-    return 3 * (long long)align256(2 * S * npad * real_bytes) + (long long)align256(2 * npad * 8) +
-           (long long)align256((size_t)n_E * S * real_bytes) + (long long)align256((size_t)4 * n_E * 8);
+    const long long ref = precision == XF_FP32_M64_RENORM ? (long long)align256(2 * npad * rb) : 0;
+    return 3 * (long long)align256(2 * S * npad * rb) + (long long)align256(2 * npad * 8) +
+           (long long)align256((size_t)n_E * S * rb) + (long long)align256((size_t)4 * n_E * 8) + ref;
 }
 
 // Fill slot i with a problem: tables on the host, a block of the arena, the
@@ -595,7 +597,7 @@ int setup_problem(xf_ctx *c, int i, const xf_problem &prob)
     h.n_bins = 2ll * h.n_pairs;
     h.p = prob.params;
     const int rb = c->real_bytes;
-    h.block_bytes = block_bytes(h.n_E, h.n_u, h.nf, rb);
+    h.block_bytes = block_bytes(h.n_E, h.n_u, h.nf, c->precision);
     h.block = c->blocks.alloc(h.block_bytes);
     if (h.block < 0) return fail(c, XF_E_NOMEM, "no room for the problem in the arena");
     const long long plane = (long long)align256((size_t)2 * h.S * h.npad * rb);
@@ -605,6 +607,9 @@ int setup_problem(xf_ctx *c, int i, const xf_problem &prob)
     h.trace_off = (h.block + 3 * plane) / 8;
     h.hvac_off = (h.block + 3 * plane + tr) / rb;
     h.phi_off = (h.block + 3 * plane + tr + hv) / 8;
+    h.ref_off = c->precision == XF_FP32_M64_RENORM
+                    ? (h.block + 3 * plane + tr + hv + (long long)align256((size_t)4 * h.n_E * 8)) / rb
+                    : 0;
     build_tables(h);
     const size_t need = (size_t)h.n_bins * h.nf * h.nf;
     if (need > c->staging_doubles) {
@@ -642,6 +647,7 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
         c->has_alloc = true;
     }
     c->real_bytes = (precision == XF_FP64) ? 8 : 4;
+    c->precision = precision;
     c->stepper = stepper;
     c->nfm = nfm;
     auto bail = [&](int code) {
@@ -654,7 +660,10 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "no usable CUDA device"));
     const int st = (stepper == XF_RK4) ? STEP_RK4 : STEP_EXPH;
-    c->kern = (c->real_bytes == 8) ? run_kernel_fp64(nfm, st) : run_kernel_fp32(nfm, st);
+    c->kern = (c->real_bytes == 8) ? run_kernel_fp64(nfm, st)
+              : precision == XF_FP32_COMP ? run_kernel_fp32(nfm, st, VAR_COMP)
+              : precision == XF_FP32_M64_RENORM ? run_kernel_fp32(nfm, st, VAR_RENORM)
+                                                 : run_kernel_fp32(nfm, st, VAR_PLAIN);
     if (!c->kern.fn) return bail(fail(c, XF_E_UNSUPPORTED, "kernel variant not built"));
     c->in.resize(n_slots);
     c->arena = (unsigned char *)dev_alloc(c, (size_t)std::max(arena_bytes, 256ll));
@@ -707,9 +716,9 @@ int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ct
             return fail(nullptr, XF_E_ARG, "all problems of a pack need the same stepper and precision");
         (probs[i].n_flavor == 2 ? has2 : has3) = true;
     }
-    const int rb = probs[0].params.precision == XF_FP64 ? 8 : 4;
     long long bytes = 0;
-    for (int i = 0; i < n; ++i) bytes += block_bytes(probs[i].n_E, probs[i].n_u, probs[i].n_flavor, rb);
+    for (int i = 0; i < n; ++i)
+        bytes += block_bytes(probs[i].n_E, probs[i].n_u, probs[i].n_flavor, probs[0].params.precision);
     xf_ctx *c = nullptr;
     int rc = create_ctx(n, bytes, probs[0].params.stepper, probs[0].params.precision,
                         (has2 && has3) ? 0 : (has3 ? 3 : 2), alloc, &c);
@@ -740,7 +749,7 @@ int add_problem(xf_ctx *c, const xf_problem &prob, const double *rho, double r_k
 {
     int rc = validate(c, &prob.params, prob.n_E, prob.n_u, prob.n_flavor);
     if (rc) return rc;
-    if (prob.params.stepper != c->stepper || (prob.params.precision == XF_FP64) != (c->real_bytes == 8))
+    if (prob.params.stepper != c->stepper || prob.params.precision != c->precision)
         return fail(c, XF_E_ARG, "stepper or precision differs from the pack's");
     if (c->nfm && prob.n_flavor != c->nfm) return fail(c, XF_E_ARG, "flavor count differs from the pack's");
     if (!std::isfinite(dr_km) || dr_km <= 0) return fail(c, XF_E_ARG, "dr_km must be finite and > 0");
@@ -806,6 +815,14 @@ int reset_instance(xf_ctx *c, int i, double r_km, bool valid)
     return upload_instances(c);
 }
 
+// Where the layout kernels store each bin's initial tr(T^2) (renormalising
+// variant), else NULL.
+template <typename Real>
+Real *ref_ptr(xf_ctx *c, const InstHost &h)
+{
+    return c->precision == XF_FP32_M64_RENORM ? (Real *)c->arena + h.ref_off : nullptr;
+}
+
 int set_state_impl(xf_ctx *c, int i, const double *rho, size_t n_doubles, double r_km)
 {
     InstHost *hp = instance(c, i);
@@ -826,7 +843,7 @@ int set_state_impl(xf_ctx *c, int i, const double *rho, size_t n_doubles, double
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
         pack_to_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, c->staging, (Real *)c->arena + h.off[0],
-                                                                    (double *)c->arena + h.trace_off);
+                                                                    (double *)c->arena + h.trace_off, ref_ptr<Real>(c, h));
         return (int)cudaGetLastError();
     });
     if (rc) return cuda_fail(c, (cudaError_t)rc, "layout kernel");
@@ -853,7 +870,7 @@ int init_state_impl(xf_ctx *c, int i, double r_km)
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
         init_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (Real *)c->arena + h.off[0],
-                                                                 (double *)c->arena + h.trace_off);
+                                                                 (double *)c->arena + h.trace_off, ref_ptr<Real>(c, h));
         return (int)cudaGetLastError();
     });
     if (rc) return cuda_fail(c, (cudaError_t)rc, "init kernel");
@@ -1152,6 +1169,41 @@ int xf_batch_status(xf_ctx *c, int inst, int *status, int64_t *steps_done, doubl
     if (status) *status = !h->state_valid ? XF_E_STATE : (h->err & ERR_NONFINITE) ? XF_E_NONFINITE : XF_OK;
     if (steps_done) *steps_done = h->steps;
     if (r_km) *r_km = radius(*h);
+    return XF_OK;
+}
+
+int xf_batch_run_moments(xf_ctx *c, int inst, double *M0, double *M1, size_t n_doubles)
+{
+    InstHost *h = instance(c, inst);
+    if (!h) return c ? fail(c, XF_E_ARG, "bad instance index %d", inst) : XF_E_ARG;
+    if (!M0 || !M1) return fail(c, XF_E_ARG, "M0/M1 NULL");
+    if (n_doubles != (size_t)h->nf * h->nf) return fail(c, XF_E_ARG, "n_doubles must be n_f*n_f");
+    if (c->pending) {
+        int rc = sync_status(c);
+        if (rc) return rc;
+    }
+    if (!h->state_valid || h->steps == 0 || (h->err & ERR_NONFINITE))
+        return fail(c, XF_E_STATE, "no finite step taken since the state was set");
+    double t[NVMAX];
+    XF_CUDA(c, cudaMemcpyAsync(t, c->mom_out + (size_t)inst * NVMAX, sizeof t, cudaMemcpyDeviceToHost, c->stream),
+            "copy moments");
+    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    const int S = h->S;
+    for (int w = 0; w < 2; ++w) {
+        const double *m = t + w * S;
+        double *x = (w == 0) ? M0 : M1;
+        if (h->nf == 2) {
+            x[0] = m[0];
+            x[1] = -m[0];
+            x[2] = m[1];
+            x[3] = m[2];
+        } else {
+            x[0] = m[0];
+            x[1] = m[1];
+            x[2] = -(m[0] + m[1]);
+            for (int k = 0; k < 6; ++k) x[3 + k] = m[2 + k];
+        }
+    }
     return XF_OK;
 }
 

@@ -37,8 +37,10 @@ __device__ __forceinline__ void bin_split(const LayoutArgs &a, long long b, int 
 
 // Seeded initial state (one thread per bin): rho = diag(phi_e, phi_x[, phi_x])
 // plus eps sqrt(rho_ii rho_jj) exp(2 pi i U) on each upper entry.
+// ref (may be NULL): receives tr(T^2) of each bin's traceless part, the
+// quantity the renormalising variant restores after every step.
 template <int NF, typename Real>
-__global__ void init_state_kernel(LayoutArgs a, Real *state, double *trace)
+__global__ void init_state_kernel(LayoutArgs a, Real *state, double *trace, Real *ref)
 {
     constexpr int S = Comp<NF>::S, NOFF = NF * (NF - 1) / 2;
     const long long nb = 2ll * a.n_pairs;
@@ -74,12 +76,13 @@ __global__ void init_state_kernel(LayoutArgs a, Real *state, double *trace)
 #pragma unroll
         for (int c = 0; c < S; ++c) state[(size_t)(c * 2 + s) * a.npad + p] = (Real)t[c];
         trace[(size_t)s * a.npad + p] = tr;
+        if (ref) ref[(size_t)s * a.npad + p] = (Real)purity<NF, double>(t);
     }
 }
 
-// packed host layout -> traceless components + trace
+// packed host layout -> traceless components + trace (+ tr(T^2) into ref)
 template <int NF, typename Real>
-__global__ void pack_to_state_kernel(LayoutArgs a, const double *packed, Real *state, double *trace)
+__global__ void pack_to_state_kernel(LayoutArgs a, const double *packed, Real *state, double *trace, Real *ref)
 {
     constexpr int S = Comp<NF>::S, M = NF * NF;
     const long long nb = 2ll * a.n_pairs;
@@ -107,6 +110,7 @@ __global__ void pack_to_state_kernel(LayoutArgs a, const double *packed, Real *s
 #pragma unroll
         for (int c = 0; c < S; ++c) state[(size_t)(c * 2 + s) * a.npad + p] = (Real)t[c];
         trace[(size_t)s * a.npad + p] = tr;
+        if (ref) ref[(size_t)s * a.npad + p] = (Real)purity<NF, double>(t);
     }
 }
 
@@ -144,7 +148,7 @@ __global__ void state_to_pack_kernel(LayoutArgs a, const Real *state, const doub
 // Per-bin outputs: survival probability, trace, tr(T^2) of the traceless part.
 template <int NF, typename Real>
 __global__ void outputs_kernel(LayoutArgs a, const Real *state, const double *trace, double *p_surv,
-                               double *trace_out, double *purity)
+                               double *trace_out, double *purity_out)
 {
     constexpr int S = Comp<NF>::S;
     const long long nb = 2ll * a.n_pairs;
@@ -157,21 +161,13 @@ __global__ void outputs_kernel(LayoutArgs a, const Real *state, const double *tr
 #pragma unroll
         for (int c = 0; c < S; ++c) t[c] = (double)state[(size_t)(c * 2 + s) * a.npad + p];
         const double tr = trace[(size_t)s * a.npad + p];
-        double ree, pur;
-        if constexpr (NF == 2) {
-            ree = 0.5 * tr + t[0];
-            pur = 2.0 * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-        } else {
-            ree = tr / 3.0 + t[0];
-            const double t3 = -(t[0] + t[1]);
-            pur = t[0] * t[0] + t[1] * t[1] + t3 * t3;
-            for (int c = 2; c < 8; ++c) pur += 2.0 * t[c] * t[c];
-        }
+        const double ree = (NF == 2 ? 0.5 * tr : tr / 3.0) + t[0];
+        const double pur = purity<NF, double>(t);
         const double pe = a.phi[(s == 0 ? 0 : 1) * a.n_E + e];
         const double px = a.phi[(s == 0 ? 2 : 3) * a.n_E + e];
         if (p_surv) p_surv[b] = (pe != px) ? (ree - px) / (pe - px) : (double)NAN;
         if (trace_out) trace_out[b] = tr;
-        if (purity) purity[b] = pur;
+        if (purity_out) purity_out[b] = pur;
     }
 }
 

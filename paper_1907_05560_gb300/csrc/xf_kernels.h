@@ -12,8 +12,9 @@ struct RunKernel {
 };
 
 // nfm: 2 or 3 (all instances of the pack have that many flavors) or 0
-// (mixed pack); stepper STEP_RK4 / STEP_EXPH.  fn == nullptr if not built.
+// (mixed pack); stepper STEP_RK4 / STEP_EXPH; var VAR_PLAIN / VAR_COMP /
+// VAR_RENORM (FP32 only; mixed packs plain only).  fn == nullptr if not built.
 RunKernel run_kernel_fp64(int nfm, int stepper);
-RunKernel run_kernel_fp32(int nfm, int stepper);
+RunKernel run_kernel_fp32(int nfm, int stepper, int var);
 
 } // namespace xf

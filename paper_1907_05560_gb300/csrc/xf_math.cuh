@@ -373,4 +373,34 @@ __host__ __device__ __forceinline__ void hamiltonians(const Real *hv, Real A, co
     }
 }
 
+// tr(T^2) of a traceless Hermitian matrix T in packed form (2(a^2 + x^2 + y^2)
+// in two flavors; with the trace fixed, tr(rho^2) and |P| follow from it).
+template <int NF, typename Real>
+__host__ __device__ __forceinline__ Real purity(const Real *t)
+{
+    if constexpr (NF == 2) {
+        return Real(2) * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    } else {
+        const Real t3 = -(t[0] + t[1]);
+        Real q = t[0] * t[0] + t[1] * t[1] + t3 * t3;
+#pragma unroll
+        for (int c = 2; c < 8; ++c) q += Real(2) * t[c] * t[c];
+        return q;
+    }
+}
+
+// Scale the traceless part back to the initial tr(T^2) = ref (the exact flow
+// conserves it; the FP32 update lets it drift).
+template <int NF, typename Real>
+__host__ __device__ __forceinline__ void renormalise(Real *t, Real ref)
+{
+    constexpr int S = Comp<NF>::S;
+    const Real q = purity<NF, Real>(t);
+    if (q > Real(0) && ref > Real(0)) {
+        const Real f = sqrt_r(ref / q);
+#pragma unroll
+        for (int c = 0; c < S; ++c) t[c] *= f;
+    }
+}
+
 } // namespace xf

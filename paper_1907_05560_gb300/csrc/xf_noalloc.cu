@@ -144,7 +144,9 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
     const int n_pairs = n_E * n_u;
     const int npad = (n_pairs + 63) & ~63;
     const int st = (p->stepper == XF_RK4) ? STEP_RK4 : STEP_EXPH;
-    const RunKernel kern = std::is_same<Real, double>::value ? run_kernel_fp64(NF, st) : run_kernel_fp32(NF, st);
+    const int var = p->precision == XF_FP32_COMP ? VAR_COMP : p->precision == XF_FP32_M64_RENORM ? VAR_RENORM : VAR_PLAIN;
+    const bool renorm = var == VAR_RENORM;
+    const RunKernel kern = std::is_same<Real, double>::value ? run_kernel_fp64(NF, st) : run_kernel_fp32(NF, st, var);
     if (!kern.fn) return noalloc_fail(XF_E_UNSUPPORTED, "kernel variant not built");
 
     int dev = 0, sms = 0;
@@ -191,6 +193,8 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
     off += align256(sizeof(double) * 2 * (size_t)npad);
     Real *hvac = (Real *)(base + off);
     off += align256(sizeof(Real) * (size_t)n_E * S);
+    Real *ref = renorm ? (Real *)(base + off) : nullptr;
+    if (renorm) off += align256(sizeof(Real) * 2 * (size_t)npad);
     double *partials = (double *)(base + off);
     off += align256(sizeof(double) * 2 * (size_t)T * NVMAX);
     Tile *tiles = (Tile *)(base + off);
@@ -261,6 +265,7 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
     d.off[1] = rho1 - (Real *)base;
     d.off[2] = aux - (Real *)base;
     d.hvac_off = hvac - (Real *)base;
+    d.ref_off = renorm ? ref - (Real *)base : 0;
     d.R = p->R_nu_km;
     d.mu0 = p->mu0_per_km;
     d.du = 1.0 / n_u;
@@ -287,7 +292,7 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
     la.npad = npad;
     la.bad = bad;
     const int egrid = (int)std::min<long long>((2ll * n_pairs + 255) / 256, (long long)sms * 16);
-    pack_to_state_kernel<NF, Real><<<egrid, 256, 0, stream>>>(la, rho_dev, rho0, trace);
+    pack_to_state_kernel<NF, Real><<<egrid, 256, 0, stream>>>(la, rho_dev, rho0, trace, ref);
     NA_CUDA(cudaGetLastError(), "layout kernel");
 
     // the persistent integrator, in launches of at most 65536 steps
@@ -351,8 +356,7 @@ extern "C" int xf_step_noalloc(int n_E, int n_u, int n_flavor, const xf_params *
         return noalloc_fail(XF_E_ARG, "need n_E, n_u > 0 and n_flavor in {2, 3}");
     if ((long long)n_E * n_u > (long long)(INT_MAX / 16)) return noalloc_fail(XF_E_ARG, "n_E * n_u too large");
     if (p->stepper != XF_RK4 && p->stepper != XF_EXPH) return noalloc_fail(XF_E_ARG, "bad stepper");
-    if (p->precision != XF_FP64 && p->precision != XF_FP32_M64)
-        return noalloc_fail(XF_E_UNSUPPORTED, "precision not built for the no-allocation entry point");
+    if (p->precision < XF_FP64 || p->precision > XF_FP32_M64_RENORM) return noalloc_fail(XF_E_ARG, "bad precision");
     if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CONST) return noalloc_fail(XF_E_ARG, "bad geometry");
     if (p->geometry == XF_GEOM_SINGLE_ANGLE && n_u != 1)
         return noalloc_fail(XF_E_ARG, "single-angle geometry needs n_u == 1");

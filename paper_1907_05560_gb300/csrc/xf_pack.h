@@ -87,6 +87,7 @@ struct InstHost {
     long long off[3] = {0, 0, 0};     // Real: rho (two copies) and the stage buffer
     long long trace_off = 0;          // double: trace per bin (2 npad)
     long long hvac_off = 0;           // Real: vacuum table (n_E x S)
+    long long ref_off = 0;            // Real: initial tr(T^2) per bin (2 npad), renormalising variant only
     long long phi_off = 0;            // double: number-flux weights (4 n_E)
     int tile_begin = 0, tile_end = 0;
     // position (host view, valid after a sync): r = r0 + k0 h
@@ -101,7 +102,7 @@ struct InstHost {
 
 struct xf_ctx {
     std::vector<xfp::InstHost> in;
-    int real_bytes = 8, stepper = XF_RK4, nfm = 2;
+    int real_bytes = 8, precision = XF_FP64, stepper = XF_RK4, nfm = 2;
     cudaStream_t stream = nullptr;
     xf_allocator alloc{};
     bool has_alloc = false;
@@ -157,7 +158,7 @@ double radius(const InstHost &h);
 int enqueue_requests(xf_ctx *c, long long n, const std::vector<long long> &req);
 int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ctx **out);
 int create_slots(int n_slots, long long arena_bytes, int stepper, int precision, int nfm, xf_ctx **out);
-long long block_bytes(int n_E, int n_u, int nf, int real_bytes);
+long long block_bytes(int n_E, int n_u, int nf, int precision);
 int add_problem(xf_ctx *c, const xf_problem &prob, const double *rho, double r_km, double dr_km, int *slot);
 int remove_problem(xf_ctx *c, int slot);
 int set_state_impl(xf_ctx *c, int i, const double *rho, size_t n_doubles, double r_km);

@@ -34,6 +34,10 @@ enum { GEOM_BULB = 0, GEOM_MU_R4 = 1, GEOM_SA = 2, GEOM_CONST = 3 };
 enum { MAT_NONE = 0, MAT_POWER = 1, MAT_EXP = 2 };
 enum { STEP_RK4 = 0, STEP_EXPH = 1 };
 enum { ERR_NONFINITE = 1, ERR_BARRIER = 2 };
+// variants of the per-bin arithmetic: plain; moments summed in compensated
+// FP32 (TwoSum) up to the warp; plain with the per-step restoration of each
+// bin's tr(rho0^2) (|P|^2 / 2 in two flavors) to its initial value
+enum { VAR_PLAIN = 0, VAR_COMP = 1, VAR_RENORM = 2 };
 constexpr int NVMAX = 16; // 2 (n_f^2 - 1) for three flavors
 
 // One problem of a pack.  Its three state buffers (the two ping-pong copies
@@ -44,6 +48,7 @@ struct Inst {
     int n_E, n_u, nf, geometry;
     int matter, n_pairs, npad, pad0_;
     long long off[3], hvac_off;
+    long long ref_off;      // Real: per-bin tr(rho0^2) of the initial state (renormalising variant)
     double R, mu0, du, dE;
     double ne_ref, r_ref, ne_power, nb0, h_ns, Ye, gf;
     double r0, h;           // step k of the run starts at r0 + k h
@@ -242,6 +247,49 @@ struct Shared {
     int flag, m_inst;       // barrier flag; instance whose moments sit in M
 };
 
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e)
+{
+    s = a + b;
+    T bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// Compensated version of cta_partial: the per-thread sums carry their
+// rounding errors mc; the warp tree adds pairs with TwoSum; the warp leaders
+// hand s + e to the FP64 sum over warps.
+template <int NV, int NT, typename Acc>
+__device__ __forceinline__ void cta_partial_comp(Acc *m, Acc *mc, Shared &sh, double *part)
+{
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+        Acc v = m[c], e = mc[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            Acc v2 = __shfl_down_sync(0xffffffffu, v, off), e2 = __shfl_down_sync(0xffffffffu, e, off);
+            Acc s, er;
+            two_sum(v, v2, s, er);
+            v = s;
+            e = e + e2 + er;
+        }
+        m[c] = v;
+        mc[c] = e;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < NV; ++c) sh.w[w][c] = (double)m[c] + (double)mc[c];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < NT / 32; ++q) s += sh.w[q][threadIdx.x];
+        __stcg(part + threadIdx.x, s);
+    }
+    __syncthreads();
+}
+
 // Reduce per-thread partial sums over the CTA in fixed order: warp shuffle
 // tree in Acc precision, warps in order in FP64; writes NV doubles to part.
 template <int NV, int NT, typename Acc>
@@ -317,22 +365,46 @@ __device__ __forceinline__ void accum(const Real *tn, const Real *tb, Acc wa, Ac
     }
 }
 
+// As accum, with each running sum's rounding error carried in mc (TwoSum).
+template <int NF, typename Real, typename Acc>
+__device__ __forceinline__ void accum_comp(const Real *tn, const Real *tb, Acc wa, Acc wb, Acc *m, Acc *mc)
+{
+    constexpr int S = Comp<NF>::S;
+    Real d[S];
+    nu_minus_conj_nubar<NF, Real>(tn, tb, d);
+#pragma unroll
+    for (int c = 0; c < S; ++c) {
+        Acc dc = (Acc)d[c], s, e;
+        two_sum(m[c], wa * dc, s, e);
+        m[c] = s;
+        mc[c] += e;
+        two_sum(m[S + c], wb * dc, s, e);
+        m[S + c] = s;
+        mc[S + c] += e;
+    }
+}
+
 // The fields of an instance a tile's inner loop needs, held in registers.
 template <typename Real>
 struct TileView {
-    const Real *cur, *hvac;
+    const Real *cur, *hvac, *ref;
     Real *nxt, *aux;
     int n_E, npad, p0, p1, j_lo;
     double h;
 };
 
 // One stage of one tile: update every pair, accumulate and reduce the sums.
-template <int NF, int STEP, typename Real, int NT>
+template <int NF, int STEP, typename Real, int NT, int VAR>
 __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int st, const Real *tb, Shared &sh,
                                            double *part_out)
 {
     constexpr int S = Comp<NF>::S, NV = 2 * S;
     using Acc = Real; // warp-level accumulation precision
+    constexpr int NC = (VAR == VAR_COMP) ? NV : 1;
+    Acc mc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) mc[c] = Acc(0);
+    const bool last_stage = (STEP == STEP_RK4) ? (st == 3) : (st == 1);
     const double h = v.h;
     const double mu = sh.mu;
     const Real A = (Real)sh.A;
@@ -383,6 +455,7 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
 #pragma unroll
                     for (int c = 0; c < S; ++c) bb[c] += cb * kk[c];
                 }
+                if (VAR == VAR_RENORM && last_stage) renormalise<NF, Real>(bb, v.ref[(size_t)s * v.npad + p]);
                 store_state<Real, S>(v.nxt, v.npad, s, p, bb);
                 Real *o = (s == 0) ? on : ob;
                 if (st < 3) {
@@ -411,33 +484,41 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
                     load_state<Real, S>(v.aux, v.npad, s, p, pp);
 #pragma unroll
                     for (int c = 0; c < S; ++c) o[c] = Real(0.5) * (pp[c] + pr[c]);
+                    if (VAR == VAR_RENORM && last_stage) renormalise<NF, Real>(o, v.ref[(size_t)s * v.npad + p]);
                     store_state<Real, S>(v.nxt, v.npad, s, p, o);
                 }
             }
         }
-        accum<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], m);
+        if constexpr (VAR == VAR_COMP) accum_comp<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], m, mc);
+        else accum<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], m);
     }
-    cta_partial<NV, NT, Acc>(m, sh, part_out);
+    if constexpr (VAR == VAR_COMP) cta_partial_comp<NV, NT, Acc>(m, mc, sh, part_out);
+    else cta_partial<NV, NT, Acc>(m, sh, part_out);
 }
 
 // Prologue for one tile: weighted sums of the input state.
-template <int NF, typename Real, int NT>
+template <int NF, typename Real, int NT, int VAR>
 __device__ __forceinline__ void prologue_tile(const TileView<Real> v, int smax, const Real *tb, Shared &sh,
                                               double *part_out)
 {
     constexpr int S = Comp<NF>::S, NV = 2 * S;
     using Acc = Real;
-    Acc m[NV];
+    constexpr int NC = (VAR == VAR_COMP) ? NV : 1;
+    Acc m[NV], mc[NC];
 #pragma unroll
     for (int c = 0; c < NV; ++c) m[c] = Acc(0);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) mc[c] = Acc(0);
     for (int p = v.p0 + threadIdx.x; p < v.p1; p += NT) {
         const int q = p / v.n_E - v.j_lo;
         Real tn[S], tb_[S];
         load_state<Real, S>(v.cur, v.npad, 0, p, tn);
         load_state<Real, S>(v.cur, v.npad, 1, p, tb_);
-        accum<NF, Real, Acc>(tn, tb_, tb[2 * smax + q], tb[3 * smax + q], m);
+        if constexpr (VAR == VAR_COMP) accum_comp<NF, Real, Acc>(tn, tb_, tb[2 * smax + q], tb[3 * smax + q], m, mc);
+        else accum<NF, Real, Acc>(tn, tb_, tb[2 * smax + q], tb[3 * smax + q], m);
     }
-    cta_partial<NV, NT, Acc>(m, sh, part_out);
+    if constexpr (VAR == VAR_COMP) cta_partial_comp<NV, NT, Acc>(m, mc, sh, part_out);
+    else cta_partial<NV, NT, Acc>(m, sh, part_out);
 }
 
 __device__ __forceinline__ bool moments_finite(const double *M, int nv)
@@ -467,6 +548,7 @@ __device__ __forceinline__ TileView<Real> make_view(const RunArgs &a, const Inst
     v.nxt = odd ? b0 : b1;
     v.aux = base + in.off[2];
     v.hvac = base + in.hvac_off;
+    v.ref = base + in.ref_off;
     v.n_E = in.n_E;
     v.npad = in.npad;
     v.p0 = tl.p0;
@@ -511,8 +593,9 @@ __device__ __forceinline__ void finish_instance(const RunArgs &a, const Inst &in
     __syncthreads();
 }
 
-// NFM: 2 or 3 (every instance has that many flavors) or 0 (mixed pack).
-template <int NFM, int STEP, typename Real, int NT>
+// NFM: 2 or 3 (every instance has that many flavors) or 0 (mixed pack);
+// VAR: VAR_PLAIN, VAR_COMP or VAR_RENORM.
+template <int NFM, int STEP, typename Real, int NT, int VAR>
 __global__ void __launch_bounds__(NT) xf_run_kernel(RunArgs a)
 {
     extern __shared__ double s_dyn[];
@@ -541,9 +624,9 @@ __global__ void __launch_bounds__(NT) xf_run_kernel(RunArgs a)
         __syncthreads();
         double *out = a.partials + (size_t)t * NVMAX;
         if (nf == 2) {
-            if constexpr (NFM != 3) prologue_tile<2, Real, NT>(v, smax, s_tab, sh, out);
+            if constexpr (NFM != 3) prologue_tile<2, Real, NT, VAR>(v, smax, s_tab, sh, out);
         } else {
-            if constexpr (NFM != 2) prologue_tile<3, Real, NT>(v, smax, s_tab, sh, out);
+            if constexpr (NFM != 2) prologue_tile<3, Real, NT, VAR>(v, smax, s_tab, sh, out);
         }
     }
     if (!grid_barrier(a, ++nbar, &sh.flag)) return;
@@ -609,9 +692,9 @@ __global__ void __launch_bounds__(NT) xf_run_kernel(RunArgs a)
                 }
                 __syncthreads();
                 if (nf == 2) {
-                    if constexpr (NFM != 3) stage_tile<2, STEP, Real, NT>(v, smax, st, s_tab, sh, out);
+                    if constexpr (NFM != 3) stage_tile<2, STEP, Real, NT, VAR>(v, smax, st, s_tab, sh, out);
                 } else {
-                    if constexpr (NFM != 2) stage_tile<3, STEP, Real, NT>(v, smax, st, s_tab, sh, out);
+                    if constexpr (NFM != 2) stage_tile<3, STEP, Real, NT, VAR>(v, smax, st, s_tab, sh, out);
                 }
             }
             if (!grid_barrier(a, ++nbar, &sh.flag)) return;

@@ -60,8 +60,6 @@ struct xf_server {
 
 namespace {
 
-int real_bytes_of(int precision) { return precision == XF_FP64 ? 8 : 4; }
-
 // Admit queued jobs while a slot is free and the budget allows (called with
 // the lock held; drops it around device work).
 void admit(xf_server *s, std::unique_lock<std::mutex> &lk)
@@ -185,7 +183,7 @@ int xf_server_create(const xf_server_cfg *cfg, xf_server **out)
     if (cfg->max_jobs < 1 || cfg->mem_budget_bytes <= 0 || cfg->chunk_steps < 1 || cfg->queue_cap < 1)
         return XF_E_ARG;
     if (cfg->stepper != XF_RK4 && cfg->stepper != XF_EXPH) return XF_E_ARG;
-    if (cfg->precision != XF_FP64 && cfg->precision != XF_FP32_M64) return XF_E_UNSUPPORTED;
+    if (cfg->precision < XF_FP64 || cfg->precision > XF_FP32_M64_RENORM) return XF_E_ARG;
     if (cfg->n_flavor != 0 && cfg->n_flavor != 2 && cfg->n_flavor != 3) return XF_E_ARG;
     if (cfg->tile_pairs < 0) return XF_E_ARG;
     xf_server *s = new (std::nothrow) xf_server();
@@ -223,7 +221,7 @@ int xf_submit(xf_server *s, const xf_job *job, uint64_t *job_id)
         return XF_E_ARG;
     Job j;
     j.spec = *job;
-    j.bytes = block_bytes(p.n_E, p.n_u, p.n_flavor, real_bytes_of(s->cfg.precision));
+    j.bytes = block_bytes(p.n_E, p.n_u, p.n_flavor, s->cfg.precision);
     if (j.bytes > s->cfg.mem_budget_bytes) return XF_E_TOO_BIG;
     if (job->rho0) {
         const size_t n = (size_t)2 * p.n_u * p.n_E * p.n_flavor * p.n_flavor;

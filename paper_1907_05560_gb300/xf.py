@@ -119,6 +119,7 @@ SIGNATURES = {
     "xf_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.c_size_t, _D,
                                           ctypes.POINTER(ctypes.c_int64)]),
     "xf_batch_outputs": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, ctypes.c_size_t]),
+    "xf_batch_run_moments": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, ctypes.c_size_t]),
     "xf_batch_step": (ctypes.c_int, [_P, ctypes.c_int64, _D]),
     "xf_batch_status": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int64), _D]),
@@ -272,6 +273,13 @@ class Context:
         m = self.n_f * self.n_f
         M0, M1 = np.empty(m), np.empty(m)
         self._check(self.L.xf_moments(self.h, _dp(M0), _dp(M1), m))
+        return M0, M1
+
+    def run_moments(self, i: int = 0):
+        """Traceless M0, M1 of problem i's state as the integrator summed them."""
+        n_f = self.problems[i].n_f if hasattr(self, "problems") else self.n_f
+        M0, M1 = np.empty(n_f * n_f), np.empty(n_f * n_f)
+        self._check(self.L.xf_batch_run_moments(self.h, i, _dp(M0), _dp(M1), n_f * n_f))
         return M0, M1
 
     def outputs(self):

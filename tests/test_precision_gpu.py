@@ -1,0 +1,206 @@
+"""FP32 precision variants (XF_FP32_M64, XF_FP32_COMP, XF_FP32_M64_RENORM)
+against the FP64 oracle.
+
+* The compensated variant sums the moments (Eq. 3.13) more accurately than
+  the plain one: both are compared with the FP64 sum over the same FP32
+  state.
+* The renormalising variant holds every bin's tr(T^2) (|P| in two flavors)
+  at its initial value, a constant of the exact flow (Eq. 3.10).
+* The precision study: the two-flavor single-bulb physics (16 angles x 32
+  energies, mu0 = 1e5 km^-1, inverted hierarchy) from 10 km with h = 0.1 km
+  (EXPH) and from 50 km with h = 0.01 km (RK4 and EXPH), checked at 100, 300
+  and 1000 km: max |dP_surv| against the oracle, trace and tr(T^2) drift.
+  Set XF_PRECISION_REPORT=<path> to write the numbers as JSON.
+"""
+import ctypes
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1907_05560_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+VARIANTS = {"fp32_m64": I.FP32_M64, "fp32_comp": I.FP32_COMP, "fp32_m64_renorm": I.FP32_M64_RENORM}
+
+
+@pytest.fixture(scope="module")
+def xf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_05560_gb300 import build, xf as X
+    build.build()
+    X.load()
+    return X
+
+
+def traceless(M, n_f):
+    M = M.copy()
+    d = M[:n_f].mean()
+    M[:n_f] -= d
+    return M
+
+
+@pytest.mark.parametrize("n_f", [2, 3])
+def test_compensated_moments_beat_plain_fp32_sums(xf, n_f):
+    """One tile, so every thread sums n_pairs / 256 (or / 128) terms; the
+    plain FP32 running sum loses ~sqrt(n) ulps of the total, the TwoSum one
+    only the products' own rounding."""
+    kw = dict(dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.72)) if n_f == 3 else dict(theta=(0.1, 0, 0))
+    p = I.Problem(n_E=200, n_u=1000, n_f=n_f, mu0=1e4, hierarchy=-1, stepper=I.EXPH, r0=50.0, r1=50.01,
+                  n_steps=1, eps=1e-3, seed=7, **kw)
+    err = {}
+    for name in ("fp32_m64", "fp32_comp"):
+        c = xf.Context(p.replace(precision=VARIANTS[name]))
+        c.set_option(xf.OPT_TILE_PAIRS, p.n_E * p.n_u)
+        c.init_state(p.r0)
+        with pytest.raises(xf.XFError):
+            c.run_moments()  # no step taken yet
+        c.step(1, p.h)
+        R0, R1 = c.run_moments()
+        F0, F1 = c.moments()
+        F0, F1 = traceless(F0, n_f), traceless(F1, n_f)
+        assert abs(R0[:n_f].sum()) <= 1e-12 * np.abs(F0).max()
+        err[name] = max(np.abs(R0 - F0).max() / np.abs(F0).max(), np.abs(R1 - F1).max() / np.abs(F1).max())
+        c.close()
+    assert err["fp32_comp"] < 1e-7, err
+    assert err["fp32_comp"] < err["fp32_m64"], err
+
+
+def purity_drift(c, q0):
+    q = c.outputs()[2]
+    return float(np.abs(q / q0 - 1.0).max())
+
+
+@pytest.mark.parametrize("n_f,stepper", [(2, I.RK4), (2, I.EXPH), (3, I.RK4), (3, I.EXPH)])
+def test_renormalised_variant_holds_purity(xf, orc, n_f, stepper):
+    kw = dict(dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.72), hierarchy=+1) if n_f == 3 else {}
+    p = I.c1().replace(n_f=n_f, stepper=stepper, r0=50.0, r1=70.0, n_steps=2000, **kw)
+    drift = {}
+    for name in ("fp32_m64", "fp32_m64_renorm"):
+        c = xf.Context(p.replace(precision=VARIANTS[name]))
+        if name == "fp32_m64":
+            c.init_state(p.r0)
+        else:
+            c.set_state(orc.init_state(p), p.r0)  # reference values from the host state
+        q0 = c.outputs()[2]
+        c.step(p.n_steps, p.h)
+        drift[name] = purity_drift(c, q0)
+        assert np.isfinite(c.get_state()[0]).all()
+        c.close()
+    assert drift["fp32_m64_renorm"] < 2e-6, drift
+    assert drift["fp32_m64_renorm"] <= drift["fp32_m64"], drift
+
+
+def test_renormalised_variant_through_init_state_and_no_alloc(xf, orc):
+    import torch
+    p = I.c1().replace(stepper=I.EXPH, precision=I.FP32_M64_RENORM, r0=50.0, r1=60.0, n_steps=1000)
+    c = xf.Context(p)
+    c.init_state(p.r0)
+    q0 = c.outputs()[2]
+    c.step(p.n_steps, p.h)
+    assert purity_drift(c, q0) < 2e-6
+    ctx_state = c.get_state()[0]
+    c.close()
+    rho = torch.tensor(orc.init_state(p), dtype=torch.float64, device="cuda")
+    L = xf.load()
+    prm = xf.params_from(p)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.xf_step_noalloc(p.n_E, p.n_u, p.n_f, ctypes.byref(prm), ctypes.c_void_p(rho.data_ptr()), p.r0,
+                           p.n_steps, p.h, stream)
+    assert rc == 0, xf.status_str(rc)
+    torch.cuda.synchronize()
+    out = rho.cpu().numpy()
+    # same arithmetic, different tiling of the moment sums: agree to FP32 level
+    assert np.abs(out - ctx_state).max() < 1e-4 * np.abs(ctx_state).max()
+
+
+# ---- the precision study -----------------------------------------------------
+
+CHECK_R = (100.0, 300.0, 1000.0)
+CASES = {
+    "c3_exph_h0.1": lambda prec: I.c3(prec),
+    "c3a_rk4_h0.01": lambda prec: I.c3a(prec, I.RK4),
+    "c3a_exph_h0.01": lambda prec: I.c3a(prec, I.EXPH),
+}
+_oracle_cache = {}
+
+
+def p_surv(rho, rho0, n_f):
+    x = rho.reshape(-1, n_f * n_f)
+    x0 = rho0.reshape(-1, n_f * n_f)
+    den = x0[:, 0] - x0[:, 1]
+    ok = np.abs(den) > 1e-12 * np.abs(x0[:, 0])
+    return (x[ok, 0] - x0[ok, 1]) / den[ok]
+
+
+def trace_of(rho, n_f):
+    return rho.reshape(-1, n_f * n_f)[:, :n_f].sum(1)
+
+
+def purity_of(rho, n_f):
+    x = rho.reshape(-1, n_f * n_f)
+    tr = x[:, :n_f].sum(1)
+    d = x[:, :n_f] - tr[:, None] / n_f
+    return (d * d).sum(1) + 2.0 * (x[:, n_f:] ** 2).sum(1)
+
+
+def oracle_checkpoints(orc, case, p):
+    if case not in _oracle_cache:
+        rho = orc.init_state(p)
+        out, r, k = {}, rho, 0
+        for R in CHECK_R:
+            n = int(round((R - p.r0) / p.h))
+            r, ok, done = orc.evolve(p, r, p.r0 + k * p.h, p.h, n - k, n_threads=THREADS)
+            assert ok == 0 and done == n - k
+            k = n
+            out[R] = r
+        _oracle_cache[case] = (rho, out)
+    return _oracle_cache[case]
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_precision_study(xf, orc, case):
+    base = CASES[case](I.FP64)
+    rho0, ref = oracle_checkpoints(orc, case, base)
+    n_f = base.n_f
+    q_ref0 = purity_of(rho0, n_f)
+    rows = []
+    for name, prec in [("fp64", I.FP64)] + list(VARIANTS.items()):
+        p = base.replace(precision=prec)
+        c = xf.Context(p)
+        c.set_state(rho0, p.r0)
+        k = 0
+        for R in CHECK_R:
+            n = int(round((R - p.r0) / p.h))
+            c.step(n - k, p.h)
+            k = n
+            got, r, done = c.get_state()
+            assert done == n and r == pytest.approx(R, rel=1e-12)
+            dP = float(np.abs(p_surv(got, rho0, n_f) - p_surv(ref[R], rho0, n_f)).max())
+            tr_gpu = float(np.abs(trace_of(got, n_f) / trace_of(rho0, n_f) - 1).max())
+            tr_orc = float(np.abs(trace_of(ref[R], n_f) / trace_of(rho0, n_f) - 1).max())
+            pur_gpu = float(np.abs(purity_of(got, n_f) / q_ref0 - 1).max())
+            pur_orc = float(np.abs(purity_of(ref[R], n_f) / q_ref0 - 1).max())
+            rows.append(dict(case=case, variant=name, r_km=R, steps=n, max_dP_surv=dP, trace_drift=tr_gpu,
+                             trace_drift_oracle=tr_orc, purity_drift=pur_gpu, purity_drift_oracle=pur_orc))
+            # the trace is never updated on the GPU: exact in every variant
+            assert tr_gpu <= 1e-14
+            if name == "fp64":
+                assert dP < 1e-8, rows[-1]
+            elif case.startswith("c3a"):
+                assert dP < 1e-3, rows[-1]  # FP32 gate where the integration is stable
+            if name == "fp32_m64_renorm":
+                assert pur_gpu < 2e-6, rows[-1]
+        c.close()
+    path = os.environ.get("XF_PRECISION_REPORT")
+    if path:
+        old = json.load(open(path)) if os.path.exists(path) else []
+        old = [r for r in old if r["case"] != case] + rows
+        with open(path, "w") as f:
+            json.dump(old, f, indent=1)
+    for r in rows:
+        print(json.dumps(r))
