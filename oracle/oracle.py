@@ -29,7 +29,7 @@ class OrcParams(ctypes.Structure):
         ("n_E", ctypes.c_int32), ("n_u", ctypes.c_int32), ("n_f", ctypes.c_int32),
         ("stepper", ctypes.c_int32), ("geometry", ctypes.c_int32),
         ("hierarchy", ctypes.c_int32), ("matter", ctypes.c_int32),
-        ("n_threads", ctypes.c_int32),
+        ("n_threads", ctypes.c_int32), ("renorm", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("R_nu", ctypes.c_double), ("mu0", ctypes.c_double),
         ("E_min", ctypes.c_double), ("E_max", ctypes.c_double),
         ("dm2", ctypes.c_double * 2), ("theta", ctypes.c_double * 3),
@@ -74,12 +74,14 @@ def lib():
     return _lib
 
 
-def params(p, n_threads: int = 0) -> OrcParams:
-    """Oracle parameter block from an inputs.Problem."""
+def params(p, n_threads: int = 0, renorm: bool = False) -> OrcParams:
+    """Oracle parameter block from an inputs.Problem (renorm: restore each
+    bin's entry tr(T^2) after every step)."""
     o = OrcParams()
     o.n_E, o.n_u, o.n_f = p.n_E, p.n_u, p.n_f
     o.stepper, o.geometry, o.hierarchy, o.matter = p.stepper, p.geometry, p.hierarchy, p.matter
     o.n_threads = n_threads
+    o.renorm = 1 if renorm else 0
     o.R_nu, o.mu0, o.E_min, o.E_max = p.R_nu, p.mu0, p.E_min, p.E_max
     o.dm2[:] = list(p.dm2)
     o.theta[:] = list(p.theta)
@@ -122,9 +124,9 @@ def init_state(p) -> np.ndarray:
     return rho
 
 
-def evolve(p, rho: np.ndarray, r0: float, h: float, n_steps: int, n_threads: int = 0):
+def evolve(p, rho: np.ndarray, r0: float, h: float, n_steps: int, n_threads: int = 0, renorm: bool = False):
     """Returns (rho_out, status, steps_done); status 1 = non-finite stop."""
-    o = params(p, n_threads)
+    o = params(p, n_threads, renorm)
     out = np.ascontiguousarray(rho, dtype=np.float64).copy()
     done = ctypes.c_int64(0)
     rc = lib().orc_evolve(ctypes.byref(o), _dp(out), r0, h, int(n_steps), ctypes.byref(done))

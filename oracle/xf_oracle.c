@@ -25,7 +25,9 @@
  *                             exponential from a complex Jacobi eigensolver
  *   - integrators             classic RK4 on d(rho)/dr = -i[H,rho] dl/dr, and
  *                             the fixed-step coarse predictor-corrector of
- *                             Sec. 4.2.3 / Listing 5.1 (S1-S3) in rho form
+ *                             Sec. 4.2.3 / Listing 5.1 (S1-S3) in rho form;
+ *                             either optionally renormalised after each step
+ *                             to the entry tr(T^2) (a constant of Eq. 3.10)
  *
  * Readings taken where the paper is silent (each listed in the design doc):
  *   angle variable u = sin^2(theta_0) on a midpoint grid; energy midpoint grid;
@@ -54,6 +56,9 @@ enum { ORC_MATTER_NONE = 0, ORC_MATTER_POWER = 1, ORC_MATTER_EXP = 2 };
 
 typedef struct {
     int32_t n_E, n_u, n_f, stepper, geometry, hierarchy, matter, n_threads;
+    int32_t renorm;   /* 1: after every step, scale each bin's traceless part back to
+                         the tr(T^2) it had on entry (see renormalise()) */
+    int32_t reserved;
     double R_nu;      /* neutrinosphere radius, km */
     double mu0;       /* nu-nu coupling, km^-1 */
     double E_min, E_max; /* MeV */
@@ -588,6 +593,42 @@ static int step_exph(const orc_ctx *c, scratch_t *w, const cplx *rho, double r, 
     return 1;
 }
 
+/* Renormalised method: the exact flow d(rho)/dr = -i[H, rho] dl/dr (Eq. 3.2,
+ * 3.10) is a unitary conjugation per bin, so it keeps tr(rho), and with it
+ * tr(T^2) of the traceless part T = rho - tr(rho)/n I (|P|^2 / 2 in two
+ * flavors).  Neither RK4 nor the averaged predictor-corrector keeps tr(T^2);
+ * this variant of either method restores it after every step:
+ *     rho <- tr(rho)/n I + sqrt(q0 / q) T,   q = tr(T^2), q0 its value on entry. */
+static void purity_of(int n, const cplx *rho, double *q)
+{
+    double tau = 0;
+    for (int i = 0; i < n; ++i) tau += creal(rho[i * n + i]);
+    tau /= n;
+    double s = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            cplx t = rho[i * n + j] - (i == j ? tau : 0.0);
+            s += creal(t) * creal(t) + cimag(t) * cimag(t);
+        }
+    *q = s;
+}
+
+static void renormalise(int n, cplx *rho, double q0)
+{
+    double q;
+    purity_of(n, rho, &q);
+    if (!(q > 0) || !(q0 > 0)) return;
+    double tau = 0;
+    for (int i = 0; i < n; ++i) tau += creal(rho[i * n + i]);
+    tau /= n;
+    double f = sqrt(q0 / q);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            cplx d = (i == j) ? tau : 0.0;
+            rho[i * n + j] = d + f * (rho[i * n + j] - d);
+        }
+}
+
 /* ---- exported entry points (ctypes) --------------------------------------- */
 
 /* Tables for inspection: E[nE], u[nu], phi[4*nE], Hvac[nE*n*n] packed. */
@@ -670,6 +711,11 @@ int orc_evolve(const orc_params *p, double *rho_packed, double r0, double h, int
     w.kap = malloc(sizeof(double) * c.nu);
     w.Sbuf = malloc(sizeof(cplx) * c.nu * c.m);
     for (int b = 0; b < c.nbins; ++b) unpack(c.n, rho_packed + (size_t)b * c.m, rho + (size_t)b * c.m);
+    double *q0 = NULL;
+    if (p->renorm) {
+        q0 = malloc(sizeof(double) * c.nbins);
+        for (int b = 0; b < c.nbins; ++b) purity_of(c.n, rho + (size_t)b * c.m, &q0[b]);
+    }
     int status = 0;
     int64_t done = 0;
     for (int64_t st = 0; st < n_steps; ++st) {
@@ -687,8 +733,11 @@ int orc_evolve(const orc_params *p, double *rho_packed, double r0, double h, int
         cplx *t = rho;
         rho = Y;
         Y = t;
+        if (q0)
+            for (int b = 0; b < c.nbins; ++b) renormalise(c.n, rho + (size_t)b * c.m, q0[b]);
         ++done;
     }
+    free(q0);
     for (int b = 0; b < c.nbins; ++b) pack(c.n, rho + (size_t)b * c.m, rho_packed + (size_t)b * c.m);
     if (steps_done) *steps_done = done;
     free(rho);

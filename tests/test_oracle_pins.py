@@ -472,3 +472,54 @@ def test_literal_mu_r4_breaks_lepton_number(orc):
     I0, scale = _lepton_invariants(orc, p, rho)
     I1, _ = _lepton_invariants(orc, p, out)
     assert np.abs(I1 - I0).max() > 1e-6 * scale
+
+
+# ---------------------------------------------------------------- renormalised method
+
+@pytest.mark.parametrize("stepper", [I.RK4, I.EXPH])
+@pytest.mark.parametrize("n_f", [2, 3])
+def test_renormalised_method_keeps_purity_and_trace(orc, stepper, n_f):
+    """The renormalised method holds each bin's tr(T^2) (a constant of the
+    exact flow, Eq. 3.10) and its trace, in a regime where the plain method
+    visibly loses tr(T^2) (strong coupling, coarse step)."""
+    kw = dict(dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.72)) if n_f == 3 else {}
+    p = _small(n_f=n_f, stepper=stepper, mu0=3e4, eps=1e-2, r0=50.0, r1=52.0, n_steps=100, **kw)
+    rho = orc.init_state(p)
+    plain, st0, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    ren, st1, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps, renorm=True)
+    assert st0 == 0 and st1 == 0
+    q0, qp, qr = _purity_like(rho, n_f), _purity_like(plain, n_f), _purity_like(ren, n_f)
+    assert np.abs(qp / q0 - 1).max() > 1e-6      # the plain method drifts here
+    assert np.abs(qr / q0 - 1).max() < 1e-13     # the renormalised one does not
+    assert np.abs(_trace(ren, n_f) - _trace(rho, n_f)).max() < 1e-13 * np.abs(_trace(rho, n_f)).max()
+
+
+def test_renormalised_method_is_exact_in_vacuum(orc):
+    """In vacuum the predictor-corrector is exact (P1), so it keeps tr(T^2) by
+    itself and the renormalisation must not change anything; the result is
+    the textbook survival probability."""
+    p = _small(n_E=12, n_u=5, stepper=I.EXPH, eps=0.0, theta=(0.3, 0, 0), hierarchy=-1,
+               E_min=1.0, E_max=13.0, r0=20.0, r1=30.0, n_steps=1000)
+    rho = orc.init_state(p)
+    plain, _, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    ren, _, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps, renorm=True)
+    assert np.abs(ren - plain).max() < 1e-13 * np.abs(plain).max()
+
+
+def test_renormalised_rk4_converges_to_the_same_flow(orc):
+    """On an oscillation RK4's amplification factor has modulus
+    sqrt(1 - z^6/72 + ...) (z = lambda h), so plain RK4 loses tr(T^2) by
+    O(h^6) per step, O(h^5) over a fixed interval; the renormalisation
+    removes just that, so halving h shrinks the plain-vs-renormalised gap
+    about 32x and both approach the same exact flow.  A renormalisation that
+    rescaled anything but the traceless part would leave an O(1) gap."""
+    base = _small(n_E=6, n_u=4, mu0=1e5, eps=1e-2, r0=50.0, r1=51.0)
+    rho = orc.init_state(base)
+
+    def gap(n):
+        a, _, _ = orc.evolve(base, rho, 50.0, 1.0 / n, n)
+        b, _, _ = orc.evolve(base, rho, 50.0, 1.0 / n, n, renorm=True)
+        return np.abs(a - b).max()
+
+    g = [gap(n) for n in (25, 50, 100)]
+    assert 26 < g[0] / g[1] < 38 and 26 < g[1] / g[2] < 38
