@@ -342,41 +342,45 @@ int plan_launch(xf_ctx *c)
     return XF_OK;
 }
 
-// Device copy of the instance table (static fields and the current r0, h).
+// The device descriptor of one problem (static fields and the current r0, h).
+Inst make_inst(const InstHost &h)
+{
+    const double gf = matter_coefficient();
+    Inst d;
+    std::memset(&d, 0, sizeof d);
+    d.n_E = h.n_E;
+    d.n_u = h.n_u;
+    d.nf = h.nf;
+    d.geometry = h.p.geometry;
+    d.matter = h.p.matter;
+    d.n_pairs = h.n_pairs;
+    d.npad = h.npad;
+    d.hvac_off = h.hvac_off;
+    d.ref_off = h.ref_off;
+    for (int b = 0; b < 3; ++b) d.off[b] = h.off[b];
+    d.R = h.p.R_nu_km;
+    d.mu0 = h.p.mu0_per_km;
+    d.du = 1.0 / h.n_u;
+    d.dE = (h.p.E_max_MeV - h.p.E_min_MeV) / h.n_E;
+    d.ne_ref = h.p.ne_ref_cm3;
+    d.r_ref = h.p.r_ref_km;
+    d.ne_power = h.p.ne_power;
+    d.nb0 = h.p.nb0_cm3;
+    d.h_ns = h.p.h_ns_km;
+    d.Ye = h.p.Ye;
+    d.gf = gf;
+    d.r0 = h.r0;
+    d.h = h.h;
+    d.tile_begin = h.tile_begin;
+    d.tile_end = h.tile_end;
+    return d;
+}
+
+// Device copy of the instance table.
 int upload_instances(xf_ctx *c)
 {
     std::vector<Inst> v(c->in.size());
-    const double gf = matter_coefficient();
-    for (size_t i = 0; i < c->in.size(); ++i) {
-        const InstHost &h = c->in[i];
-        Inst &d = v[i];
-        std::memset(&d, 0, sizeof d);
-        d.n_E = h.n_E;
-        d.n_u = h.n_u;
-        d.nf = h.nf;
-        d.geometry = h.p.geometry;
-        d.matter = h.p.matter;
-        d.n_pairs = h.n_pairs;
-        d.npad = h.npad;
-        d.hvac_off = h.hvac_off;
-        d.ref_off = h.ref_off;
-        for (int b = 0; b < 3; ++b) d.off[b] = h.off[b];
-        d.R = h.p.R_nu_km;
-        d.mu0 = h.p.mu0_per_km;
-        d.du = 1.0 / h.n_u;
-        d.dE = (h.p.E_max_MeV - h.p.E_min_MeV) / h.n_E;
-        d.ne_ref = h.p.ne_ref_cm3;
-        d.r_ref = h.p.r_ref_km;
-        d.ne_power = h.p.ne_power;
-        d.nb0 = h.p.nb0_cm3;
-        d.h_ns = h.p.h_ns_km;
-        d.Ye = h.p.Ye;
-        d.gf = gf;
-        d.r0 = h.r0;
-        d.h = h.h;
-        d.tile_begin = h.tile_begin;
-        d.tile_end = h.tile_end;
-    }
+    for (size_t i = 0; i < c->in.size(); ++i) v[i] = make_inst(c->in[i]);
     XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
     XF_CUDA(c, cudaMemcpy(c->inst_d, v.data(), sizeof(Inst) * v.size(), cudaMemcpyHostToDevice), "copy instances");
     return XF_OK;
@@ -1092,6 +1096,58 @@ int xf_batch_init_state(xf_ctx *c, int inst, double r_km)
     return XF_OK;
 }
 
+namespace xfp {
+
+// Frobenius norm of the traceless part of a packed n x n Hermitian matrix.
+double traceless_norm(const double *x, int nf)
+{
+    double tr = 0.0, q = 0.0;
+    for (int i = 0; i < nf; ++i) tr += x[i];
+    for (int i = 0; i < nf; ++i) q += (x[i] - tr / nf) * (x[i] - tr / nf);
+    for (int k = nf; k < nf * nf; ++k) q += 2.0 * x[k] * x[k];
+    return std::sqrt(q);
+}
+
+// Strict mode, RK4 only: refuse a step size outside RK4's stable region.
+// d(rho)/dr = -i kappa [H, rho] has eigenvalues -i kappa (l_a - l_b), and for
+// a traceless Hermitian H the spread l_max - l_min is at most sqrt(2) ||H||_F.
+// Classic RK4 is stable on the imaginary axis for |z| <= 2 sqrt(2), so the
+// step is refused when
+//   h kappa_max sqrt(2) (max_E ||H_vac|| + A ||P_e|| + mu (||M0|| + ||M1||)) > 2 sqrt(2)
+// with every term taken at the current radius (the matter density, the
+// coupling and the bulb weights all fall with r, so the start of the call is
+// the worst point; the moments are those of the current state).
+int check_rk4_stable(xf_ctx *c, int i, double h_km)
+{
+    InstHost &h = c->in[i];
+    if (!h.p.strict || c->stepper != XF_RK4) return XF_OK;
+    const int nf = h.nf, m = nf * nf;
+    double M0[9], M1[9];
+    int rc = moments_impl(c, i, M0, M1, (size_t)m);
+    if (rc) return rc;
+    const double r = radius(h);
+    const Inst d = make_inst(h);
+    double hv = 0.0;
+    for (int e = 0; e < h.n_E; ++e) {
+        const double *t = &h.hvac[(size_t)e * h.S];
+        hv = std::max(hv, std::sqrt(nf == 2 ? purity<2, double>(t) : purity<3, double>(t)));
+    }
+    const double pe = std::sqrt((nf - 1.0) / nf); // ||diag(1, 0[, 0]) - I/n||_F
+    double kappa = 1.0;
+    if (h.p.geometry == XF_GEOM_BULB || h.p.geometry == XF_GEOM_MU_R4) {
+        const double x = h.p.R_nu_km / r;
+        kappa = 1.0 / std::sqrt(1.0 - x * x * (h.n_u - 0.5) / h.n_u);
+    }
+    const double norm = hv + matter_A(d, r) * pe + mu_eff(d, r) * (traceless_norm(M0, nf) + traceless_norm(M1, nf));
+    const double z = h_km * kappa * std::sqrt(2.0) * norm;
+    if (!(z <= 2.0 * std::sqrt(2.0)))
+        return fail(c, XF_E_UNSTABLE, "RK4 step %.6g km at r = %.6g km is outside the stable region (|z| = %.3g > 2.83)",
+                    h_km, r, z);
+    return XF_OK;
+}
+
+} // namespace xfp
+
 int xf_step_async(xf_ctx *c, int64_t n_steps, double dr_km)
 {
     if (!c) return XF_E_ARG;
@@ -1100,6 +1156,8 @@ int xf_step_async(xf_ctx *c, int64_t n_steps, double dr_km)
     InstHost &h = c->in[0];
     if (!h.state_valid) return fail(c, XF_E_STATE, "no valid state (call xf_set_state or xf_init_state)");
     if (n_steps == 0) return XF_OK;
+    int rs = check_rk4_stable(c, 0, dr_km);
+    if (rs) return rs;
     if (dr_km != h.h) {
         int rc = set_step_size(c, 0, dr_km);
         if (rc) return rc;
@@ -1136,6 +1194,10 @@ int xf_batch_step(xf_ctx *c, int64_t n_steps, const double *dr_km)
         if (!h.state_valid) return fail(c, XF_E_STATE, "problem %zu has no valid state", i);
         const double dr = dr_km ? dr_km[i] : h.h;
         if (!std::isfinite(dr) || dr <= 0) return fail(c, XF_E_ARG, "step size of problem %zu invalid", i);
+        if (n_steps > 0) {
+            int rs = check_rk4_stable(c, (int)i, dr);
+            if (rs) return rs;
+        }
         if (dr != h.h) {
             int rc = set_step_size(c, (int)i, dr);
             if (rc) return rc;

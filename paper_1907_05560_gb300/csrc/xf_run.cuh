@@ -141,14 +141,14 @@ __device__ __forceinline__ bool grid_barrier(const RunArgs &a, unsigned k, int *
     return *s_flag != 0;
 }
 
-__device__ __forceinline__ double matter_A(const Inst &a, double r)
+__host__ __device__ __forceinline__ double matter_A(const Inst &a, double r)
 {
     if (a.matter == MAT_POWER) return a.gf * a.ne_ref * pow(a.r_ref / r, a.ne_power);
     if (a.matter == MAT_EXP) return a.gf * a.Ye * a.nb0 * exp(-(r - a.R) / a.h_ns);
     return 0.0;
 }
 
-__device__ __forceinline__ double mu_eff(const Inst &a, double r)
+__host__ __device__ __forceinline__ double mu_eff(const Inst &a, double r)
 {
     double x = a.R / r, x2 = x * x;
     if (a.geometry == GEOM_MU_R4) return a.mu0 * x2 * x2;

@@ -36,6 +36,7 @@ class Problem:
     stepper: int = RK4
     geometry: int = BULB
     precision: int = FP64
+    strict: int = 0                   # 1: refuse RK4 steps outside the stable region
     R_nu: float = 10.0                # km, neutrinosphere radius
     mu0: float = 1.0e5                # km^-1
     E_min: float = 1.0                # MeV

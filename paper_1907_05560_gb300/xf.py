@@ -165,7 +165,7 @@ def params_from(p: I.Problem) -> XFParams:
     x = XFParams()
     L.xf_params_default(ctypes.byref(x))
     x.stepper, x.precision, x.geometry = p.stepper, p.precision, p.geometry
-    x.hierarchy, x.matter = p.hierarchy, p.matter
+    x.hierarchy, x.matter, x.strict = p.hierarchy, p.matter, p.strict
     x.R_nu_km, x.mu0_per_km, x.E_min_MeV, x.E_max_MeV = p.R_nu, p.mu0, p.E_min, p.E_max
     x.dm2_eV2[:] = list(p.dm2)
     x.theta[:] = list(p.theta)

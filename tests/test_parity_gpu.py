@@ -197,6 +197,30 @@ def test_literal_rk4_reports_nonfinite_like_oracle(xf, orc):
     assert abs(done - done_o) <= 1
 
 
+def test_strict_rk4_refuses_unstable_step_sizes(xf, orc):
+    """Strict mode: the literal 10 km RK4 step (h = 0.095 km, mu0 = 1e5) is
+    refused before any step is taken; the stable 50 km companion
+    (h = 0.01 km) runs and matches the oracle."""
+    p = I.c1().replace(stepper=I.RK4, strict=1)
+    rho0 = orc.init_state(p)
+    c = xf.Context(p)
+    c.set_state(rho0, p.r0)
+    with pytest.raises(xf.XFError) as ei:
+        c.step(10, p.h)
+    assert ei.value.name == "XF_E_UNSTABLE"
+    got, r, done = c.get_state()
+    assert done == 0 and r == p.r0 and np.array_equal(got, rho0)
+    c.close()
+    q = I.c1a().replace(strict=1, n_steps=200, r1=52.0)
+    rho0 = orc.init_state(q)
+    c = xf.Context(q)
+    c.set_state(rho0, q.r0)
+    c.step(q.n_steps, q.h)
+    ref, ok, _ = orc.evolve(q, rho0, q.r0, q.h, q.n_steps, n_threads=THREADS)
+    assert rel_err(c.get_state()[0], ref, q.n_f) < 1e-9
+    c.close()
+
+
 def test_step_before_state_and_bad_state(xf):
     p = small()
     c = xf.Context(p)
