@@ -37,6 +37,7 @@ class OrcParams(ctypes.Structure):
         ("nb0", ctypes.c_double), ("h_ns", ctypes.c_double), ("Ye", ctypes.c_double),
         ("T", ctypes.c_double * 4), ("eta", ctypes.c_double * 4), ("L", ctypes.c_double * 4),
         ("eps", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("eps0", ctypes.c_double), ("ksi", ctypes.c_double), ("dr_max", ctypes.c_double),
     ]
 
 
@@ -62,6 +63,10 @@ def lib():
         L.orc_evolve.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                  ctypes.POINTER(ctypes.c_int64)]
         L.orc_moments.argtypes = [P, dp, ctypes.c_double, dp, dp]
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        L.orc_evolve_adaptive.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int64, dp, dp, i64p, i64p]
+        L.orc_attempt_adaptive.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, dp, dp]
         L.orc_expm.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp]
         L.orc_eigh.argtypes = [ctypes.c_int, dp, dp, dp]
         L.orc_fd_integral.argtypes = [ctypes.c_int, ctypes.c_double]
@@ -91,6 +96,7 @@ def params(p, n_threads: int = 0, renorm: bool = False) -> OrcParams:
     o.eta[:] = list(p.eta)
     o.L[:] = list(p.L)
     o.eps, o.seed = p.eps, p.seed
+    o.eps0, o.ksi, o.dr_max = p.eps0, p.ksi, p.dr_max
     return o
 
 
@@ -133,6 +139,34 @@ def evolve(p, rho: np.ndarray, r0: float, h: float, n_steps: int, n_threads: int
     if rc < 0:
         raise ValueError(f"orc_evolve: {rc}")
     return out, rc, done.value
+
+
+def evolve_adaptive(p, rho: np.ndarray, r0: float, r_end: float, h0: float, max_iters: int = 1 << 40,
+                    n_threads: int = 0):
+    """Error-controlled evolution (eps0, ksi, dr_max from p).  Returns
+    (rho_out, status, r, h_next, n_accepted, n_rejected); status 0 = reached
+    r_end, 1 = non-finite, 2 = iteration budget spent, 3 = step underflow."""
+    o = params(p, n_threads)
+    out = np.ascontiguousarray(rho, dtype=np.float64).copy()
+    r, h = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    na, nr = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib().orc_evolve_adaptive(ctypes.byref(o), _dp(out), r0, r_end, h0, int(max_iters), ctypes.byref(r),
+                                   ctypes.byref(h), ctypes.byref(na), ctypes.byref(nr))
+    if rc < 0:
+        raise ValueError(f"orc_evolve_adaptive: {rc}")
+    return out, rc, r.value, h.value, na.value, nr.value
+
+
+def attempt_adaptive(p, rho: np.ndarray, r: float, h: float, n_threads: int = 0):
+    """One attempt: returns (rho_coarse, rho_fine, err, status)."""
+    o = params(p, n_threads)
+    out = np.ascontiguousarray(rho, dtype=np.float64).copy()
+    fine = np.zeros_like(out)
+    err = ctypes.c_double(0.0)
+    rc = lib().orc_attempt_adaptive(ctypes.byref(o), _dp(out), r, h, ctypes.byref(err), _dp(fine))
+    if rc < 0:
+        raise ValueError(f"orc_attempt_adaptive: {rc}")
+    return out, fine, err.value, rc
 
 
 def moments(p, rho: np.ndarray, r: float):

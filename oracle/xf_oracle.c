@@ -69,6 +69,9 @@ typedef struct {
     double T[4], eta[4], L[4];      /* nu_e, nubar_e, nu_x, nubar_x */
     double eps;       /* off-diagonal seed amplitude */
     uint64_t seed;
+    double eps0;      /* error-controlled step: tolerance on max |rho_c - rho_f| / tr rho */
+    double ksi;       /* safety factor of the step-size update, 0 < ksi <= 1 */
+    double dr_max;    /* largest step, km */
 } orc_params;
 
 /* ---- physical constants, stated here from CODATA 2018 / PDG ------------- */
@@ -629,6 +632,95 @@ static void renormalise(int n, cplx *rho, double q0)
         }
 }
 
+/* One attempt of the error-controlled step of Sec. 4.2.3 (Fig. 4.9; the
+ * sections S1-S5 of Listings 5.1-5.3), in rho form.  From rho0 at r with
+ * step h, U(H; r, h) = exp(-i H dl_j(r, h)) along trajectory j:
+ *   S1  H0 from rho0 at r
+ *   S2  rho1 = U(H0; r, h/2) rho0 U^+ (half step), rho2 = U(H0; r, h) rho0 U^+
+ *       (full step); H1 from rho2 at r + h, H2 from rho1 at r + h/2
+ *   S3  rho3 = U(H1; r, h) rho0 U^+, coarse result rho_c = (rho2 + rho3) / 2
+ *   S4  rho5 = U(H2; r + h/2, h/2) rho1 U^+ (midpoint to r + h); H3 from rho5
+ *       at r + h
+ *   S5  rho6 = U(H3; r, h) rho0 U^+, fine result rho_f = (rho5 + rho6) / 2;
+ *       err = max over bins b and packed entries of |rho_c - rho_f| / tr rho0_b
+ * Writes rho_c to out.  Returns 0 if a moment or a result was not finite. */
+static int hamiltonians_at(const orc_ctx *c, scratch_t *w, const cplx *src, double r, cplx *M0, cplx *M1,
+                           double *mu, double *A, double *g)
+{
+    geometry(c, r, w->a, w->b, w->g, w->kap, mu);
+    moments(c, src, w->a, w->b, M0, M1, w->Sbuf);
+    memcpy(g, w->g, sizeof(double) * c->nu);
+    *A = matter_A(c, r);
+    return all_finite(c->m, M0) && all_finite(c->m, M1);
+}
+
+/* rho_out[b] = U rho_in[b] U^+ for every bin, U = exp(-i H_b dl_j), H_b from
+ * the moments (M0, M1) with angle factors g and scalars mu, A. */
+static void propagate_all(const orc_ctx *c, const cplx *M0, const cplx *M1, double mu, double A, const double *g,
+                          const double *dl, const cplx *rho_in, cplx *rho_out)
+{
+    int n = c->n, m = c->m, nE = c->nE, nu = c->nu;
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < c->nbins; ++b) {
+        int s = b / (nu * nE), j = (b / nE) % nu, e = b % nE;
+        cplx G[NFMAX * NFMAX], H[NFMAX * NFMAX], U[NFMAX * NFMAX];
+        for (int k = 0; k < m; ++k) G[k] = mu * (M0[k] - g[j] * M1[k]);
+        hamiltonian(c, s, e, G, A, H);
+        expm_minus_iHt(n, H, dl[j], U);
+        conjugate_by(n, U, rho_in + (size_t)b * m, rho_out + (size_t)b * m);
+    }
+}
+
+typedef struct {
+    cplx *r1, *r2, *r3, *r5, *r6;
+    double *g, *dl_full, *dl_half, *dl_mid;
+} adapt_buf;
+
+static int attempt_adaptive(const orc_ctx *c, scratch_t *w, adapt_buf *B, const cplx *rho0, double r, double h,
+                            cplx *out, double *err)
+{
+    int m = c->m, nu = c->nu, nE = c->nE;
+    size_t N = (size_t)c->nbins * m;
+    cplx M0[NFMAX * NFMAX], M1[NFMAX * NFMAX];
+    double mu, A;
+    for (int j = 0; j < nu; ++j) {
+        B->dl_full[j] = path_length(c, j, r, h);
+        B->dl_half[j] = path_length(c, j, r, 0.5 * h);
+        B->dl_mid[j] = path_length(c, j, r + 0.5 * h, 0.5 * h);
+    }
+    /* S1 */
+    if (!hamiltonians_at(c, w, rho0, r, M0, M1, &mu, &A, B->g)) return 0;
+    /* S2 */
+    propagate_all(c, M0, M1, mu, A, B->g, B->dl_half, rho0, B->r1);
+    propagate_all(c, M0, M1, mu, A, B->g, B->dl_full, rho0, B->r2);
+    /* S3: H1 from rho2 at r + h */
+    if (!hamiltonians_at(c, w, B->r2, r + h, M0, M1, &mu, &A, B->g)) return 0;
+    propagate_all(c, M0, M1, mu, A, B->g, B->dl_full, rho0, B->r3);
+    for (size_t i = 0; i < N; ++i) out[i] = 0.5 * (B->r2[i] + B->r3[i]);
+    /* S4: H2 from rho1 at r + h/2 */
+    if (!hamiltonians_at(c, w, B->r1, r + 0.5 * h, M0, M1, &mu, &A, B->g)) return 0;
+    propagate_all(c, M0, M1, mu, A, B->g, B->dl_mid, B->r1, B->r5);
+    /* S5: H3 from rho5 at r + h */
+    if (!hamiltonians_at(c, w, B->r5, r + h, M0, M1, &mu, &A, B->g)) return 0;
+    propagate_all(c, M0, M1, mu, A, B->g, B->dl_full, rho0, B->r6);
+    double e = 0.0;
+    for (int b = 0; b < c->nbins; ++b) {
+        double tr = 0.0;
+        for (int i = 0; i < c->n; ++i) tr += creal(rho0[(size_t)b * m + i * c->n + i]);
+        for (int k = 0; k < m; ++k) {
+            size_t i = (size_t)b * m + k;
+            cplx f = 0.5 * (B->r5[i] + B->r6[i]);
+            double d = cabs(out[i] - f) / fabs(tr);
+            if (!(d <= e)) e = d; /* a NaN difference propagates */
+        }
+    }
+    (void)nE;
+    *err = e;
+    for (size_t i = 0; i < N; ++i)
+        if (!isfinite(creal(out[i])) || !isfinite(cimag(out[i]))) return 0;
+    return 1;
+}
+
 /* ---- exported entry points (ctypes) --------------------------------------- */
 
 /* Tables for inspection: E[nE], u[nu], phi[4*nE], Hvac[nE*n*n] packed. */
@@ -751,6 +843,180 @@ int orc_evolve(const orc_params *p, double *rho_packed, double r0, double h, int
     free(w.Sbuf);
     ctx_free(&c);
     return status;
+}
+
+/* Step-size update after an attempt with error err at step h (Sec. 4.2.3 and
+ * the eps0 / ksi / max_dr keywords of Appendix A.3): the error estimate of
+ * one attempt scales as h^2 (measured; see the tests), so the step that would
+ * just meet eps0 is h (eps0 / err)^(1/2); ksi < 1 keeps the next try on the
+ * safe side, and dr_max trims it.  err = 0 gives dr_max. */
+static double next_step(const orc_params *p, double h, double err)
+{
+    double hn = (err > 0.0) ? p->ksi * h * sqrt(p->eps0 / err) : p->dr_max;
+    return hn < p->dr_max ? hn : p->dr_max;
+}
+
+/* Error-controlled evolution from r0 to r_end (Fig. 4.8-4.9): repeat
+ * attempts; an attempt with err <= eps0 is accepted (rho <- rho_c, r <- r + h),
+ * otherwise rho and r stay; either way h <- next_step(h, err).  The last step
+ * is shortened to land on r_end, and a radius within 1e-12 r_end of r_end
+ * counts as arrived (and is set to r_end).  Stops at r_end (status 0), after max_iters
+ * attempts (status 2), at a non-finite attempt (status 1; rho is the last
+ * accepted state) or when h falls below 1e-12 r (status 3).  r_out, h_out:
+ * final radius and the next step size; n_acc / n_rej: accepted and rejected
+ * attempts. */
+int orc_evolve_adaptive(const orc_params *p, double *rho_packed, double r0, double r_end, double h0,
+                        int64_t max_iters, double *r_out, double *h_out, int64_t *n_acc, int64_t *n_rej)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, p);
+    if (rc) {
+        ctx_free(&c);
+        return rc;
+    }
+    if (!(h0 > 0) || !(r_end >= r0) || !(p->eps0 > 0) || !(p->ksi > 0) || !(p->dr_max > 0)) {
+        ctx_free(&c);
+        return -1;
+    }
+#ifdef _OPENMP
+    if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+#endif
+    size_t N = (size_t)c.nbins * c.m;
+    cplx *rho = malloc(sizeof(cplx) * N), *out = malloc(sizeof(cplx) * N);
+    adapt_buf B;
+    B.r1 = malloc(sizeof(cplx) * N);
+    B.r2 = malloc(sizeof(cplx) * N);
+    B.r3 = malloc(sizeof(cplx) * N);
+    B.r5 = malloc(sizeof(cplx) * N);
+    B.r6 = malloc(sizeof(cplx) * N);
+    B.g = malloc(sizeof(double) * c.nu);
+    B.dl_full = malloc(sizeof(double) * c.nu);
+    B.dl_half = malloc(sizeof(double) * c.nu);
+    B.dl_mid = malloc(sizeof(double) * c.nu);
+    scratch_t w;
+    w.a = malloc(sizeof(double) * c.nu);
+    w.b = malloc(sizeof(double) * c.nu);
+    w.g = malloc(sizeof(double) * c.nu);
+    w.kap = malloc(sizeof(double) * c.nu);
+    w.Sbuf = malloc(sizeof(cplx) * c.nu * c.m);
+    for (int b = 0; b < c.nbins; ++b) unpack(c.n, rho_packed + (size_t)b * c.m, rho + (size_t)b * c.m);
+    double r = r0, h = h0 < p->dr_max ? h0 : p->dr_max;
+    int64_t acc = 0, rej = 0, it = 0;
+    int status = 0;
+    /* arrival: within 1e-12 r_end of the end (the accumulated radius of many
+     * steps lands a few ulps short of it) */
+    while (r_end - r > 1e-12 * r_end) {
+        if (it >= max_iters) {
+            status = 2;
+            break;
+        }
+        if (h < 1e-12 * r) {
+            status = 3;
+            break;
+        }
+        const int last = (h >= r_end - r);
+        const double ht = last ? r_end - r : h;
+        double err = 0.0;
+        ++it;
+        if (!attempt_adaptive(&c, &w, &B, rho, r, ht, out, &err) || !isfinite(err)) {
+            status = 1;
+            break;
+        }
+        if (err <= p->eps0) {
+            cplx *t = rho;
+            rho = out;
+            out = t;
+            r = last ? r_end : r + ht;
+            ++acc;
+        } else {
+            ++rej;
+        }
+        h = next_step(p, ht, err);
+    }
+    if (status == 0) r = r_end;
+    for (int b = 0; b < c.nbins; ++b) pack(c.n, rho + (size_t)b * c.m, rho_packed + (size_t)b * c.m);
+    if (r_out) *r_out = r;
+    if (h_out) *h_out = h;
+    if (n_acc) *n_acc = acc;
+    if (n_rej) *n_rej = rej;
+    free(rho);
+    free(out);
+    free(B.r1);
+    free(B.r2);
+    free(B.r3);
+    free(B.r5);
+    free(B.r6);
+    free(B.g);
+    free(B.dl_full);
+    free(B.dl_half);
+    free(B.dl_mid);
+    free(w.a);
+    free(w.b);
+    free(w.g);
+    free(w.kap);
+    free(w.Sbuf);
+    ctx_free(&c);
+    return status;
+}
+
+/* One attempt only (no acceptance logic): rho_packed <- rho_c; *err as above;
+ * *fine (optional, packed) <- rho_f.  Returns 0, or 1 if not finite. */
+int orc_attempt_adaptive(const orc_params *p, double *rho_packed, double r, double h, double *err, double *fine)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, p);
+    if (rc) {
+        ctx_free(&c);
+        return rc;
+    }
+#ifdef _OPENMP
+    if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+#endif
+    size_t N = (size_t)c.nbins * c.m;
+    cplx *rho = malloc(sizeof(cplx) * N), *out = malloc(sizeof(cplx) * N);
+    adapt_buf B;
+    B.r1 = malloc(sizeof(cplx) * N);
+    B.r2 = malloc(sizeof(cplx) * N);
+    B.r3 = malloc(sizeof(cplx) * N);
+    B.r5 = malloc(sizeof(cplx) * N);
+    B.r6 = malloc(sizeof(cplx) * N);
+    B.g = malloc(sizeof(double) * c.nu);
+    B.dl_full = malloc(sizeof(double) * c.nu);
+    B.dl_half = malloc(sizeof(double) * c.nu);
+    B.dl_mid = malloc(sizeof(double) * c.nu);
+    scratch_t w;
+    w.a = malloc(sizeof(double) * c.nu);
+    w.b = malloc(sizeof(double) * c.nu);
+    w.g = malloc(sizeof(double) * c.nu);
+    w.kap = malloc(sizeof(double) * c.nu);
+    w.Sbuf = malloc(sizeof(cplx) * c.nu * c.m);
+    for (int b = 0; b < c.nbins; ++b) unpack(c.n, rho_packed + (size_t)b * c.m, rho + (size_t)b * c.m);
+    int ok = attempt_adaptive(&c, &w, &B, rho, r, h, out, err);
+    for (int b = 0; b < c.nbins; ++b) pack(c.n, out + (size_t)b * c.m, rho_packed + (size_t)b * c.m);
+    if (fine)
+        for (int b = 0; b < c.nbins; ++b) {
+            cplx f[NFMAX * NFMAX];
+            for (int k = 0; k < c.m; ++k) f[k] = 0.5 * (B.r5[(size_t)b * c.m + k] + B.r6[(size_t)b * c.m + k]);
+            pack(c.n, f, fine + (size_t)b * c.m);
+        }
+    free(rho);
+    free(out);
+    free(B.r1);
+    free(B.r2);
+    free(B.r3);
+    free(B.r5);
+    free(B.r6);
+    free(B.g);
+    free(B.dl_full);
+    free(B.dl_half);
+    free(B.dl_mid);
+    free(w.a);
+    free(w.b);
+    free(w.g);
+    free(w.kap);
+    free(w.Sbuf);
+    ctx_free(&c);
+    return ok ? 0 : 1;
 }
 
 /* Moments of a packed state at radius r (packed Hermitian n*n each). */

@@ -56,6 +56,9 @@ class Problem:
     L: Tuple[float, float, float, float] = (1.0, 1.0, 1.0, 1.0)
     eps: float = 1.0e-6
     seed: int = 1
+    eps0: float = 1.0e-6              # error-controlled step: tolerance
+    ksi: float = 0.9                  # error-controlled step: safety factor
+    dr_max: float = 1.0               # error-controlled step: largest step, km
     r0: float = 10.0                  # km, start radius
     r1: float = 200.0                 # km, end radius
     n_steps: int = 2000

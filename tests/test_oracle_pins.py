@@ -523,3 +523,75 @@ def test_renormalised_rk4_converges_to_the_same_flow(orc):
 
     g = [gap(n) for n in (25, 50, 100)]
     assert 26 < g[0] / g[1] < 38 and 26 < g[1] / g[2] < 38
+
+
+# ---------------------------------------------------------------- error-controlled step
+
+def test_adaptive_error_estimate_scales_as_h_squared(orc):
+    """The coarse path of an attempt is the second-order predictor-corrector;
+    the fine path (two exponential half steps averaged with a full step under
+    the end-point Hamiltonian) is first order, so their difference, the
+    error estimate, falls 4x per halving of h.  This fixes the exponent 1/2
+    of the step-size update."""
+    p = _small(stepper=I.EXPH, mu0=1e5, eps=1e-2, n_E=6, n_u=4)
+    rho = orc.init_state(p)
+    e = [orc.attempt_adaptive(p, rho, 50.0, h)[2] for h in (0.02, 0.01, 0.005)]
+    assert 3.6 < e[0] / e[1] < 4.6 and 3.6 < e[1] / e[2] < 4.6
+
+
+def test_adaptive_coarse_result_is_the_fixed_step(orc):
+    """With a tolerance no attempt can miss and h0 = dr_max, every attempt is
+    accepted at the same h, and the result is the fixed-step
+    predictor-corrector (pinned against the textbook cases P1-P3)."""
+    p = _small(stepper=I.EXPH, mu0=1e5, eps=1e-2, n_f=3, dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.72),
+               matter=I.MATTER_POWER, ne_ref=1e31, eps0=1e300, dr_max=0.01, r0=50.0, r1=50.5, n_steps=50)
+    rho = orc.init_state(p)
+    fixed, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    out, st, r, h, na, nr = orc.evolve_adaptive(p, rho, p.r0, p.r1, p.h)
+    assert st == 0 and r == p.r1 and nr == 0 and na == p.n_steps
+    assert np.abs(out - fixed).max() < 1e-13 * np.abs(fixed).max()
+
+
+def test_adaptive_is_exact_in_vacuum(orc):
+    """In vacuum both paths are exact (the propagator composes along the
+    trajectory), the error estimate is rounding, every step is dr_max and the
+    result is the textbook two-flavor survival probability (P1)."""
+    p = _small(n_E=12, n_u=5, stepper=I.EXPH, eps=0.0, theta=(0.3, 0, 0), hierarchy=-1,
+               E_min=1.0, E_max=13.0, r0=20.0, r1=30.0, eps0=1e-10, dr_max=0.25)
+    E, u, phi, Hv = orc.tables(p)
+    rho = orc.init_state(p)
+    out, st, r, h, na, nr = orc.evolve_adaptive(p, rho, p.r0, p.r1, 0.01)
+    assert st == 0 and r == p.r1 and nr == 0
+    assert na <= 2 + int(np.ceil((p.r1 - p.r0) / p.dr_max))  # one short start, then dr_max
+    M = orc.unpack(out, 2).reshape(2, p.n_u, p.n_E, 2, 2)
+    Lj = _path_length(p, p.r1)
+    Delta = orc.vac_coeff() * p.hierarchy * p.dm2[0] / E
+    Pee = 1 - np.sin(2 * 0.3) ** 2 * np.sin(np.outer(Lj, Delta) / 2) ** 2
+    for s, (ie, ix) in enumerate([(0, 2), (1, 3)]):
+        want = phi[ix] + (phi[ie] - phi[ix]) * Pee
+        assert np.abs(M[s, :, :, 0, 0].real - want).max() < 1e-11 * phi[0].max()
+
+
+def test_adaptive_converges_with_tolerance(orc):
+    """Single-angle model against the independent Bloch-vector integrator
+    (P6, at a step far below any adaptive one): tightening eps0 tightens the
+    result, the step sequence adapts (some attempts rejected from a large
+    h0), and the run ends exactly on r_end."""
+    p = _small(n_E=9, n_u=1, geometry=I.SINGLE_ANGLE, stepper=I.EXPH, mu0=1e5, eps=1e-2, r0=40.0,
+               r1=42.0, n_steps=4000, dr_max=0.5)
+    rho = orc.init_state(p)
+    ref = _sa_bloch_rk4(orc, p, rho)
+    errs = []
+    for eps0 in (1e-4, 1e-5, 1e-6):
+        out, st, r, h, na, nr = orc.evolve_adaptive(p.replace(eps0=eps0), rho, p.r0, p.r1, 0.5)
+        assert st == 0 and r == p.r1 and nr >= 1
+        errs.append(np.abs(out - ref).max() / np.abs(rho).max())
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-4
+
+
+def test_adaptive_budget_and_status(orc):
+    p = _small(stepper=I.EXPH, mu0=1e5, eps=1e-2, eps0=1e-8, dr_max=0.1)
+    rho = orc.init_state(p)
+    out, st, r, h, na, nr = orc.evolve_adaptive(p, rho, 50.0, 60.0, 0.1, max_iters=3)
+    assert st == 2 and na + nr == 3 and 50.0 <= r < 60.0
