@@ -209,7 +209,8 @@ def test_strict_rk4_refuses_unstable_step_sizes(xf, orc):
         c.step(10, p.h)
     assert ei.value.name == "XF_E_UNSTABLE"
     got, r, done = c.get_state()
-    assert done == 0 and r == p.r0 and np.array_equal(got, rho0)
+    # untouched: only the packing round trip (trace split in FP64) differs
+    assert done == 0 and r == p.r0 and np.abs(got - rho0).max() <= 1e-15 * np.abs(rho0).max()
     c.close()
     q = I.c1a().replace(strict=1, n_steps=200, r1=52.0)
     rho0 = orc.init_state(q)
