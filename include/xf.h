@@ -60,12 +60,22 @@ extern "C" {
 #define XF_E_NOTFOUND (-10)       /* serving: unknown job id */
 #define XF_E_TIMEOUT (-11)        /* serving: job exceeded its time limit */
 #define XF_E_UNSUPPORTED (-12)    /* combination not built */
+#define XF_E_STEPSIZE (-13)       /* error-controlled step: step size fell below 1e-12 r */
+#define XF_E_BUDGET (-14)         /* error-controlled step: attempt budget spent before r_end */
 
 /* ---- enums -------------------------------------------------------------- */
 enum xf_stepper {
     XF_RK4 = 0,  /* classic fixed-step RK4 on d rho/dr = -i[H,rho] dl/dr: 4 fused stages */
-    XF_EXPH = 1  /* the paper's coarse predictor-corrector (Sec. 4.2.3, Listing 5.1 S1-S3)
+    XF_EXPH = 1, /* the paper's coarse predictor-corrector (Sec. 4.2.3, Listing 5.1 S1-S3)
                     with the exact propagator exp(-i H dl) (Eq. 3.10-3.12): 2 stages */
+    XF_EXPH_ADAPTIVE = 2 /* the paper's error-controlled step (Sec. 4.2.3, Fig. 4.8-4.9,
+                    S1-S5 of Listings 5.1-5.3): per attempt a coarse path (the XF_EXPH step)
+                    and a fine path (half step, midpoint half step, full step under the end-
+                    point Hamiltonian, averaged) from four Hamiltonians in 3 fused stages;
+                    error = max over bins of |rho_c - rho_f| / tr rho; accepted (coarse
+                    result kept) when error <= eps0; next step ksi h (eps0/error)^(1/2)
+                    trimmed to dr_max.  Driven by xf_evolve / xf_batch_evolve, FP64 and
+                    XF_FP32_M64 only */
 };
 enum xf_precision {
     XF_FP64 = 0,        /* FP64 everywhere */
@@ -90,7 +100,7 @@ enum xf_matter {
     XF_MATTER_EXP = 2    /* n_e = Ye nb0 exp(-(r - R)/h_ns)      (Eq. 4.4) */
 };
 
-#define XF_PARAMS_VERSION 1u
+#define XF_PARAMS_VERSION 2u
 
 /* Problem parameters.  Fill with xf_params_default, then set fields.
  * Keyword names of the paper's configuration file (App. A.3) in brackets. */
@@ -118,6 +128,9 @@ typedef struct xf_params {
     double L[4];        /* luminosities, any common unit [L*] */
     double eps_perturb; /* seeded off-diagonal amplitude (fraction of sqrt(rho_ii rho_jj)) */
     uint64_t seed;      /* seed of the SplitMix64 phases of the perturbation */
+    double eps0;        /* XF_EXPH_ADAPTIVE: error tolerance [eps0], default 1e-6 */
+    double ksi;         /* XF_EXPH_ADAPTIVE: safety factor of the step update, (0, 1] [ksi], default 0.9 */
+    double dr_max_km;   /* XF_EXPH_ADAPTIVE: largest step [max_dr], default 1 km */
 } xf_params;
 
 typedef struct xf_ctx xf_ctx;
@@ -247,6 +260,29 @@ int xf_batch_status(xf_ctx *ctx, int inst, int *status, int64_t *steps_done, dou
  * XF_E_STATE before that (and after a state reset or a non-finite stop).
  * Also accepts a single-problem context with inst = 0. */
 int xf_batch_run_moments(xf_ctx *ctx, int inst, double *M0, double *M1, size_t n_doubles);
+
+/* ---- error-controlled integration (stepper XF_EXPH_ADAPTIVE) -------------
+ * Integrate until r_end_km (the last step is shortened to land on it; a
+ * radius within 1e-12 r_end counts as arrived), making at most max_iters
+ * attempts (accepted + rejected).  dr0_km: the first step to try; <= 0
+ * keeps the step size the previous call ended with (dr_max if none).
+ * Synchronous.  Returns XF_OK when r_end was reached; XF_E_BUDGET when the
+ * attempts ran out first (state and radius are those of the last accepted
+ * step, and a further call continues); XF_E_NONFINITE when an attempt was
+ * not finite (state kept at the last accepted step); XF_E_STEPSIZE when the
+ * step fell below 1e-12 r.  XF_E_ARG on a context of another stepper.
+ * xf_step / xf_batch_step are XF_E_ARG on an XF_EXPH_ADAPTIVE context. */
+int xf_evolve(xf_ctx *ctx, double r_end_km, int64_t max_iters, double dr0_km);
+/* Every problem of a batch to its own r_end_km[i] (dr0_km: NULL, or one
+ * value per problem as above).  Returns XF_OK if all arrived, else the first
+ * non-OK status in problem order (xf_adapt_status tells each). */
+int xf_batch_evolve(xf_ctx *ctx, const double *r_end_km, int64_t max_iters, const double *dr0_km);
+/* Outcome of problem `inst`'s last error-controlled call: status (XF_OK,
+ * XF_E_BUDGET, XF_E_NONFINITE, XF_E_STEPSIZE), radius, the next step size,
+ * accepted and rejected attempts of the call, and the last attempt's error.
+ * Any output pointer may be NULL. */
+int xf_adapt_status(xf_ctx *ctx, int inst, int *status, double *r_km, double *h_next_km, int64_t *n_accepted,
+                    int64_t *n_rejected, double *last_error);
 
 /* ---- serving: a continuous-batching job server ---------------------------
  * A server owns one pack of `max_jobs` slots and a device arena of

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/xf.h"
+#include "xf_adapt.cuh"
 #include "xf_aux.cuh"
 #include "xf_kernels.h"
 #include "xf_pack.h"
@@ -132,7 +133,15 @@ int validate(xf_ctx *c, const xf_params *p, int n_E, int n_u, int nf)
     if (n_E <= 0 || n_u <= 0) return fail(c, XF_E_ARG, "n_E and n_u must be positive (got %d, %d)", n_E, n_u);
     if (nf != 2 && nf != 3) return fail(c, XF_E_ARG, "n_flavor must be 2 or 3 (got %d)", nf);
     if ((long long)n_E * n_u > (long long)(INT_MAX / 16)) return fail(c, XF_E_ARG, "n_E * n_u too large");
-    if (p->stepper != XF_RK4 && p->stepper != XF_EXPH) return fail(c, XF_E_ARG, "bad stepper %d", p->stepper);
+    if (p->stepper != XF_RK4 && p->stepper != XF_EXPH && p->stepper != XF_EXPH_ADAPTIVE)
+        return fail(c, XF_E_ARG, "bad stepper %d", p->stepper);
+    if (p->stepper == XF_EXPH_ADAPTIVE) {
+        if (p->precision != XF_FP64 && p->precision != XF_FP32_M64)
+            return fail(c, XF_E_UNSUPPORTED, "the error-controlled step runs in FP64 or FP32_M64 only");
+        if (!(p->eps0 > 0) || !std::isfinite(p->eps0)) return fail(c, XF_E_ARG, "eps0 must be finite and > 0");
+        if (!(p->ksi > 0) || !(p->ksi <= 1)) return fail(c, XF_E_ARG, "ksi must be in (0, 1]");
+        if (!(p->dr_max_km > 0) || !std::isfinite(p->dr_max_km)) return fail(c, XF_E_ARG, "dr_max must be finite and > 0");
+    }
     if (p->precision < XF_FP64 || p->precision > XF_FP32_M64_RENORM)
         return fail(c, XF_E_ARG, "bad precision %d", p->precision);
     if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CONST) return fail(c, XF_E_ARG, "bad geometry %d", p->geometry);
@@ -292,8 +301,13 @@ int plan_launch(xf_ctx *c)
         const InstHost &in = c->in[t.inst];
         span = std::max(span, (t.p0 + t.np - 1) / in.n_E - t.p0 / in.n_E + 1);
     }
-    // per-angle tables: 5 FP64 slots, or 6 FP32 slots (step length as hi + lo)
-    size_t smem = (c->real_bytes == 8 ? 5 * sizeof(double) : 6 * sizeof(float)) * (size_t)span;
+    // per-angle tables: 5 FP64 slots, or 6 FP32 slots (step length as hi + lo);
+    // the error-controlled step: 8 FP64 or 10 FP32 slots
+    const bool ad = c->stepper == XF_EXPH_ADAPTIVE;
+    const size_t per_angle = ad ? (c->real_bytes == 8 ? xf::ASlots<double>::n * sizeof(double)
+                                                      : xf::ASlots<float>::n * sizeof(float))
+                                : (c->real_bytes == 8 ? 5 * sizeof(double) : 6 * sizeof(float));
+    size_t smem = per_angle * (size_t)span;
     smem = (smem + 15) & ~size_t(15);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(c->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -326,7 +340,12 @@ int plan_launch(xf_ctx *c)
     c->cta_tiles = ct;
     // device copies (the tile buffers are sized for the most tiles seen)
     if (T > c->max_tiles) {
-        c->partials = (double *)dev_alloc(c, sizeof(double) * 2 * (size_t)T * NVMAX);
+        c->partials = (double *)dev_alloc(c, ad ? sizeof(double) * 4 * (size_t)T * xf::APS
+                                                : sizeof(double) * 2 * (size_t)T * NVMAX);
+        if (ad) {
+            c->tstate_d = (AdaptPos *)dev_alloc(c, sizeof(AdaptPos) * (size_t)T);
+            if (!c->tstate_d) return fail(c, XF_E_NOMEM, "device allocation of the tile tables failed");
+        }
         c->tiles_d = (Tile *)dev_alloc(c, sizeof(Tile) * (size_t)T);
         c->cta_tiles_d = (int *)dev_alloc(c, sizeof(int) * (size_t)(T + 1));
         if (!c->partials || !c->tiles_d || !c->cta_tiles_d)
@@ -357,6 +376,7 @@ Inst make_inst(const InstHost &h)
     d.npad = h.npad;
     d.hvac_off = h.hvac_off;
     d.ref_off = h.ref_off;
+    d.trace_off = h.trace_off;
     for (int b = 0; b < 3; ++b) d.off[b] = h.off[b];
     d.R = h.p.R_nu_km;
     d.mu0 = h.p.mu0_per_km;
@@ -371,6 +391,9 @@ Inst make_inst(const InstHost &h)
     d.gf = gf;
     d.r0 = h.r0;
     d.h = h.h;
+    d.eps0 = h.p.eps0;
+    d.ksi = h.p.ksi;
+    d.dr_max = h.p.dr_max_km;
     d.tile_begin = h.tile_begin;
     d.tile_end = h.tile_end;
     return d;
@@ -403,6 +426,8 @@ __global__ void reset_pos_kernel(InstPos *pos, int i, int cur, int keep)
     }
 }
 
+__global__ void set_apos_kernel(AdaptPos *apos, int i, AdaptPos v) { apos[i] = v; }
+
 // Read the device progress of every instance into the host view.
 int sync_status(xf_ctx *c)
 {
@@ -411,12 +436,29 @@ int sync_status(xf_ctx *c)
     int err = 0;
     XF_CUDA(c, cudaMemcpy(ps.data(), c->pos_d, sizeof(InstPos) * ps.size(), cudaMemcpyDeviceToHost), "read progress");
     XF_CUDA(c, cudaMemcpy(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
-    for (size_t i = 0; i < c->in.size(); ++i) {
-        InstHost &h = c->in[i];
-        h.k0 = ps[i].k0;
-        h.cur = ps[i].cur;
-        h.steps = (long long)ps[i].steps;
-        h.err = ps[i].err;
+    if (c->stepper == XF_EXPH_ADAPTIVE) {
+        std::vector<AdaptPos> ap(c->in.size());
+        XF_CUDA(c, cudaMemcpy(ap.data(), c->apos_d, sizeof(AdaptPos) * ap.size(), cudaMemcpyDeviceToHost),
+                "read progress");
+        for (size_t i = 0; i < c->in.size(); ++i) {
+            InstHost &h = c->in[i];
+            h.cur = ap[i].cur;
+            h.r_ad = ap[i].r;
+            h.h_ad = ap[i].h;
+            h.err_ad = ap[i].err;
+            h.n_acc = ap[i].n_acc;
+            h.n_rej = ap[i].n_rej;
+            h.ad_status = ap[i].status;
+            h.steps = ap[i].n_acc;
+        }
+    } else {
+        for (size_t i = 0; i < c->in.size(); ++i) {
+            InstHost &h = c->in[i];
+            h.k0 = ps[i].k0;
+            h.cur = ps[i].cur;
+            h.steps = (long long)ps[i].steps;
+            h.err = ps[i].err;
+        }
     }
     c->pending = 0;
     if (err) {
@@ -427,7 +469,11 @@ int sync_status(xf_ctx *c)
     return XF_OK;
 }
 
-double radius(const InstHost &h) { return h.h != 0.0 ? h.r0 + (double)h.k0 * h.h : h.r0; }
+double radius(const InstHost &h)
+{
+    if (h.adaptive) return h.r_ad;
+    return h.h != 0.0 ? h.r0 + (double)h.k0 * h.h : h.r0;
+}
 
 // Enqueue one integrator launch of n steps (every instance with remaining > 0).
 int enqueue_run(xf_ctx *c, long long n, cudaStream_t stream)
@@ -449,6 +495,8 @@ int enqueue_run(xf_ctx *c, long long n, cudaStream_t stream)
     a.err = c->err;
     a.timeout_ns = c->timeout_ns;
     a.skip_cta = c->skip_cta;
+    a.apos = c->apos_d;
+    a.tstate = c->tstate_d;
     if (c->G == 0) return XF_OK;
     XF_CUDA(c, cudaMemsetAsync(c->bar, 0, sizeof(unsigned), stream), "reset barrier");
     void *args[] = {&a};
@@ -534,6 +582,103 @@ int enqueue_requests(xf_ctx *c, long long n, const std::vector<long long> &req)
     int rc = enqueue_run(c, n, c->stream);
     if (rc) return rc;
     ++c->pending;
+    return XF_OK;
+}
+
+int adapt_code(int status)
+{
+    switch (status) {
+    case xf::AD_DONE: return XF_OK;
+    case xf::AD_BUDGET: return XF_E_BUDGET;
+    case xf::AD_NONFINITE: return XF_E_NONFINITE;
+    case xf::AD_STEPSIZE: return XF_E_STEPSIZE;
+    default: return XF_E_STATE;
+    }
+}
+
+// Error-controlled integration of every active problem (or only `only`) to
+// its r_end: set the device progress records, then launch chunks of
+// attempts until no problem is running.  Each chunk is sized from the
+// largest number of steps left at the current step sizes.
+int evolve_impl(xf_ctx *c, const double *r_end, long long max_iters, const double *dr0, int only)
+{
+    if (c->stepper != XF_EXPH_ADAPTIVE) return fail(c, XF_E_ARG, "xf_evolve needs the XF_EXPH_ADAPTIVE stepper");
+    if (max_iters < 0) return fail(c, XF_E_ARG, "max_iters must be >= 0");
+    if (c->pending) {
+        int rc = sync_status(c);
+        if (rc) return rc;
+    }
+    if (c->dirty) {
+        int rc = plan_launch(c);
+        if (!rc) rc = upload_instances(c);
+        if (rc) return rc;
+    }
+    const int ni = (int)c->in.size();
+    std::vector<AdaptPos> ap(ni);
+    for (int i = 0; i < ni; ++i) {
+        InstHost &h = c->in[i];
+        AdaptPos &a = ap[i];
+        std::memset(&a, 0, sizeof a);
+        a.r = a.r_end = h.r_ad;
+        a.h = h.h_ad;
+        a.cur = h.cur;
+        a.err = h.err_ad;
+        a.n_acc = h.n_acc;
+        a.n_rej = h.n_rej;
+        a.status = h.ad_status == xf::AD_RUN ? xf::AD_DONE : h.ad_status;
+        if (!h.active || (only >= 0 && i != only)) continue;
+        if (!h.state_valid) return fail(c, XF_E_STATE, "problem %d has no valid state", i);
+        const double re = r_end[only >= 0 ? 0 : i];
+        if (!std::isfinite(re) || re < h.r_ad) return fail(c, XF_E_ARG, "r_end of problem %d is behind its radius", i);
+        const double d0 = dr0 ? dr0[only >= 0 ? 0 : i] : 0.0;
+        if (!std::isfinite(d0)) return fail(c, XF_E_ARG, "dr0 of problem %d not finite", i);
+        double h0 = d0 > 0 ? d0 : (h.h_ad > 0 ? h.h_ad : h.p.dr_max_km);
+        h0 = h0 < h.p.dr_max_km ? h0 : h.p.dr_max_km;
+        a.h = h0;
+        a.r_end = re;
+        a.iters_left = max_iters;
+        a.n_acc = a.n_rej = 0;
+        a.err = 0.0;
+        if (!(re - a.r > 1e-12 * re)) {
+            a.status = xf::AD_DONE;
+            a.r = re;
+        } else if (max_iters == 0) {
+            a.status = xf::AD_BUDGET;
+        } else if (h0 < 1e-12 * a.r) {
+            a.status = xf::AD_STEPSIZE;
+        } else {
+            a.status = xf::AD_RUN;
+        }
+    }
+    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    XF_CUDA(c, cudaMemcpy(c->apos_d, ap.data(), sizeof(AdaptPos) * ni, cudaMemcpyHostToDevice), "copy progress");
+    for (int i = 0; i < ni; ++i) c->in[i].ad_status = ap[i].status;
+    long long left = max_iters;
+    for (;;) {
+        long long want = 0;
+        for (int i = 0; i < ni; ++i) {
+            const InstHost &h = c->in[i];
+            if (h.ad_status != xf::AD_RUN) continue;
+            const double hh = h.h_ad > 0 ? h.h_ad : ap[i].h;
+            const double est = std::ceil((ap[i].r_end - h.r_ad) / hh) + 1.0;
+            want = std::max(want, (long long)std::min(est, 4096.0));
+        }
+        if (want == 0) break;
+        const long long K = std::max(1ll, std::min(want, left));
+        int rc = enqueue_run(c, K, c->stream);
+        if (rc) return rc;
+        ++c->pending;
+        rc = sync_status(c);
+        if (rc) return rc;
+        left -= K;
+        if (left <= 0) break; // every running problem has spent its budget (the kernel set AD_BUDGET)
+    }
+    for (int i = 0; i < ni; ++i) {
+        if (!c->in[i].active || (only >= 0 && i != only)) continue;
+        const int code = adapt_code(c->in[i].ad_status);
+        if (code) return fail(c, code, "problem %d: error-controlled run stopped at r = %.9g km (%s)", i,
+                              c->in[i].r_ad, xf_status_str(code));
+    }
     return XF_OK;
 }
 
@@ -664,10 +809,13 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "no usable CUDA device"));
     const int st = (stepper == XF_RK4) ? STEP_RK4 : STEP_EXPH;
-    c->kern = (c->real_bytes == 8) ? run_kernel_fp64(nfm, st)
-              : precision == XF_FP32_COMP ? run_kernel_fp32(nfm, st, VAR_COMP)
-              : precision == XF_FP32_M64_RENORM ? run_kernel_fp32(nfm, st, VAR_RENORM)
-                                                 : run_kernel_fp32(nfm, st, VAR_PLAIN);
+    if (stepper == XF_EXPH_ADAPTIVE)
+        c->kern = run_kernel_adapt(nfm, c->real_bytes == 8);
+    else
+        c->kern = (c->real_bytes == 8) ? run_kernel_fp64(nfm, st)
+                  : precision == XF_FP32_COMP ? run_kernel_fp32(nfm, st, VAR_COMP)
+                  : precision == XF_FP32_M64_RENORM ? run_kernel_fp32(nfm, st, VAR_RENORM)
+                                                     : run_kernel_fp32(nfm, st, VAR_PLAIN);
     if (!c->kern.fn) return bail(fail(c, XF_E_UNSUPPORTED, "kernel variant not built"));
     c->in.resize(n_slots);
     c->arena = (unsigned char *)dev_alloc(c, (size_t)std::max(arena_bytes, 256ll));
@@ -676,6 +824,10 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
     c->staging = (double *)dev_alloc(c, sizeof(double) * c->staging_doubles);
     c->inst_d = (Inst *)dev_alloc(c, sizeof(Inst) * n_slots);
     c->pos_d = (InstPos *)dev_alloc(c, sizeof(InstPos) * n_slots);
+    if (stepper == XF_EXPH_ADAPTIVE) {
+        c->apos_d = (AdaptPos *)dev_alloc(c, sizeof(AdaptPos) * n_slots);
+        if (!c->apos_d) return bail(fail(c, XF_E_NOMEM, "device allocation failed"));
+    }
     c->mom_out = (double *)dev_alloc(c, sizeof(double) * NVMAX * n_slots);
     c->mom_full = (double *)dev_alloc(c, sizeof(double) * 18);
     c->bar = (unsigned *)dev_alloc(c, 64);
@@ -688,6 +840,7 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
     if (e == cudaSuccess) e = cudaMemset(c->bar, 0, 64);
     if (e == cudaSuccess) e = cudaMemset(c->pos_d, 0, sizeof(InstPos) * n_slots);
     if (e == cudaSuccess) e = cudaMemset(c->inst_d, 0, sizeof(Inst) * n_slots);
+    if (e == cudaSuccess && c->apos_d) e = cudaMemset(c->apos_d, 0, sizeof(AdaptPos) * n_slots);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "device set-up"));
     *out = c;
     return XF_OK;
@@ -816,6 +969,20 @@ int reset_instance(xf_ctx *c, int i, double r_km, bool valid)
     h.state_valid = valid;
     reset_pos_kernel<<<1, 1, 0, c->stream>>>(c->pos_d, i, 0, 0);
     XF_CUDA(c, cudaGetLastError(), "position kernel");
+    if (c->stepper == XF_EXPH_ADAPTIVE) {
+        h.adaptive = true;
+        h.r_ad = r_km;
+        h.h_ad = 0.0;
+        h.err_ad = 0.0;
+        h.n_acc = h.n_rej = 0;
+        h.ad_status = xf::AD_DONE;
+        AdaptPos a;
+        std::memset(&a, 0, sizeof a);
+        a.r = a.r_end = r_km;
+        a.status = xf::AD_DONE;
+        set_apos_kernel<<<1, 1, 0, c->stream>>>(c->apos_d, i, a);
+        XF_CUDA(c, cudaGetLastError(), "position kernel");
+    }
     return upload_instances(c);
 }
 
@@ -1022,6 +1189,9 @@ void xf_params_default(xf_params *p)
     }
     p->eps_perturb = 1e-6;
     p->seed = 1;
+    p->eps0 = 1e-6;
+    p->ksi = 0.9;
+    p->dr_max_km = 1.0;
 }
 
 int xf_create(int n_E, int n_u, int n_flavor, const xf_params *p, xf_ctx **out)
@@ -1151,6 +1321,7 @@ int check_rk4_stable(xf_ctx *c, int i, double h_km)
 int xf_step_async(xf_ctx *c, int64_t n_steps, double dr_km)
 {
     if (!c) return XF_E_ARG;
+    if (c->stepper == XF_EXPH_ADAPTIVE) return fail(c, XF_E_ARG, "an XF_EXPH_ADAPTIVE context steps with xf_evolve");
     if (n_steps < 0) return fail(c, XF_E_ARG, "n_steps must be >= 0");
     if (!std::isfinite(dr_km) || dr_km <= 0) return fail(c, XF_E_ARG, "dr_km must be finite and > 0");
     InstHost &h = c->in[0];
@@ -1187,6 +1358,7 @@ int xf_step(xf_ctx *c, int64_t n_steps, double dr_km)
 int xf_batch_step(xf_ctx *c, int64_t n_steps, const double *dr_km)
 {
     if (!c) return XF_E_ARG;
+    if (c->stepper == XF_EXPH_ADAPTIVE) return fail(c, XF_E_ARG, "an XF_EXPH_ADAPTIVE context steps with xf_batch_evolve");
     if (n_steps < 0) return fail(c, XF_E_ARG, "n_steps must be >= 0");
     bool changed = false;
     for (size_t i = 0; i < c->in.size(); ++i) {
@@ -1231,6 +1403,38 @@ int xf_batch_status(xf_ctx *c, int inst, int *status, int64_t *steps_done, doubl
     if (status) *status = !h->state_valid ? XF_E_STATE : (h->err & ERR_NONFINITE) ? XF_E_NONFINITE : XF_OK;
     if (steps_done) *steps_done = h->steps;
     if (r_km) *r_km = radius(*h);
+    return XF_OK;
+}
+
+int xf_evolve(xf_ctx *c, double r_end_km, int64_t max_iters, double dr0_km)
+{
+    if (!c) return XF_E_ARG;
+    return evolve_impl(c, &r_end_km, max_iters, &dr0_km, 0);
+}
+
+int xf_batch_evolve(xf_ctx *c, const double *r_end_km, int64_t max_iters, const double *dr0_km)
+{
+    if (!c) return XF_E_ARG;
+    if (!r_end_km) return fail(c, XF_E_ARG, "r_end_km is NULL");
+    return evolve_impl(c, r_end_km, max_iters, dr0_km, -1);
+}
+
+int xf_adapt_status(xf_ctx *c, int inst, int *status, double *r_km, double *h_next_km, int64_t *n_accepted,
+                    int64_t *n_rejected, double *last_error)
+{
+    InstHost *h = instance(c, inst);
+    if (!h) return c ? fail(c, XF_E_ARG, "bad instance index %d", inst) : XF_E_ARG;
+    if (c->stepper != XF_EXPH_ADAPTIVE) return fail(c, XF_E_ARG, "not an XF_EXPH_ADAPTIVE context");
+    if (c->pending) {
+        int rc = sync_status(c);
+        if (rc) return rc;
+    }
+    if (status) *status = h->state_valid ? adapt_code(h->ad_status) : XF_E_STATE;
+    if (r_km) *r_km = h->r_ad;
+    if (h_next_km) *h_next_km = h->h_ad;
+    if (n_accepted) *n_accepted = h->n_acc;
+    if (n_rejected) *n_rejected = h->n_rej;
+    if (last_error) *last_error = h->err_ad;
     return XF_OK;
 }
 
@@ -1352,7 +1556,7 @@ int xf_launch_info(xf_ctx *c, int *ctas, int *threads, int *barriers_per_step)
     if (!c) return XF_E_ARG;
     if (ctas) *ctas = c->G;
     if (threads) *threads = c->kern.nt;
-    if (barriers_per_step) *barriers_per_step = (c->stepper == XF_RK4) ? 4 : 2;
+    if (barriers_per_step) *barriers_per_step = (c->stepper == XF_RK4) ? 4 : (c->stepper == XF_EXPH) ? 2 : 3;
     return XF_OK;
 }
 
@@ -1373,6 +1577,8 @@ const char *xf_status_str(int s)
     case XF_E_NOTFOUND: return "XF_E_NOTFOUND";
     case XF_E_TIMEOUT: return "XF_E_TIMEOUT";
     case XF_E_UNSUPPORTED: return "XF_E_UNSUPPORTED";
+    case XF_E_STEPSIZE: return "XF_E_STEPSIZE";
+    case XF_E_BUDGET: return "XF_E_BUDGET";
     default: return "XF_E_UNKNOWN";
     }
 }

@@ -1,5 +1,5 @@
 // xf_kernels.h -- host-visible handles of the persistent integrator kernels
-// (instantiated in xf_k64.cu and xf_k32.cu, compiled in parallel).
+// (instantiated in xf_k64.cu, xf_k32*.cu and xf_ka.cu, compiled in parallel).
 #pragma once
 
 #include "xf_run.cuh"
@@ -16,5 +16,7 @@ struct RunKernel {
 // VAR_RENORM (FP32 only; mixed packs plain only).  fn == nullptr if not built.
 RunKernel run_kernel_fp64(int nfm, int stepper);
 RunKernel run_kernel_fp32(int nfm, int stepper, int var);
+// the error-controlled step (xf_adapt_kernel), FP64 or FP32 bins
+RunKernel run_kernel_adapt(int nfm, bool fp64);
 
 } // namespace xf

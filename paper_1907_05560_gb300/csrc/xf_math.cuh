@@ -230,14 +230,16 @@ template <> struct JacobiTol<float> {
 };
 
 // T' = U T U^dagger with U = exp(-i H dl), H traceless Hermitian 3x3:
-// H = V diag(lam) V^dagger by cyclic Jacobi, then
-// T' = V (E o (V^dagger T V)) V^dagger with E_jk = exp(-i (lam_j - lam_k) dl).
+// H = V diag(lam) V^dagger by cyclic Jacobi (eig3), then
+// T' = V (E o (V^dagger T V)) V^dagger with E_jk = exp(-i (lam_j - lam_k) dl)
+// (apply3); prop3 is the two in sequence.
 template <typename Real>
-__host__ __device__ __forceinline__ void prop3(const Real *h, StepLen<Real> dl, const Real *t, Real *out)
+__host__ __device__ __forceinline__ void eig3(const Real *h, Real *dg, cx<Real> (*V)[3])
 {
-    Real dg[3] = {h[0], h[1], -(h[0] + h[1])};
+    dg[0] = h[0];
+    dg[1] = h[1];
+    dg[2] = -(h[0] + h[1]);
     cx<Real> o[3] = {mk(h[2], h[3]), mk(h[4], h[5]), mk(h[6], h[7])};
-    cx<Real> V[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -253,6 +255,12 @@ __host__ __device__ __forceinline__ void prop3(const Real *h, StepLen<Real> dl, 
         jacobi_rot<Real, 0, 2>(dg, o, V);
         jacobi_rot<Real, 1, 2>(dg, o, V);
     }
+}
+
+template <typename Real>
+__host__ __device__ __forceinline__ void apply3(const Real *dg, const cx<Real> (*V)[3], StepLen<Real> dl, const Real *t,
+                                                Real *out)
+{
     // T as a full Hermitian matrix
     const Real t3 = -(t[0] + t[1]);
     const cx<Real> T[3][3] = {{mk(t[0], Real(0)), mk(t[2], t[3]), mk(t[4], t[5])},
@@ -311,6 +319,15 @@ __host__ __device__ __forceinline__ void prop3(const Real *h, StepLen<Real> dl, 
     out[7] = o12.i;
 }
 
+template <typename Real>
+__host__ __device__ __forceinline__ void prop3(const Real *h, StepLen<Real> dl, const Real *t, Real *out)
+{
+    Real dg[3];
+    cx<Real> V[3][3];
+    eig3<Real>(h, dg, V);
+    apply3<Real>(dg, V, dl, t, out);
+}
+
 // ---------------------------------------------------------------- dispatch
 template <int NF, typename Real>
 __host__ __device__ __forceinline__ void comm(const Real *h, const Real *t, Real *d)
@@ -323,6 +340,41 @@ __host__ __device__ __forceinline__ void prop(const Real *h, StepLen<Real> dl, c
 {
     if constexpr (NF == 2) prop2<Real>(h, dl, t, out);
     else prop3<Real>(h, dl, t, out);
+}
+
+// Two propagations of the same T under the same H for two path lengths
+// (one eigendecomposition / one Bloch-vector rotation axis for both).
+template <int NF, typename Real>
+__host__ __device__ __forceinline__ void prop_pair(const Real *h, StepLen<Real> dl1, StepLen<Real> dl2, const Real *t,
+                                                   Real *out1, Real *out2)
+{
+    if constexpr (NF == 2) {
+        Real lam = sqrt_r(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+        Real w[3], q[3];
+        w[0] = h[2] * t[1] - h[1] * t[2];
+        w[1] = h[0] * t[2] - t[0] * h[2];
+        w[2] = t[0] * h[1] - h[0] * t[1];
+        q[0] = h[2] * w[1] - h[1] * w[2];
+        q[1] = h[0] * w[2] - w[0] * h[2];
+        q[2] = w[0] * h[1] - h[0] * w[1];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const StepLen<Real> dl = i ? dl2 : dl1;
+            Real sn, cs;
+            phase_sincos(lam, dl, &sn, &cs);
+            Real sig = (lam > Real(0)) ? sn / lam : step_len_value(dl);
+            Real c1 = Real(2) * sig * cs, c2 = Real(2) * sig * sig;
+            Real *o = i ? out2 : out1;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) o[k] = t[k] + c1 * w[k] + c2 * q[k];
+        }
+    } else {
+        Real dg[3];
+        cx<Real> V[3][3];
+        eig3<Real>(h, dg, V);
+        apply3<Real>(dg, V, dl1, t, out1);
+        apply3<Real>(dg, V, dl2, t, out2);
+    }
 }
 
 // Traceless components of rho_nu - conj(rho_nubar): conjugation flips the

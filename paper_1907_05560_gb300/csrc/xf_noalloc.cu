@@ -355,6 +355,8 @@ extern "C" int xf_step_noalloc(int n_E, int n_u, int n_flavor, const xf_params *
     if (n_E <= 0 || n_u <= 0 || (n_flavor != 2 && n_flavor != 3))
         return noalloc_fail(XF_E_ARG, "need n_E, n_u > 0 and n_flavor in {2, 3}");
     if ((long long)n_E * n_u > (long long)(INT_MAX / 16)) return noalloc_fail(XF_E_ARG, "n_E * n_u too large");
+    if (p->stepper == XF_EXPH_ADAPTIVE)
+        return noalloc_fail(XF_E_UNSUPPORTED, "the error-controlled step is not built for this entry point");
     if (p->stepper != XF_RK4 && p->stepper != XF_EXPH) return noalloc_fail(XF_E_ARG, "bad stepper");
     if (p->precision < XF_FP64 || p->precision > XF_FP32_M64_RENORM) return noalloc_fail(XF_E_ARG, "bad precision");
     if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CONST) return noalloc_fail(XF_E_ARG, "bad geometry");

@@ -14,6 +14,7 @@
 
 namespace xfp {
 
+using xf::AdaptPos;
 using xf::Inst;
 using xf::InstPos;
 using xf::RunKernel;
@@ -95,6 +96,11 @@ struct InstHost {
     double r0 = 0.0, h = 0.0;
     long long k0 = 0, steps = 0;
     int cur = 0, err = 0;
+    // error-controlled step (host view of the device AdaptPos)
+    bool adaptive = false;
+    double r_ad = 0.0, h_ad = 0.0, err_ad = 0.0;
+    long long n_acc = 0, n_rej = 0;
+    int ad_status = 1; // AD_DONE
 };
 
 
@@ -126,6 +132,7 @@ struct xf_ctx {
     int *cta_tiles_d = nullptr;
     xfp::Inst *inst_d = nullptr;
     xfp::InstPos *pos_d = nullptr;
+    xfp::AdaptPos *apos_d = nullptr, *tstate_d = nullptr; // error-controlled step only
     double *partials = nullptr, *mom_out = nullptr, *mom_part = nullptr, *mom_full = nullptr;
     int mom_part_slots = 0;
     unsigned *bar = nullptr;

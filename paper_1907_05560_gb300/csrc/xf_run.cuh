@@ -32,7 +32,7 @@ namespace xf {
 
 enum { GEOM_BULB = 0, GEOM_MU_R4 = 1, GEOM_SA = 2, GEOM_CONST = 3 };
 enum { MAT_NONE = 0, MAT_POWER = 1, MAT_EXP = 2 };
-enum { STEP_RK4 = 0, STEP_EXPH = 1 };
+enum { STEP_RK4 = 0, STEP_EXPH = 1, STEP_ADAPT = 2 };
 enum { ERR_NONFINITE = 1, ERR_BARRIER = 2 };
 // variants of the per-bin arithmetic: plain; moments summed in compensated
 // FP32 (TwoSum) up to the warp; plain with the per-step restoration of each
@@ -49,9 +49,11 @@ struct Inst {
     int matter, n_pairs, npad, pad0_;
     long long off[3], hvac_off;
     long long ref_off;      // Real: per-bin tr(rho0^2) of the initial state (renormalising variant)
+    long long trace_off;    // double: trace per bin [2][npad]
     double R, mu0, du, dE;
     double ne_ref, r_ref, ne_power, nb0, h_ns, Ye, gf;
     double r0, h;           // step k of the run starts at r0 + k h
+    double eps0, ksi, dr_max; // error-controlled step: tolerance, safety factor, largest step
     int tile_begin, tile_end;
 };
 
@@ -63,6 +65,18 @@ struct InstPos {
     unsigned long long steps; // steps taken in total (reported to the host)
     int cur;                // buffer (0/1) holding the current state
     int err;                // ERR_NONFINITE once the instance stopped
+};
+
+// Progress of an instance under the error-controlled step.  The device
+// keeps one copy per instance between launches and one per tile within a
+// launch; every tile of an instance makes the same accept / reject decision
+// from the same sums, so the copies stay equal without a further barrier.
+enum { AD_RUN = 0, AD_DONE = 1, AD_BUDGET = 2, AD_NONFINITE = 3, AD_STEPSIZE = 4 };
+struct AdaptPos {
+    double r, h, ht, r_end, err; // radius, next step, step of the attempt in flight, end, last error
+    long long iters_left, n_acc, n_rej;
+    int cur, in_slot, status, last; // state buffer 0..2; partial slot of its moments; AD_*; attempt ends on r_end
+    int ran, pad_;                  // attempted in this launch
 };
 
 struct Tile {
@@ -83,6 +97,8 @@ struct RunArgs {
     int *err;               // launch-wide error bits (barrier)
     unsigned long long timeout_ns;
     int skip_cta;           // test hook: this CTA leaves at its first barrier (-1: none)
+    AdaptPos *apos;         // error-controlled step: [n_inst] progress (else unused)
+    AdaptPos *tstate;       // error-controlled step: [n_tiles] per-tile copies of it
 };
 
 __device__ __forceinline__ unsigned long long gtimer()
@@ -188,54 +204,67 @@ __device__ __forceinline__ StepLen<float> load_dl(const float *tb, int smax, int
     return {tb[4 * smax + q], tb[5 * smax + q]};
 }
 
+// Angle factor gamma of G = mu (M0 - gamma M1) and kappa = dl/dr of
+// trajectory j at radius r.
+__device__ __forceinline__ void gamma_kappa(const Inst &a, int j, double r, double *g, double *k)
+{
+    *g = 0.0;
+    *k = 1.0;
+    if (a.geometry == GEOM_BULB || a.geometry == GEOM_MU_R4) {
+        double c = cos_u(a, j, r);
+        *g = c;
+        *k = 1.0 / c;
+    }
+}
+// Weights of the nu-nu sums at radius r (Eq. 3.13-3.15).
+__device__ __forceinline__ void nu_weights(const Inst &a, int j, double r, double *wa, double *wb)
+{
+    *wa = a.du;
+    *wb = 0.0;
+    if (a.geometry == GEOM_BULB) {
+        double x = a.R / r, x2 = x * x;
+        double c = sqrt(1.0 - x2 * ((j + 0.5) * a.du));
+        *wa = x2 * a.du / (2.0 * c);
+        *wb = *wa * c;
+    } else if (a.geometry == GEOM_MU_R4) {
+        *wb = a.du * cos_u(a, j, r);
+    }
+}
+// Exact path length from r to r + h along trajectory j (Eq. 3.3, l = r cos):
+// l(r+h) - l(r) = h (2r + h) / (l(r) + l(r+h)), free of cancellation.
+__device__ __forceinline__ double path_length(const Inst &a, int j, double r, double h)
+{
+    if (a.geometry == GEOM_BULB || a.geometry == GEOM_MU_R4) {
+        double l0 = r * cos_u(a, j, r), l1 = (r + h) * cos_u(a, j, r + h);
+        return h * (2.0 * r + h) / (l0 + l1);
+    }
+    return h;
+}
+
 template <typename Real>
 __device__ inline void build_rhs_table(const Inst &a, Real *tb, int smax, int j_lo, int span, double r)
 {
     for (int q = threadIdx.x; q < span; q += blockDim.x) {
-        int j = j_lo + q;
-        double g = 0.0, k = 1.0;
-        if (a.geometry == GEOM_BULB || a.geometry == GEOM_MU_R4) {
-            double c = cos_u(a, j, r);
-            g = c;
-            k = 1.0 / c;
-        }
+        double g, k;
+        gamma_kappa(a, j_lo + q, r, &g, &k);
         tb[0 * smax + q] = (Real)g;
         tb[1 * smax + q] = (Real)k;
     }
 }
-// weights of the nu-nu sums at radius r (Eq. 3.13-3.15)
 template <typename Real>
 __device__ inline void build_weight_table(const Inst &a, Real *tb, int smax, int j_lo, int span, double r)
 {
     for (int q = threadIdx.x; q < span; q += blockDim.x) {
-        int j = j_lo + q;
-        double wa = a.du, wb = 0.0;
-        if (a.geometry == GEOM_BULB) {
-            double x = a.R / r, x2 = x * x;
-            double c = sqrt(1.0 - x2 * ((j + 0.5) * a.du));
-            wa = x2 * a.du / (2.0 * c);
-            wb = wa * c;
-        } else if (a.geometry == GEOM_MU_R4) {
-            wb = a.du * cos_u(a, j, r);
-        }
+        double wa, wb;
+        nu_weights(a, j_lo + q, r, &wa, &wb);
         tb[2 * smax + q] = (Real)wa;
         tb[3 * smax + q] = (Real)wb;
     }
 }
-// exact path length from r to r + h along trajectory j (Eq. 3.3, l = r cos):
-// l(r+h) - l(r) = h (2r + h) / (l(r) + l(r+h)), free of cancellation.
 template <typename Real>
 __device__ inline void build_dl_table(const Inst &a, Real *tb, int smax, int j_lo, int span, double r, double h)
 {
-    for (int q = threadIdx.x; q < span; q += blockDim.x) {
-        int j = j_lo + q;
-        double dl = h;
-        if (a.geometry == GEOM_BULB || a.geometry == GEOM_MU_R4) {
-            double l0 = r * cos_u(a, j, r), l1 = (r + h) * cos_u(a, j, r + h);
-            dl = h * (2.0 * r + h) / (l0 + l1);
-        }
-        store_dl(tb, smax, q, dl);
-    }
+    for (int q = threadIdx.x; q < span; q += blockDim.x) store_dl(tb, smax, q, path_length(a, j_lo + q, r, h));
 }
 
 // Shared per-CTA scratch of the kernel.
@@ -259,8 +288,8 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e)
 // Compensated version of cta_partial: the per-thread sums carry their
 // rounding errors mc; the warp tree adds pairs with TwoSum; the warp leaders
 // hand s + e to the FP64 sum over warps.
-template <int NV, int NT, typename Acc>
-__device__ __forceinline__ void cta_partial_comp(Acc *m, Acc *mc, Shared &sh, double *part)
+template <int NV, int NT, typename Acc, typename SH>
+__device__ __forceinline__ void cta_partial_comp(Acc *m, Acc *mc, SH &sh, double *part)
 {
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
@@ -292,8 +321,8 @@ __device__ __forceinline__ void cta_partial_comp(Acc *m, Acc *mc, Shared &sh, do
 
 // Reduce per-thread partial sums over the CTA in fixed order: warp shuffle
 // tree in Acc precision, warps in order in FP64; writes NV doubles to part.
-template <int NV, int NT, typename Acc>
-__device__ __forceinline__ void cta_partial(Acc *m, Shared &sh, double *part)
+template <int NV, int NT, typename Acc, typename SH>
+__device__ __forceinline__ void cta_partial(Acc *m, SH &sh, double *part)
 {
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
@@ -497,8 +526,8 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
 }
 
 // Prologue for one tile: weighted sums of the input state.
-template <int NF, typename Real, int NT, int VAR>
-__device__ __forceinline__ void prologue_tile(const TileView<Real> v, int smax, const Real *tb, Shared &sh,
+template <int NF, typename Real, int NT, int VAR, typename SH>
+__device__ __forceinline__ void prologue_tile(const TileView<Real> v, int smax, const Real *tb, SH &sh,
                                               double *part_out)
 {
     constexpr int S = Comp<NF>::S, NV = 2 * S;

@@ -182,6 +182,7 @@ int xf_server_create(const xf_server_cfg *cfg, xf_server **out)
     if (!cfg || cfg->size != sizeof(xf_server_cfg)) return XF_E_ARG;
     if (cfg->max_jobs < 1 || cfg->mem_budget_bytes <= 0 || cfg->chunk_steps < 1 || cfg->queue_cap < 1)
         return XF_E_ARG;
+    if (cfg->stepper == XF_EXPH_ADAPTIVE) return XF_E_UNSUPPORTED; // jobs advance in fixed chunks of steps
     if (cfg->stepper != XF_RK4 && cfg->stepper != XF_EXPH) return XF_E_ARG;
     if (cfg->precision < XF_FP64 || cfg->precision > XF_FP32_M64_RENORM) return XF_E_ARG;
     if (cfg->n_flavor != 0 && cfg->n_flavor != 2 && cfg->n_flavor != 3) return XF_E_ARG;

@@ -22,7 +22,7 @@ XF_PENDING = 1
 STATUS = {0: "XF_OK", 1: "XF_PENDING", -1: "XF_E_ARG", -2: "XF_E_STATE", -3: "XF_E_NOMEM",
           -4: "XF_E_CUDA", -5: "XF_E_NONFINITE", -6: "XF_E_BARRIER_TIMEOUT", -7: "XF_E_UNSTABLE",
           -8: "XF_E_BUSY", -9: "XF_E_TOO_BIG", -10: "XF_E_NOTFOUND", -11: "XF_E_TIMEOUT",
-          -12: "XF_E_UNSUPPORTED"}
+          -12: "XF_E_UNSUPPORTED", -13: "XF_E_STEPSIZE", -14: "XF_E_BUDGET"}
 STATUS_CODE = {v: k for k, v in STATUS.items()}
 
 
@@ -46,6 +46,7 @@ class XFParams(ctypes.Structure):
         ("nb0_cm3", ctypes.c_double), ("h_ns_km", ctypes.c_double), ("Ye", ctypes.c_double),
         ("T_MeV", ctypes.c_double * 4), ("eta", ctypes.c_double * 4), ("L", ctypes.c_double * 4),
         ("eps_perturb", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("eps0", ctypes.c_double), ("ksi", ctypes.c_double), ("dr_max_km", ctypes.c_double),
     ]
 
 
@@ -120,6 +121,10 @@ SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_int64)]),
     "xf_batch_outputs": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, ctypes.c_size_t]),
     "xf_batch_run_moments": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, ctypes.c_size_t]),
+    "xf_evolve": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int64, ctypes.c_double]),
+    "xf_batch_evolve": (ctypes.c_int, [_P, _D, ctypes.c_int64, _D]),
+    "xf_adapt_status": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D,
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _D]),
     "xf_batch_step": (ctypes.c_int, [_P, ctypes.c_int64, _D]),
     "xf_batch_status": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int64), _D]),
@@ -175,6 +180,7 @@ def params_from(p: I.Problem) -> XFParams:
     x.eta[:] = list(p.eta)
     x.L[:] = list(p.L)
     x.eps_perturb, x.seed = p.eps, p.seed
+    x.eps0, x.ksi, x.dr_max_km = p.eps0, p.ksi, p.dr_max
     return x
 
 
@@ -275,6 +281,18 @@ class Context:
         self._check(self.L.xf_moments(self.h, _dp(M0), _dp(M1), m))
         return M0, M1
 
+    def evolve(self, r_end_km: float, max_iters: int = 1 << 40, dr0_km: float = 0.0):
+        """Error-controlled integration to r_end_km (XF_EXPH_ADAPTIVE)."""
+        return self._check(self.L.xf_evolve(self.h, float(r_end_km), int(max_iters), float(dr0_km)))
+
+    def adapt_status(self, i: int = 0):
+        st, r, h, e = ctypes.c_int(0), ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        na, nr = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._check(self.L.xf_adapt_status(self.h, i, ctypes.byref(st), ctypes.byref(r), ctypes.byref(h),
+                                           ctypes.byref(na), ctypes.byref(nr), ctypes.byref(e)))
+        return dict(status=STATUS.get(st.value, st.value), r=r.value, h_next=h.value, n_accepted=na.value,
+                    n_rejected=nr.value, err=e.value)
+
     def run_moments(self, i: int = 0):
         """Traceless M0, M1 of problem i's state as the integrator summed them."""
         n_f = self.problems[i].n_f if hasattr(self, "problems") else self.n_f
@@ -363,6 +381,14 @@ class Batch(Context):
         dr = None if dr_km is None else np.ascontiguousarray(
             np.broadcast_to(np.asarray(dr_km, dtype=np.float64), (len(self.problems),)))
         return self._check(self.L.xf_batch_step(self.h, int(n_steps), _dp(dr) if dr is not None else None))
+
+    def evolve_all(self, r_end_km, max_iters: int = 1 << 40, dr0_km=None):
+        n = len(self.problems)
+        re = np.ascontiguousarray(np.broadcast_to(np.asarray(r_end_km, dtype=np.float64), (n,)))
+        d0 = None if dr0_km is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(dr0_km, dtype=np.float64), (n,)))
+        return self._check(self.L.xf_batch_evolve(self.h, _dp(re), int(max_iters),
+                                                  _dp(d0) if d0 is not None else None))
 
     def status_i(self, i: int):
         st, n, r = ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_double(0.0)

@@ -41,7 +41,8 @@ def test_params_default_and_status_strings(lib):
     p = xf.XFParams()
     lib.xf_params_default(ctypes.byref(p))
     assert p.size == ctypes.sizeof(xf.XFParams)
-    assert p.version == 1 and p.stepper == 0 and p.hierarchy == -1
+    assert p.version == 2 and p.stepper == 0 and p.hierarchy == -1
+    assert (p.eps0, p.ksi, p.dr_max_km) == (1e-6, 0.9, 1.0)
     assert list(p.T_MeV) == [2.76, 4.01, 6.26, 6.26]
     for code, name in xf.STATUS.items():
         assert lib.xf_status_str(code).decode() == name
@@ -54,6 +55,9 @@ def test_params_default_and_status_strings(lib):
     (lambda p: setattr(p, "size", 12), (32, 16, 2)),
     (lambda p: setattr(p, "version", 99), (32, 16, 2)),
     (lambda p: setattr(p, "stepper", 7), (32, 16, 2)),
+    (lambda p: (setattr(p, "stepper", 2), setattr(p, "eps0", 0.0)), (32, 16, 2)),
+    (lambda p: (setattr(p, "stepper", 2), setattr(p, "ksi", 1.5)), (32, 16, 2)),
+    (lambda p: (setattr(p, "stepper", 2), setattr(p, "dr_max_km", -1.0)), (32, 16, 2)),
     (lambda p: setattr(p, "hierarchy", 0), (32, 16, 2)),
     (lambda p: setattr(p, "geometry", 2), (32, 16, 2)),  # single angle needs n_u == 1
     (lambda p: setattr(p, "R_nu_km", float("nan")), (32, 16, 2)),
