@@ -113,9 +113,10 @@ typedef struct xf_params {
     int32_t hierarchy;  /* +1 normal, -1 inverted: sign of dm2 (2 fl) / dm2_31 (3 fl) */
     int32_t matter;     /* enum xf_matter */
     int32_t strict;     /* 1: xf_step / xf_batch_step with RK4 return XF_E_UNSTABLE, without
-                           stepping, when h kappa sqrt(2) (max_E |H_vac| + A |P_e| + mu (|M0| + |M1|))
+                           stepping, when for some angle u
+                           h kappa_u sqrt(2) (max_E |H_vac| + A |P_e| + mu |M0 - gamma_u M1|)
                            exceeds RK4's imaginary-axis bound 2 sqrt(2) (Frobenius norms of the
-                           traceless parts at the current radius and state, kappa = max dl/dr) */
+                           traceless parts at the current radius and state, kappa_u = dl/dr) */
     double R_nu_km;     /* neutrinosphere radius [R0 is the start radius; R_nu is Eq. 3.14's R] */
     double mu0_per_km;  /* nu-nu coupling, absorbs the normalisation of Eq. 3.8 */
     double E_min_MeV, E_max_MeV; /* [E0, E1] */

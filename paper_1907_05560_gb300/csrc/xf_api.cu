@@ -1279,14 +1279,16 @@ double traceless_norm(const double *x, int nf)
 }
 
 // Strict mode, RK4 only: refuse a step size outside RK4's stable region.
-// d(rho)/dr = -i kappa [H, rho] has eigenvalues -i kappa (l_a - l_b), and for
-// a traceless Hermitian H the spread l_max - l_min is at most sqrt(2) ||H||_F.
-// Classic RK4 is stable on the imaginary axis for |z| <= 2 sqrt(2), so the
-// step is refused when
-//   h kappa_max sqrt(2) (max_E ||H_vac|| + A ||P_e|| + mu (||M0|| + ||M1||)) > 2 sqrt(2)
-// with every term taken at the current radius (the matter density, the
-// coupling and the bulb weights all fall with r, so the start of the call is
-// the worst point; the moments are those of the current state).
+// d(rho)/dr = -i kappa_u [H, rho] has eigenvalues -i kappa_u (l_a - l_b), and
+// for a traceless Hermitian H the spread l_max - l_min is at most
+// sqrt(2) ||H||_F.  Classic RK4 is stable on the imaginary axis for
+// |z| <= 2 sqrt(2), so the step is refused when, for some angle u,
+//   h kappa_u sqrt(2) (max_E ||H_vac|| + A ||P_e|| + mu ||M0 - gamma_u M1||) > 2 sqrt(2)
+// (Frobenius norms of traceless parts; the nu-nu term is taken per angle, so
+// the near cancellation of M0 and gamma_u M1 far from the neutrinosphere is
+// kept).  Every term is taken at the current radius and state: the matter
+// density, the coupling and the bulb weights all fall with r, so the start
+// of a call is the worst point.
 int check_rk4_stable(xf_ctx *c, int i, double h_km)
 {
     InstHost &h = c->in[i];
@@ -1303,13 +1305,17 @@ int check_rk4_stable(xf_ctx *c, int i, double h_km)
         hv = std::max(hv, std::sqrt(nf == 2 ? purity<2, double>(t) : purity<3, double>(t)));
     }
     const double pe = std::sqrt((nf - 1.0) / nf); // ||diag(1, 0[, 0]) - I/n||_F
-    double kappa = 1.0;
-    if (h.p.geometry == XF_GEOM_BULB || h.p.geometry == XF_GEOM_MU_R4) {
-        const double x = h.p.R_nu_km / r;
-        kappa = 1.0 / std::sqrt(1.0 - x * x * (h.n_u - 0.5) / h.n_u);
+    const double base = hv + matter_A(d, r) * pe, mu = mu_eff(d, r);
+    const bool bulb = h.p.geometry == XF_GEOM_BULB || h.p.geometry == XF_GEOM_MU_R4;
+    const double x = h.p.R_nu_km / r;
+    double z = 0.0;
+    for (int j = 0; j < h.n_u; ++j) {
+        const double cu = bulb ? std::sqrt(1.0 - x * x * (j + 0.5) / h.n_u) : 1.0;
+        const double gam = bulb ? cu : 0.0, kappa = bulb ? 1.0 / cu : 1.0;
+        double G[9];
+        for (int k = 0; k < m; ++k) G[k] = M0[k] - gam * M1[k];
+        z = std::max(z, h_km * kappa * std::sqrt(2.0) * (base + mu * traceless_norm(G, nf)));
     }
-    const double norm = hv + matter_A(d, r) * pe + mu_eff(d, r) * (traceless_norm(M0, nf) + traceless_norm(M1, nf));
-    const double z = h_km * kappa * std::sqrt(2.0) * norm;
     if (!(z <= 2.0 * std::sqrt(2.0)))
         return fail(c, XF_E_UNSTABLE, "RK4 step %.6g km at r = %.6g km is outside the stable region (|z| = %.3g > 2.83)",
                     h_km, r, z);

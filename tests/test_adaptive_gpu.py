@@ -120,28 +120,43 @@ def test_step_size_underflow(xf, orc):
     assert np.abs(got - rho0).max() <= 1e-15 * np.abs(rho0).max()  # state untouched
 
 
+def _batch(xf, probs, rho0s, r_end, tile=64):
+    b = xf.Batch([p.replace(stepper=I.EXPH_ADAPTIVE) for p in probs])
+    b.set_option(xf.OPT_TILE_PAIRS, tile)
+    for i, (p, r0) in enumerate(zip(probs, rho0s)):
+        b.set_state_i(i, r0, p.r0)
+    b.evolve_all(r_end, 1 << 40, 0.3)
+    out = [(b.get_state_i(i)[0], b.adapt_status(i)) for i in range(len(probs))]
+    b.close()
+    return out
+
+
 def test_batch_each_problem_follows_its_own_steps(xf, orc):
     """Problems of different sizes, flavors, tolerances and end radii in one
-    launch: each takes its own step sequence, equal to the oracle's and
-    bitwise equal to the same problem run alone."""
+    launch: each takes its own step sequence, equal to the oracle's, and its
+    state equals the same problem run alone (a mixed 2/3-flavor pack runs
+    128-thread CTAs, so the 2-flavor problems' sums round differently from
+    their 256-thread runs alone: equal to 1e-12, not bitwise)."""
     probs = [CASES["2f-bulb"], CASES["3f-matter"], CASES["2f-mu-r4"],
              CASES["2f-bulb"].replace(seed=21, eps0=1e-5, n_E=7, n_u=30)]
     r_end = [p.r0 + s for p, s in zip(probs, (3.0, 2.0, 2.5, 1.5))]
     rho0s = [orc.init_state(p) for p in probs]
-    b = xf.Batch([p.replace(stepper=I.EXPH_ADAPTIVE) for p in probs])
-    b.set_option(xf.OPT_TILE_PAIRS, 64)
-    for i, (p, r0) in enumerate(zip(probs, rho0s)):
-        b.set_state_i(i, r0, p.r0)
-    b.evolve_all(r_end, 1 << 40, 0.3)
-    for i, (p, r0, re) in enumerate(zip(probs, rho0s, r_end)):
+    for p, r0, re, (got, s) in zip(probs, rho0s, r_end, _batch(xf, probs, rho0s, r_end)):
         ref, st, r, h, na, nr = orc.evolve_adaptive(p, r0, p.r0, re, 0.3, n_threads=THREADS)
-        s = b.adapt_status(i)
-        got = b.get_state_i(i)[0]
         assert s["status"] == "XF_OK" and (s["n_accepted"], s["n_rejected"]) == (na, nr) and s["r"] == re
         assert rel_err(got, ref, p.n_f) < TOL
         alone, _, _ = run_gpu(xf, p, r0, re, 0.3, tile=64)
+        assert rel_err(got, alone, p.n_f) < 1e-12
+
+
+def test_same_flavor_batch_is_bitwise_alone(xf, orc):
+    probs = [CASES["2f-bulb"], CASES["2f-mu-r4"], CASES["2f-bulb"].replace(seed=21, eps0=1e-5, n_E=7, n_u=30)]
+    r_end = [p.r0 + s for p, s in zip(probs, (3.0, 2.5, 1.5))]
+    rho0s = [orc.init_state(p) for p in probs]
+    for p, r0, re, (got, s) in zip(probs, rho0s, r_end, _batch(xf, probs, rho0s, r_end)):
+        alone, sa, _ = run_gpu(xf, p, r0, re, 0.3, tile=64)
+        assert (s["n_accepted"], s["n_rejected"]) == (sa["n_accepted"], sa["n_rejected"])
         assert np.array_equal(got, alone)
-    b.close()
 
 
 def test_fp32_bins_reach_the_end_close_to_the_fp64_run(xf, orc):
