@@ -113,6 +113,9 @@ def measured_peaks():
 # Jacobi eigensolver is counted at the sweep number measured on this
 # workload.  Derivation in DESIGN.md ("Algorithmic work").
 FLOPS_PER_BIN_STEP = {("exph", 3): 2846, ("rk4", 3): 684, ("exph", 2): 120, ("rk4", 2): 172}
+# one attempt of the error-controlled step (four Hamiltonians, five propagations,
+# one shared eigendecomposition), counted the same way
+FLOPS_PER_BIN_ATTEMPT = {3: 6339, 2: 272}
 
 
 def oracle_sample(problem, n_steps, threads):
@@ -256,6 +259,11 @@ def run_xf(args):
     if args.precision == "fp64" and not args.skip_batch:
         batched = run_batched(args, xf, I, torch, stream, flush, barrier, world)
 
+    adaptive = None
+    if args.precision == "fp64" and not args.skip_adapt:
+        sm_max0 = 2070.0
+        adaptive = run_adaptive(args, xf, I, torch, stream, flush, barrier, world, 152 * 4 * sm_max0 * 1e6 / 1e12)
+
     serving = None
     if args.precision == "fp64" and not args.skip_serve and rank == 0:
         serving = run_serving(args, xf, I, torch)
@@ -317,13 +325,56 @@ def run_xf(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "fp32_m64": fp32, "fp32_variants": variants, "batched": batched, "serving": serving, "clocks": clk, "gpu_launches": args.steps,
+            "fp32_m64": fp32, "fp32_variants": variants, "batched": batched, "adaptive": adaptive, "serving": serving, "clocks": clk, "gpu_launches": args.steps,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def run_adaptive(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
+    """The paper's error-controlled step on the three-flavor 400,000-bin
+    workload from 250 km (eps0 = 1e-6, dr_max = 0.05 km), FP64: one bench step
+    = a fixed budget of attempts (xf_evolve toward 1000 km stops on the budget)."""
+    p = I.c2().replace(stepper=I.EXPH_ADAPTIVE, r0=250.0, eps0=1e-6, dr_max=0.05)
+    c = xf.Context(p, stream=stream)
+    c.init_state(p.r0)
+    iters = args.adapt_iters
+
+    def call():
+        try:
+            c.evolve(1000.0, iters, 0.0)
+        except xf.XFError as e:
+            if e.name != "XF_E_BUDGET":
+                raise
+
+    for _ in range(args.warmup):
+        call()
+    acc = rej = 0
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        call()
+        ends[k].record(stream)
+        st = c.adapt_status()
+        acc += st["n_accepted"]
+        rej += st["n_rejected"]
+    barrier()
+    t = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) * 1e-3
+    st = c.adapt_status()
+    c.close()
+    attempts = iters * args.steps
+    flops = FLOPS_PER_BIN_ATTEMPT[p.n_f] * p.n_bins * attempts
+    return {"value": p.n_bins * acc * world / t, "unit": UNIT + " (accepted)",
+            "bin_attempts_per_s": p.n_bins * attempts * world / t, "attempts": attempts, "accepted": acc,
+            "rejected": rej, "ms_per_attempt": 1e3 * t / attempts, "r_km": st["r"], "h_next_km": st["h_next"],
+            "eps0": p.eps0, "dr_max_km": p.dr_max, "precision": "FP64",
+            "achieved_tflops_fp64": flops / t / 1e12, "frac_of_fp64_peak": flops / t / 1e12 / peak_tflops}
 
 
 def run_batched(args, xf, I, torch, stream, flush, barrier, world):
@@ -448,6 +499,8 @@ def main():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--batch-chunk", type=int, default=10, help="radial steps per batched bench step")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--skip-adapt", action="store_true")
+    ap.add_argument("--adapt-iters", type=int, default=30, help="attempts per error-controlled bench step")
     ap.add_argument("--serve-rate", type=float, default=10.0, help="sustained arrival rate, jobs/s")
     ap.add_argument("--serve-window", type=float, default=5.0, help="arrival window at the sustained rate, s")
     ap.add_argument("--serve-chunk", type=int, default=200, help="radial steps per serving epoch")
