@@ -380,6 +380,19 @@ enum xf_option {
 };
 int xf_set_option(xf_ctx *ctx, int option, int64_t value);
 
+/* Measured search of the tile size of a fixed-step context or batch: for
+ * each candidate (pairs per tile; 0 = the automatic rule; candidates = NULL
+ * takes 0, 128, 256, ..., 16384), time n_probe steps of size dr_km (<= 0:
+ * each problem's current step size) after one untimed launch, and keep the
+ * fastest, which stays set as XF_OPT_TILE_PAIRS.  Every problem's state,
+ * radius and step count are restored afterwards (device copies of the state
+ * planes), so the search does not advance the problems.  Needs a valid
+ * state in every problem.  *best_tile (may be NULL) receives the chosen
+ * size, *best_ms (may be NULL) its time per step in milliseconds.  Results
+ * depend on the tile size only by rounding (see XF_OPT_TILE_PAIRS). */
+int xf_autotune(xf_ctx *ctx, int64_t n_probe, double dr_km, const int *candidates, int n_candidates,
+                int *best_tile, double *best_ms);
+
 /* Measured ALU peaks of the current device, for roofline denominators:
  * XF_PEAK_FP64_FMA / XF_PEAK_FP32_FMA write the FMA throughput in FLOP/s
  * (an FMA counts 2) of a register-resident FMA loop over 8 CTAs per SM,

@@ -391,9 +391,17 @@ __device__ __forceinline__ void adapt_decide_tile(const RunArgs &a, const Inst &
     store_ts(a, t, sh);
 }
 
+// Resident CTAs per SM the register allocation is fitted to: stage A keeps
+// two moment sets per thread, so the FP64 kernel stays at 2 (a third would
+// spill about 1 KB per thread); FP32 fits 3, the 256-thread kernels 2.
+__host__ __device__ constexpr int adapt_min_blocks(int nt, int real_bytes)
+{
+    return nt == 128 ? (real_bytes == 8 ? 2 : 3) : 2;
+}
+
 // NFM: 2 or 3 (all instances) or 0 (mixed pack).  a.n_steps = attempts in this launch.
 template <int NFM, typename Real, int NT>
-__global__ void __launch_bounds__(NT) xf_adapt_kernel(RunArgs a)
+__global__ void __launch_bounds__(NT, adapt_min_blocks(NT, sizeof(Real))) xf_adapt_kernel(RunArgs a)
 {
     extern __shared__ double s_dyn[];
     Real *const tb = (Real *)s_dyn;

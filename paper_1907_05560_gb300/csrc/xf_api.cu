@@ -107,6 +107,16 @@ void *dev_alloc(xf_ctx *c, size_t bytes)
     return p;
 }
 
+void dev_free(xf_ctx *c, void *p)
+{
+    if (!p) return;
+    auto it = std::find(c->owned.begin(), c->owned.end(), p);
+    if (it == c->owned.end()) return;
+    c->owned.erase(it);
+    if (c->has_alloc) c->alloc.free(p, c->alloc.user);
+    else cudaFree(p);
+}
+
 void free_all(xf_ctx *c)
 {
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -1508,6 +1518,107 @@ int xf_outputs(xf_ctx *c, double *p_surv, double *trace, double *purity, size_t 
 {
     if (!c) return XF_E_ARG;
     return outputs_impl(c, 0, p_surv, trace, purity, n_bins);
+}
+
+int xf_autotune(xf_ctx *c, int64_t n_probe, double dr_km, const int *cand_in, int n_cand, int *best_tile,
+                double *best_ms)
+{
+    if (!c) return XF_E_ARG;
+    if (c->stepper == XF_EXPH_ADAPTIVE) return fail(c, XF_E_ARG, "tile search runs fixed steps");
+    if (n_probe < 1 || (cand_in && n_cand < 1) || !std::isfinite(dr_km)) return fail(c, XF_E_ARG, "bad arguments");
+    if (c->pending) {
+        int rc = sync_status(c);
+        if (rc) return rc;
+    }
+    std::vector<int> cands;
+    if (cand_in) {
+        for (int k = 0; k < n_cand; ++k) {
+            if (cand_in[k] < 0 || cand_in[k] > (1 << 20)) return fail(c, XF_E_ARG, "candidate %d out of range", k);
+            cands.push_back(cand_in[k]);
+        }
+    } else {
+        cands.push_back(0);
+        for (int t = 128; t <= 16384; t *= 2) cands.push_back(t);
+    }
+    // snapshot: the state planes of every active problem, the progress
+    // records and the host views
+    std::vector<size_t> offs;
+    size_t total = 0;
+    for (const InstHost &h : c->in) {
+        if (!h.active) continue;
+        if (!h.state_valid) return fail(c, XF_E_STATE, "every problem needs a valid state");
+        offs.push_back(total);
+        total += 3 * align256((size_t)2 * h.S * h.npad * c->real_bytes);
+    }
+    unsigned char *snap = (unsigned char *)dev_alloc(c, std::max<size_t>(total, 256));
+    if (!snap) return fail(c, XF_E_NOMEM, "device allocation of the state snapshot failed");
+    const std::vector<InstHost> views = c->in;
+    const int ni = (int)c->in.size();
+    std::vector<InstPos> pos(ni);
+    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    XF_CUDA(c, cudaMemcpy(pos.data(), c->pos_d, sizeof(InstPos) * ni, cudaMemcpyDeviceToHost), "read progress");
+    auto planes = [&](bool save) -> int {
+        size_t k = 0;
+        for (const InstHost &h : views) {
+            if (!h.active) continue;
+            const size_t bytes = 3 * align256((size_t)2 * h.S * h.npad * c->real_bytes);
+            unsigned char *src = c->arena + h.block, *dst = snap + offs[k++];
+            XF_CUDA(c, cudaMemcpyAsync(save ? dst : src, save ? src : dst, bytes, cudaMemcpyDeviceToDevice, c->stream),
+                    "state snapshot");
+        }
+        return XF_OK;
+    };
+    int rc = planes(true);
+    const int tile0 = c->tile_request;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = cuda_fail(c, cudaErrorUnknown, "event");
+    int best = -1;
+    double best_t = 0.0;
+    for (size_t k = 0; k < cands.size() && !rc; ++k) {
+        c->tile_request = cands[k];
+        rc = plan_launch(c);
+        if (!rc) rc = upload_instances(c);
+        for (int i = 0; i < ni && !rc; ++i)
+            if (c->in[i].active && dr_km > 0) rc = set_step_size(c, i, dr_km);
+        if (!rc) rc = upload_instances(c);
+        if (!rc) rc = enqueue_steps(c, n_probe, -1); // untimed
+        if (!rc && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = cuda_fail(c, cudaErrorUnknown, "event");
+        if (!rc) rc = enqueue_steps(c, n_probe, -1);
+        if (!rc && cudaEventRecord(e1, c->stream) != cudaSuccess) rc = cuda_fail(c, cudaErrorUnknown, "event");
+        if (!rc) rc = sync_status(c);
+        float ms = 0.0f;
+        if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = cuda_fail(c, cudaErrorUnknown, "event");
+        if (!rc && (best < 0 || ms < best_t)) {
+            best = cands[k];
+            best_t = ms;
+        }
+    }
+    // restore states, progress and host views whatever happened
+    int rr = planes(false);
+    if (!rr) {
+        XF_CUDA(c, cudaMemcpyAsync(c->pos_d, pos.data(), sizeof(InstPos) * ni, cudaMemcpyHostToDevice, c->stream),
+                "restore progress");
+        XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    }
+    for (int i = 0; i < ni; ++i) {
+        InstHost &h = c->in[i];
+        const int tb = h.tile_begin, te = h.tile_end;
+        h = views[i];
+        h.tile_begin = tb;
+        h.tile_end = te;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(c, snap);
+    c->tile_request = rc ? tile0 : best;
+    int rp = plan_launch(c);
+    if (!rp) rp = upload_instances(c);
+    if (rc) return rc;
+    if (rr) return rr;
+    if (rp) return rp;
+    if (best_tile) *best_tile = best;
+    if (best_ms) *best_ms = best_t / (double)n_probe;
+    return XF_OK;
 }
 
 int xf_set_option(xf_ctx *c, int option, int64_t value)

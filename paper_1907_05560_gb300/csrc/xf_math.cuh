@@ -28,6 +28,24 @@ __host__ __device__ __forceinline__ void sincos_r(double x, double *s, double *c
 __host__ __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
 __host__ __device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
 __host__ __device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+// 1/sqrt(x): the device's reciprocal square root (1 ulp in FP64, 2 in FP32);
+// the host build (used only to count operations) divides.
+__host__ __device__ __forceinline__ double rsqrt_r(double x)
+{
+#ifdef __CUDA_ARCH__
+    return rsqrt(x);
+#else
+    return 1.0 / sqrt(x);
+#endif
+}
+__host__ __device__ __forceinline__ float rsqrt_r(float x)
+{
+#ifdef __CUDA_ARCH__
+    return rsqrtf(x);
+#else
+    return 1.0f / sqrtf(x);
+#endif
+}
 
 // Step path length in the precision of the phase arithmetic: FP64 for the
 // FP64 path; for FP32 an unevaluated sum hi + lo of two floats (about 48
@@ -181,9 +199,14 @@ __host__ __device__ constexpr int oidx(int a, int b) { return a == 0 ? b - 1 : 2
 // One Jacobi rotation on pivot (P, Q) of the Hermitian matrix held as diag
 // dg[3] and upper entries o[3], accumulating V <- V J with
 // J = [[c, s e^{i phi}], [-s e^{-i phi}, c]] on rows/cols (P, Q),
-// e^{i phi} = A_PQ / |A_PQ|, t = tan(theta) the smaller root of
-// t^2 + 2 tau t - 1 = 0, tau = (A_QQ - A_PP) / (2 |A_PQ|).  J^dagger A J has
-// a zero (P, Q) entry, A_PP -> A_PP - t |A_PQ|, A_QQ -> A_QQ + t |A_PQ|.
+// e^{i phi} = A_PQ / |A_PQ| and theta the smaller rotation angle that zeroes
+// the (P, Q) entry: with d = (A_QQ - A_PP)/2 and D = sqrt(d^2 + |A_PQ|^2),
+//   tan(theta) = sgn(d) |A_PQ| / (|d| + D),  c^2 = (1 + |d|/D) / 2,
+// from which (using 1/(|d| + D) = 1/(2 D c^2))
+//   s e^{i phi} = sgn(d) A_PQ / (2 D c),  t |A_PQ| = sgn(d) |A_PQ|^2 / (2 D c^2),
+// and A_PP -> A_PP - t |A_PQ|, A_QQ -> A_QQ + t |A_PQ|.  With rD = 1/D and
+// rc = 1/c from two reciprocal square roots, the rotation needs no division
+// and no square root.
 template <typename Real, int P, int Q>
 __host__ __device__ __forceinline__ void jacobi_rot(Real *dg, cx<Real> *o, cx<Real> (*V)[3])
 {
@@ -191,22 +214,23 @@ __host__ __device__ __forceinline__ void jacobi_rot(Real *dg, cx<Real> *o, cx<Re
     cx<Real> g = o[oidx(P, Q)];
     Real ag2 = g.r * g.r + g.i * g.i;
     if (!(ag2 > Real(0))) return;
-    Real ag = sqrt_r(ag2);
-    Real er = g.r / ag, ei = g.i / ag; // e^{i phi}
-    Real tau = (dg[Q] - dg[P]) / (Real(2) * ag);
-    Real t = (tau >= Real(0) ? Real(1) : Real(-1)) / (fabs(tau) + sqrt_r(Real(1) + tau * tau));
-    Real c = Real(1) / sqrt_r(Real(1) + t * t);
-    Real s = t * c;
-    dg[P] -= t * ag;
-    dg[Q] += t * ag;
+    const Real d = Real(0.5) * (dg[Q] - dg[P]);
+    const Real rD = rsqrt_r(d * d + ag2);
+    const Real u = Real(0.5) + Real(0.5) * fabs(d) * rD; // c^2, in [1/2, 1]
+    const Real rc = rsqrt_r(u);
+    const Real c = u * rc;
+    const Real h = (d >= Real(0) ? Real(0.5) : Real(-0.5)) * rD * rc; // sgn(d) / (2 D c)
+    const Real tg = h * rc * ag2;                                     // t |A_PQ|
+    const cx<Real> se = mk(h * g.r, h * g.i), sec = mk(h * g.r, -h * g.i); // s e^{+-i phi}
+    dg[P] -= tg;
+    dg[Q] += tg;
     o[oidx(P, Q)] = mk(Real(0), Real(0));
     // A_RP and A_RQ: stored when R is the row of an upper entry, else conjugated
     cx<Real> aRP = (R < P) ? o[oidx(R, P)] : cj(o[oidx(P, R)]);
     cx<Real> aRQ = (R < Q) ? o[oidx(R, Q)] : cj(o[oidx(Q, R)]);
-    const cx<Real> e = mk(er, ei), ec = mk(er, -ei);
     // (J^dagger A J)_RP = c A_RP - s e^{-i phi} A_RQ,  (.)_RQ = s e^{i phi} A_RP + c A_RQ
-    cx<Real> nRP = c * aRP - s * (ec * aRQ);
-    cx<Real> nRQ = s * (e * aRP) + c * aRQ;
+    cx<Real> nRP = c * aRP - sec * aRQ;
+    cx<Real> nRQ = se * aRP + c * aRQ;
     if (R < P) o[oidx(R, P)] = nRP;
     else o[oidx(P, R)] = cj(nRP);
     if (R < Q) o[oidx(R, Q)] = nRQ;
@@ -214,8 +238,8 @@ __host__ __device__ __forceinline__ void jacobi_rot(Real *dg, cx<Real> *o, cx<Re
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         cx<Real> vp = V[k][P], vq = V[k][Q];
-        V[k][P] = c * vp - s * (ec * vq);
-        V[k][Q] = s * (e * vp) + c * vq;
+        V[k][P] = c * vp - sec * vq;
+        V[k][Q] = se * vp + c * vq;
     }
 }
 

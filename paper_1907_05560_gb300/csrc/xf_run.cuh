@@ -622,10 +622,21 @@ __device__ __forceinline__ void finish_instance(const RunArgs &a, const Inst &in
     __syncthreads();
 }
 
+// Resident CTAs per SM the register allocation is fitted to (occupancy for
+// latency hiding; no kernel here is limited by shared memory):
+//   FP64, 128 threads (three flavors / mixed): 3 (168 registers, a few words
+//     spilled) instead of 2 at 252;
+//   FP32, 128 threads: 4 (128 registers, no spills) instead of 2 at ~200;
+//   256 threads (two flavors): 2 (<= 128 registers, no spills).
+__host__ __device__ constexpr int min_blocks(int nt, int real_bytes)
+{
+    return nt == 128 ? (real_bytes == 8 ? 3 : 4) : 2;
+}
+
 // NFM: 2 or 3 (every instance has that many flavors) or 0 (mixed pack);
 // VAR: VAR_PLAIN, VAR_COMP or VAR_RENORM.
 template <int NFM, int STEP, typename Real, int NT, int VAR>
-__global__ void __launch_bounds__(NT) xf_run_kernel(RunArgs a)
+__global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real))) xf_run_kernel(RunArgs a)
 {
     extern __shared__ double s_dyn[];
     Real *const s_tab = (Real *)s_dyn;

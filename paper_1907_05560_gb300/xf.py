@@ -122,6 +122,8 @@ SIGNATURES = {
     "xf_batch_outputs": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, ctypes.c_size_t]),
     "xf_batch_run_moments": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, ctypes.c_size_t]),
     "xf_evolve": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int64, ctypes.c_double]),
+    "xf_autotune": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int), _D]),
     "xf_batch_evolve": (ctypes.c_int, [_P, _D, ctypes.c_int64, _D]),
     "xf_adapt_status": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D,
                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _D]),
@@ -284,6 +286,18 @@ class Context:
     def evolve(self, r_end_km: float, max_iters: int = 1 << 40, dr0_km: float = 0.0):
         """Error-controlled integration to r_end_km (XF_EXPH_ADAPTIVE)."""
         return self._check(self.L.xf_evolve(self.h, float(r_end_km), int(max_iters), float(dr0_km)))
+
+    def autotune(self, n_probe: int, dr_km: float = 0.0, candidates=None):
+        """Measured tile-size search (xf_autotune); returns (tile, ms per step)."""
+        best, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+        if candidates is None:
+            arr, n = None, 0
+        else:
+            arr = (ctypes.c_int * len(candidates))(*candidates)
+            n = len(candidates)
+        self._check(self.L.xf_autotune(self.h, int(n_probe), float(dr_km), arr, n, ctypes.byref(best),
+                                       ctypes.byref(ms)))
+        return best.value, ms.value
 
     def adapt_status(self, i: int = 0):
         st, r, h, e = ctypes.c_int(0), ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)

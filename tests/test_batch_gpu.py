@@ -160,3 +160,37 @@ def test_full_c4_batch_sampled_against_oracle(xf, orc):
         assert rel_err(got, ref, q.n_f) < 1e-5, i
     b.close()
     torch.cuda.synchronize()
+
+
+def test_autotune_restores_state_and_keeps_the_chosen_tile(xf, orc):
+    """The tile search steps the pack, then puts every state, radius and
+    step count back; later steps run with the chosen tile, bitwise like a
+    pack that was set to that tile by hand."""
+    probs, common = two_flavor_mix(I.FP32_M64)
+    probs = [q.replace(**common) for q in probs]
+    h = probs[0].h
+    rho0s = [orc.init_state(q) for q in probs]
+
+    def fresh():
+        b = xf.Batch(probs)
+        for i, (q, r0) in enumerate(zip(probs, rho0s)):
+            b.set_state_i(i, r0, q.r0)
+        b.step_all(5, h)
+        return b
+
+    b = fresh()
+    before = [b.get_state_i(i) for i in range(len(probs))]
+    tile, ms = b.autotune(4, h, [64, 256, 1024])
+    assert tile in (64, 256, 1024) and ms > 0
+    for i, (x, r, n) in enumerate(before):
+        y, r2, n2 = b.get_state_i(i)
+        assert np.array_equal(x, y) and r == r2 and n == n2
+    b.step_all(5, h)
+    got = [b.get_state_i(i)[0] for i in range(len(probs))]
+    b.close()
+    c = fresh()
+    c.set_option(xf.OPT_TILE_PAIRS, tile)
+    c.step_all(5, h)
+    for i in range(len(probs)):
+        assert np.array_equal(got[i], c.get_state_i(i)[0])
+    c.close()
