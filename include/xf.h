@@ -285,6 +285,36 @@ int xf_batch_evolve(xf_ctx *ctx, const double *r_end_km, int64_t max_iters, cons
 int xf_adapt_status(xf_ctx *ctx, int inst, int *status, double *r_km, double *h_next_km, int64_t *n_accepted,
                     int64_t *n_rejected, double *last_error);
 
+/* ---- snapshots, checkpoints and reduced outputs (the paper's I/O module,
+ * Sec. 4.2.4: dump mode 1 = a snapshot of every bin's state from which a run
+ * resumes; dump mode 2 = the flavor state of each trajectory averaged over
+ * its energy bins) ------------------------------------------------------------
+ * A checkpoint is the problem's state in the library's own device layout
+ * (traceless components in the working precision, the FP64 trace per bin,
+ * the renormalising variant's reference values) plus its position (radius,
+ * step size, step counts, error-controlled progress), so loading it and
+ * continuing gives bitwise the same result as never having stopped.  The
+ * buffer is opaque, versioned and tied to the problem's shape, stepper and
+ * precision.  inst = 0 for a single-problem context. */
+int xf_checkpoint_bytes(xf_ctx *ctx, int inst, size_t *bytes);
+/* Synchronous save into host memory of xf_checkpoint_bytes bytes. */
+int xf_checkpoint_save(xf_ctx *ctx, int inst, void *buf, size_t bytes);
+/* Asynchronous save: the state is copied on the device in the context's
+ * stream order (after the steps already enqueued), then to `buf` on a
+ * separate copy stream, so steps enqueued after this call run while the
+ * copy to the host is in flight.  `buf` must stay valid until
+ * xf_checkpoint_wait; pinned host memory makes the copy truly asynchronous.
+ * One save may be in flight per context (XF_E_BUSY otherwise). */
+int xf_checkpoint_save_async(xf_ctx *ctx, int inst, void *buf, size_t bytes);
+int xf_checkpoint_wait(xf_ctx *ctx);
+/* Restore problem `inst` from a checkpoint (XF_E_ARG if the buffer is not a
+ * checkpoint of a problem of this shape, stepper and precision). */
+int xf_checkpoint_load(xf_ctx *ctx, int inst, const void *buf, size_t bytes);
+/* Dump mode 2: out[s][u][n_f*n_f] (packed like a bin) = the mean over the
+ * n_E energy bins of trajectory u's density matrices, s = 0 nu, 1 nubar;
+ * summed in FP64 on the device in energy order.  n_doubles = 2 n_u n_f^2. */
+int xf_angle_average(xf_ctx *ctx, int inst, double *out, size_t n_doubles);
+
 /* ---- serving: a continuous-batching job server ---------------------------
  * A server owns one pack of `max_jobs` slots and a device arena of
  * `mem_budget_bytes`, and a scheduler thread that repeats epochs:

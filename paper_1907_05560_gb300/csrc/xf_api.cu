@@ -126,6 +126,16 @@ void free_all(xf_ctx *c)
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     c->gstream = nullptr;
     c->ev_in = c->ev_out = nullptr;
+    if (c->ck_stream) {
+        cudaStreamSynchronize(c->ck_stream);
+        cudaStreamDestroy(c->ck_stream);
+    }
+    if (c->ck_event) cudaEventDestroy(c->ck_event);
+    c->ck_stream = nullptr;
+    c->ck_event = nullptr;
+    c->ck_buf = nullptr;
+    c->ck_bytes = 0;
+    c->ck_pending = false;
     for (void *p : c->owned) {
         if (c->has_alloc) c->alloc.free(p, c->alloc.user);
         else cudaFree(p);
@@ -437,6 +447,7 @@ __global__ void reset_pos_kernel(InstPos *pos, int i, int cur, int keep)
 }
 
 __global__ void set_apos_kernel(AdaptPos *apos, int i, AdaptPos v) { apos[i] = v; }
+__global__ void set_pos_kernel(InstPos *pos, int i, InstPos v) { pos[i] = v; }
 
 // Read the device progress of every instance into the host view.
 int sync_status(xf_ctx *c)
@@ -692,17 +703,6 @@ int evolve_impl(xf_ctx *c, const double *r_end, long long max_iters, const doubl
     return XF_OK;
 }
 
-template <typename F>
-int dispatch_layout(xf_ctx *c, const InstHost &in, F &&f)
-{
-    if (in.nf == 2) {
-        if (c->real_bytes == 8) return f(std::integral_constant<int, 2>(), (double *)nullptr);
-        return f(std::integral_constant<int, 2>(), (float *)nullptr);
-    }
-    if (c->real_bytes == 8) return f(std::integral_constant<int, 3>(), (double *)nullptr);
-    return f(std::integral_constant<int, 3>(), (float *)nullptr);
-}
-
 InstHost *instance(xf_ctx *c, int i)
 {
     if (!c || i < 0 || i >= (int)c->in.size()) return nullptr;
@@ -755,6 +755,7 @@ int setup_problem(xf_ctx *c, int i, const xf_problem &prob)
     h.npad = (h.n_pairs + 63) & ~63;
     h.n_bins = 2ll * h.n_pairs;
     h.p = prob.params;
+    h.adaptive = c->stepper == XF_EXPH_ADAPTIVE;
     const int rb = c->real_bytes;
     h.block_bytes = block_bytes(h.n_E, h.n_u, h.nf, c->precision);
     h.block = c->blocks.alloc(h.block_bytes);

@@ -270,4 +270,47 @@ __global__ void moments_final_kernel(const double *part, int G, double dE, doubl
     }
 }
 
+// Dump mode 2 (Sec. 4.2.4): the flavor state of each trajectory averaged over
+// its energy bins.  One block per (s, u); threads stride the energies, sum
+// the packed entries in FP64, then the block adds the threads' sums in a
+// fixed order.  out[(s n_u + j) NF^2 + c].
+template <int NF, typename Real, int NT>
+__global__ void __launch_bounds__(NT) angle_average_kernel(LayoutArgs a, const Real *state, const double *trace,
+                                                           double *out)
+{
+    constexpr int S = Comp<NF>::S, M = NF * NF;
+    __shared__ double sm[NT][M];
+    const int s = blockIdx.x / a.n_u, j = blockIdx.x % a.n_u;
+    double acc[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) acc[c] = 0.0;
+    for (int e = threadIdx.x; e < a.n_E; e += NT) {
+        const int p = j * a.n_E + e;
+        double t[S];
+#pragma unroll
+        for (int c = 0; c < S; ++c) t[c] = (double)state[(size_t)(c * 2 + s) * a.npad + p];
+        const double tau = trace[(size_t)s * a.npad + p] / NF;
+        if constexpr (NF == 2) {
+            acc[0] += tau + t[0];
+            acc[1] += tau - t[0];
+            acc[2] += t[1];
+            acc[3] += t[2];
+        } else {
+            acc[0] += tau + t[0];
+            acc[1] += tau + t[1];
+            acc[2] += tau - (t[0] + t[1]);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[3 + c] += t[2 + c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) sm[threadIdx.x][c] = acc[c];
+    __syncthreads();
+    if (threadIdx.x < M) {
+        double v = 0.0;
+        for (int q = 0; q < NT; ++q) v += sm[q][threadIdx.x];
+        out[(size_t)blockIdx.x * M + threadIdx.x] = v / a.n_E;
+    }
+}
+
 } // namespace xf

@@ -7,9 +7,11 @@
 
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/xf.h"
+#include "xf_aux.cuh"
 #include "xf_kernels.h"
 
 namespace xfp {
@@ -148,6 +150,12 @@ struct xf_ctx {
     cudaGraphExec_t graph = nullptr;
     long long graph_steps = 0;
     cudaStream_t gstream = nullptr;
+    // asynchronous checkpoint: device copy, then a copy stream to the host
+    cudaStream_t ck_stream = nullptr;
+    cudaEvent_t ck_event = nullptr;
+    unsigned char *ck_buf = nullptr;
+    size_t ck_bytes = 0;
+    bool ck_pending = false;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
     std::string last_error;
@@ -172,5 +180,27 @@ int set_state_impl(xf_ctx *c, int i, const double *rho, size_t n_doubles, double
 int init_state_impl(xf_ctx *c, int i, double r_km);
 int get_state_impl(xf_ctx *c, int i, double *rho, size_t n_doubles, double *r_km, int64_t *steps_done);
 void destroy_pack(xf_ctx *c);
+int moments_impl(xf_ctx *c, int i, double *M0, double *M1, size_t n_doubles);
+InstHost *instance(xf_ctx *c, int i);
+xf::LayoutArgs layout_args(xf_ctx *c, const InstHost &in);
+int elementwise_grid(xf_ctx *c, const InstHost &in);
+void *dev_alloc(xf_ctx *c, size_t bytes);
+void dev_free(xf_ctx *c, void *p);
+int upload_instances(xf_ctx *c);
+__global__ void set_apos_kernel(AdaptPos *apos, int i, AdaptPos v);
+__global__ void set_pos_kernel(InstPos *pos, int i, InstPos v);
+
+// Run f(std::integral_constant<int, NF>, (Real *)nullptr) for the problem's
+// flavor count and the context's working precision.
+template <typename F>
+int dispatch_layout(xf_ctx *c, const InstHost &in, F &&f)
+{
+    if (in.nf == 2) {
+        if (c->real_bytes == 8) return f(std::integral_constant<int, 2>(), (double *)nullptr);
+        return f(std::integral_constant<int, 2>(), (float *)nullptr);
+    }
+    if (c->real_bytes == 8) return f(std::integral_constant<int, 3>(), (double *)nullptr);
+    return f(std::integral_constant<int, 3>(), (float *)nullptr);
+}
 
 } // namespace xfp

@@ -122,6 +122,12 @@ SIGNATURES = {
     "xf_batch_outputs": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, ctypes.c_size_t]),
     "xf_batch_run_moments": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, ctypes.c_size_t]),
     "xf_evolve": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int64, ctypes.c_double]),
+    "xf_checkpoint_bytes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "xf_checkpoint_save": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
+    "xf_checkpoint_save_async": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
+    "xf_checkpoint_wait": (ctypes.c_int, [_P]),
+    "xf_checkpoint_load": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
+    "xf_angle_average": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.c_size_t]),
     "xf_autotune": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int), _D]),
     "xf_batch_evolve": (ctypes.c_int, [_P, _D, ctypes.c_int64, _D]),
@@ -286,6 +292,37 @@ class Context:
     def evolve(self, r_end_km: float, max_iters: int = 1 << 40, dr0_km: float = 0.0):
         """Error-controlled integration to r_end_km (XF_EXPH_ADAPTIVE)."""
         return self._check(self.L.xf_evolve(self.h, float(r_end_km), int(max_iters), float(dr0_km)))
+
+    def checkpoint_bytes(self, i: int = 0) -> int:
+        n = ctypes.c_size_t(0)
+        self._check(self.L.xf_checkpoint_bytes(self.h, i, ctypes.byref(n)))
+        return n.value
+
+    def checkpoint_save(self, i: int = 0, buf: np.ndarray | None = None) -> np.ndarray:
+        """Synchronous checkpoint of problem i into a uint8 array."""
+        n = self.checkpoint_bytes(i)
+        b = buf if buf is not None else np.empty(n, dtype=np.uint8)
+        self._check(self.L.xf_checkpoint_save(self.h, i, ctypes.c_void_p(b.ctypes.data), n))
+        return b
+
+    def checkpoint_save_async(self, buf: np.ndarray, i: int = 0):
+        """Start an asynchronous checkpoint into `buf` (kept alive by the
+        caller until checkpoint_wait)."""
+        self._check(self.L.xf_checkpoint_save_async(self.h, i, ctypes.c_void_p(buf.ctypes.data), buf.size))
+
+    def checkpoint_wait(self):
+        return self._check(self.L.xf_checkpoint_wait(self.h))
+
+    def checkpoint_load(self, buf: np.ndarray, i: int = 0):
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        return self._check(self.L.xf_checkpoint_load(self.h, i, ctypes.c_void_p(b.ctypes.data), b.size))
+
+    def angle_average(self, i: int = 0) -> np.ndarray:
+        """Dump mode 2: [2][n_u][n_f^2] energy-averaged density matrices."""
+        p = self.problems[i] if hasattr(self, "problems") else self.problem
+        out = np.empty(2 * p.n_u * p.n_f * p.n_f)
+        self._check(self.L.xf_angle_average(self.h, i, _dp(out), out.size))
+        return out
 
     def autotune(self, n_probe: int, dr_km: float = 0.0, candidates=None):
         """Measured tile-size search (xf_autotune); returns (tile, ms per step)."""

@@ -86,3 +86,9 @@ def test_null_handles_are_errors_not_crashes(lib):
     assert lib.xf_get_state(None, None, 0, None, None) == E
     assert lib.xf_moments(None, None, None, 0) == E
     assert lib.xf_create(32, 16, 2, None, None) == E
+    assert lib.xf_checkpoint_save(None, 0, None, 0) == E
+    assert lib.xf_checkpoint_load(None, 0, None, 0) == E
+    assert lib.xf_checkpoint_wait(None) == E
+    assert lib.xf_angle_average(None, 0, None, 0) == E
+    assert lib.xf_evolve(None, 1.0, 1, 0.1) == E
+    assert lib.xf_autotune(None, 1, 0.0, None, 0, None, None) == E
