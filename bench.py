@@ -112,10 +112,10 @@ def measured_peaks():
 # per-bin formulas (+ - * / sqrt each 1, FMA 2, sincos not counted); the
 # Jacobi eigensolver is counted at the sweep number measured on this
 # workload.  Derivation in DESIGN.md ("Algorithmic work").
-FLOPS_PER_BIN_STEP = {("exph", 3): 2660, ("rk4", 3): 684, ("exph", 2): 122, ("rk4", 2): 172}
+FLOPS_PER_BIN_STEP = {("exph", 3): 2631, ("rk4", 3): 684, ("exph", 2): 120, ("rk4", 2): 172}
 # one attempt of the error-controlled step (four Hamiltonians, five propagations,
 # one shared eigendecomposition), counted the same way
-FLOPS_PER_BIN_ATTEMPT = {3: 5955, 2: 272}
+FLOPS_PER_BIN_ATTEMPT = {3: 5897, 2: 268}
 
 
 def oracle_sample(problem, n_steps, threads):

@@ -393,7 +393,7 @@ __device__ __forceinline__ void adapt_decide_tile(const RunArgs &a, const Inst &
 
 // Resident CTAs per SM the register allocation is fitted to: stage A keeps
 // two moment sets per thread, so the FP64 kernel stays at 2 (a third would
-// spill about 1 KB per thread); FP32 fits 3, the 256-thread kernels 2.
+// spill about 1 KB per thread); FP32 fits 3; the 256-thread kernels 2.
 __host__ __device__ constexpr int adapt_min_blocks(int nt, int real_bytes)
 {
     return nt == 128 ? (real_bytes == 8 ? 2 : 3) : 2;

@@ -271,10 +271,19 @@ __host__ __device__ __forceinline__ void eig3(const Real *h, Real *dg, cx<Real> 
     const Real scale2 = dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2] +
                         Real(2) * (o[0].r * o[0].r + o[0].i * o[0].i + o[1].r * o[1].r +
                                    o[1].i * o[1].i + o[2].r * o[2].r + o[2].i * o[2].i);
-    for (int sweep = 0; sweep < JacobiTol<Real>::sweeps; ++sweep) {
-        Real off2 = o[0].r * o[0].r + o[0].i * o[0].i + o[1].r * o[1].r + o[1].i * o[1].i +
-                    o[2].r * o[2].r + o[2].i * o[2].i;
-        if (!(off2 > JacobiTol<Real>::rel2 * scale2)) break;
+    // cyclic sweeps until the off-diagonal part is below the tolerance; the
+    // first sweep is written out so that it starts from the constant V = I
+    auto converged = [&]() {
+        const Real off2 = o[0].r * o[0].r + o[0].i * o[0].i + o[1].r * o[1].r + o[1].i * o[1].i +
+                          o[2].r * o[2].r + o[2].i * o[2].i;
+        return !(off2 > JacobiTol<Real>::rel2 * scale2);
+    };
+    if (converged()) return;
+    jacobi_rot<Real, 0, 1>(dg, o, V);
+    jacobi_rot<Real, 0, 2>(dg, o, V);
+    jacobi_rot<Real, 1, 2>(dg, o, V);
+    for (int sweep = 1; sweep < JacobiTol<Real>::sweeps; ++sweep) {
+        if (converged()) break;
         jacobi_rot<Real, 0, 1>(dg, o, V);
         jacobi_rot<Real, 0, 2>(dg, o, V);
         jacobi_rot<Real, 1, 2>(dg, o, V);

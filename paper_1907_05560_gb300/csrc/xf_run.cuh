@@ -627,10 +627,11 @@ __device__ __forceinline__ void finish_instance(const RunArgs &a, const Inst &in
 //   FP64, 128 threads (three flavors / mixed): 3 (168 registers, a few words
 //     spilled) instead of 2 at 252;
 //   FP32, 128 threads: 4 (128 registers, no spills) instead of 2 at ~200;
-//   256 threads (two flavors): 2 (<= 128 registers, no spills).
+//   FP64, 256 threads (two flavors): 2 (~120 registers, no spills);
+//   FP32, 256 threads: 4 (64 registers, no spills).
 __host__ __device__ constexpr int min_blocks(int nt, int real_bytes)
 {
-    return nt == 128 ? (real_bytes == 8 ? 3 : 4) : 2;
+    return nt == 128 ? (real_bytes == 8 ? 3 : 4) : (real_bytes == 8 ? 2 : 4);
 }
 
 // NFM: 2 or 3 (every instance has that many flavors) or 0 (mixed pack);
