@@ -298,8 +298,14 @@ def run_xf(args):
     # derived ALU peak: 152 SMs x (FP64: 2 FMA, FP32: 128 FMA) per clock x 2 flop x max clock
     per_clk = 2 if args.precision == "fp64" else 128
     peak_nom = 152 * per_clk * 2 * sm_max * 1e6 / 1e12
+    # DRAM bytes (read + write) per radial step of this kernel on this workload, from
+    # one ncu capture of a 5-step launch (dram__bytes_read.sum + dram__bytes_write.sum
+    # = 147.6 MB), scaled to the bench's launch; null for other precisions
+    traffic = 29.52e6 * chunk if args.precision == "fp64" else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_nom, "unit": "TFLOP/s",
-                "frac": achieved / peak_nom, "traffic": None,
+                "frac": achieved / peak_nom, "traffic": traffic,
+                "traffic_note": "bytes per launch from ncu DRAM counters (5-step capture, scaled to %d steps); "
+                                "the state planes are L2-resident" % chunk,
                 "kernel": "xf_run_kernel<3,EXPH,%s>" % ("double" if args.precision == "fp64" else "float"),
                 "peak_source": "derived: 152 SMs x %d FMA/clk x 2 x %.0f MHz (recipe FP64 1.25 TFLOP/s)" % (per_clk, sm_max),
                 "peak_measured_fma": peak_meas}
