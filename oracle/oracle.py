@@ -29,7 +29,7 @@ class OrcParams(ctypes.Structure):
         ("n_E", ctypes.c_int32), ("n_u", ctypes.c_int32), ("n_f", ctypes.c_int32),
         ("stepper", ctypes.c_int32), ("geometry", ctypes.c_int32),
         ("hierarchy", ctypes.c_int32), ("matter", ctypes.c_int32),
-        ("n_threads", ctypes.c_int32), ("renorm", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("n_threads", ctypes.c_int32), ("renorm", ctypes.c_int32), ("n_phi", ctypes.c_int32),
         ("R_nu", ctypes.c_double), ("mu0", ctypes.c_double),
         ("E_min", ctypes.c_double), ("E_max", ctypes.c_double),
         ("dm2", ctypes.c_double * 2), ("theta", ctypes.c_double * 3),
@@ -63,6 +63,7 @@ def lib():
         L.orc_evolve.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                  ctypes.POINTER(ctypes.c_int64)]
         L.orc_moments.argtypes = [P, dp, ctypes.c_double, dp, dp]
+        L.orc_moments_ex.argtypes = [P, dp, ctypes.c_double, dp]
         i64p = ctypes.POINTER(ctypes.c_int64)
         L.orc_evolve_adaptive.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int64, dp, dp, i64p, i64p]
@@ -87,6 +88,7 @@ def params(p, n_threads: int = 0, renorm: bool = False) -> OrcParams:
     o.stepper, o.geometry, o.hierarchy, o.matter = p.stepper, p.geometry, p.hierarchy, p.matter
     o.n_threads = n_threads
     o.renorm = 1 if renorm else 0
+    o.n_phi = getattr(p, "n_phi", 1)
     o.R_nu, o.mu0, o.E_min, o.E_max = p.R_nu, p.mu0, p.E_min, p.E_max
     o.dm2[:] = list(p.dm2)
     o.theta[:] = list(p.theta)
@@ -106,7 +108,7 @@ def _dp(a: np.ndarray):
 
 
 def state_size(p) -> int:
-    return 2 * p.n_u * p.n_E * p.n_f * p.n_f
+    return 2 * p.n_u * getattr(p, "n_phi", 1) * p.n_E * p.n_f * p.n_f
 
 
 def tables(p):
@@ -167,6 +169,17 @@ def attempt_adaptive(p, rho: np.ndarray, r: float, h: float, n_threads: int = 0)
     if rc < 0:
         raise ValueError(f"orc_attempt_adaptive: {rc}")
     return out, fine, err.value, rc
+
+
+def moments_ex(p, rho: np.ndarray, r: float) -> np.ndarray:
+    """All four moments [4][n_f*n_f] packed (M2 = M3 = 0 without azimuth bins)."""
+    o = params(p)
+    M = np.zeros(4 * p.n_f * p.n_f)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    rc = lib().orc_moments_ex(ctypes.byref(o), _dp(rho), r, _dp(M))
+    if rc:
+        raise ValueError(f"orc_moments_ex: {rc}")
+    return M.reshape(4, -1)
 
 
 def moments(p, rho: np.ndarray, r: float):

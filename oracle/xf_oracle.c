@@ -58,7 +58,7 @@ typedef struct {
     int32_t n_E, n_u, n_f, stepper, geometry, hierarchy, matter, n_threads;
     int32_t renorm;   /* 1: after every step, scale each bin's traceless part back to
                          the tr(T^2) it had on entry (see renormalise()) */
-    int32_t reserved;
+    int32_t n_phi;    /* azimuth bins of the extended bulb model (Eq. 3.18); 0 or 1: none */
     double R_nu;      /* neutrinosphere radius, km */
     double mu0;       /* nu-nu coupling, km^-1 */
     double E_min, E_max; /* MeV */
@@ -302,7 +302,7 @@ int orc_expm(int n, const double *Hp, double t, double *Uri)
 /* ---- problem set-up -------------------------------------------------------- */
 typedef struct {
     orc_params p;
-    int n, nE, nu, nbins, m; /* m = n*n */
+    int n, nE, nu, nphi, nt, nbins, m; /* m = n*n; nt = nu * nphi trajectories */
     double dE, du;
     double *E, *u, *phi; /* phi[a*nE + e], a = nu_e, nubar_e, nu_x, nubar_x */
     cplx *Hvac;          /* [nE][n][n] */
@@ -317,7 +317,10 @@ static int ctx_init(orc_ctx *c, const orc_params *p)
     c->m = p->n_f * p->n_f;
     c->nE = p->n_E;
     c->nu = p->n_u;
-    c->nbins = 2 * p->n_u * p->n_E;
+    c->nphi = p->n_phi > 1 ? p->n_phi : 1;
+    if (c->nphi > 1 && p->geometry != ORC_BULB) return -1; /* azimuth bins extend the bulb model only */
+    c->nt = c->nu * c->nphi;
+    c->nbins = 2 * c->nt * p->n_E;
     c->dE = (p->E_max - p->E_min) / p->n_E;
     c->du = 1.0 / p->n_u;
     c->E = malloc(sizeof(double) * c->nE);
@@ -394,38 +397,57 @@ static double matter_A(const orc_ctx *c, double r)
     return orc_matter_coeff() * ne;
 }
 
-/* Per-angle geometry at radius r for the configured mode.
- *   a[j], b[j]: weights with M0 = dE sum_j a_j S_j, M1 = dE sum_j b_j S_j
- *   g[j]      : G_j = mu_eff (M0 - g_j M1)
- *   kap[j]    : dl/dr along trajectory j
+/* Per-trajectory geometry at one radius.  Trajectory t = j n_phi + k (zenith
+ * bin j, azimuth bin k).  The moments are M_q = dE sum_t w_q(t) S_t, q = 0..3,
+ * and G_t = mu_eff (M0 - g1_t M1 - g2_t M2 - g3_t M3); kap[t] = dl/dr.
  * BULB: Eq. 3.13-3.15 with u = sin^2(theta_0):  cos(theta') = sqrt(1 - x^2 u),
  *       d cos(theta') = x^2 du / (2 cos(theta')), and l = r cos(theta) (Eq. 3.3)
- *       gives dl/dr = 1/cos(theta). */
-static void geometry(const orc_ctx *c, double r, double *a, double *b, double *g, double *kap,
-                     double *mu_eff)
+ *       gives dl/dr = 1/cos(theta).
+ * Extended bulb (Eq. 3.18, n_phi > 1): 1 - cos(gamma) = 1 - cos(th) cos(th')
+ *       - sin(th) sin(th') (cos(ph) cos(ph') + sin(ph) sin(ph')), with
+ *       sin(theta') = x sqrt(u) and azimuth midpoints ph_k = (k + 1/2) 2 pi / n_phi
+ *       of weight 1/n_phi: four moments.  With one azimuth bin the model is the
+ *       azimuthally symmetric bulb (M2 = M3 = 0). */
+typedef struct {
+    double *w[4], *g1, *g2, *g3, *kap;
+} geom_t;
+
+static void geometry(const orc_ctx *c, double r, geom_t *g, double *mu_eff)
 {
     const orc_params *p = &c->p;
     double x = p->R_nu / r, x2 = x * x;
-    for (int j = 0; j < c->nu; ++j) {
+    for (int t = 0; t < c->nt; ++t) {
+        const int j = t / c->nphi, k = t % c->nphi;
         double cth = sqrt(1.0 - x2 * c->u[j]);
+        g->w[2][t] = g->w[3][t] = g->g2[t] = g->g3[t] = 0.0;
         switch (p->geometry) {
-        case ORC_BULB:
-            a[j] = x2 * c->du / (2.0 * cth);
-            b[j] = a[j] * cth;
-            g[j] = cth;
-            kap[j] = 1.0 / cth;
+        case ORC_BULB: {
+            double a = x2 * c->du / (2.0 * cth);
+            g->w[0][t] = a / c->nphi;
+            g->w[1][t] = a * cth / c->nphi;
+            g->g1[t] = cth;
+            g->kap[t] = 1.0 / cth;
+            if (c->nphi > 1) {
+                double sth = sqrt(x2 * c->u[j]);
+                double ph = (k + 0.5) * 2.0 * PI / c->nphi;
+                g->w[2][t] = a * sth * cos(ph) / c->nphi;
+                g->w[3][t] = a * sth * sin(ph) / c->nphi;
+                g->g2[t] = sth * cos(ph);
+                g->g3[t] = sth * sin(ph);
+            }
             break;
+        }
         case ORC_MU_R4:
-            a[j] = c->du;
-            b[j] = c->du * cth;
-            g[j] = cth;
-            kap[j] = 1.0 / cth;
+            g->w[0][t] = c->du;
+            g->w[1][t] = c->du * cth;
+            g->g1[t] = cth;
+            g->kap[t] = 1.0 / cth;
             break;
         default: /* single-angle and constant-coupling modes: radial, no angle factor */
-            a[j] = c->du;
-            b[j] = 0.0;
-            g[j] = 0.0;
-            kap[j] = 1.0;
+            g->w[0][t] = c->du;
+            g->w[1][t] = 0.0;
+            g->g1[t] = 0.0;
+            g->kap[t] = 1.0;
             break;
         }
     }
@@ -436,12 +458,14 @@ static void geometry(const orc_ctx *c, double r, double *a, double *b, double *g
     } else *mu_eff = p->mu0;
 }
 
-/* Exact path length along trajectory j from r to r+h (Eq. 3.3, l = r cos):
+/* Exact path length along trajectory t from r to r+h (Eq. 3.3, l = r cos):
  * l(r+h) - l(r) = ((r+h)^2 - r^2) / (l(r+h) + l(r)), since l^2 = r^2 - b^2 with
- * b the impact parameter; written this way it has no cancellation. */
-static double path_length(const orc_ctx *c, int j, double r, double h)
+ * b the impact parameter; written this way it has no cancellation.  It depends
+ * on the zenith bin only. */
+static double path_length(const orc_ctx *c, int t, double r, double h)
 {
     if (c->p.geometry != ORC_BULB && c->p.geometry != ORC_MU_R4) return h;
+    const int j = t / c->nphi;
     double R = c->p.R_nu;
     double x0 = R / r, x1 = R / (r + h);
     double l0 = r * sqrt(1.0 - x0 * x0 * c->u[j]);
@@ -449,35 +473,49 @@ static double path_length(const orc_ctx *c, int j, double r, double h)
     return h * (2.0 * r + h) / (l0 + l1);
 }
 
-/* nu-nu moments (Eq. 3.13): S_j = sum_e (rho_nu - conj(rho_nubar)),
- * M0 = dE sum_j a_j S_j, M1 = dE sum_j b_j S_j.  Sequential sums in index
- * order; the angle loop may run in parallel (each S_j is one thread's). */
-static void moments(const orc_ctx *c, const cplx *rho, const double *a, const double *b,
-                    cplx *M0, cplx *M1, cplx *Sbuf)
+/* nu-nu moments (Eq. 3.13 / 3.18): S_t = sum_e (rho_nu - conj(rho_nubar)) per
+ * trajectory, M_q = dE sum_t w_q(t) S_t.  Sequential sums in index order; the
+ * trajectory loop may run in parallel (each S_t is one thread's).  M[2], M[3]
+ * are zero without azimuth bins. */
+typedef cplx mom_t[4][NFMAX * NFMAX];
+
+static void moments(const orc_ctx *c, const cplx *rho, const geom_t *g, mom_t M, cplx *Sbuf)
 {
-    int n = c->n, m = c->m, nE = c->nE, nu = c->nu;
+    int m = c->m, nE = c->nE, nt = c->nt;
+    const int nmom = c->nphi > 1 ? 4 : 2;
 #pragma omp parallel for schedule(static)
-    for (int j = 0; j < nu; ++j) {
+    for (int t = 0; t < nt; ++t) {
         cplx S[NFMAX * NFMAX];
         for (int k = 0; k < m; ++k) S[k] = 0;
         for (int e = 0; e < nE; ++e) {
-            const cplx *rn = rho + ((size_t)(0 * nu + j) * nE + e) * m;
-            const cplx *ra = rho + ((size_t)(1 * nu + j) * nE + e) * m;
+            const cplx *rn = rho + ((size_t)(0 * nt + t) * nE + e) * m;
+            const cplx *ra = rho + ((size_t)(1 * nt + t) * nE + e) * m;
             for (int k = 0; k < m; ++k) S[k] += rn[k] - conj(ra[k]);
         }
-        memcpy(Sbuf + (size_t)j * m, S, sizeof(cplx) * m);
+        memcpy(Sbuf + (size_t)t * m, S, sizeof(cplx) * m);
     }
-    for (int k = 0; k < m; ++k) M0[k] = M1[k] = 0;
-    for (int j = 0; j < nu; ++j)
-        for (int k = 0; k < m; ++k) {
-            M0[k] += a[j] * Sbuf[(size_t)j * m + k];
-            M1[k] += b[j] * Sbuf[(size_t)j * m + k];
-        }
-    for (int k = 0; k < m; ++k) {
-        M0[k] *= c->dE;
-        M1[k] *= c->dE;
-    }
-    (void)n;
+    for (int q = 0; q < 4; ++q)
+        for (int k = 0; k < m; ++k) M[q][k] = 0;
+    for (int t = 0; t < nt; ++t)
+        for (int q = 0; q < nmom; ++q)
+            for (int k = 0; k < m; ++k) M[q][k] += g->w[q][t] * Sbuf[(size_t)t * m + k];
+    for (int q = 0; q < nmom; ++q)
+        for (int k = 0; k < m; ++k) M[q][k] *= c->dE;
+}
+
+/* G_t = mu (M0 - g1_t M1 - g2_t M2 - g3_t M3) */
+static void g_of(const orc_ctx *c, const geom_t *g, int t, double mu, mom_t M, cplx *G)
+{
+    for (int k = 0; k < c->m; ++k)
+        G[k] = mu * (M[0][k] - g->g1[t] * M[1][k] - g->g2[t] * M[2][k] - g->g3[t] * M[3][k]);
+}
+
+static int moments_finite(const orc_ctx *c, mom_t M)
+{
+    for (int q = 0; q < 4; ++q)
+        for (int k = 0; k < c->m; ++k)
+            if (!isfinite(creal(M[q][k])) || !isfinite(cimag(M[q][k]))) return 0;
+    return 1;
 }
 
 /* Hamiltonian of bin (s, j, e):  nu:    H_vac + A P_e + G_j
@@ -499,31 +537,53 @@ static int all_finite(int m, const cplx *M)
 }
 
 typedef struct {
-    double *a, *b, *g, *kap;
+    geom_t g;
     cplx *Sbuf;
 } scratch_t;
+
+static int scratch_alloc(const orc_ctx *c, scratch_t *w)
+{
+    memset(w, 0, sizeof(*w));
+    for (int q = 0; q < 4; ++q) w->g.w[q] = malloc(sizeof(double) * c->nt);
+    w->g.g1 = malloc(sizeof(double) * c->nt);
+    w->g.g2 = malloc(sizeof(double) * c->nt);
+    w->g.g3 = malloc(sizeof(double) * c->nt);
+    w->g.kap = malloc(sizeof(double) * c->nt);
+    w->Sbuf = malloc(sizeof(cplx) * c->nt * c->m);
+    return w->g.w[3] && w->g.kap && w->Sbuf ? 0 : -2;
+}
+
+static void scratch_free(scratch_t *w)
+{
+    for (int q = 0; q < 4; ++q) free(w->g.w[q]);
+    free(w->g.g1);
+    free(w->g.g2);
+    free(w->g.g3);
+    free(w->g.kap);
+    free(w->Sbuf);
+}
 
 /* d(rho)/dr = -i [H, rho] dl/dr for every bin; returns 0 if the moments were
  * not finite. */
 static int rhs(const orc_ctx *c, scratch_t *w, double r, const cplx *rho, cplx *K)
 {
-    int n = c->n, m = c->m, nE = c->nE, nu = c->nu;
+    int n = c->n, m = c->m, nE = c->nE, nt = c->nt;
     double mu;
-    geometry(c, r, w->a, w->b, w->g, w->kap, &mu);
-    cplx M0[NFMAX * NFMAX], M1[NFMAX * NFMAX];
-    moments(c, rho, w->a, w->b, M0, M1, w->Sbuf);
-    if (!all_finite(m, M0) || !all_finite(m, M1)) return 0;
+    geometry(c, r, &w->g, &mu);
+    mom_t M;
+    moments(c, rho, &w->g, M, w->Sbuf);
+    if (!moments_finite(c, M)) return 0;
     double A = matter_A(c, r);
 #pragma omp parallel for schedule(static)
     for (int b = 0; b < c->nbins; ++b) {
-        int s = b / (nu * nE), j = (b / nE) % nu, e = b % nE;
+        int s = b / (nt * nE), t = (b / nE) % nt, e = b % nE;
         cplx G[NFMAX * NFMAX], H[NFMAX * NFMAX], X[NFMAX * NFMAX], Y[NFMAX * NFMAX];
-        for (int k = 0; k < m; ++k) G[k] = mu * (M0[k] - w->g[j] * M1[k]);
+        g_of(c, &w->g, t, mu, M, G);
         hamiltonian(c, s, e, G, A, H);
         const cplx *rb = rho + (size_t)b * m;
         mat_mul(n, H, rb, X);
         mat_mul(n, rb, H, Y);
-        for (int k = 0; k < m; ++k) K[(size_t)b * m + k] = -I * (X[k] - Y[k]) * w->kap[j];
+        for (int k = 0; k < m; ++k) K[(size_t)b * m + k] = -I * (X[k] - Y[k]) * w->g.kap[t];
     }
     return 1;
 }
@@ -563,28 +623,28 @@ static int step_rk4(const orc_ctx *c, scratch_t *w, cplx *rho, double r, double 
 static int step_exph(const orc_ctx *c, scratch_t *w, const cplx *rho, double r, double h,
                      cplx *rp, cplx *out)
 {
-    int n = c->n, m = c->m, nE = c->nE, nu = c->nu;
+    int n = c->n, m = c->m, nE = c->nE, nt = c->nt;
     double mu;
-    cplx M0[NFMAX * NFMAX], M1[NFMAX * NFMAX];
-    double *dl = malloc(sizeof(double) * nu);
-    for (int j = 0; j < nu; ++j) dl[j] = path_length(c, j, r, h);
+    mom_t M;
+    double *dl = malloc(sizeof(double) * nt);
+    for (int t = 0; t < nt; ++t) dl[t] = path_length(c, t, r, h);
     for (int pass = 0; pass < 2; ++pass) {
         double rr = (pass == 0) ? r : r + h;
         const cplx *src = (pass == 0) ? rho : rp;
-        geometry(c, rr, w->a, w->b, w->g, w->kap, &mu);
-        moments(c, src, w->a, w->b, M0, M1, w->Sbuf);
-        if (!all_finite(m, M0) || !all_finite(m, M1)) {
+        geometry(c, rr, &w->g, &mu);
+        moments(c, src, &w->g, M, w->Sbuf);
+        if (!moments_finite(c, M)) {
             free(dl);
             return 0;
         }
         double A = matter_A(c, rr);
 #pragma omp parallel for schedule(static)
         for (int b = 0; b < c->nbins; ++b) {
-            int s = b / (nu * nE), j = (b / nE) % nu, e = b % nE;
+            int s = b / (nt * nE), t = (b / nE) % nt, e = b % nE;
             cplx G[NFMAX * NFMAX], H[NFMAX * NFMAX], U[NFMAX * NFMAX], X[NFMAX * NFMAX];
-            for (int k = 0; k < m; ++k) G[k] = mu * (M0[k] - w->g[j] * M1[k]);
+            g_of(c, &w->g, t, mu, M, G);
             hamiltonian(c, s, e, G, A, H);
-            expm_minus_iHt(n, H, dl[j], U);
+            expm_minus_iHt(n, H, dl[t], U);
             conjugate_by(n, U, rho + (size_t)b * m, X);
             if (pass == 0) memcpy(rp + (size_t)b * m, X, sizeof(cplx) * m);
             else
@@ -644,65 +704,91 @@ static void renormalise(int n, cplx *rho, double q0)
  *   S5  rho6 = U(H3; r, h) rho0 U^+, fine result rho_f = (rho5 + rho6) / 2;
  *       err = max over bins b and packed entries of |rho_c - rho_f| / tr rho0_b
  * Writes rho_c to out.  Returns 0 if a moment or a result was not finite. */
-static int hamiltonians_at(const orc_ctx *c, scratch_t *w, const cplx *src, double r, cplx *M0, cplx *M1,
-                           double *mu, double *A, double *g)
+static int hamiltonians_at(const orc_ctx *c, scratch_t *w, geom_t *gsave, const cplx *src, double r, mom_t M,
+                           double *mu, double *A)
 {
-    geometry(c, r, w->a, w->b, w->g, w->kap, mu);
-    moments(c, src, w->a, w->b, M0, M1, w->Sbuf);
-    memcpy(g, w->g, sizeof(double) * c->nu);
+    geometry(c, r, gsave, mu);
+    moments(c, src, gsave, M, w->Sbuf);
     *A = matter_A(c, r);
-    return all_finite(c->m, M0) && all_finite(c->m, M1);
+    return moments_finite(c, M);
 }
 
-/* rho_out[b] = U rho_in[b] U^+ for every bin, U = exp(-i H_b dl_j), H_b from
- * the moments (M0, M1) with angle factors g and scalars mu, A. */
-static void propagate_all(const orc_ctx *c, const cplx *M0, const cplx *M1, double mu, double A, const double *g,
-                          const double *dl, const cplx *rho_in, cplx *rho_out)
+/* rho_out[b] = U rho_in[b] U^+ for every bin, U = exp(-i H_b dl_t), H_b from
+ * the moments M with the geometry g and the scalars mu, A. */
+static void propagate_all(const orc_ctx *c, mom_t M, double mu, double A, const geom_t *g, const double *dl,
+                          const cplx *rho_in, cplx *rho_out)
 {
-    int n = c->n, m = c->m, nE = c->nE, nu = c->nu;
+    int n = c->n, m = c->m, nE = c->nE, nt = c->nt;
 #pragma omp parallel for schedule(static)
     for (int b = 0; b < c->nbins; ++b) {
-        int s = b / (nu * nE), j = (b / nE) % nu, e = b % nE;
+        int s = b / (nt * nE), t = (b / nE) % nt, e = b % nE;
         cplx G[NFMAX * NFMAX], H[NFMAX * NFMAX], U[NFMAX * NFMAX];
-        for (int k = 0; k < m; ++k) G[k] = mu * (M0[k] - g[j] * M1[k]);
+        g_of(c, g, t, mu, M, G);
         hamiltonian(c, s, e, G, A, H);
-        expm_minus_iHt(n, H, dl[j], U);
+        expm_minus_iHt(n, H, dl[t], U);
         conjugate_by(n, U, rho_in + (size_t)b * m, rho_out + (size_t)b * m);
     }
 }
 
 typedef struct {
     cplx *r1, *r2, *r3, *r5, *r6;
-    double *g, *dl_full, *dl_half, *dl_mid;
+    double *dl_full, *dl_half, *dl_mid;
 } adapt_buf;
+
+static int adapt_alloc(const orc_ctx *c, adapt_buf *B)
+{
+    size_t N = (size_t)c->nbins * c->m;
+    B->r1 = malloc(sizeof(cplx) * N);
+    B->r2 = malloc(sizeof(cplx) * N);
+    B->r3 = malloc(sizeof(cplx) * N);
+    B->r5 = malloc(sizeof(cplx) * N);
+    B->r6 = malloc(sizeof(cplx) * N);
+    B->dl_full = malloc(sizeof(double) * c->nt);
+    B->dl_half = malloc(sizeof(double) * c->nt);
+    B->dl_mid = malloc(sizeof(double) * c->nt);
+    return B->r6 && B->dl_mid ? 0 : -2;
+}
+
+static void adapt_free(adapt_buf *B)
+{
+    free(B->r1);
+    free(B->r2);
+    free(B->r3);
+    free(B->r5);
+    free(B->r6);
+    free(B->dl_full);
+    free(B->dl_half);
+    free(B->dl_mid);
+}
 
 static int attempt_adaptive(const orc_ctx *c, scratch_t *w, adapt_buf *B, const cplx *rho0, double r, double h,
                             cplx *out, double *err)
 {
-    int m = c->m, nu = c->nu, nE = c->nE;
+    int m = c->m, nt = c->nt;
     size_t N = (size_t)c->nbins * m;
-    cplx M0[NFMAX * NFMAX], M1[NFMAX * NFMAX];
+    mom_t M;
     double mu, A;
-    for (int j = 0; j < nu; ++j) {
-        B->dl_full[j] = path_length(c, j, r, h);
-        B->dl_half[j] = path_length(c, j, r, 0.5 * h);
-        B->dl_mid[j] = path_length(c, j, r + 0.5 * h, 0.5 * h);
+    geom_t *g = &w->g;
+    for (int t = 0; t < nt; ++t) {
+        B->dl_full[t] = path_length(c, t, r, h);
+        B->dl_half[t] = path_length(c, t, r, 0.5 * h);
+        B->dl_mid[t] = path_length(c, t, r + 0.5 * h, 0.5 * h);
     }
     /* S1 */
-    if (!hamiltonians_at(c, w, rho0, r, M0, M1, &mu, &A, B->g)) return 0;
+    if (!hamiltonians_at(c, w, g, rho0, r, M, &mu, &A)) return 0;
     /* S2 */
-    propagate_all(c, M0, M1, mu, A, B->g, B->dl_half, rho0, B->r1);
-    propagate_all(c, M0, M1, mu, A, B->g, B->dl_full, rho0, B->r2);
+    propagate_all(c, M, mu, A, g, B->dl_half, rho0, B->r1);
+    propagate_all(c, M, mu, A, g, B->dl_full, rho0, B->r2);
     /* S3: H1 from rho2 at r + h */
-    if (!hamiltonians_at(c, w, B->r2, r + h, M0, M1, &mu, &A, B->g)) return 0;
-    propagate_all(c, M0, M1, mu, A, B->g, B->dl_full, rho0, B->r3);
+    if (!hamiltonians_at(c, w, g, B->r2, r + h, M, &mu, &A)) return 0;
+    propagate_all(c, M, mu, A, g, B->dl_full, rho0, B->r3);
     for (size_t i = 0; i < N; ++i) out[i] = 0.5 * (B->r2[i] + B->r3[i]);
     /* S4: H2 from rho1 at r + h/2 */
-    if (!hamiltonians_at(c, w, B->r1, r + 0.5 * h, M0, M1, &mu, &A, B->g)) return 0;
-    propagate_all(c, M0, M1, mu, A, B->g, B->dl_mid, B->r1, B->r5);
+    if (!hamiltonians_at(c, w, g, B->r1, r + 0.5 * h, M, &mu, &A)) return 0;
+    propagate_all(c, M, mu, A, g, B->dl_mid, B->r1, B->r5);
     /* S5: H3 from rho5 at r + h */
-    if (!hamiltonians_at(c, w, B->r5, r + h, M0, M1, &mu, &A, B->g)) return 0;
-    propagate_all(c, M0, M1, mu, A, B->g, B->dl_full, rho0, B->r6);
+    if (!hamiltonians_at(c, w, g, B->r5, r + h, M, &mu, &A)) return 0;
+    propagate_all(c, M, mu, A, g, B->dl_full, rho0, B->r6);
     double e = 0.0;
     for (int b = 0; b < c->nbins; ++b) {
         double tr = 0.0;
@@ -714,7 +800,6 @@ static int attempt_adaptive(const orc_ctx *c, scratch_t *w, adapt_buf *B, const 
             if (!(d <= e)) e = d; /* a NaN difference propagates */
         }
     }
-    (void)nE;
     *err = e;
     for (size_t i = 0; i < N; ++i)
         if (!isfinite(creal(out[i])) || !isfinite(cimag(out[i]))) return 0;
@@ -755,7 +840,7 @@ int orc_init_state(const orc_params *p, double *rho_packed)
     }
     int n = c.n, m = c.m, noff = n * (n - 1) / 2;
     for (int b = 0; b < c.nbins; ++b) {
-        int s = b / (c.nu * c.nE), e = b % c.nE;
+        int s = b / (c.nt * c.nE), e = b % c.nE;
         double pe = c.phi[(s == 0 ? 0 : 1) * c.nE + e];
         double px = c.phi[(s == 0 ? 2 : 3) * c.nE + e];
         cplx M[NFMAX * NFMAX];
@@ -797,11 +882,7 @@ int orc_evolve(const orc_params *p, double *rho_packed, double r0, double h, int
     cplx *rho = malloc(sizeof(cplx) * N), *Y = malloc(sizeof(cplx) * N);
     cplx *K = malloc(sizeof(cplx) * N), *acc = malloc(sizeof(cplx) * N);
     scratch_t w;
-    w.a = malloc(sizeof(double) * c.nu);
-    w.b = malloc(sizeof(double) * c.nu);
-    w.g = malloc(sizeof(double) * c.nu);
-    w.kap = malloc(sizeof(double) * c.nu);
-    w.Sbuf = malloc(sizeof(cplx) * c.nu * c.m);
+    scratch_alloc(&c, &w);
     for (int b = 0; b < c.nbins; ++b) unpack(c.n, rho_packed + (size_t)b * c.m, rho + (size_t)b * c.m);
     double *q0 = NULL;
     if (p->renorm) {
@@ -836,11 +917,7 @@ int orc_evolve(const orc_params *p, double *rho_packed, double r0, double h, int
     free(Y);
     free(K);
     free(acc);
-    free(w.a);
-    free(w.b);
-    free(w.g);
-    free(w.kap);
-    free(w.Sbuf);
+    scratch_free(&w);
     ctx_free(&c);
     return status;
 }
@@ -884,21 +961,9 @@ int orc_evolve_adaptive(const orc_params *p, double *rho_packed, double r0, doub
     size_t N = (size_t)c.nbins * c.m;
     cplx *rho = malloc(sizeof(cplx) * N), *out = malloc(sizeof(cplx) * N);
     adapt_buf B;
-    B.r1 = malloc(sizeof(cplx) * N);
-    B.r2 = malloc(sizeof(cplx) * N);
-    B.r3 = malloc(sizeof(cplx) * N);
-    B.r5 = malloc(sizeof(cplx) * N);
-    B.r6 = malloc(sizeof(cplx) * N);
-    B.g = malloc(sizeof(double) * c.nu);
-    B.dl_full = malloc(sizeof(double) * c.nu);
-    B.dl_half = malloc(sizeof(double) * c.nu);
-    B.dl_mid = malloc(sizeof(double) * c.nu);
+    adapt_alloc(&c, &B);
     scratch_t w;
-    w.a = malloc(sizeof(double) * c.nu);
-    w.b = malloc(sizeof(double) * c.nu);
-    w.g = malloc(sizeof(double) * c.nu);
-    w.kap = malloc(sizeof(double) * c.nu);
-    w.Sbuf = malloc(sizeof(cplx) * c.nu * c.m);
+    scratch_alloc(&c, &w);
     for (int b = 0; b < c.nbins; ++b) unpack(c.n, rho_packed + (size_t)b * c.m, rho + (size_t)b * c.m);
     double r = r0, h = h0 < p->dr_max ? h0 : p->dr_max;
     int64_t acc = 0, rej = 0, it = 0;
@@ -941,20 +1006,8 @@ int orc_evolve_adaptive(const orc_params *p, double *rho_packed, double r0, doub
     if (n_rej) *n_rej = rej;
     free(rho);
     free(out);
-    free(B.r1);
-    free(B.r2);
-    free(B.r3);
-    free(B.r5);
-    free(B.r6);
-    free(B.g);
-    free(B.dl_full);
-    free(B.dl_half);
-    free(B.dl_mid);
-    free(w.a);
-    free(w.b);
-    free(w.g);
-    free(w.kap);
-    free(w.Sbuf);
+    adapt_free(&B);
+    scratch_free(&w);
     ctx_free(&c);
     return status;
 }
@@ -975,21 +1028,9 @@ int orc_attempt_adaptive(const orc_params *p, double *rho_packed, double r, doub
     size_t N = (size_t)c.nbins * c.m;
     cplx *rho = malloc(sizeof(cplx) * N), *out = malloc(sizeof(cplx) * N);
     adapt_buf B;
-    B.r1 = malloc(sizeof(cplx) * N);
-    B.r2 = malloc(sizeof(cplx) * N);
-    B.r3 = malloc(sizeof(cplx) * N);
-    B.r5 = malloc(sizeof(cplx) * N);
-    B.r6 = malloc(sizeof(cplx) * N);
-    B.g = malloc(sizeof(double) * c.nu);
-    B.dl_full = malloc(sizeof(double) * c.nu);
-    B.dl_half = malloc(sizeof(double) * c.nu);
-    B.dl_mid = malloc(sizeof(double) * c.nu);
+    adapt_alloc(&c, &B);
     scratch_t w;
-    w.a = malloc(sizeof(double) * c.nu);
-    w.b = malloc(sizeof(double) * c.nu);
-    w.g = malloc(sizeof(double) * c.nu);
-    w.kap = malloc(sizeof(double) * c.nu);
-    w.Sbuf = malloc(sizeof(cplx) * c.nu * c.m);
+    scratch_alloc(&c, &w);
     for (int b = 0; b < c.nbins; ++b) unpack(c.n, rho_packed + (size_t)b * c.m, rho + (size_t)b * c.m);
     int ok = attempt_adaptive(&c, &w, &B, rho, r, h, out, err);
     for (int b = 0; b < c.nbins; ++b) pack(c.n, out + (size_t)b * c.m, rho_packed + (size_t)b * c.m);
@@ -1001,26 +1042,16 @@ int orc_attempt_adaptive(const orc_params *p, double *rho_packed, double r, doub
         }
     free(rho);
     free(out);
-    free(B.r1);
-    free(B.r2);
-    free(B.r3);
-    free(B.r5);
-    free(B.r6);
-    free(B.g);
-    free(B.dl_full);
-    free(B.dl_half);
-    free(B.dl_mid);
-    free(w.a);
-    free(w.b);
-    free(w.g);
-    free(w.kap);
-    free(w.Sbuf);
+    adapt_free(&B);
+    scratch_free(&w);
     ctx_free(&c);
     return ok ? 0 : 1;
 }
 
 /* Moments of a packed state at radius r (packed Hermitian n*n each). */
-int orc_moments(const orc_params *p, const double *rho_packed, double r, double *M0p, double *M1p)
+/* All four moments of a packed state at radius r (Eq. 3.13 / 3.18): Mp holds
+ * M0, M1, M2, M3 packed (n*n each); M2 = M3 = 0 without azimuth bins. */
+int orc_moments_ex(const orc_params *p, const double *rho_packed, double r, double *Mp)
 {
     orc_ctx c;
     int rc = ctx_init(&c, p);
@@ -1031,22 +1062,28 @@ int orc_moments(const orc_params *p, const double *rho_packed, double r, double 
     size_t N = (size_t)c.nbins * c.m;
     cplx *rho = malloc(sizeof(cplx) * N);
     for (int b = 0; b < c.nbins; ++b) unpack(c.n, rho_packed + (size_t)b * c.m, rho + (size_t)b * c.m);
-    double *a = malloc(sizeof(double) * c.nu), *bb = malloc(sizeof(double) * c.nu);
-    double *g = malloc(sizeof(double) * c.nu), *kap = malloc(sizeof(double) * c.nu);
-    cplx *Sbuf = malloc(sizeof(cplx) * c.nu * c.m);
+    scratch_t w;
+    scratch_alloc(&c, &w);
     double mu;
-    cplx M0[NFMAX * NFMAX], M1[NFMAX * NFMAX];
-    geometry(&c, r, a, bb, g, kap, &mu);
-    moments(&c, rho, a, bb, M0, M1, Sbuf);
-    pack(c.n, M0, M0p);
-    pack(c.n, M1, M1p);
+    mom_t M;
+    geometry(&c, r, &w.g, &mu);
+    moments(&c, rho, &w.g, M, w.Sbuf);
+    for (int q = 0; q < 4; ++q) pack(c.n, M[q], Mp + (size_t)q * c.m);
     free(rho);
-    free(a);
-    free(bb);
-    free(g);
-    free(kap);
-    free(Sbuf);
+    scratch_free(&w);
     ctx_free(&c);
+    return 0;
+}
+
+/* Moments M0 and M1 of a packed state at radius r (packed Hermitian n*n each). */
+int orc_moments(const orc_params *p, const double *rho_packed, double r, double *M0p, double *M1p)
+{
+    double M[4 * NFMAX * NFMAX];
+    int rc = orc_moments_ex(p, rho_packed, r, M);
+    if (rc) return rc;
+    const int m = p->n_f * p->n_f;
+    memcpy(M0p, M, sizeof(double) * m);
+    memcpy(M1p, M + m, sizeof(double) * m);
     return 0;
 }
 

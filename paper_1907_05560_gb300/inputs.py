@@ -33,6 +33,7 @@ class Problem:
     n_E: int = 32                     # Ebins
     n_u: int = 16                     # Abins
     n_f: int = 2                      # Flvs
+    n_phi: int = 1                    # Pbins: azimuth bins of the extended bulb model (1: none)
     stepper: int = RK4
     geometry: int = BULB
     precision: int = FP64
@@ -69,7 +70,7 @@ class Problem:
 
     @property
     def n_bins(self) -> int:
-        return 2 * self.n_u * self.n_E
+        return 2 * self.n_u * self.n_phi * self.n_E
 
     def replace(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)

@@ -595,3 +595,82 @@ def test_adaptive_budget_and_status(orc):
     rho = orc.init_state(p)
     out, st, r, h, na, nr = orc.evolve_adaptive(p, rho, 50.0, 60.0, 0.1, max_iters=3)
     assert st == 2 and na + nr == 3 and 50.0 <= r < 60.0
+
+
+# ---------------------------------------------------------------- extended bulb (Eq. 3.18)
+
+def _maa(**kw):
+    base = dict(n_E=6, n_u=5, n_phi=6, n_f=2, stepper=I.EXPH, mu0=1e5, eps=1e-2, r0=50.0, r1=51.0,
+                n_steps=100, seed=9)
+    base.update(kw)
+    return I.Problem(**base)
+
+
+def _replicate_over_azimuths(rho_ma, p):
+    x = rho_ma.reshape(2, p.n_u, 1, p.n_E, -1)
+    return np.ascontiguousarray(np.broadcast_to(x, (2, p.n_u, p.n_phi, p.n_E, x.shape[-1]))).reshape(-1)
+
+
+@pytest.mark.parametrize("n_f,stepper", [(2, I.EXPH), (2, I.RK4), (3, I.EXPH)])
+def test_extended_bulb_with_symmetric_azimuths_is_the_bulb(orc, n_f, stepper):
+    """Integrating 1 - cos(gamma) over the azimuth of an azimuthally symmetric
+    state leaves the bulb model's 1 - cos(th) cos(th') (Eq. 3.18 -> 3.13): a
+    state equal in every azimuth bin evolves exactly like the bulb model, in
+    every bin, and its azimuthal moments M2, M3 vanish."""
+    kw = dict(dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.72), hierarchy=+1, mu0=1e4) if n_f == 3 else {}
+    p = _maa(n_f=n_f, stepper=stepper, **kw)
+    ma = p.replace(n_phi=1)
+    rho_ma = orc.init_state(ma)
+    rho = _replicate_over_azimuths(rho_ma, p)
+    M = orc.moments_ex(p, rho, p.r0)
+    M_ma = orc.moments_ex(ma, rho_ma, p.r0)
+    scale = np.abs(M[0]).max()
+    assert np.abs(M[2:]).max() < 1e-15 * scale
+    assert np.abs(M[:2] - M_ma[:2]).max() < 1e-14 * scale
+    out, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    out_ma, st_ma, _ = orc.evolve(ma, rho_ma, p.r0, p.h, p.n_steps)
+    assert st == 0 and st_ma == 0
+    assert np.abs(orc.unpack(out_ma, n_f) - orc.unpack(rho_ma, n_f)).max() > 1e-6  # it moved
+    want = _replicate_over_azimuths(out_ma, p)
+    assert np.abs(out - want).max() < 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n_f", [2, 3])
+def test_extended_bulb_is_azimuth_rotation_equivariant(orc, n_f):
+    """The azimuth grid is uniform, so rotating every state by one azimuth bin
+    and evolving equals evolving and then rotating (the moments M2, M3 rotate
+    with the state and G follows): an inconsistent sign or weight between the
+    cos(ph) / sin(ph) moments and their factors in G breaks it."""
+    kw = dict(dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.72), hierarchy=+1, mu0=1e4) if n_f == 3 else {}
+    p = _maa(n_f=n_f, n_phi=7, **kw)
+    rho = orc.init_state(p)
+    shape = (2, p.n_u, p.n_phi, p.n_E, n_f * n_f)
+    shift = lambda x: np.roll(x.reshape(shape), 1, axis=2).reshape(-1)
+    a, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    b, st2, _ = orc.evolve(p, shift(rho), p.r0, p.h, p.n_steps)
+    assert st == 0 and st2 == 0
+    assert np.abs(shift(a) - b).max() < 1e-12 * np.abs(a).max()
+    # and the azimuthal structure matters: the unshifted result differs
+    assert np.abs(shift(a) - a).max() > 1e-9 * np.abs(a).max()
+
+
+def test_extended_bulb_moment_weights_give_the_trajectory_direction(orc):
+    """With the difference nu - conj(nubar) carried by one trajectory (zenith u,
+    azimuth ph) only, the moment ratios are that trajectory's unit direction
+    (cos th, sin th cos ph, sin th sin ph) at radius r, with cos th from
+    Eq. 3.14 and sin^2 + cos^2 = 1 (so 1 - cos(gamma) of Eq. 3.18 is one minus
+    a dot product of unit vectors)."""
+    p = _maa(n_phi=8, eps=0.0)
+    r = 23.0
+    rho = np.zeros(orc.state_size(p)).reshape(2, p.n_u, p.n_phi, p.n_E, 4)
+    j, k = 3, 5
+    rho[0, j, k, 2, 2] = 1.0  # Re rho_12 of one nu bin
+    M = orc.moments_ex(p, rho.reshape(-1), r)
+    u = (j + 0.5) / p.n_u
+    x = p.R_nu / r
+    cth = math.sqrt(1 - x * x * u)
+    ph = (k + 0.5) * 2 * math.pi / p.n_phi
+    n_hat = np.array([cth, math.sqrt(1 - cth * cth) * math.cos(ph), math.sqrt(1 - cth * cth) * math.sin(ph)])
+    ratios = M[1:, 2] / M[0, 2]
+    assert np.abs(ratios - n_hat).max() < 1e-14
+    assert abs(np.linalg.norm(ratios) - 1.0) < 1e-14
