@@ -264,6 +264,10 @@ def run_xf(args):
         sm_max0 = 2070.0
         adaptive = run_adaptive(args, xf, I, torch, stream, flush, barrier, world, 152 * 4 * sm_max0 * 1e6 / 1e12)
 
+    azimuth = None
+    if args.precision == "fp64" and not args.skip_azimuth:
+        azimuth = run_azimuth(args, xf, I, torch, stream, flush, barrier, world, 152 * 4 * 2070.0 * 1e6 / 1e12)
+
     serving = None
     if args.precision == "fp64" and not args.skip_serve and rank == 0:
         serving = run_serving(args, xf, I, torch)
@@ -331,7 +335,7 @@ def run_xf(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "fp32_m64": fp32, "fp32_variants": variants, "batched": batched, "adaptive": adaptive, "serving": serving, "clocks": clk, "gpu_launches": args.steps,
+            "fp32_m64": fp32, "fp32_variants": variants, "batched": batched, "adaptive": adaptive, "azimuth": azimuth, "serving": serving, "clocks": clk, "gpu_launches": args.steps,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -381,6 +385,39 @@ def run_adaptive(args, xf, I, torch, stream, flush, barrier, world, peak_tflops)
             "rejected": rej, "ms_per_attempt": 1e3 * t / attempts, "r_km": st["r"], "h_next_km": st["h_next"],
             "eps0": p.eps0, "dr_max_km": p.dr_max, "precision": "FP64",
             "achieved_tflops_fp64": flops / t / 1e12, "frac_of_fp64_peak": flops / t / 1e12 / peak_tflops}
+
+
+def run_azimuth(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
+    """The extended bulb model (Eq. 3.18) at the size the paper quotes for it:
+    1000 zenith x 100 azimuth x 100 energy bins (2 x 10^7 bins), two flavors,
+    FP64, the predictor-corrector from 50 km; one bench step = 10 radial steps."""
+    p = I.Problem(n_E=100, n_u=1000, n_phi=100, n_f=2, stepper=I.EXPH, mu0=1e5, eps=1e-6, r0=50.0, r1=60.0,
+                  n_steps=1000, seed=7)
+    c = xf.Context(p, stream=stream)
+    c.init_state(p.r0)
+    chunk = 10
+    for _ in range(args.warmup):
+        c.step_async(chunk, p.h)
+    c.sync()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        c.step_async(chunk, p.h)
+        ends[k].record(stream)
+    c.sync()
+    barrier()
+    t = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) * 1e-3
+    ctas, threads, _ = c.launch_info()
+    c.close()
+    steps = chunk * args.steps
+    flops = FLOPS_PER_BIN_STEP[("exph", 2)] * p.n_bins * steps  # the two-moment count; G adds 6 flop per pair
+    return {"value": p.n_bins * steps * world / t, "unit": UNIT, "bins": p.n_bins, "n_u": p.n_u, "n_phi": p.n_phi,
+            "n_E": p.n_E, "n_f": p.n_f, "ms_per_radial_step": 1e3 * t / steps, "precision": "FP64",
+            "ctas": ctas, "threads": threads, "achieved_tflops_fp64": flops / t / 1e12,
+            "frac_of_fp64_peak": flops / t / 1e12 / peak_tflops}
 
 
 def run_batched(args, xf, I, torch, stream, flush, barrier, world):
@@ -509,6 +546,7 @@ def main():
     ap.add_argument("--batch-chunk", type=int, default=10, help="radial steps per batched bench step")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-adapt", action="store_true")
+    ap.add_argument("--skip-azimuth", action="store_true")
     ap.add_argument("--skip-tune", action="store_true", help="batched leg: keep the automatic tile size")
     ap.add_argument("--adapt-iters", type=int, default=30, help="attempts per error-controlled bench step")
     ap.add_argument("--serve-rate", type=float, default=10.0, help="sustained arrival rate, jobs/s")

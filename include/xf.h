@@ -100,7 +100,7 @@ enum xf_matter {
     XF_MATTER_EXP = 2    /* n_e = Ye nb0 exp(-(r - R)/h_ns)      (Eq. 4.4) */
 };
 
-#define XF_PARAMS_VERSION 2u
+#define XF_PARAMS_VERSION 3u
 
 /* Problem parameters.  Fill with xf_params_default, then set fields.
  * Keyword names of the paper's configuration file (App. A.3) in brackets. */
@@ -112,6 +112,11 @@ typedef struct xf_params {
     int32_t geometry;   /* enum xf_geometry */
     int32_t hierarchy;  /* +1 normal, -1 inverted: sign of dm2 (2 fl) / dm2_31 (3 fl) */
     int32_t matter;     /* enum xf_matter */
+    int32_t n_phi;      /* azimuth bins of the extended bulb model (Eq. 3.18) [Pbins]; 1 = the
+                           azimuthally symmetric bulb model (default).  > 1 needs XF_GEOM_BULB, a
+                           fixed-step stepper and XF_FP64 or XF_FP32_M64.  A problem then has
+                           2 n_u n_phi n_E bins, ordered [s][u][phi][E] in every host array */
+    int32_t reserved;   /* 0 */
     int32_t strict;     /* 1: xf_step / xf_batch_step with RK4 return XF_E_UNSTABLE, without
                            stepping, when for some angle u
                            h kappa_u sqrt(2) (max_E |H_vac| + A |P_e| + mu |M0 - gamma_u M1|)
@@ -202,6 +207,10 @@ int xf_get_state(xf_ctx *ctx, double *rho, size_t n_doubles, double *r_km, int64
  *   M0 = dE sum_{u,E} a_u (rho_nu - conj rho_nubar),  M1 = dE sum b_u (...),
  *   BULB: a_u = x^2 du / (2 cos_u), b_u = a_u cos_u. */
 int xf_moments(xf_ctx *ctx, double *M0, double *M1, size_t n_doubles);
+/* All four moments of the extended bulb model (Eq. 3.18): M[4][n_f*n_f],
+ * M0 and M1 as above, M2 and M3 the sin th cos ph / sin th sin ph weighted
+ * ones (zero with one azimuth bin).  inst = 0 for a single problem. */
+int xf_moments_ex(xf_ctx *ctx, int inst, double *M, size_t n_doubles);
 
 /* Per-bin outputs of the current state (Sec. 4.5 survival probability), each
  * array n_bins = 2 n_u n_E doubles in [s][u][E] order, any may be NULL:
@@ -310,9 +319,10 @@ int xf_checkpoint_wait(xf_ctx *ctx);
 /* Restore problem `inst` from a checkpoint (XF_E_ARG if the buffer is not a
  * checkpoint of a problem of this shape, stepper and precision). */
 int xf_checkpoint_load(xf_ctx *ctx, int inst, const void *buf, size_t bytes);
-/* Dump mode 2: out[s][u][n_f*n_f] (packed like a bin) = the mean over the
- * n_E energy bins of trajectory u's density matrices, s = 0 nu, 1 nubar;
- * summed in FP64 on the device in energy order.  n_doubles = 2 n_u n_f^2. */
+/* Dump mode 2: out[s][t][n_f*n_f] (packed like a bin) = the mean over the
+ * n_E energy bins of trajectory t's density matrices (t = u n_phi + phi),
+ * s = 0 nu, 1 nubar; summed in FP64 on the device in energy order.
+ * n_doubles = 2 n_u n_phi n_f^2. */
 int xf_angle_average(xf_ctx *ctx, int inst, double *out, size_t n_doubles);
 
 /* ---- serving: a continuous-batching job server ---------------------------

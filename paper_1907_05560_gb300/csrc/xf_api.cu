@@ -166,6 +166,13 @@ int validate(xf_ctx *c, const xf_params *p, int n_E, int n_u, int nf)
         return fail(c, XF_E_ARG, "bad precision %d", p->precision);
     if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CONST) return fail(c, XF_E_ARG, "bad geometry %d", p->geometry);
     if (p->geometry == XF_GEOM_SINGLE_ANGLE && n_u != 1) return fail(c, XF_E_ARG, "single-angle geometry needs n_u == 1");
+    if (p->n_phi < 1) return fail(c, XF_E_ARG, "n_phi must be >= 1");
+    if ((long long)n_E * n_u * p->n_phi > (long long)(INT_MAX / 16)) return fail(c, XF_E_ARG, "n_E * n_u * n_phi too large");
+    if (p->n_phi > 1) {
+        if (p->geometry != XF_GEOM_BULB) return fail(c, XF_E_ARG, "azimuth bins extend the bulb geometry only");
+        if (p->stepper == XF_EXPH_ADAPTIVE || (p->precision != XF_FP64 && p->precision != XF_FP32_M64))
+            return fail(c, XF_E_UNSUPPORTED, "azimuth bins run with fixed steps in FP64 or FP32_M64");
+    }
     if (p->hierarchy != 1 && p->hierarchy != -1) return fail(c, XF_E_ARG, "hierarchy must be +1 or -1");
     if (p->matter < XF_MATTER_NONE || p->matter > XF_MATTER_EXP) return fail(c, XF_E_ARG, "bad matter %d", p->matter);
     if (!finite_pos(p->R_nu_km)) return fail(c, XF_E_ARG, "R_nu_km must be finite and > 0");
@@ -252,7 +259,7 @@ LayoutArgs layout_args(xf_ctx *c, const InstHost &in)
 {
     LayoutArgs a;
     a.n_E = in.n_E;
-    a.n_u = in.n_u;
+    a.n_u = in.n_u * in.n_phi; // trajectories
     a.n_pairs = in.n_pairs;
     a.npad = in.npad;
     a.phi = (const double *)c->arena + in.phi_off;
@@ -326,7 +333,7 @@ int plan_launch(xf_ctx *c)
     const bool ad = c->stepper == XF_EXPH_ADAPTIVE;
     const size_t per_angle = ad ? (c->real_bytes == 8 ? xf::ASlots<double>::n * sizeof(double)
                                                       : xf::ASlots<float>::n * sizeof(float))
-                                : (c->real_bytes == 8 ? 5 * sizeof(double) : 6 * sizeof(float));
+                                : (size_t)((c->real_bytes == 8 ? 5 : 6) + (c->nmom == 4 ? 4 : 0)) * c->real_bytes;
     size_t smem = per_angle * (size_t)span;
     smem = (smem + 15) & ~size_t(15);
     if (smem > 48 * 1024 &&
@@ -394,6 +401,7 @@ Inst make_inst(const InstHost &h)
     d.matter = h.p.matter;
     d.n_pairs = h.n_pairs;
     d.npad = h.npad;
+    d.n_phi = h.n_phi;
     d.hvac_off = h.hvac_off;
     d.ref_off = h.ref_off;
     d.trace_off = h.trace_off;
@@ -749,15 +757,16 @@ int setup_problem(xf_ctx *c, int i, const xf_problem &prob)
     h = InstHost();
     h.n_E = prob.n_E;
     h.n_u = prob.n_u;
+    h.n_phi = prob.params.n_phi;
     h.nf = prob.n_flavor;
     h.S = h.nf * h.nf - 1;
-    h.n_pairs = h.n_E * h.n_u;
+    h.n_pairs = h.n_E * h.n_u * h.n_phi;
     h.npad = (h.n_pairs + 63) & ~63;
     h.n_bins = 2ll * h.n_pairs;
     h.p = prob.params;
     h.adaptive = c->stepper == XF_EXPH_ADAPTIVE;
     const int rb = c->real_bytes;
-    h.block_bytes = block_bytes(h.n_E, h.n_u, h.nf, c->precision);
+    h.block_bytes = block_bytes(h.n_E, h.n_u * h.n_phi, h.nf, c->precision);
     h.block = c->blocks.alloc(h.block_bytes);
     if (h.block < 0) return fail(c, XF_E_NOMEM, "no room for the problem in the arena");
     const long long plane = (long long)align256((size_t)2 * h.S * h.npad * rb);
@@ -798,7 +807,7 @@ int setup_problem(xf_ctx *c, int i, const xf_problem &prob)
 
 // A ctx with its control buffers and an arena of arena_bytes, no problem yet.
 int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, int nfm, const xf_allocator *alloc,
-               xf_ctx **out)
+               xf_ctx **out, int nmom = 2)
 {
     xf_ctx *c = new (std::nothrow) xf_ctx();
     if (!c) return fail(nullptr, XF_E_NOMEM, "host allocation failed");
@@ -820,8 +829,11 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "no usable CUDA device"));
     const int st = (stepper == XF_RK4) ? STEP_RK4 : STEP_EXPH;
+    c->nmom = nmom;
     if (stepper == XF_EXPH_ADAPTIVE)
         c->kern = run_kernel_adapt(nfm, c->real_bytes == 8);
+    else if (nmom == 4)
+        c->kern = run_kernel_azimuth(nfm, st, c->real_bytes == 8);
     else
         c->kern = (c->real_bytes == 8) ? run_kernel_fp64(nfm, st)
                   : precision == XF_FP32_COMP ? run_kernel_fp32(nfm, st, VAR_COMP)
@@ -840,7 +852,7 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
         if (!c->apos_d) return bail(fail(c, XF_E_NOMEM, "device allocation failed"));
     }
     c->mom_out = (double *)dev_alloc(c, sizeof(double) * NVMAX * n_slots);
-    c->mom_full = (double *)dev_alloc(c, sizeof(double) * 18);
+    c->mom_full = (double *)dev_alloc(c, sizeof(double) * 36);
     c->bar = (unsigned *)dev_alloc(c, 64);
     c->err = (int *)dev_alloc(c, 64);
     c->bad = (int *)dev_alloc(c, 64);
@@ -873,8 +885,9 @@ int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ct
     *out = nullptr;
     if (n <= 0 || !probs) return fail(nullptr, XF_E_ARG, "need at least one problem");
     if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, XF_E_ARG, "allocator callbacks missing");
-    bool has2 = false, has3 = false;
+    bool has2 = false, has3 = false, has_phi = false;
     for (int i = 0; i < n; ++i) {
+        has_phi = has_phi || probs[i].params.n_phi > 1;
         int rc = validate(nullptr, &probs[i].params, probs[i].n_E, probs[i].n_u, probs[i].n_flavor);
         if (rc) {
             if (n > 1) g_create_error = "problem " + std::to_string(i) + ": " + g_create_error;
@@ -886,10 +899,11 @@ int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ct
     }
     long long bytes = 0;
     for (int i = 0; i < n; ++i)
-        bytes += block_bytes(probs[i].n_E, probs[i].n_u, probs[i].n_flavor, probs[0].params.precision);
+        bytes += block_bytes(probs[i].n_E, probs[i].n_u * probs[i].params.n_phi, probs[i].n_flavor,
+                             probs[0].params.precision);
     xf_ctx *c = nullptr;
     int rc = create_ctx(n, bytes, probs[0].params.stepper, probs[0].params.precision,
-                        (has2 && has3) ? 0 : (has3 ? 3 : 2), alloc, &c);
+                        (has2 && has3) ? 0 : (has3 ? 3 : 2), alloc, &c, has_phi ? 4 : 2);
     if (rc) return rc;
     for (int i = 0; i < n && !rc; ++i) rc = setup_problem(c, i, probs[i]);
     if (!rc) rc = plan_launch(c);
@@ -920,6 +934,7 @@ int add_problem(xf_ctx *c, const xf_problem &prob, const double *rho, double r_k
     if (prob.params.stepper != c->stepper || prob.params.precision != c->precision)
         return fail(c, XF_E_ARG, "stepper or precision differs from the pack's");
     if (c->nfm && prob.n_flavor != c->nfm) return fail(c, XF_E_ARG, "flavor count differs from the pack's");
+    if (prob.params.n_phi > 1 && c->nmom != 4) return fail(c, XF_E_UNSUPPORTED, "azimuth bins need a 4-moment pack");
     if (!std::isfinite(dr_km) || dr_km <= 0) return fail(c, XF_E_ARG, "dr_km must be finite and > 0");
     int i = -1;
     for (int k = 0; k < (int)c->in.size(); ++k)
@@ -1119,18 +1134,20 @@ int outputs_impl(xf_ctx *c, int i, double *p_surv, double *trace, double *purity
     return XF_OK;
 }
 
-int moments_impl(xf_ctx *c, int i, double *M0, double *M1, size_t n_doubles)
+// All four moments M0..M3 of problem i's current state (FP64 sums on the
+// device), packed n_f^2 each into M[4 n_f^2]; M2 = M3 = 0 without azimuth bins.
+int moments_all(xf_ctx *c, int i, double *M)
 {
     InstHost *hp = instance(c, i);
     if (!hp) return c ? fail(c, XF_E_ARG, "bad instance index %d", i) : XF_E_ARG;
     InstHost &h = *hp;
-    if (!M0 || !M1) return fail(c, XF_E_ARG, "M0/M1 NULL");
-    if (n_doubles != (size_t)h.nf * h.nf) return fail(c, XF_E_ARG, "n_doubles must be n_f*n_f");
     if (c->pending) sync_status(c);
     if (!h.state_valid) return fail(c, XF_E_STATE, "no valid state");
     MomArgs m;
+    std::memset(&m, 0, sizeof m);
     m.n_E = h.n_E;
     m.n_u = h.n_u;
+    m.n_phi = h.n_phi;
     m.n_pairs = h.n_pairs;
     m.npad = h.npad;
     m.geometry = h.p.geometry;
@@ -1141,7 +1158,7 @@ int moments_impl(xf_ctx *c, int i, double *M0, double *M1, size_t n_doubles)
     m.r = radius(h);
     const int G = (h.n_pairs + m.chunk - 1) / m.chunk;
     if (G > c->mom_part_slots) {
-        c->mom_part = (double *)dev_alloc(c, sizeof(double) * (size_t)G * (NVMAX + 2));
+        c->mom_part = (double *)dev_alloc(c, sizeof(double) * (size_t)G * 36);
         if (!c->mom_part) return fail(c, XF_E_NOMEM, "device allocation failed");
         c->mom_part_slots = G;
     }
@@ -1151,16 +1168,27 @@ int moments_impl(xf_ctx *c, int i, double *M0, double *M1, size_t n_doubles)
         using Real = std::remove_pointer_t<decltype(realp)>;
         moments_partial_kernel<NF, Real, 256><<<G, 256, 0, c->stream>>>(
             m, (const Real *)c->arena + h.off[h.cur], (const double *)c->arena + h.trace_off, c->mom_part);
-        moments_final_kernel<NF><<<1, 32, 0, c->stream>>>(c->mom_part, G, dE, c->mom_full, c->mom_full + NF * NF);
+        moments_final_kernel<NF><<<1, 32, 0, c->stream>>>(c->mom_part, G, dE, c->mom_full);
         return (int)cudaGetLastError();
     });
     if (rc) return cuda_fail(c, (cudaError_t)rc, "moments kernel");
-    double host[18];
-    XF_CUDA(c, cudaMemcpyAsync(host, c->mom_full, sizeof(double) * 2 * n_doubles, cudaMemcpyDeviceToHost, c->stream),
+    XF_CUDA(c, cudaMemcpyAsync(M, c->mom_full, sizeof(double) * 4 * h.nf * h.nf, cudaMemcpyDeviceToHost, c->stream),
             "copy moments");
     XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
-    std::memcpy(M0, host, sizeof(double) * n_doubles);
-    std::memcpy(M1, host + n_doubles, sizeof(double) * n_doubles);
+    return XF_OK;
+}
+
+int moments_impl(xf_ctx *c, int i, double *M0, double *M1, size_t n_doubles)
+{
+    InstHost *hp = instance(c, i);
+    if (!hp) return c ? fail(c, XF_E_ARG, "bad instance index %d", i) : XF_E_ARG;
+    if (!M0 || !M1) return fail(c, XF_E_ARG, "M0/M1 NULL");
+    if (n_doubles != (size_t)hp->nf * hp->nf) return fail(c, XF_E_ARG, "n_doubles must be n_f*n_f");
+    double M[36];
+    int rc = moments_all(c, i, M);
+    if (rc) return rc;
+    std::memcpy(M0, M, sizeof(double) * n_doubles);
+    std::memcpy(M1, M + n_doubles, sizeof(double) * n_doubles);
     return XF_OK;
 }
 
@@ -1203,6 +1231,7 @@ void xf_params_default(xf_params *p)
     p->eps0 = 1e-6;
     p->ksi = 0.9;
     p->dr_max_km = 1.0;
+    p->n_phi = 1;
 }
 
 int xf_create(int n_E, int n_u, int n_flavor, const xf_params *p, xf_ctx **out)
@@ -1305,8 +1334,8 @@ int check_rk4_stable(xf_ctx *c, int i, double h_km)
     InstHost &h = c->in[i];
     if (!h.p.strict || c->stepper != XF_RK4) return XF_OK;
     const int nf = h.nf, m = nf * nf;
-    double M0[9], M1[9];
-    int rc = moments_impl(c, i, M0, M1, (size_t)m);
+    double M[36];
+    int rc = moments_all(c, i, M);
     if (rc) return rc;
     const double r = radius(h);
     const Inst d = make_inst(h);
@@ -1320,11 +1349,19 @@ int check_rk4_stable(xf_ctx *c, int i, double h_km)
     const bool bulb = h.p.geometry == XF_GEOM_BULB || h.p.geometry == XF_GEOM_MU_R4;
     const double x = h.p.R_nu_km / r;
     double z = 0.0;
-    for (int j = 0; j < h.n_u; ++j) {
-        const double cu = bulb ? std::sqrt(1.0 - x * x * (j + 0.5) / h.n_u) : 1.0;
+    for (int t = 0; t < h.n_u * h.n_phi; ++t) {
+        const int j = t / h.n_phi, k = t % h.n_phi;
+        const double u = (j + 0.5) / h.n_u;
+        const double cu = bulb ? std::sqrt(1.0 - x * x * u) : 1.0;
         const double gam = bulb ? cu : 0.0, kappa = bulb ? 1.0 / cu : 1.0;
+        double g2 = 0.0, g3 = 0.0;
+        if (h.n_phi > 1) {
+            const double sn = std::sqrt(x * x * u), ph = (k + 0.5) * 2.0 * 3.14159265358979323846 / h.n_phi;
+            g2 = sn * std::cos(ph);
+            g3 = sn * std::sin(ph);
+        }
         double G[9];
-        for (int k = 0; k < m; ++k) G[k] = M0[k] - gam * M1[k];
+        for (int q = 0; q < m; ++q) G[q] = M[q] - gam * M[m + q] - g2 * M[2 * m + q] - g3 * M[3 * m + q];
         z = std::max(z, h_km * kappa * std::sqrt(2.0) * (base + mu * traceless_norm(G, nf)));
     }
     if (!(z <= 2.0 * std::sqrt(2.0)))
@@ -1421,6 +1458,14 @@ int xf_batch_status(xf_ctx *c, int inst, int *status, int64_t *steps_done, doubl
     if (steps_done) *steps_done = h->steps;
     if (r_km) *r_km = radius(*h);
     return XF_OK;
+}
+
+int xf_moments_ex(xf_ctx *c, int inst, double *M, size_t n_doubles)
+{
+    InstHost *h = instance(c, inst);
+    if (!h) return c ? fail(c, XF_E_ARG, "bad instance index %d", inst) : XF_E_ARG;
+    if (!M || n_doubles != (size_t)4 * h->nf * h->nf) return fail(c, XF_E_ARG, "M must hold 4 n_f^2 doubles");
+    return moments_all(c, inst, M);
 }
 
 int xf_evolve(xf_ctx *c, double r_end_km, int64_t max_iters, double dr0_km)

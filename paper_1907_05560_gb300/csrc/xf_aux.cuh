@@ -177,40 +177,53 @@ __global__ void outputs_kernel(LayoutArgs a, const Real *state, const double *tr
 // a- and b-weights; a single CTA then sums the partials in order and writes
 // the packed Hermitian M0, M1 (trace restored on the diagonal).
 struct MomArgs {
-    int n_E, n_u, n_pairs, npad, geometry, chunk;
+    int n_E, n_u, n_phi, n_pairs, npad, geometry, chunk, pad_;
     double R, du, dE, r;
 };
 
-__device__ __forceinline__ void mom_weights(const MomArgs &m, int j, double *wa, double *wb)
+// Weights of trajectory t = j n_phi + k for the moments M0..M3 at radius m.r
+// (Eq. 3.13-3.15 and, with azimuth bins, Eq. 3.18: each bin carries 1/n_phi
+// of its zenith bin's weight, M2 / M3 weighted by sin th' cos / sin ph').
+__device__ __forceinline__ void mom_weights(const MomArgs &m, int t, double *w)
 {
-    *wa = m.du;
-    *wb = 0.0;
+    const int j = t / m.n_phi, k = t - j * m.n_phi;
+    w[0] = m.du;
+    w[1] = w[2] = w[3] = 0.0;
     if (m.geometry == 0 || m.geometry == 1) {
-        double x = m.R / m.r, x2 = x * x;
-        double c = sqrt(1.0 - x2 * ((j + 0.5) * m.du));
+        double x = m.R / m.r, x2 = x * x, u = (j + 0.5) * m.du;
+        double c = sqrt(1.0 - x2 * u);
         if (m.geometry == 0) {
-            *wa = x2 * m.du / (2.0 * c);
-            *wb = *wa * c;
+            double a = x2 * m.du / (2.0 * c);
+            w[0] = a / m.n_phi;
+            w[1] = a * c / m.n_phi;
+            if (m.n_phi > 1) {
+                double sn = sqrt(x2 * u), sp, cp;
+                sincos((k + 0.5) * 2.0 * 3.14159265358979323846 / m.n_phi, &sp, &cp);
+                w[2] = a * sn * cp / m.n_phi;
+                w[3] = a * sn * sp / m.n_phi;
+            }
         } else {
-            *wb = m.du * c;
+            w[1] = m.du * c;
         }
     }
 }
 
+// FP64 sums of the four moments over chunks of pairs: per component the
+// traceless parts (4 S values) and the trace parts (4 values).
 template <int NF, typename Real, int NT>
 __global__ void __launch_bounds__(NT) moments_partial_kernel(MomArgs m, const Real *state,
                                                              const double *trace, double *part)
 {
-    constexpr int S = Comp<NF>::S, NV = 2 * S + 2;
+    constexpr int S = Comp<NF>::S, NV = 4 * S + 4;
     __shared__ double s_w[NT / 32][NV];
     double acc[NV];
 #pragma unroll
     for (int c = 0; c < NV; ++c) acc[c] = 0.0;
     const int p0 = blockIdx.x * m.chunk, p1 = min(p0 + m.chunk, m.n_pairs);
     for (int p = p0 + threadIdx.x; p < p1; p += NT) {
-        const int j = p / m.n_E;
-        double wa, wb;
-        mom_weights(m, j, &wa, &wb);
+        const int t = p / m.n_E;
+        double w[4];
+        mom_weights(m, t, w);
         Real tn[S], tb[S], d[S];
 #pragma unroll
         for (int c = 0; c < S; ++c) {
@@ -218,14 +231,13 @@ __global__ void __launch_bounds__(NT) moments_partial_kernel(MomArgs m, const Re
             tb[c] = state[(size_t)(c * 2 + 1) * m.npad + p];
         }
         nu_minus_conj_nubar<NF, Real>(tn, tb, d);
-#pragma unroll
-        for (int c = 0; c < S; ++c) {
-            acc[c] += wa * (double)d[c];
-            acc[S + c] += wb * (double)d[c];
-        }
         const double dtr = trace[p] - trace[(size_t)m.npad + p];
-        acc[2 * S] += wa * dtr;
-        acc[2 * S + 1] += wb * dtr;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int c = 0; c < S; ++c) acc[q * S + c] += w[q] * (double)d[c];
+            acc[4 * S + q] += w[q] * dtr;
+        }
     }
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
@@ -242,19 +254,20 @@ __global__ void __launch_bounds__(NT) moments_partial_kernel(MomArgs m, const Re
     }
 }
 
+// Sum the chunk partials in order; M[q] (q = 0..3) packed like a bin, times dE.
 template <int NF>
-__global__ void moments_final_kernel(const double *part, int G, double dE, double *M0, double *M1)
+__global__ void moments_final_kernel(const double *part, int G, double dE, double *M)
 {
-    constexpr int S = Comp<NF>::S, NV = 2 * S + 2, M = NF * NF;
+    constexpr int S = Comp<NF>::S, NV = 4 * S + 4, MM = NF * NF;
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double tot[NV];
     for (int c = 0; c < NV; ++c) tot[c] = 0.0;
     for (int g = 0; g < G; ++g)
         for (int c = 0; c < NV; ++c) tot[c] += part[(size_t)g * NV + c];
-    for (int w = 0; w < 2; ++w) {
-        const double *t = tot + w * S;
-        const double tau = tot[2 * S + w] / NF * dE;
-        double *x = (w == 0) ? M0 : M1;
+    for (int q = 0; q < 4; ++q) {
+        const double *t = tot + q * S;
+        const double tau = tot[4 * S + q] / NF * dE;
+        double *x = M + q * MM;
         if constexpr (NF == 2) {
             x[0] = tau + t[0] * dE;
             x[1] = tau - t[0] * dE;
@@ -266,14 +279,13 @@ __global__ void moments_final_kernel(const double *part, int G, double dE, doubl
             x[2] = tau - (t[0] + t[1]) * dE;
             for (int c = 0; c < 6; ++c) x[3 + c] = t[2 + c] * dE;
         }
-        (void)M;
     }
 }
 
 // Dump mode 2 (Sec. 4.2.4): the flavor state of each trajectory averaged over
-// its energy bins.  One block per (s, u); threads stride the energies, sum
-// the packed entries in FP64, then the block adds the threads' sums in a
-// fixed order.  out[(s n_u + j) NF^2 + c].
+// its energy bins.  One block per (s, trajectory); threads stride the
+// energies, sum the packed entries in FP64, then the block adds the threads'
+// sums in a fixed order.  out[(s n_traj + t) NF^2 + c] (a.n_u = trajectories).
 template <int NF, typename Real, int NT>
 __global__ void __launch_bounds__(NT) angle_average_kernel(LayoutArgs a, const Real *state, const double *trace,
                                                            double *out)

@@ -263,13 +263,14 @@ int xf_angle_average(xf_ctx *c, int inst, double *out, size_t n_doubles)
     int rc = prepare(c, inst, &h, &L);
     if (rc) return rc;
     if (!h->state_valid) return fail(c, XF_E_STATE, "no valid state");
-    const size_t need = (size_t)2 * h->n_u * h->nf * h->nf;
+    const size_t n_traj = (size_t)h->n_u * h->n_phi;
+    const size_t need = 2 * n_traj * h->nf * h->nf;
     if (n_doubles != need) return fail(c, XF_E_ARG, "n_doubles %zu != %zu", n_doubles, need);
     xf::LayoutArgs la = layout_args(c, *h);
     rc = dispatch_layout(c, *h, [&](auto nfc, auto *realp) {
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
-        xf::angle_average_kernel<NF, Real, 128><<<2 * h->n_u, 128, 0, c->stream>>>(
+        xf::angle_average_kernel<NF, Real, 128><<<(unsigned)(2 * n_traj), 128, 0, c->stream>>>(
             la, (const Real *)c->arena + h->off[h->cur], (const double *)c->arena + h->trace_off, c->staging);
         return (int)cudaGetLastError();
     });

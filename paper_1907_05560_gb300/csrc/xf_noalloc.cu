@@ -261,6 +261,7 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
     d.matter = p->matter;
     d.n_pairs = n_pairs;
     d.npad = npad;
+    d.n_phi = 1;
     d.off[0] = rho0 - (Real *)base;
     d.off[1] = rho1 - (Real *)base;
     d.off[2] = aux - (Real *)base;
@@ -357,6 +358,7 @@ extern "C" int xf_step_noalloc(int n_E, int n_u, int n_flavor, const xf_params *
     if ((long long)n_E * n_u > (long long)(INT_MAX / 16)) return noalloc_fail(XF_E_ARG, "n_E * n_u too large");
     if (p->stepper == XF_EXPH_ADAPTIVE)
         return noalloc_fail(XF_E_UNSUPPORTED, "the error-controlled step is not built for this entry point");
+    if (p->n_phi != 1) return noalloc_fail(XF_E_UNSUPPORTED, "azimuth bins are not built for this entry point");
     if (p->stepper != XF_RK4 && p->stepper != XF_EXPH) return noalloc_fail(XF_E_ARG, "bad stepper");
     if (p->precision < XF_FP64 || p->precision > XF_FP32_M64_RENORM) return noalloc_fail(XF_E_ARG, "bad precision");
     if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CONST) return noalloc_fail(XF_E_ARG, "bad geometry");

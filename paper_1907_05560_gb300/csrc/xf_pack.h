@@ -80,7 +80,7 @@ class Arena {
 // Host record of one problem of a pack.
 struct InstHost {
     bool active = false;              // slot holds a problem
-    int n_E = 0, n_u = 0, nf = 0, S = 0, n_pairs = 0, npad = 0;
+    int n_E = 0, n_u = 0, n_phi = 1, nf = 0, S = 0, n_pairs = 0, npad = 0; // pairs = n_u n_phi n_E
     long long n_bins = 0;
     xf_params p{};
     std::vector<double> E, phi, hvac; // tables: E[n_E], phi[4][n_E], hvac[n_E][S]
@@ -111,6 +111,7 @@ struct InstHost {
 struct xf_ctx {
     std::vector<xfp::InstHost> in;
     int real_bytes = 8, precision = XF_FP64, stepper = XF_RK4, nfm = 2;
+    int nmom = 2; // moments per stage: 2, or 4 when a problem has azimuth bins (extended bulb model)
     cudaStream_t stream = nullptr;
     xf_allocator alloc{};
     bool has_alloc = false;
@@ -181,6 +182,7 @@ int init_state_impl(xf_ctx *c, int i, double r_km);
 int get_state_impl(xf_ctx *c, int i, double *rho, size_t n_doubles, double *r_km, int64_t *steps_done);
 void destroy_pack(xf_ctx *c);
 int moments_impl(xf_ctx *c, int i, double *M0, double *M1, size_t n_doubles);
+int moments_all(xf_ctx *c, int i, double *M);
 InstHost *instance(xf_ctx *c, int i);
 xf::LayoutArgs layout_args(xf_ctx *c, const InstHost &in);
 int elementwise_grid(xf_ctx *c, const InstHost &in);

@@ -38,7 +38,7 @@ enum { ERR_NONFINITE = 1, ERR_BARRIER = 2 };
 // FP32 (TwoSum) up to the warp; plain with the per-step restoration of each
 // bin's tr(rho0^2) (|P|^2 / 2 in two flavors) to its initial value
 enum { VAR_PLAIN = 0, VAR_COMP = 1, VAR_RENORM = 2 };
-constexpr int NVMAX = 16; // 2 (n_f^2 - 1) for three flavors
+constexpr int NVMAX = 32; // 4 moments x (n_f^2 - 1) for three flavors (extended bulb model)
 
 // One problem of a pack.  Its three state buffers (the two ping-pong copies
 // of rho and the auxiliary stage buffer) are component-major planes at Real
@@ -46,7 +46,7 @@ constexpr int NVMAX = 16; // 2 (n_f^2 - 1) for three flavors
 // off[b] + (c * 2 + s) * npad + p.  Its vacuum table is at Real offset hvac_off.
 struct Inst {
     int n_E, n_u, nf, geometry;
-    int matter, n_pairs, npad, pad0_;
+    int matter, n_pairs, npad, n_phi; // n_phi: azimuth bins (1: the bulb model); pairs = n_u n_phi n_E
     long long off[3], hvac_off;
     long long ref_off;      // Real: per-bin tr(rho0^2) of the initial state (renormalising variant)
     long long trace_off;    // double: trace per bin [2][npad]
@@ -204,37 +204,63 @@ __device__ __forceinline__ StepLen<float> load_dl(const float *tb, int smax, int
     return {tb[4 * smax + q], tb[5 * smax + q]};
 }
 
-// Angle factor gamma of G = mu (M0 - gamma M1) and kappa = dl/dr of
-// trajectory j at radius r.
-__device__ __forceinline__ void gamma_kappa(const Inst &a, int j, double r, double *g, double *k)
+// Trajectory t = j n_phi + k: zenith bin j, azimuth bin k (n_phi = 1: the
+// bulb model's trajectory j).
+
+// Angle factor gamma of G = mu (M0 - gamma M1 - ...) and kappa = dl/dr of
+// trajectory t at radius r.
+__device__ __forceinline__ void gamma_kappa(const Inst &a, int t, double r, double *g, double *k)
 {
     *g = 0.0;
     *k = 1.0;
     if (a.geometry == GEOM_BULB || a.geometry == GEOM_MU_R4) {
-        double c = cos_u(a, j, r);
+        double c = cos_u(a, t / a.n_phi, r);
         *g = c;
         *k = 1.0 / c;
     }
 }
-// Weights of the nu-nu sums at radius r (Eq. 3.13-3.15).
-__device__ __forceinline__ void nu_weights(const Inst &a, int j, double r, double *wa, double *wb)
+// Weights of the nu-nu sums M0, M1 at radius r (Eq. 3.13-3.15; with azimuth
+// bins each carries 1/n_phi of its zenith bin's weight).
+__device__ __forceinline__ void nu_weights(const Inst &a, int t, double r, double *wa, double *wb)
 {
+    const int j = t / a.n_phi;
     *wa = a.du;
     *wb = 0.0;
     if (a.geometry == GEOM_BULB) {
         double x = a.R / r, x2 = x * x;
         double c = sqrt(1.0 - x2 * ((j + 0.5) * a.du));
-        *wa = x2 * a.du / (2.0 * c);
-        *wb = *wa * c;
+        double w = x2 * a.du / (2.0 * c);
+        *wa = w / a.n_phi;
+        *wb = w * c / a.n_phi;
     } else if (a.geometry == GEOM_MU_R4) {
         *wb = a.du * cos_u(a, j, r);
     }
 }
-// Exact path length from r to r + h along trajectory j (Eq. 3.3, l = r cos):
+// Extended bulb model (Eq. 3.18): with cos(gamma) = cos th cos th'
+// + sin th sin th' cos(ph - ph'), the azimuthal moments M2, M3 carry the
+// weights w sin th' (cos ph', sin ph') / n_phi and enter G with the factors
+// sin th (cos ph, sin ph); sin th = x sqrt(u), azimuth midpoints
+// ph_k = (k + 1/2) 2 pi / n_phi.
+__device__ __forceinline__ void azimuth_terms(const Inst &a, int t, double r, double *g2, double *g3, double *wc,
+                                              double *wd)
+{
+    const int j = t / a.n_phi, k = t - j * a.n_phi;
+    double x = a.R / r, x2 = x * x, u = (j + 0.5) * a.du;
+    double c = sqrt(1.0 - x2 * u), sn = sqrt(x2 * u);
+    double sp, cp;
+    sincos((k + 0.5) * 2.0 * 3.14159265358979323846 / a.n_phi, &sp, &cp);
+    double w = x2 * a.du / (2.0 * c);
+    *g2 = sn * cp;
+    *g3 = sn * sp;
+    *wc = w * sn * cp / a.n_phi;
+    *wd = w * sn * sp / a.n_phi;
+}
+// Exact path length from r to r + h along trajectory t (Eq. 3.3, l = r cos):
 // l(r+h) - l(r) = h (2r + h) / (l(r) + l(r+h)), free of cancellation.
-__device__ __forceinline__ double path_length(const Inst &a, int j, double r, double h)
+__device__ __forceinline__ double path_length(const Inst &a, int t, double r, double h)
 {
     if (a.geometry == GEOM_BULB || a.geometry == GEOM_MU_R4) {
+        const int j = t / a.n_phi;
         double l0 = r * cos_u(a, j, r), l1 = (r + h) * cos_u(a, j, r + h);
         return h * (2.0 * r + h) / (l0 + l1);
     }
@@ -265,6 +291,22 @@ template <typename Real>
 __device__ inline void build_dl_table(const Inst &a, Real *tb, int smax, int j_lo, int span, double r, double h)
 {
     for (int q = threadIdx.x; q < span; q += blockDim.x) store_dl(tb, smax, q, path_length(a, j_lo + q, r, h));
+}
+// Extended bulb model: slots base + 0, 1 = the G factors of M2, M3 at r_rhs;
+// base + 2, 3 = the weights of M2, M3 at r_out.
+template <typename Real>
+__device__ inline void build_azimuth_table(const Inst &a, Real *tb, int smax, int base, int j_lo, int span,
+                                           double r_rhs, double r_out)
+{
+    for (int q = threadIdx.x; q < span; q += blockDim.x) {
+        double g2, g3, wc, wd;
+        azimuth_terms(a, j_lo + q, r_rhs, &g2, &g3, &wc, &wd);
+        tb[(base + 0) * smax + q] = (Real)g2;
+        tb[(base + 1) * smax + q] = (Real)g3;
+        if (r_out != r_rhs) azimuth_terms(a, j_lo + q, r_out, &g2, &g3, &wc, &wd);
+        tb[(base + 2) * smax + q] = (Real)wc;
+        tb[(base + 3) * smax + q] = (Real)wd;
+    }
 }
 
 // Shared per-CTA scratch of the kernel.
@@ -394,6 +436,23 @@ __device__ __forceinline__ void accum(const Real *tn, const Real *tb, Acc wa, Ac
     }
 }
 
+// The extended bulb model's four weighted sums (M0..M3).
+template <int NF, typename Real, typename Acc>
+__device__ __forceinline__ void accum4(const Real *tn, const Real *tb, Acc wa, Acc wb, Acc wc, Acc wd, Acc *m)
+{
+    constexpr int S = Comp<NF>::S;
+    Real d[S];
+    nu_minus_conj_nubar<NF, Real>(tn, tb, d);
+#pragma unroll
+    for (int c = 0; c < S; ++c) {
+        Acc dc = (Acc)d[c];
+        m[c] += wa * dc;
+        m[S + c] += wb * dc;
+        m[2 * S + c] += wc * dc;
+        m[3 * S + c] += wd * dc;
+    }
+}
+
 // As accum, with each running sum's rounding error carried in mc (TwoSum).
 template <int NF, typename Real, typename Acc>
 __device__ __forceinline__ void accum_comp(const Real *tn, const Real *tb, Acc wa, Acc wb, Acc *m, Acc *mc)
@@ -423,11 +482,12 @@ struct TileView {
 };
 
 // One stage of one tile: update every pair, accumulate and reduce the sums.
-template <int NF, int STEP, typename Real, int NT, int VAR>
+template <int NF, int STEP, typename Real, int NT, int VAR, int NMOM>
 __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int st, const Real *tb, Shared &sh,
                                            double *part_out)
 {
-    constexpr int S = Comp<NF>::S, NV = 2 * S;
+    static_assert(NMOM == 2 || (NMOM == 4 && VAR == VAR_PLAIN), "azimuth moments: plain arithmetic only");
+    constexpr int S = Comp<NF>::S, NV = NMOM * S, AB = TabSlots<Real>::n;
     using Acc = Real; // warp-level accumulation precision
     constexpr int NC = (VAR == VAR_COMP) ? NV : 1;
     Acc mc[NC];
@@ -437,12 +497,11 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
     const double h = v.h;
     const double mu = sh.mu;
     const Real A = (Real)sh.A;
-    Real M0[S], M1[S];
+    Real Mq[NMOM][S];
 #pragma unroll
-    for (int c = 0; c < S; ++c) {
-        M0[c] = (Real)(mu * sh.M[c]);
-        M1[c] = (Real)(mu * sh.M[S + c]);
-    }
+    for (int k = 0; k < NMOM; ++k)
+#pragma unroll
+        for (int c = 0; c < S; ++c) Mq[k][c] = (Real)(mu * sh.M[k * S + c]);
     Acc m[NV];
 #pragma unroll
     for (int c = 0; c < NV; ++c) m[c] = Acc(0);
@@ -453,8 +512,13 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
         Real g[S], hv[S], hn[S], hb[S];
 #pragma unroll
         for (int c = 0; c < S; ++c) {
-            g[c] = M0[c] - gam * M1[c];
+            g[c] = Mq[0][c] - gam * Mq[1][c];
             hv[c] = v.hvac[(size_t)e * S + c];
+        }
+        if constexpr (NMOM == 4) {
+            const Real g2 = tb[AB * smax + q], g3 = tb[(AB + 1) * smax + q];
+#pragma unroll
+            for (int c = 0; c < S; ++c) g[c] = g[c] - g2 * Mq[2][c] - g3 * Mq[3][c];
         }
         hamiltonians<NF, Real>(hv, A, g, hn, hb);
         Real on[S], ob[S]; // stage outputs (nu, nubar)
@@ -518,7 +582,11 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
                 }
             }
         }
-        if constexpr (VAR == VAR_COMP) accum_comp<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], m, mc);
+        if constexpr (NMOM == 4)
+            accum4<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], tb[(AB + 2) * smax + q],
+                                  tb[(AB + 3) * smax + q], m);
+        else if constexpr (VAR == VAR_COMP)
+            accum_comp<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], m, mc);
         else accum<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], m);
     }
     if constexpr (VAR == VAR_COMP) cta_partial_comp<NV, NT, Acc>(m, mc, sh, part_out);
@@ -526,11 +594,11 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
 }
 
 // Prologue for one tile: weighted sums of the input state.
-template <int NF, typename Real, int NT, int VAR, typename SH>
+template <int NF, typename Real, int NT, int VAR, typename SH, int NMOM = 2>
 __device__ __forceinline__ void prologue_tile(const TileView<Real> v, int smax, const Real *tb, SH &sh,
                                               double *part_out)
 {
-    constexpr int S = Comp<NF>::S, NV = 2 * S;
+    constexpr int S = Comp<NF>::S, NV = NMOM * S, AB = TabSlots<Real>::n;
     using Acc = Real;
     constexpr int NC = (VAR == VAR_COMP) ? NV : 1;
     Acc m[NV], mc[NC];
@@ -543,7 +611,11 @@ __device__ __forceinline__ void prologue_tile(const TileView<Real> v, int smax, 
         Real tn[S], tb_[S];
         load_state<Real, S>(v.cur, v.npad, 0, p, tn);
         load_state<Real, S>(v.cur, v.npad, 1, p, tb_);
-        if constexpr (VAR == VAR_COMP) accum_comp<NF, Real, Acc>(tn, tb_, tb[2 * smax + q], tb[3 * smax + q], m, mc);
+        if constexpr (NMOM == 4)
+            accum4<NF, Real, Acc>(tn, tb_, tb[2 * smax + q], tb[3 * smax + q], tb[(AB + 2) * smax + q],
+                                  tb[(AB + 3) * smax + q], m);
+        else if constexpr (VAR == VAR_COMP)
+            accum_comp<NF, Real, Acc>(tn, tb_, tb[2 * smax + q], tb[3 * smax + q], m, mc);
         else accum<NF, Real, Acc>(tn, tb_, tb[2 * smax + q], tb[3 * smax + q], m);
     }
     if constexpr (VAR == VAR_COMP) cta_partial_comp<NV, NT, Acc>(m, mc, sh, part_out);
@@ -636,7 +708,9 @@ __host__ __device__ constexpr int min_blocks(int nt, int real_bytes)
 
 // NFM: 2 or 3 (every instance has that many flavors) or 0 (mixed pack);
 // VAR: VAR_PLAIN, VAR_COMP or VAR_RENORM.
-template <int NFM, int STEP, typename Real, int NT, int VAR>
+// NMOM: 2 moments (the bulb model) or 4 (the extended bulb model, Eq. 3.18;
+// its problems may also have a single azimuth bin).
+template <int NFM, int STEP, typename Real, int NT, int VAR, int NMOM = 2>
 __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real))) xf_run_kernel(RunArgs a)
 {
     extern __shared__ double s_dyn[];
@@ -661,13 +735,15 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real))) xf_run_kerne
         const TileView<Real> v = make_view<Real>(a, in, ps, tl, 0);
         const int span = (v.p1 - 1) / in.n_E - v.j_lo + 1;
         __syncthreads();
-        build_weight_table(in, s_tab, smax, v.j_lo, span, in.r0 + (double)ps.k0 * in.h);
+        const double r_in = in.r0 + (double)ps.k0 * in.h;
+        build_weight_table(in, s_tab, smax, v.j_lo, span, r_in);
+        if constexpr (NMOM == 4) build_azimuth_table(in, s_tab, smax, TabSlots<Real>::n, v.j_lo, span, r_in, r_in);
         __syncthreads();
         double *out = a.partials + (size_t)t * NVMAX;
         if (nf == 2) {
-            if constexpr (NFM != 3) prologue_tile<2, Real, NT, VAR>(v, smax, s_tab, sh, out);
+            if constexpr (NFM != 3) prologue_tile<2, Real, NT, VAR, Shared, NMOM>(v, smax, s_tab, sh, out);
         } else {
-            if constexpr (NFM != 2) prologue_tile<3, Real, NT, VAR>(v, smax, s_tab, sh, out);
+            if constexpr (NFM != 2) prologue_tile<3, Real, NT, VAR, Shared, NMOM>(v, smax, s_tab, sh, out);
         }
     }
     if (!grid_barrier(a, ++nbar, &sh.flag)) return;
@@ -685,7 +761,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real))) xf_run_kerne
                 const InstPos ps = a.pos[tl.inst];
                 const long long n_i = launch_steps(a, ps);
                 if (n_i <= 0 || k > n_i) continue;
-                const int nf = NFM ? NFM : in.nf, nv = 2 * (nf * nf - 1);
+                const int nf = NFM ? NFM : in.nf, nv = NMOM * (nf * nf - 1);
                 if (k == n_i) { // the instance's last step of this launch just completed
                     if (st == 0 && t == in.tile_begin) finish_instance<NT>(a, in, tl.inst, n_i, part_in, nv, sh);
                     continue;
@@ -727,15 +803,17 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real))) xf_run_kerne
                 // the step's path lengths serve both stages; a CTA holding several
                 // tiles rebuilds them for every tile
                 if (STEP == STEP_EXPH) build_dl_table(in, s_tab, smax, v.j_lo, span, r, h);
+                if constexpr (NMOM == 4)
+                    build_azimuth_table(in, s_tab, smax, TabSlots<Real>::n, v.j_lo, span, r_rhs, r_out);
                 if (threadIdx.x == 0) {
                     sh.mu = mu_eff(in, r_rhs);
                     sh.A = matter_A(in, r_rhs);
                 }
                 __syncthreads();
                 if (nf == 2) {
-                    if constexpr (NFM != 3) stage_tile<2, STEP, Real, NT, VAR>(v, smax, st, s_tab, sh, out);
+                    if constexpr (NFM != 3) stage_tile<2, STEP, Real, NT, VAR, NMOM>(v, smax, st, s_tab, sh, out);
                 } else {
-                    if constexpr (NFM != 2) stage_tile<3, STEP, Real, NT, VAR>(v, smax, st, s_tab, sh, out);
+                    if constexpr (NFM != 2) stage_tile<3, STEP, Real, NT, VAR, NMOM>(v, smax, st, s_tab, sh, out);
                 }
             }
             if (!grid_barrier(a, ++nbar, &sh.flag)) return;
@@ -750,7 +828,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real))) xf_run_kerne
         const long long n_i = launch_steps(a, a.pos[tl.inst]);
         if (n_i != a.n_steps || n_i <= 0) continue;
         const int nf = NFM ? NFM : in.nf;
-        finish_instance<NT>(a, in, tl.inst, n_i, part_in, 2 * (nf * nf - 1), sh);
+        finish_instance<NT>(a, in, tl.inst, n_i, part_in, NMOM * (nf * nf - 1), sh);
     }
 }
 

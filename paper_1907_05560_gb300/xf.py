@@ -38,7 +38,8 @@ class XFParams(ctypes.Structure):
         ("size", ctypes.c_uint32), ("version", ctypes.c_uint32),
         ("stepper", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("geometry", ctypes.c_int32), ("hierarchy", ctypes.c_int32),
-        ("matter", ctypes.c_int32), ("strict", ctypes.c_int32),
+        ("matter", ctypes.c_int32), ("n_phi", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("strict", ctypes.c_int32),
         ("R_nu_km", ctypes.c_double), ("mu0_per_km", ctypes.c_double),
         ("E_min_MeV", ctypes.c_double), ("E_max_MeV", ctypes.c_double),
         ("dm2_eV2", ctypes.c_double * 2), ("theta", ctypes.c_double * 3),
@@ -122,6 +123,7 @@ SIGNATURES = {
     "xf_batch_outputs": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, ctypes.c_size_t]),
     "xf_batch_run_moments": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, ctypes.c_size_t]),
     "xf_evolve": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int64, ctypes.c_double]),
+    "xf_moments_ex": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.c_size_t]),
     "xf_checkpoint_bytes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     "xf_checkpoint_save": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
     "xf_checkpoint_save_async": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
@@ -179,6 +181,7 @@ def params_from(p: I.Problem) -> XFParams:
     L.xf_params_default(ctypes.byref(x))
     x.stepper, x.precision, x.geometry = p.stepper, p.precision, p.geometry
     x.hierarchy, x.matter, x.strict = p.hierarchy, p.matter, p.strict
+    x.n_phi = p.n_phi
     x.R_nu_km, x.mu0_per_km, x.E_min_MeV, x.E_max_MeV = p.R_nu, p.mu0, p.E_min, p.E_max
     x.dm2_eV2[:] = list(p.dm2)
     x.theta[:] = list(p.theta)
@@ -220,7 +223,7 @@ class Context:
         self.L = load()
         self.problem = problem
         self.n_f = problem.n_f
-        self.n_bins = 2 * problem.n_u * problem.n_E
+        self.n_bins = problem.n_bins
         self.n_doubles = self.n_bins * self.n_f * self.n_f
         prm = params_from(problem)
         h = _P()
@@ -320,7 +323,7 @@ class Context:
     def angle_average(self, i: int = 0) -> np.ndarray:
         """Dump mode 2: [2][n_u][n_f^2] energy-averaged density matrices."""
         p = self.problems[i] if hasattr(self, "problems") else self.problem
-        out = np.empty(2 * p.n_u * p.n_f * p.n_f)
+        out = np.empty(2 * p.n_u * p.n_phi * p.n_f * p.n_f)
         self._check(self.L.xf_angle_average(self.h, i, _dp(out), out.size))
         return out
 
@@ -343,6 +346,13 @@ class Context:
                                            ctypes.byref(na), ctypes.byref(nr), ctypes.byref(e)))
         return dict(status=STATUS.get(st.value, st.value), r=r.value, h_next=h.value, n_accepted=na.value,
                     n_rejected=nr.value, err=e.value)
+
+    def moments_ex(self, i: int = 0):
+        """M0..M3 [4][n_f^2] (FP64 sums of the current state)."""
+        n_f = self.problems[i].n_f if hasattr(self, "problems") else self.n_f
+        M = np.empty(4 * n_f * n_f)
+        self._check(self.L.xf_moments_ex(self.h, i, _dp(M), M.size))
+        return M.reshape(4, -1)
 
     def run_moments(self, i: int = 0):
         """Traceless M0, M1 of problem i's state as the integrator summed them."""
@@ -395,7 +405,7 @@ class Batch(Context):
             raise XFError(rc, self.L.xf_last_error(None).decode())
         self.h = h
         self.n_f = self.problem.n_f
-        self.n_bins = 2 * self.problem.n_u * self.problem.n_E
+        self.n_bins = self.problem.n_bins
         self.n_doubles = self.n_bins * self.n_f * self.n_f
         if stream is not None:
             self.set_stream(stream)
@@ -405,7 +415,7 @@ class Batch(Context):
 
     def _size(self, i):
         p = self.problems[i]
-        return 2 * p.n_u * p.n_E * p.n_f * p.n_f
+        return p.n_bins * p.n_f * p.n_f
 
     def set_state_i(self, i: int, rho: np.ndarray, r_km: float):
         rho = np.ascontiguousarray(rho, dtype=np.float64)
@@ -423,7 +433,7 @@ class Batch(Context):
 
     def outputs_i(self, i: int):
         p = self.problems[i]
-        nb = 2 * p.n_u * p.n_E
+        nb = p.n_bins
         a, b, c = np.empty(nb), np.empty(nb), np.empty(nb)
         self._check(self.L.xf_batch_outputs(self.h, i, _dp(a), _dp(b), _dp(c), nb))
         return a, b, c
@@ -499,7 +509,7 @@ class Server:
         rc = self.L.xf_submit(self.h, ctypes.byref(job), ctypes.byref(jid))
         if rc != XF_OK:
             raise XFError(rc, "xf_submit")
-        self._sizes[jid.value] = 2 * p.n_u * p.n_E * p.n_f * p.n_f
+        self._sizes[jid.value] = p.n_bins * p.n_f * p.n_f
         return jid.value
 
     def poll(self, job_id: int, want_state: bool = False):

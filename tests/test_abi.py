@@ -41,7 +41,7 @@ def test_params_default_and_status_strings(lib):
     p = xf.XFParams()
     lib.xf_params_default(ctypes.byref(p))
     assert p.size == ctypes.sizeof(xf.XFParams)
-    assert p.version == 2 and p.stepper == 0 and p.hierarchy == -1
+    assert p.version == 3 and p.stepper == 0 and p.hierarchy == -1 and p.n_phi == 1
     assert (p.eps0, p.ksi, p.dr_max_km) == (1e-6, 0.9, 1.0)
     assert list(p.T_MeV) == [2.76, 4.01, 6.26, 6.26]
     for code, name in xf.STATUS.items():
@@ -59,6 +59,8 @@ def test_params_default_and_status_strings(lib):
     (lambda p: (setattr(p, "stepper", 2), setattr(p, "ksi", 1.5)), (32, 16, 2)),
     (lambda p: (setattr(p, "stepper", 2), setattr(p, "dr_max_km", -1.0)), (32, 16, 2)),
     (lambda p: setattr(p, "hierarchy", 0), (32, 16, 2)),
+    (lambda p: setattr(p, "n_phi", 0), (32, 16, 2)),
+    (lambda p: (setattr(p, "n_phi", 4), setattr(p, "geometry", 1)), (32, 16, 2)),  # azimuths: bulb only
     (lambda p: setattr(p, "geometry", 2), (32, 16, 2)),  # single angle needs n_u == 1
     (lambda p: setattr(p, "R_nu_km", float("nan")), (32, 16, 2)),
     (lambda p: setattr(p, "E_max_MeV", 0.5), (32, 16, 2)),
