@@ -413,7 +413,9 @@ def run_azimuth(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
     ctas, threads, _ = c.launch_info()
     c.close()
     steps = chunk * args.steps
-    flops = FLOPS_PER_BIN_STEP[("exph", 2)] * p.n_bins * steps  # the two-moment count; G adds 6 flop per pair
+    # the two-moment count plus, per bin and stage, the two extra moments in G
+    # (2 x 3 FMA) and in the sums (2 x 3 FMA): +24 flop per bin-step
+    flops = (FLOPS_PER_BIN_STEP[("exph", 2)] + 24) * p.n_bins * steps
     return {"value": p.n_bins * steps * world / t, "unit": UNIT, "bins": p.n_bins, "n_u": p.n_u, "n_phi": p.n_phi,
             "n_E": p.n_E, "n_f": p.n_f, "ms_per_radial_step": 1e3 * t / steps, "precision": "FP64",
             "ctas": ctas, "threads": threads, "achieved_tflops_fp64": flops / t / 1e12,
