@@ -44,6 +44,25 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest of every rank's x: a multi-GPU job takes as long as its
+    slowest replica.  Uses the process group's own device (GPU under NCCL,
+    host under gloo)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, t_max: float) -> float:
+    """Units all replicas processed per second of the slowest replica's time."""
+    return units_per_rank * world / t_max
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -214,13 +233,9 @@ def run_xf(args):
     barrier()
     clk = clocks.stop()
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms per chunk (one launch)
-    t_sum = sum(per) * 1e-3
-    if world > 1:
-        t = torch.tensor([t_sum], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_sum = float(t.item())
+    t_sum = max_over_ranks(sum(per) * 1e-3, world)
     bin_steps = p.n_bins * chunk * args.steps
-    value = bin_steps * world / t_sum
+    value = whole_job_rate(bin_steps, world, t_sum)
 
     # FP32 variants on the same input (same workload, same launch pattern)
     def time_precision(prec):
@@ -240,7 +255,7 @@ def run_xf(args):
             e32[k].record(stream)
         c32.sync()
         barrier()
-        t32 = sum(s.elapsed_time(e) for s, e in zip(s32, e32)) * 1e-3
+        t32 = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(s32, e32)) * 1e-3, world)
         c32.close()
         return {"value": q.n_bins * chunk * args.steps * world / t32, "unit": UNIT,
                 "ms_per_step": 1e3 * t32 / args.steps}
@@ -284,12 +299,8 @@ def run_xf(args):
         ctx.get_state(host)
         e2e_times.append(time.perf_counter() - t0)
     barrier()
-    e2e_t = sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = p.n_bins * chunk * len(e2e_times) * world / e2e_t
+    e2e_t = max_over_ranks(sum(e2e_times), world)
+    e2e_value = whole_job_rate(p.n_bins * chunk * len(e2e_times), world, e2e_t)
     nbytes = ctx.n_doubles * 8
 
     # roofline of the dominant kernel (the persistent integrator, one launch per chunk)
@@ -375,7 +386,7 @@ def run_adaptive(args, xf, I, torch, stream, flush, barrier, world, peak_tflops)
         acc += st["n_accepted"]
         rej += st["n_rejected"]
     barrier()
-    t = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) * 1e-3
+    t = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) * 1e-3, world)
     st = c.adapt_status()
     c.close()
     attempts = iters * args.steps
@@ -409,7 +420,7 @@ def run_azimuth(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
         ends[k].record(stream)
     c.sync()
     barrier()
-    t = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) * 1e-3
+    t = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) * 1e-3, world)
     ctas, threads, _ = c.launch_info()
     c.close()
     steps = chunk * args.steps
@@ -446,11 +457,7 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
         b.step_all(chunk, h)
         e_ev[k].record(stream)
     barrier()
-    t = sum(s.elapsed_time(e) for s, e in zip(s_ev, e_ev)) * 1e-3
-    if world > 1:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(s_ev, e_ev)) * 1e-3, world)
     bins = sum(p.n_bins for p in probs)
     # algorithmic state bytes per bin-step (predictor-corrector): 5 x (n_f^2-1) x 4 B
     state_bytes = sum(p.n_bins * 5 * (p.n_f * p.n_f - 1) * 4 for p in probs) * chunk
