@@ -466,12 +466,34 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
     ok = sum(1 for i in range(len(probs)) if b.status_i(i)[0] == "XF_OK")
     ctas, threads, _ = b.launch_info()
     b.close()
+    # the plain FP64 path on the same inputs (same ensemble, seeds and steps)
+    fp64 = None
+    if not args.skip_batch_fp64:
+        probs64 = [q.replace(precision=I.FP64) for q in probs]
+        c = xf.Batch(probs64, stream=stream)
+        c.init_state_i(-1, probs64[0].r0)
+        c.step_all(chunk, h)  # warm-up
+        n64 = max(1, min(args.steps, 2))
+        s64 = torch.cuda.Event(enable_timing=True)
+        e64 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        s64.record(stream)
+        for _ in range(n64):
+            c.step_all(chunk, h)
+        e64.record(stream)
+        barrier()
+        t64 = max_over_ranks(s64.elapsed_time(e64) * 1e-3, world)
+        c.close()
+        fp64 = {"value": bins * chunk * n64 * world / t64, "unit": UNIT, "ms_per_step": 1e3 * t64 / n64,
+                "precision": "FP64", "steps": n64}
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     return {"value": bins * chunk * args.steps * world / t, "unit": UNIT, "problems": len(probs), "bins": bins,
             "radial_steps_per_step": chunk, "ms_per_step": 1e3 * avg, "problems_ok": ok,
             "precision": "FP32 bins, FP64 moments/radius/phase", "graph": True, "ctas": ctas, "threads": threads,
             "tile_pairs": tile if tile is not None else "rule", "autotune_ms_per_step": tile_ms,
+            "fp64_plain_same_inputs": fp64,
+            "speedup_vs_fp64_plain": (bins * chunk * args.steps * world / t / fp64["value"]) if fp64 else None,
             "achieved_gbs": state_bytes / avg / 1e9, "hbm_peak_gbs": hbm,
             "hbm_frac": (state_bytes / avg / 1e9 / hbm) if hbm else None,
             "achieved_tflops_fp32": flops / avg / 1e12}
@@ -557,6 +579,7 @@ def main():
     ap.add_argument("--skip-adapt", action="store_true")
     ap.add_argument("--skip-azimuth", action="store_true")
     ap.add_argument("--skip-tune", action="store_true", help="batched leg: keep the automatic tile size")
+    ap.add_argument("--skip-batch-fp64", action="store_true", help="batched leg: skip the FP64 run of the ensemble")
     ap.add_argument("--adapt-iters", type=int, default=30, help="attempts per error-controlled bench step")
     ap.add_argument("--serve-rate", type=float, default=10.0, help="sustained arrival rate, jobs/s")
     ap.add_argument("--serve-window", type=float, default=5.0, help="arrival window at the sustained rate, s")

@@ -240,10 +240,14 @@ __device__ __forceinline__ void nu_weights(const Inst &a, int t, double r, doubl
 // + sin th sin th' cos(ph - ph'), the azimuthal moments M2, M3 carry the
 // weights w sin th' (cos ph', sin ph') / n_phi and enter G with the factors
 // sin th (cos ph, sin ph); sin th = x sqrt(u), azimuth midpoints
-// ph_k = (k + 1/2) 2 pi / n_phi.
+// ph_k = (k + 1/2) 2 pi / n_phi; a problem with one azimuth bin has none.
 __device__ __forceinline__ void azimuth_terms(const Inst &a, int t, double r, double *g2, double *g3, double *wc,
                                               double *wd)
 {
+    if (a.n_phi == 1) { // one azimuth bin: the azimuthally symmetric bulb model, M2 = M3 = 0
+        *g2 = *g3 = *wc = *wd = 0.0;
+        return;
+    }
     const int j = t / a.n_phi, k = t - j * a.n_phi;
     double x = a.R / r, x2 = x * x, u = (j + 0.5) * a.du;
     double c = sqrt(1.0 - x2 * u), sn = sqrt(x2 * u);
