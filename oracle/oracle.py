@@ -64,6 +64,10 @@ def lib():
                                  ctypes.POINTER(ctypes.c_int64)]
         L.orc_moments.argtypes = [P, dp, ctypes.c_double, dp, dp]
         L.orc_moments_ex.argtypes = [P, dp, ctypes.c_double, dp]
+        L.orc_init_psi.argtypes = [P, dp]
+        L.orc_psi_to_rho.argtypes = [P, dp, dp]
+        L.orc_evolve_psi.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                     ctypes.POINTER(ctypes.c_int64)]
         i64p = ctypes.POINTER(ctypes.c_int64)
         L.orc_evolve_adaptive.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int64, dp, dp, i64p, i64p]
@@ -169,6 +173,40 @@ def attempt_adaptive(p, rho: np.ndarray, r: float, h: float, n_threads: int = 0)
     if rc < 0:
         raise ValueError(f"orc_attempt_adaptive: {rc}")
     return out, fine, err.value, rc
+
+
+def psi_size(p) -> int:
+    return 2 * p.n_u * getattr(p, "n_phi", 1) * p.n_E * 2 * p.n_f * p.n_f
+
+
+def init_psi(p) -> np.ndarray:
+    """Seeded wavefunctions [s][t][E][a][i] (Re, Im): one per initial flavor."""
+    o = params(p)
+    psi = np.zeros(psi_size(p))
+    rc = lib().orc_init_psi(ctypes.byref(o), _dp(psi))
+    if rc:
+        raise ValueError(f"orc_init_psi: {rc}")
+    return psi
+
+
+def psi_to_rho(p, psi: np.ndarray) -> np.ndarray:
+    o = params(p)
+    rho = np.zeros(state_size(p))
+    rc = lib().orc_psi_to_rho(ctypes.byref(o), _dp(np.ascontiguousarray(psi, dtype=np.float64)), _dp(rho))
+    if rc:
+        raise ValueError(f"orc_psi_to_rho: {rc}")
+    return rho
+
+
+def evolve_psi(p, psi: np.ndarray, r0: float, h: float, n_steps: int, n_threads: int = 0):
+    """Wavefunction form: returns (psi_out, status, steps_done)."""
+    o = params(p, n_threads)
+    out = np.ascontiguousarray(psi, dtype=np.float64).copy()
+    done = ctypes.c_int64(0)
+    rc = lib().orc_evolve_psi(ctypes.byref(o), _dp(out), r0, h, int(n_steps), ctypes.byref(done))
+    if rc < 0:
+        raise ValueError(f"orc_evolve_psi: {rc}")
+    return out, rc, done.value
 
 
 def moments_ex(p, rho: np.ndarray, r: float) -> np.ndarray:

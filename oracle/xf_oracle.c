@@ -1048,6 +1048,243 @@ int orc_attempt_adaptive(const orc_params *p, double *rho_packed, double r, doub
     return ok ? 0 : 1;
 }
 
+/* ---- wavefunction form (Eq. 3.1, 3.4, 3.9-3.11; Fig. 4.9) ----------------
+ * Each bin carries one wavefunction psi_a (n complex components) per initial
+ * flavor a, and its density matrix is rho = sum_a phi_a psi_a psi_a^+ with
+ * phi_a the number-flux weight of flavor a (nu_e, or nu_x for the others; the
+ * antineutrino spectra for nubar bins).  Each psi evolves with the same
+ * Hamiltonian as rho: psi' = exp(-i H dl) psi (Eq. 3.10-3.11).  The
+ * predictor-corrector averages wavefunctions (Sec. 4.2.3: "averaging between
+ * two flavor states"): psi_p = U(H0) psi_n, psi_{n+1} = (psi_p + U(H1) psi_n)/2,
+ * with no renormalisation.  RK4 integrates d(psi)/dr = -i H psi dl/dr.
+ * Packed layout: [s][t][E][a][i] complex, as (Re, Im) doubles, 2 n^2 per bin. */
+
+static double flux_weight(const orc_ctx *c, int s, int e, int a)
+{
+    return c->phi[(s == 0 ? (a == 0 ? 0 : 2) : (a == 0 ? 1 : 3)) * c->nE + e];
+}
+
+/* rho of every bin from the wavefunctions (psi: [b][a][i]). */
+static void psi_to_rho(const orc_ctx *c, const cplx *psi, cplx *rho)
+{
+    int n = c->n, m = c->m, nE = c->nE, nt = c->nt;
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < c->nbins; ++b) {
+        int s = b / (nt * nE), e = b % nE;
+        cplx *R = rho + (size_t)b * m;
+        for (int k = 0; k < m; ++k) R[k] = 0;
+        for (int a = 0; a < n; ++a) {
+            const cplx *v = psi + ((size_t)b * n + a) * n;
+            double w = flux_weight(c, s, e, a);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) R[i * n + j] += w * v[i] * conj(v[j]);
+        }
+    }
+}
+
+/* out_a = U in_a for every bin and flavor, U = exp(-i H_b dl_t). */
+static void propagate_psi(const orc_ctx *c, mom_t M, double mu, double A, const geom_t *g, const double *dl,
+                          const cplx *in, cplx *out)
+{
+    int n = c->n, m = c->m, nE = c->nE, nt = c->nt;
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < c->nbins; ++b) {
+        int s = b / (nt * nE), t = (b / nE) % nt, e = b % nE;
+        cplx G[NFMAX * NFMAX], H[NFMAX * NFMAX], U[NFMAX * NFMAX];
+        g_of(c, g, t, mu, M, G);
+        hamiltonian(c, s, e, G, A, H);
+        expm_minus_iHt(n, H, dl[t], U);
+        for (int a = 0; a < n; ++a) {
+            const cplx *v = in + ((size_t)b * n + a) * n;
+            cplx *o = out + ((size_t)b * n + a) * n;
+            for (int i = 0; i < n; ++i) {
+                cplx z = 0;
+                for (int j = 0; j < n; ++j) z += U[i * n + j] * v[j];
+                o[i] = z;
+            }
+        }
+    }
+    (void)m;
+}
+
+/* d(psi)/dr = -i H psi dl/dr for every bin and flavor. */
+static int rhs_psi(const orc_ctx *c, scratch_t *w, cplx *rho_scr, double r, const cplx *psi, cplx *K)
+{
+    int n = c->n, nE = c->nE, nt = c->nt;
+    double mu;
+    geometry(c, r, &w->g, &mu);
+    psi_to_rho(c, psi, rho_scr);
+    mom_t M;
+    moments(c, rho_scr, &w->g, M, w->Sbuf);
+    if (!moments_finite(c, M)) return 0;
+    double A = matter_A(c, r);
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < c->nbins; ++b) {
+        int s = b / (nt * nE), t = (b / nE) % nt, e = b % nE;
+        cplx G[NFMAX * NFMAX], H[NFMAX * NFMAX];
+        g_of(c, &w->g, t, mu, M, G);
+        hamiltonian(c, s, e, G, A, H);
+        for (int a = 0; a < n; ++a) {
+            const cplx *v = psi + ((size_t)b * n + a) * n;
+            cplx *k = K + ((size_t)b * n + a) * n;
+            for (int i = 0; i < n; ++i) {
+                cplx z = 0;
+                for (int j = 0; j < n; ++j) z += H[i * n + j] * v[j];
+                k[i] = -I * z * w->g.kap[t];
+            }
+        }
+    }
+    return 1;
+}
+
+int orc_init_psi(const orc_params *p, double *psi_packed)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, p);
+    if (rc) {
+        ctx_free(&c);
+        return rc;
+    }
+    int n = c.n, nperm = n * (n - 1);
+    /* psi_a = (e_a + eps sum_{b != a} exp(2 pi i U_ab) e_b) / sqrt(1 + (n-1) eps^2),
+     * U_ab the SplitMix64 uniform number at counter bin * n(n-1) + k, k running
+     * over (a, b != a) in row order */
+    double norm = 1.0 / sqrt(1.0 + (n - 1) * p->eps * p->eps);
+    for (int b = 0; b < c.nbins; ++b) {
+        int k = 0;
+        for (int a = 0; a < n; ++a) {
+            double *v = psi_packed + ((size_t)b * n + a) * 2 * n;
+            for (int i = 0; i < n; ++i) {
+                cplx z;
+                if (i == a) z = norm;
+                else {
+                    double ph = 2.0 * PI * uniform01(p->seed, (uint64_t)b * nperm + k);
+                    z = norm * p->eps * cexp(I * ph);
+                    ++k;
+                }
+                v[2 * i] = creal(z);
+                v[2 * i + 1] = cimag(z);
+            }
+        }
+    }
+    ctx_free(&c);
+    return 0;
+}
+
+int orc_psi_to_rho(const orc_params *p, const double *psi_packed, double *rho_packed)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, p);
+    if (rc) {
+        ctx_free(&c);
+        return rc;
+    }
+    size_t NP = (size_t)c.nbins * c.n * c.n, N = (size_t)c.nbins * c.m;
+    cplx *psi = malloc(sizeof(cplx) * NP), *rho = malloc(sizeof(cplx) * N);
+    for (size_t i = 0; i < NP; ++i) psi[i] = psi_packed[2 * i] + I * psi_packed[2 * i + 1];
+    psi_to_rho(&c, psi, rho);
+    for (int b = 0; b < c.nbins; ++b) pack(c.n, rho + (size_t)b * c.m, rho_packed + (size_t)b * c.m);
+    free(psi);
+    free(rho);
+    ctx_free(&c);
+    return 0;
+}
+
+/* Advance the wavefunctions (packed, in/out) by n_steps fixed steps of size h
+ * from r0 with the configured stepper.  Status as orc_evolve. */
+int orc_evolve_psi(const orc_params *p, double *psi_packed, double r0, double h, int64_t n_steps,
+                   int64_t *steps_done)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, p);
+    if (rc) {
+        ctx_free(&c);
+        return rc;
+    }
+#ifdef _OPENMP
+    if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+#endif
+    const int n = c.n, nt = c.nt;
+    size_t NP = (size_t)c.nbins * n * n, N = (size_t)c.nbins * c.m;
+    cplx *psi = malloc(sizeof(cplx) * NP), *nxt = malloc(sizeof(cplx) * NP);
+    cplx *Y = malloc(sizeof(cplx) * NP), *K = malloc(sizeof(cplx) * NP), *acc = malloc(sizeof(cplx) * NP);
+    cplx *rho = malloc(sizeof(cplx) * N);
+    double *dl = malloc(sizeof(double) * nt);
+    scratch_t w;
+    scratch_alloc(&c, &w);
+    for (size_t i = 0; i < NP; ++i) psi[i] = psi_packed[2 * i] + I * psi_packed[2 * i + 1];
+    int status = 0;
+    int64_t done = 0;
+    for (int64_t st = 0; st < n_steps; ++st) {
+        const double r = r0 + (double)st * h;
+        int ok = 1;
+        if (p->stepper == ORC_RK4) {
+            ok = rhs_psi(&c, &w, rho, r, psi, K);
+            for (size_t i = 0; ok && i < NP; ++i) {
+                acc[i] = K[i];
+                Y[i] = psi[i] + (0.5 * h) * K[i];
+            }
+            ok = ok && rhs_psi(&c, &w, rho, r + 0.5 * h, Y, K);
+            for (size_t i = 0; ok && i < NP; ++i) {
+                acc[i] += 2.0 * K[i];
+                Y[i] = psi[i] + (0.5 * h) * K[i];
+            }
+            ok = ok && rhs_psi(&c, &w, rho, r + 0.5 * h, Y, K);
+            for (size_t i = 0; ok && i < NP; ++i) {
+                acc[i] += 2.0 * K[i];
+                Y[i] = psi[i] + h * K[i];
+            }
+            ok = ok && rhs_psi(&c, &w, rho, r + h, Y, K);
+            for (size_t i = 0; ok && i < NP; ++i) nxt[i] = psi[i] + (h / 6.0) * (acc[i] + K[i]);
+        } else {
+            for (int t = 0; t < nt; ++t) dl[t] = path_length(&c, t, r, h);
+            for (int pass = 0; pass < 2 && ok; ++pass) {
+                const double rr = pass == 0 ? r : r + h;
+                double mu;
+                mom_t M;
+                geometry(&c, rr, &w.g, &mu);
+                psi_to_rho(&c, pass == 0 ? psi : Y, rho);
+                moments(&c, rho, &w.g, M, w.Sbuf);
+                if (!moments_finite(&c, M)) {
+                    ok = 0;
+                    break;
+                }
+                const double A = matter_A(&c, rr);
+                if (pass == 0) propagate_psi(&c, M, mu, A, &w.g, dl, psi, Y); /* predictor */
+                else {
+                    propagate_psi(&c, M, mu, A, &w.g, dl, psi, K);
+                    for (size_t i = 0; i < NP; ++i) nxt[i] = 0.5 * (Y[i] + K[i]);
+                }
+            }
+        }
+        for (size_t i = 0; ok && i < NP; ++i)
+            if (!isfinite(creal(nxt[i])) || !isfinite(cimag(nxt[i]))) ok = 0;
+        if (!ok) {
+            status = 1;
+            break;
+        }
+        cplx *tmp = psi;
+        psi = nxt;
+        nxt = tmp;
+        ++done;
+    }
+    for (size_t i = 0; i < NP; ++i) {
+        psi_packed[2 * i] = creal(psi[i]);
+        psi_packed[2 * i + 1] = cimag(psi[i]);
+    }
+    if (steps_done) *steps_done = done;
+    free(psi);
+    free(nxt);
+    free(Y);
+    free(K);
+    free(acc);
+    free(rho);
+    free(dl);
+    scratch_free(&w);
+    ctx_free(&c);
+    return status;
+}
+
 /* Moments of a packed state at radius r (packed Hermitian n*n each). */
 /* All four moments of a packed state at radius r (Eq. 3.13 / 3.18): Mp holds
  * M0, M1, M2, M3 packed (n*n each); M2 = M3 = 0 without azimuth bins. */

@@ -674,3 +674,90 @@ def test_extended_bulb_moment_weights_give_the_trajectory_direction(orc):
     ratios = M[1:, 2] / M[0, 2]
     assert np.abs(ratios - n_hat).max() < 1e-14
     assert abs(np.linalg.norm(ratios) - 1.0) < 1e-14
+
+
+# ---------------------------------------------------------------- wavefunction form
+
+def _psi_norms(psi, n_f):
+    v = psi.reshape(-1, n_f, n_f, 2)
+    return (v ** 2).sum(axis=(2, 3))  # [bin][flavor]
+
+
+@pytest.mark.parametrize("n_f", [2, 3])
+def test_psi_initial_state_gives_a_physical_rho(orc, n_f):
+    """rho = sum_a phi_a psi_a psi_a^+ of the seeded unit wavefunctions: trace
+    phi_e + (n_f - 1) phi_x per bin, Hermitian and positive semidefinite,
+    off-diagonal of order eps."""
+    kw = dict(dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.72)) if n_f == 3 else {}
+    p = _small(n_f=n_f, eps=1e-3, **kw)
+    psi = orc.init_psi(p)
+    assert np.abs(_psi_norms(psi, n_f) - 1).max() < 1e-15
+    rho = orc.psi_to_rho(p, psi)
+    E, u, phi, Hv = orc.tables(p)
+    M = orc.unpack(rho, n_f).reshape(2, p.n_u, p.n_E, n_f, n_f)
+    for s, (ie, ix) in enumerate([(0, 2), (1, 3)]):
+        tr = np.trace(M[s], axis1=-2, axis2=-1).real
+        assert np.abs(tr - (phi[ie] + (n_f - 1) * phi[ix])).max() < 1e-14 * phi[0].max()
+    w = np.linalg.eigvalsh(orc.unpack(rho, n_f))
+    assert w.min() > -1e-15
+    off = np.abs(orc.unpack(rho, n_f)[:, 0, 1])
+    assert 1e-5 * phi.max() < off.max() < 3e-3 * phi.max()
+
+
+def test_psi_form_is_exact_in_vacuum(orc):
+    """P1 in the wavefunction form: the predictor and corrector rotations
+    coincide in vacuum, so the average is the exact rotation."""
+    p = _small(n_E=12, n_u=5, stepper=I.EXPH, eps=0.0, theta=(0.3, 0, 0), hierarchy=-1,
+               E_min=1.0, E_max=13.0, r0=20.0, r1=30.0, n_steps=1000)
+    E, u, phi, Hv = orc.tables(p)
+    psi = orc.init_psi(p)
+    out, st, done = orc.evolve_psi(p, psi, p.r0, p.h, p.n_steps)
+    assert st == 0 and done == p.n_steps
+    M = orc.unpack(orc.psi_to_rho(p, out), 2).reshape(2, p.n_u, p.n_E, 2, 2)
+    Lj = _path_length(p, p.r1)
+    Delta = orc.vac_coeff() * p.hierarchy * p.dm2[0] / E
+    Pee = 1 - np.sin(2 * 0.3) ** 2 * np.sin(np.outer(Lj, Delta) / 2) ** 2
+    for s, (ie, ix) in enumerate([(0, 2), (1, 3)]):
+        want = phi[ix] + (phi[ie] - phi[ix]) * Pee
+        assert np.abs(M[s, :, :, 0, 0].real - want).max() < 1e-11 * phi[0].max()
+
+
+@pytest.mark.parametrize("stepper,ratio", [(I.RK4, 16.0), (I.EXPH, 8.0)])
+def test_psi_form_and_rho_form_converge_to_one_flow(orc, stepper, ratio):
+    """Both forms integrate the same flow (rho = sum phi psi psi^+ evolves as
+    U rho U^+), so from the same initial rho they converge together.  RK4:
+    the gap is the methods' truncation error, ~16x smaller per halving of h.
+    Predictor-corrector: averaging density matrices or wavefunctions differs
+    per step by (1/4) phi (U0 psi - U1 psi)(U0 psi - U1 psi)^+ = O(h^4) (the
+    two rotations differ by (H1 - H0) h = O(h^2)), O(h^3) over the run: ~8x."""
+    base = _small(n_E=6, n_u=4, mu0=1e5, eps=1e-2, r0=50.0, r1=51.0, stepper=stepper)
+    psi = orc.init_psi(base)
+    rho = orc.psi_to_rho(base, psi)
+
+    def gap(n):
+        a, st, _ = orc.evolve_psi(base, psi, 50.0, 1.0 / n, n)
+        b, st2, _ = orc.evolve(base, rho, 50.0, 1.0 / n, n)
+        assert st == 0 and st2 == 0
+        return np.abs(orc.psi_to_rho(base, a) - b).max()
+
+    g = [gap(n) for n in (50, 100, 200)]
+    assert 0.7 * ratio < g[0] / g[1] < 1.4 * ratio and 0.7 * ratio < g[1] / g[2] < 1.4 * ratio
+
+
+def test_psi_norms_under_the_two_steppers(orc):
+    """RK4 keeps |psi| to its truncation order (O(h^5)); the averaged predictor-
+    corrector shortens psi: |(U0 psi + U1 psi)/2|^2 = 1 - |U0 psi - U1 psi|^2/4
+    = 1 - O(h^4) per step, O(h^3) over the run, ~8x less per halving of h."""
+    base = _small(n_E=6, n_u=4, mu0=1e5, eps=1e-2, r0=50.0, r1=51.0)
+    psi = orc.init_psi(base)
+    loss = []
+    for n in (50, 100):
+        a, _, _ = orc.evolve_psi(base.replace(stepper=I.EXPH), psi, 50.0, 1.0 / n, n)
+        loss.append(np.abs(_psi_norms(a, 2) - 1).max())
+    assert 6.0 < loss[0] / loss[1] < 10.0
+    # RK4 on an oscillation: |R(iz)|^2 = 1 - z^6/72 per step, O(h^5) over the run
+    drift = []
+    for n in (100, 200):
+        r, _, _ = orc.evolve_psi(base.replace(stepper=I.RK4), psi, 50.0, 1.0 / n, n)
+        drift.append(np.abs(_psi_norms(r, 2) - 1).max())
+    assert 24.0 < drift[0] / drift[1] < 40.0
