@@ -94,6 +94,18 @@ enum xf_geometry {
     XF_GEOM_SINGLE_ANGLE = 2, /* Eq. 3.16-3.17: G = mu0 D(r/R) dE sum(rho - conj rho_bar), dl = dr */
     XF_GEOM_CONST = 3         /* isotropic, constant mu0: G = mu0 dE du sum(...), dl = dr */
 };
+enum xf_form {
+    XF_FORM_RHO = 0, /* density matrices rho(u, E), Eq. 3.1-3.4 */
+    XF_FORM_PSI = 1  /* the wavefunction form (Eq. 3.9-3.11): per bin one wavefunction psi_a
+                        for each initial flavor a (nu_e and the n_f - 1 others), rho =
+                        sum_a phi_a psi_a psi_a^+ with phi_a the flavor's number-flux weight
+                        (Eq. 4.1-4.2); each psi_a evolves with the Hamiltonian of rho.  The
+                        XF_EXPH step averages the two propagated wavefunctions (no
+                        renormalisation).  Fixed steps, XF_FP64 or XF_FP32_M64, one azimuth
+                        bin; not served.  State I/O: xf_set_psi / xf_get_psi; every rho-valued
+                        output (xf_get_state, xf_outputs, the moments, the energy average) is
+                        computed from the wavefunctions */
+};
 enum xf_matter {
     XF_MATTER_NONE = 0,
     XF_MATTER_POWER = 1, /* n_e = ne_ref (r_ref/r)^ne_power   (Eq. 4.3 shape) */
@@ -116,7 +128,7 @@ typedef struct xf_params {
                            azimuthally symmetric bulb model (default).  > 1 needs XF_GEOM_BULB, a
                            fixed-step stepper and XF_FP64 or XF_FP32_M64.  A problem then has
                            2 n_u n_phi n_E bins, ordered [s][u][phi][E] in every host array */
-    int32_t reserved;   /* 0 */
+    int32_t form;       /* enum xf_form: what a bin's state is (default XF_FORM_RHO) */
     int32_t strict;     /* 1: xf_step / xf_batch_step with RK4 return XF_E_UNSTABLE, without
                            stepping, when for some angle u
                            h kappa_u sqrt(2) (max_E |H_vac| + A |P_e| + mu |M0 - gamma_u M1|)
@@ -200,6 +212,23 @@ int xf_sync(xf_ctx *ctx);
 /* Copy the current state to a packed host array (n_doubles exact); r_km and
  * steps_done (total steps since the last set/init) may be NULL. */
 int xf_get_state(xf_ctx *ctx, double *rho, size_t n_doubles, double *r_km, int64_t *steps_done);
+
+/* The wavefunction form (XF_FORM_PSI).  psi: n_doubles = 2 n_f^2 * bins
+ * doubles, [s][u][phi][E][a][i] as (re, im) pairs: bin b's wavefunction of
+ * initial flavor a has components i = 0..n_f-1.  xf_set_psi copies it in at
+ * radius r_km (>= R_nu), XF_E_STATE if a value is not finite;
+ * xf_get_psi copies the current wavefunctions out (r_km, steps_done as
+ * xf_get_state, either may be NULL).  xf_init_state seeds
+ * psi_a = (e_a + eps sum_{b != a} exp(2 pi i U_ab) e_b) / sqrt(1 + (n_f-1) eps^2),
+ * U_ab the SplitMix64 uniform number at counter bin n_f(n_f-1) + k, k running
+ * over the pairs (a, b != a) in row order.  XF_E_UNSUPPORTED on a
+ * density-matrix ctx, and xf_set_state is XF_E_UNSUPPORTED on a wavefunction
+ * ctx (a density matrix does not fix its wavefunctions). */
+int xf_set_psi(xf_ctx *ctx, const double *psi, size_t n_doubles, double r_km);
+int xf_get_psi(xf_ctx *ctx, double *psi, size_t n_doubles, double *r_km, int64_t *steps_done);
+int xf_batch_set_psi(xf_ctx *ctx, int inst, const double *psi, size_t n_doubles, double r_km);
+int xf_batch_get_psi(xf_ctx *ctx, int inst, double *psi, size_t n_doubles, double *r_km,
+                     int64_t *steps_done);
 
 /* nu-nu moments of the current state at the current radius (Eq. 3.13-3.15
  * for the ctx geometry), packed Hermitian n_f*n_f doubles each (layout of one

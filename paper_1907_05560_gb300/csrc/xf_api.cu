@@ -173,6 +173,10 @@ int validate(xf_ctx *c, const xf_params *p, int n_E, int n_u, int nf)
         if (p->stepper == XF_EXPH_ADAPTIVE || (p->precision != XF_FP64 && p->precision != XF_FP32_M64))
             return fail(c, XF_E_UNSUPPORTED, "azimuth bins run with fixed steps in FP64 or FP32_M64");
     }
+    if (p->form != XF_FORM_RHO && p->form != XF_FORM_PSI) return fail(c, XF_E_ARG, "bad form %d", p->form);
+    if (p->form == XF_FORM_PSI &&
+        (p->stepper == XF_EXPH_ADAPTIVE || (p->precision != XF_FP64 && p->precision != XF_FP32_M64) || p->n_phi != 1))
+        return fail(c, XF_E_UNSUPPORTED, "the wavefunction form runs fixed steps in FP64 or FP32_M64, one azimuth bin");
     if (p->hierarchy != 1 && p->hierarchy != -1) return fail(c, XF_E_ARG, "hierarchy must be +1 or -1");
     if (p->matter < XF_MATTER_NONE || p->matter > XF_MATTER_EXP) return fail(c, XF_E_ARG, "bad matter %d", p->matter);
     if (!finite_pos(p->R_nu_km)) return fail(c, XF_E_ARG, "R_nu_km must be finite and > 0");
@@ -405,6 +409,8 @@ Inst make_inst(const InstHost &h)
     d.hvac_off = h.hvac_off;
     d.ref_off = h.ref_off;
     d.trace_off = h.trace_off;
+    d.phi_off = h.phi_off;
+    d.form = h.p.form;
     for (int b = 0; b < 3; ++b) d.off[b] = h.off[b];
     d.R = h.p.R_nu_km;
     d.mu0 = h.p.mu0_per_km;
@@ -737,14 +743,16 @@ int set_step_size(xf_ctx *c, int i, double dr)
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Bytes of a problem's block: three state buffers, trace, vacuum table,
+// Bytes of a problem's block: three state buffers (S or, in the psi form,
+// 2 n_f^2 planes each), trace, vacuum table,
 // weights, and for the renormalising variant the initial tr(T^2) per bin.
-long long block_bytes(int n_E, int n_u, int nf, int precision)
+long long block_bytes(int n_E, int n_u, int nf, int precision, int form)
 {
     const long long rb = precision == XF_FP64 ? 8 : 4;
     const long long S = nf * nf - 1, n_pairs = (long long)n_E * n_u, npad = (n_pairs + 63) & ~63ll;
+    const long long SS = form == XF_FORM_PSI ? 2 * nf * nf : S;
     const long long ref = precision == XF_FP32_M64_RENORM ? (long long)align256(2 * npad * rb) : 0;
-    return 3 * (long long)align256(2 * S * npad * rb) + (long long)align256(2 * npad * 8) +
+    return 3 * (long long)align256(2 * SS * npad * rb) + (long long)align256(2 * npad * 8) +
            (long long)align256((size_t)n_E * S * rb) + (long long)align256((size_t)4 * n_E * 8) + ref;
 }
 
@@ -760,16 +768,17 @@ int setup_problem(xf_ctx *c, int i, const xf_problem &prob)
     h.n_phi = prob.params.n_phi;
     h.nf = prob.n_flavor;
     h.S = h.nf * h.nf - 1;
+    h.SS = prob.params.form == XF_FORM_PSI ? 2 * h.nf * h.nf : h.S;
     h.n_pairs = h.n_E * h.n_u * h.n_phi;
     h.npad = (h.n_pairs + 63) & ~63;
     h.n_bins = 2ll * h.n_pairs;
     h.p = prob.params;
     h.adaptive = c->stepper == XF_EXPH_ADAPTIVE;
     const int rb = c->real_bytes;
-    h.block_bytes = block_bytes(h.n_E, h.n_u * h.n_phi, h.nf, c->precision);
+    h.block_bytes = block_bytes(h.n_E, h.n_u * h.n_phi, h.nf, c->precision, prob.params.form);
     h.block = c->blocks.alloc(h.block_bytes);
     if (h.block < 0) return fail(c, XF_E_NOMEM, "no room for the problem in the arena");
-    const long long plane = (long long)align256((size_t)2 * h.S * h.npad * rb);
+    const long long plane = (long long)align256((size_t)2 * h.SS * h.npad * rb);
     const long long tr = (long long)align256((size_t)2 * h.npad * 8);
     const long long hv = (long long)align256((size_t)h.n_E * h.S * rb);
     for (int b = 0; b < 3; ++b) h.off[b] = (h.block + b * plane) / rb;
@@ -780,7 +789,7 @@ int setup_problem(xf_ctx *c, int i, const xf_problem &prob)
                     ? (h.block + 3 * plane + tr + hv + (long long)align256((size_t)4 * h.n_E * 8)) / rb
                     : 0;
     build_tables(h);
-    const size_t need = (size_t)h.n_bins * h.nf * h.nf;
+    const size_t need = (size_t)h.n_bins * h.nf * h.nf * (h.SS > h.S ? 2 : 1); // a packed state
     if (need > c->staging_doubles) {
         double *st = (double *)dev_alloc(c, sizeof(double) * std::max(need, (size_t)c->in.size()));
         if (!st) return fail(c, XF_E_NOMEM, "device allocation of the staging buffer failed");
@@ -807,7 +816,7 @@ int setup_problem(xf_ctx *c, int i, const xf_problem &prob)
 
 // A ctx with its control buffers and an arena of arena_bytes, no problem yet.
 int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, int nfm, const xf_allocator *alloc,
-               xf_ctx **out, int nmom = 2)
+               xf_ctx **out, int nmom = 2, int form = XF_FORM_RHO)
 {
     xf_ctx *c = new (std::nothrow) xf_ctx();
     if (!c) return fail(nullptr, XF_E_NOMEM, "host allocation failed");
@@ -830,7 +839,10 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "no usable CUDA device"));
     const int st = (stepper == XF_RK4) ? STEP_RK4 : STEP_EXPH;
     c->nmom = nmom;
-    if (stepper == XF_EXPH_ADAPTIVE)
+    c->form = form;
+    if (form == XF_FORM_PSI)
+        c->kern = run_kernel_psi(nfm, st, c->real_bytes == 8);
+    else if (stepper == XF_EXPH_ADAPTIVE)
         c->kern = run_kernel_adapt(nfm, c->real_bytes == 8);
     else if (nmom == 4)
         c->kern = run_kernel_azimuth(nfm, st, c->real_bytes == 8);
@@ -893,17 +905,18 @@ int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ct
             if (n > 1) g_create_error = "problem " + std::to_string(i) + ": " + g_create_error;
             return rc;
         }
-        if (probs[i].params.stepper != probs[0].params.stepper || probs[i].params.precision != probs[0].params.precision)
-            return fail(nullptr, XF_E_ARG, "all problems of a pack need the same stepper and precision");
+        if (probs[i].params.stepper != probs[0].params.stepper || probs[i].params.precision != probs[0].params.precision ||
+            probs[i].params.form != probs[0].params.form)
+            return fail(nullptr, XF_E_ARG, "all problems of a pack need the same stepper, precision and form");
         (probs[i].n_flavor == 2 ? has2 : has3) = true;
     }
     long long bytes = 0;
     for (int i = 0; i < n; ++i)
         bytes += block_bytes(probs[i].n_E, probs[i].n_u * probs[i].params.n_phi, probs[i].n_flavor,
-                             probs[0].params.precision);
+                             probs[0].params.precision, probs[0].params.form);
     xf_ctx *c = nullptr;
     int rc = create_ctx(n, bytes, probs[0].params.stepper, probs[0].params.precision,
-                        (has2 && has3) ? 0 : (has3 ? 3 : 2), alloc, &c, has_phi ? 4 : 2);
+                        (has2 && has3) ? 0 : (has3 ? 3 : 2), alloc, &c, has_phi ? 4 : 2, probs[0].params.form);
     if (rc) return rc;
     for (int i = 0; i < n && !rc; ++i) rc = setup_problem(c, i, probs[i]);
     if (!rc) rc = plan_launch(c);
@@ -931,8 +944,8 @@ int add_problem(xf_ctx *c, const xf_problem &prob, const double *rho, double r_k
 {
     int rc = validate(c, &prob.params, prob.n_E, prob.n_u, prob.n_flavor);
     if (rc) return rc;
-    if (prob.params.stepper != c->stepper || prob.params.precision != c->precision)
-        return fail(c, XF_E_ARG, "stepper or precision differs from the pack's");
+    if (prob.params.stepper != c->stepper || prob.params.precision != c->precision || prob.params.form != c->form)
+        return fail(c, XF_E_ARG, "stepper, precision or form differs from the pack's");
     if (c->nfm && prob.n_flavor != c->nfm) return fail(c, XF_E_ARG, "flavor count differs from the pack's");
     if (prob.params.n_phi > 1 && c->nmom != 4) return fail(c, XF_E_UNSUPPORTED, "azimuth bins need a 4-moment pack");
     if (!std::isfinite(dr_km) || dr_km <= 0) return fail(c, XF_E_ARG, "dr_km must be finite and > 0");
@@ -1025,6 +1038,8 @@ int set_state_impl(xf_ctx *c, int i, const double *rho, size_t n_doubles, double
     InstHost *hp = instance(c, i);
     if (!hp) return c ? fail(c, XF_E_ARG, "bad instance index %d", i) : XF_E_ARG;
     InstHost &h = *hp;
+    if (c->form == XF_FORM_PSI)
+        return fail(c, XF_E_UNSUPPORTED, "a wavefunction-form problem takes its state from xf_set_psi");
     if (!rho) return fail(c, XF_E_ARG, "rho is NULL");
     if (n_doubles != (size_t)h.n_bins * h.nf * h.nf)
         return fail(c, XF_E_ARG, "n_doubles %zu != %lld", n_doubles, h.n_bins * h.nf * h.nf);
@@ -1066,8 +1081,12 @@ int init_state_impl(xf_ctx *c, int i, double r_km)
     rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
-        init_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (Real *)c->arena + h.off[0],
-                                                                 (double *)c->arena + h.trace_off, ref_ptr<Real>(c, h));
+        if (c->form == XF_FORM_PSI)
+            psi_init_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (Real *)c->arena + h.off[0]);
+        else
+            init_state_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (Real *)c->arena + h.off[0],
+                                                                     (double *)c->arena + h.trace_off,
+                                                                     ref_ptr<Real>(c, h));
         return (int)cudaGetLastError();
     });
     if (rc) return cuda_fail(c, (cudaError_t)rc, "init kernel");
@@ -1084,17 +1103,99 @@ int get_state_impl(xf_ctx *c, int i, double *rho, size_t n_doubles, double *r_km
         return fail(c, XF_E_ARG, "n_doubles %zu != %lld", n_doubles, h.n_bins * h.nf * h.nf);
     if (c->pending) sync_status(c);
     if (!h.state_valid) return fail(c, XF_E_STATE, "no valid state");
+    int rc = XF_OK;
+    const long long plane = rho_plane(c, h, &rc);
+    if (rc) return rc;
+    LayoutArgs la = layout_args(c, h);
+    const int grid = elementwise_grid(c, h);
+    rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
+        constexpr int NF = decltype(nfc)::value;
+        using Real = std::remove_pointer_t<decltype(realp)>;
+        state_to_pack_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(
+            la, (const Real *)c->arena + plane, (const double *)c->arena + h.trace_off, c->staging);
+        return (int)cudaGetLastError();
+    });
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "layout kernel");
+    XF_CUDA(c, cudaMemcpyAsync(rho, c->staging, sizeof(double) * n_doubles, cudaMemcpyDeviceToHost, c->stream),
+            "copy state to host");
+    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (r_km) *r_km = radius(h);
+    if (steps_done) *steps_done = h.steps;
+    return XF_OK;
+}
+
+long long rho_plane(xf_ctx *c, InstHost &h, int *rc)
+{
+    *rc = XF_OK;
+    if (c->form != XF_FORM_PSI) return h.off[h.cur];
+    LayoutArgs la = layout_args(c, h);
+    const int grid = elementwise_grid(c, h);
+    *rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
+        constexpr int NF = decltype(nfc)::value;
+        using Real = std::remove_pointer_t<decltype(realp)>;
+        psi_to_rho_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (const Real *)c->arena + h.off[h.cur],
+                                                                 (Real *)c->arena + h.off[2],
+                                                                 (double *)c->arena + h.trace_off);
+        return (int)cudaGetLastError();
+    });
+    if (*rc) *rc = cuda_fail(c, (cudaError_t)*rc, "wavefunction conversion kernel");
+    return h.off[2];
+}
+
+int set_psi_impl(xf_ctx *c, int i, const double *psi, size_t n_doubles, double r_km)
+{
+    InstHost *hp = instance(c, i);
+    if (!hp) return c ? fail(c, XF_E_ARG, "bad instance index %d", i) : XF_E_ARG;
+    InstHost &h = *hp;
+    if (c->form != XF_FORM_PSI) return fail(c, XF_E_UNSUPPORTED, "not a wavefunction-form problem");
+    if (!psi) return fail(c, XF_E_ARG, "psi is NULL");
+    if (n_doubles != (size_t)h.n_bins * h.SS)
+        return fail(c, XF_E_ARG, "n_doubles %zu != %lld", n_doubles, h.n_bins * h.SS);
+    int rc = check_r(c, h, r_km);
+    if (rc) return rc;
+    if (c->pending) sync_status(c);
+    XF_CUDA(c, cudaMemcpyAsync(c->staging, psi, sizeof(double) * n_doubles, cudaMemcpyHostToDevice, c->stream),
+            "copy state to device");
+    XF_CUDA(c, cudaMemsetAsync(c->bad, 0, sizeof(int), c->stream), "reset flag");
+    LayoutArgs la = layout_args(c, h);
+    const int grid = elementwise_grid(c, h);
+    rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
+        constexpr int NF = decltype(nfc)::value;
+        using Real = std::remove_pointer_t<decltype(realp)>;
+        psi_pack_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, c->staging, (Real *)c->arena + h.off[0], 1);
+        return (int)cudaGetLastError();
+    });
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "layout kernel");
+    int bad = 0;
+    XF_CUDA(c, cudaMemcpyAsync(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read flag");
+    XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
+    rc = reset_instance(c, i, r_km, !bad);
+    if (rc) return rc;
+    if (bad) return fail(c, XF_E_STATE, "state contains non-finite values");
+    return XF_OK;
+}
+
+int get_psi_impl(xf_ctx *c, int i, double *psi, size_t n_doubles, double *r_km, int64_t *steps_done)
+{
+    InstHost *hp = instance(c, i);
+    if (!hp) return c ? fail(c, XF_E_ARG, "bad instance index %d", i) : XF_E_ARG;
+    InstHost &h = *hp;
+    if (c->form != XF_FORM_PSI) return fail(c, XF_E_UNSUPPORTED, "not a wavefunction-form problem");
+    if (!psi) return fail(c, XF_E_ARG, "psi is NULL");
+    if (n_doubles != (size_t)h.n_bins * h.SS)
+        return fail(c, XF_E_ARG, "n_doubles %zu != %lld", n_doubles, h.n_bins * h.SS);
+    if (c->pending) sync_status(c);
+    if (!h.state_valid) return fail(c, XF_E_STATE, "no valid state");
     LayoutArgs la = layout_args(c, h);
     const int grid = elementwise_grid(c, h);
     int rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
-        state_to_pack_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(
-            la, (const Real *)c->arena + h.off[h.cur], (const double *)c->arena + h.trace_off, c->staging);
+        psi_pack_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, c->staging, (Real *)c->arena + h.off[h.cur], 0);
         return (int)cudaGetLastError();
     });
     if (rc) return cuda_fail(c, (cudaError_t)rc, "layout kernel");
-    XF_CUDA(c, cudaMemcpyAsync(rho, c->staging, sizeof(double) * n_doubles, cudaMemcpyDeviceToHost, c->stream),
+    XF_CUDA(c, cudaMemcpyAsync(psi, c->staging, sizeof(double) * n_doubles, cudaMemcpyDeviceToHost, c->stream),
             "copy state to host");
     XF_CUDA(c, cudaStreamSynchronize(c->stream), "stream synchronize");
     if (r_km) *r_km = radius(h);
@@ -1115,12 +1216,15 @@ int outputs_impl(xf_ctx *c, int i, double *p_surv, double *trace, double *purity
     // staging holds n_bins * n_f^2 >= 4 n_bins doubles: room for three outputs
     for (int k = 0; k < 3; ++k)
         if (outs[k]) dev[k] = c->staging + (size_t)k * h.n_bins;
+    int rc = XF_OK;
+    const long long plane = rho_plane(c, h, &rc);
+    if (rc) return rc;
     LayoutArgs la = layout_args(c, h);
     const int grid = elementwise_grid(c, h);
-    int rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
+    rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
-        outputs_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (const Real *)c->arena + h.off[h.cur],
+        outputs_kernel<NF, Real><<<grid, 256, 0, c->stream>>>(la, (const Real *)c->arena + plane,
                                                               (const double *)c->arena + h.trace_off, dev[0],
                                                               dev[1], dev[2]);
         return (int)cudaGetLastError();
@@ -1163,11 +1267,14 @@ int moments_all(xf_ctx *c, int i, double *M)
         c->mom_part_slots = G;
     }
     const double dE = m.dE;
-    int rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
+    int rc = XF_OK;
+    const long long plane = rho_plane(c, h, &rc);
+    if (rc) return rc;
+    rc = dispatch_layout(c, h, [&](auto nfc, auto *realp) {
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
         moments_partial_kernel<NF, Real, 256><<<G, 256, 0, c->stream>>>(
-            m, (const Real *)c->arena + h.off[h.cur], (const double *)c->arena + h.trace_off, c->mom_part);
+            m, (const Real *)c->arena + plane, (const double *)c->arena + h.trace_off, c->mom_part);
         moments_final_kernel<NF><<<1, 32, 0, c->stream>>>(c->mom_part, G, dE, c->mom_full);
         return (int)cudaGetLastError();
     });
@@ -1288,6 +1395,27 @@ int xf_batch_set_state(xf_ctx *c, int inst, const double *rho, size_t n_doubles,
 {
     if (!c) return XF_E_ARG;
     return set_state_impl(c, inst, rho, n_doubles, r_km);
+}
+
+int xf_set_psi(xf_ctx *c, const double *psi, size_t n_doubles, double r_km)
+{
+    if (!c) return XF_E_ARG;
+    return set_psi_impl(c, 0, psi, n_doubles, r_km);
+}
+int xf_batch_set_psi(xf_ctx *c, int inst, const double *psi, size_t n_doubles, double r_km)
+{
+    if (!c) return XF_E_ARG;
+    return set_psi_impl(c, inst, psi, n_doubles, r_km);
+}
+int xf_get_psi(xf_ctx *c, double *psi, size_t n_doubles, double *r_km, int64_t *steps_done)
+{
+    if (!c) return XF_E_ARG;
+    return get_psi_impl(c, 0, psi, n_doubles, r_km, steps_done);
+}
+int xf_batch_get_psi(xf_ctx *c, int inst, double *psi, size_t n_doubles, double *r_km, int64_t *steps_done)
+{
+    if (!c) return XF_E_ARG;
+    return get_psi_impl(c, inst, psi, n_doubles, r_km, steps_done);
 }
 
 int xf_init_state(xf_ctx *c, double r_km)
@@ -1594,7 +1722,7 @@ int xf_autotune(xf_ctx *c, int64_t n_probe, double dr_km, const int *cand_in, in
         if (!h.active) continue;
         if (!h.state_valid) return fail(c, XF_E_STATE, "every problem needs a valid state");
         offs.push_back(total);
-        total += 3 * align256((size_t)2 * h.S * h.npad * c->real_bytes);
+        total += 3 * align256((size_t)2 * h.SS * h.npad * c->real_bytes);
     }
     unsigned char *snap = (unsigned char *)dev_alloc(c, std::max<size_t>(total, 256));
     if (!snap) return fail(c, XF_E_NOMEM, "device allocation of the state snapshot failed");
@@ -1607,7 +1735,7 @@ int xf_autotune(xf_ctx *c, int64_t n_probe, double dr_km, const int *cand_in, in
         size_t k = 0;
         for (const InstHost &h : views) {
             if (!h.active) continue;
-            const size_t bytes = 3 * align256((size_t)2 * h.S * h.npad * c->real_bytes);
+            const size_t bytes = 3 * align256((size_t)2 * h.SS * h.npad * c->real_bytes);
             unsigned char *src = c->arena + h.block, *dst = snap + offs[k++];
             XF_CUDA(c, cudaMemcpyAsync(save ? dst : src, save ? src : dst, bytes, cudaMemcpyDeviceToDevice, c->stream),
                     "state snapshot");

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "xf_math.cuh"
+#include "xf_psi.cuh"
 
 namespace xf {
 
@@ -322,6 +323,90 @@ __global__ void __launch_bounds__(NT) angle_average_kernel(LayoutArgs a, const R
         double v = 0.0;
         for (int q = 0; q < NT; ++q) v += sm[q][threadIdx.x];
         out[(size_t)blockIdx.x * M + threadIdx.x] = v / a.n_E;
+    }
+}
+
+// ---- wavefunction form (one psi per initial flavor; 2 n_f^2 reals per bin,
+// component c = (a n_f + i) 2 + re/im at (c 2 + s) npad + p) ---------------
+
+// Seeded wavefunctions: psi_a = (e_a + eps sum_{b != a} exp(2 pi i U_ab) e_b)
+// / sqrt(1 + (n_f - 1) eps^2), U_ab the SplitMix64 uniform number at counter
+// bin n_f (n_f - 1) + k, k running over (a, b != a) in row order.
+template <int NF, typename Real>
+__global__ void psi_init_kernel(LayoutArgs a, Real *state)
+{
+    constexpr int NPERM = NF * (NF - 1);
+    const long long nb = 2ll * a.n_pairs;
+    const double norm = 1.0 / sqrt(1.0 + (NF - 1) * a.eps * a.eps);
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        int s, p;
+        bin_split(a, b, &s, &p);
+        int k = 0;
+        for (int fa = 0; fa < NF; ++fa)
+            for (int i = 0; i < NF; ++i) {
+                double re = 0.0, im = 0.0;
+                if (i == fa) {
+                    re = norm;
+                } else {
+                    uint64_t z = splitmix64(a.seed, (uint64_t)b * NPERM + k);
+                    double U = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+                    double sn, cs;
+                    sincos(6.283185307179586476925286766559 * U, &sn, &cs);
+                    re = norm * a.eps * cs;
+                    im = norm * a.eps * sn;
+                    ++k;
+                }
+                const int c = (fa * NF + i) * 2;
+                state[(size_t)(c * 2 + s) * a.npad + p] = (Real)re;
+                state[(size_t)((c + 1) * 2 + s) * a.npad + p] = (Real)im;
+            }
+    }
+}
+
+// Density matrices of the wavefunction state (rho = sum_a phi_a psi_a psi_a^+)
+// into a traceless plane and the FP64 trace, for the outputs and moments.
+template <int NF, typename Real>
+__global__ void psi_to_rho_kernel(LayoutArgs a, const Real *psi, Real *state, double *trace)
+{
+    constexpr int S = Comp<NF>::S, SS = 2 * NF * NF;
+    const long long nb = 2ll * a.n_pairs;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        int s, p;
+        bin_split(a, b, &s, &p);
+        const int e = p % a.n_E;
+        double x[SS], t[S], tr;
+#pragma unroll
+        for (int c = 0; c < SS; ++c) x[c] = (double)psi[(size_t)(c * 2 + s) * a.npad + p];
+        const double w0 = a.phi[(s == 0 ? 0 : 1) * a.n_E + e], w1 = a.phi[(s == 0 ? 2 : 3) * a.n_E + e];
+        psi_rho<NF, double>(x, w0, w1, t, &tr);
+#pragma unroll
+        for (int c = 0; c < S; ++c) state[(size_t)(c * 2 + s) * a.npad + p] = (Real)t[c];
+        trace[(size_t)s * a.npad + p] = tr;
+    }
+}
+
+// packed host wavefunctions [s][t][E][a][i](re, im) <-> planes
+template <int NF, typename Real>
+__global__ void psi_pack_kernel(LayoutArgs a, const double *packed, Real *state, int to_device)
+{
+    constexpr int SS = 2 * NF * NF;
+    const long long nb = 2ll * a.n_pairs;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        int s, p;
+        bin_split(a, b, &s, &p);
+        double *x = (double *)packed + (size_t)b * SS;
+        for (int c = 0; c < SS; ++c) {
+            Real &y = state[(size_t)(c * 2 + s) * a.npad + p];
+            if (to_device) {
+                if (!isfinite(x[c])) *a.bad = 1;
+                y = (Real)x[c];
+            } else {
+                x[c] = (double)y;
+            }
+        }
     }
 }
 

@@ -1,8 +1,9 @@
 // xf_ckpt.cu -- checkpoints (the paper's dump mode 1 and resume, Sec. 4.2.4)
 // and the per-trajectory energy average (dump mode 2).
 //
-// A checkpoint holds the problem's current state plane in the working
-// precision, its FP64 trace per bin, the renormalising variant's reference
+// A checkpoint holds the problem's current state planes in the working
+// precision (density matrices, or the wavefunctions of the psi form), its
+// FP64 trace per bin, the renormalising variant's reference
 // values, and the position (radius, step size, step counts, error-controlled
 // progress), behind a header that ties it to the problem's shape, stepper and
 // precision.  Loading it puts the state into plane 0 and restores the
@@ -32,7 +33,7 @@ struct CkptHeader {
     int32_t err, adaptive;
     double r_ad, h_ad, err_ad;
     int64_t n_acc, n_rej;
-    int32_t ad_status, pad_;
+    int32_t ad_status, form;
 };
 
 struct Layout {
@@ -42,7 +43,7 @@ struct Layout {
 Layout layout_of(const xf_ctx *c, const InstHost &h)
 {
     Layout L;
-    L.plane = (size_t)2 * h.S * h.npad * c->real_bytes;
+    L.plane = (size_t)2 * h.SS * h.npad * c->real_bytes;
     L.trace = (size_t)2 * h.npad * sizeof(double);
     L.ref = c->precision == XF_FP32_M64_RENORM ? (size_t)2 * h.npad * c->real_bytes : 0;
     L.total = sizeof(CkptHeader) + L.plane + L.trace + L.ref;
@@ -77,6 +78,7 @@ CkptHeader header_of(const xf_ctx *c, const InstHost &h, const Layout &L)
     H.n_acc = h.n_acc;
     H.n_rej = h.n_rej;
     H.ad_status = h.ad_status;
+    H.form = c->form;
     return H;
 }
 
@@ -200,9 +202,9 @@ int xf_checkpoint_load(xf_ctx *c, int inst, const void *buf, size_t bytes)
     std::memcpy(&H, buf, sizeof H);
     if (H.magic != kMagic || H.version != kVersion) return fail(c, XF_E_ARG, "not a checkpoint of this library");
     if (H.n_E != h->n_E || H.n_u != h->n_u || H.n_f != h->nf || H.real_bytes != c->real_bytes ||
-        H.stepper != c->stepper || H.precision != c->precision || H.npad != h->npad ||
+        H.stepper != c->stepper || H.precision != c->precision || H.form != c->form || H.npad != h->npad ||
         H.plane_bytes != (int64_t)L.plane || H.trace_bytes != (int64_t)L.trace || H.ref_bytes != (int64_t)L.ref)
-        return fail(c, XF_E_ARG, "checkpoint of another problem shape, stepper or precision");
+        return fail(c, XF_E_ARG, "checkpoint of another problem shape, stepper, precision or form");
     const unsigned char *src = (const unsigned char *)buf + sizeof H;
     // the state goes to plane 0
     cudaError_t e = cudaMemcpyAsync(c->arena + (size_t)h->off[0] * c->real_bytes, src, L.plane,
@@ -266,12 +268,14 @@ int xf_angle_average(xf_ctx *c, int inst, double *out, size_t n_doubles)
     const size_t n_traj = (size_t)h->n_u * h->n_phi;
     const size_t need = 2 * n_traj * h->nf * h->nf;
     if (n_doubles != need) return fail(c, XF_E_ARG, "n_doubles %zu != %zu", n_doubles, need);
+    const long long plane = rho_plane(c, *h, &rc);
+    if (rc) return rc;
     xf::LayoutArgs la = layout_args(c, *h);
     rc = dispatch_layout(c, *h, [&](auto nfc, auto *realp) {
         constexpr int NF = decltype(nfc)::value;
         using Real = std::remove_pointer_t<decltype(realp)>;
         xf::angle_average_kernel<NF, Real, 128><<<(unsigned)(2 * n_traj), 128, 0, c->stream>>>(
-            la, (const Real *)c->arena + h->off[h->cur], (const double *)c->arena + h->trace_off, c->staging);
+            la, (const Real *)c->arena + plane, (const double *)c->arena + h->trace_off, c->staging);
         return (int)cudaGetLastError();
     });
     if (rc) return cuda_fail(c, (cudaError_t)rc, "average kernel");

@@ -20,5 +20,7 @@ RunKernel run_kernel_fp32(int nfm, int stepper, int var);
 RunKernel run_kernel_adapt(int nfm, bool fp64);
 // the extended bulb model (four moments), plain arithmetic, FP64 or FP32 bins
 RunKernel run_kernel_azimuth(int nfm, int stepper, bool fp64);
+// the wavefunction form, plain arithmetic, FP64 or FP32 bins
+RunKernel run_kernel_psi(int nfm, int stepper, bool fp64);
 
 } // namespace xf

@@ -81,13 +81,14 @@ class Arena {
 struct InstHost {
     bool active = false;              // slot holds a problem
     int n_E = 0, n_u = 0, n_phi = 1, nf = 0, S = 0, n_pairs = 0, npad = 0; // pairs = n_u n_phi n_E
+    int SS = 0;                       // state components per bin: S (rho form) or 2 n_f^2 (psi form)
     long long n_bins = 0;
     xf_params p{};
     std::vector<double> E, phi, hvac; // tables: E[n_E], phi[4][n_E], hvac[n_E][S]
     // the problem's block in the pack arena (bytes) and its parts (element
     // offsets from the arena base in the part's own type)
     long long block = -1, block_bytes = 0;
-    long long off[3] = {0, 0, 0};     // Real: rho (two copies) and the stage buffer
+    long long off[3] = {0, 0, 0};     // Real: the state (two copies) and the stage buffer, SS planes each
     long long trace_off = 0;          // double: trace per bin (2 npad)
     long long hvac_off = 0;           // Real: vacuum table (n_E x S)
     long long ref_off = 0;            // Real: initial tr(T^2) per bin (2 npad), renormalising variant only
@@ -112,6 +113,7 @@ struct xf_ctx {
     std::vector<xfp::InstHost> in;
     int real_bytes = 8, precision = XF_FP64, stepper = XF_RK4, nfm = 2;
     int nmom = 2; // moments per stage: 2, or 4 when a problem has azimuth bins (extended bulb model)
+    int form = XF_FORM_RHO; // what the state planes hold (one form per pack)
     cudaStream_t stream = nullptr;
     xf_allocator alloc{};
     bool has_alloc = false;
@@ -174,7 +176,11 @@ double radius(const InstHost &h);
 int enqueue_requests(xf_ctx *c, long long n, const std::vector<long long> &req);
 int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ctx **out);
 int create_slots(int n_slots, long long arena_bytes, int stepper, int precision, int nfm, xf_ctx **out);
-long long block_bytes(int n_E, int n_u, int nf, int precision);
+long long block_bytes(int n_E, int n_u, int nf, int precision, int form = XF_FORM_RHO);
+// The density matrices of problem i's current state: its state plane (rho
+// form), or (psi form) rho = sum_a phi_a psi_a psi_a^+ written into its stage
+// plane and trace array on the ctx stream.  Element offset from the arena base.
+long long rho_plane(xf_ctx *c, InstHost &h, int *rc);
 int add_problem(xf_ctx *c, const xf_problem &prob, const double *rho, double r_km, double dr_km, int *slot);
 int remove_problem(xf_ctx *c, int slot);
 int set_state_impl(xf_ctx *c, int i, const double *rho, size_t n_doubles, double r_km);

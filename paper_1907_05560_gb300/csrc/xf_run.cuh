@@ -27,6 +27,7 @@
 #include <stdint.h>
 
 #include "xf_math.cuh"
+#include "xf_psi.cuh"
 
 namespace xf {
 
@@ -38,6 +39,9 @@ enum { ERR_NONFINITE = 1, ERR_BARRIER = 2 };
 // FP32 (TwoSum) up to the warp; plain with the per-step restoration of each
 // bin's tr(rho0^2) (|P|^2 / 2 in two flavors) to its initial value
 enum { VAR_PLAIN = 0, VAR_COMP = 1, VAR_RENORM = 2 };
+// what the state planes hold: traceless density matrices, or one wavefunction
+// per initial flavor (2 n_f^2 reals per bin)
+enum { FORM_RHO = 0, FORM_PSI = 1 };
 constexpr int NVMAX = 32; // 4 moments x (n_f^2 - 1) for three flavors (extended bulb model)
 
 // One problem of a pack.  Its three state buffers (the two ping-pong copies
@@ -50,6 +54,8 @@ struct Inst {
     long long off[3], hvac_off;
     long long ref_off;      // Real: per-bin tr(rho0^2) of the initial state (renormalising variant)
     long long trace_off;    // double: trace per bin [2][npad]
+    long long phi_off;      // double: number-flux weights [4][n_E] (nu_e, nubar_e, nu_x, nubar_x)
+    int form, pad1_;        // FORM_RHO or FORM_PSI (state planes hold wavefunctions)
     double R, mu0, du, dE;
     double ne_ref, r_ref, ne_power, nb0, h_ns, Ye, gf;
     double r0, h;           // step k of the run starts at r0 + k h
@@ -480,6 +486,7 @@ __device__ __forceinline__ void accum_comp(const Real *tn, const Real *tb, Acc w
 template <typename Real>
 struct TileView {
     const Real *cur, *hvac, *ref;
+    const double *phi;      // number-flux weights (wavefunction form)
     Real *nxt, *aux;
     int n_E, npad, p0, p1, j_lo;
     double h;
@@ -597,6 +604,129 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
     else cta_partial<NV, NT, Acc>(m, sh, part_out);
 }
 
+// Number-flux weights of the e flavor and the others for species s at energy e.
+template <typename Real>
+__device__ __forceinline__ void psi_weights(const TileView<Real> &v, int s, int e, Real *w0, Real *w1)
+{
+    *w0 = (Real)v.phi[(s == 0 ? 0 : 1) * v.n_E + e];
+    *w1 = (Real)v.phi[(s == 0 ? 2 : 3) * v.n_E + e];
+}
+
+// One stage of one tile in the wavefunction form: the same stage structure as
+// stage_tile (RK4 on d(psi)/dr = -i H psi dl/dr, or the predictor-corrector
+// averaging wavefunctions), moments of rho = sum_a phi_a psi_a psi_a^+.
+template <int NF, int STEP, typename Real, int NT>
+__device__ __forceinline__ void psi_stage_tile(const TileView<Real> v, int smax, int st, const Real *tb, Shared &sh,
+                                               double *part_out)
+{
+    constexpr int S = Comp<NF>::S, SS = PsiComp<NF>::SS, NV = 2 * S;
+    const double h = v.h;
+    const double mu = sh.mu;
+    const Real A = (Real)sh.A;
+    Real M0[S], M1[S];
+#pragma unroll
+    for (int c = 0; c < S; ++c) {
+        M0[c] = (Real)(mu * sh.M[c]);
+        M1[c] = (Real)(mu * sh.M[S + c]);
+    }
+    Real m[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) m[c] = Real(0);
+    for (int p = v.p0 + threadIdx.x; p < v.p1; p += NT) {
+        const int j = p / v.n_E, e = p - j * v.n_E, q = j - v.j_lo;
+        const Real gam = tb[q];
+        Real g[S], hv[S], hn[S], hb[S];
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            g[c] = M0[c] - gam * M1[c];
+            hv[c] = v.hvac[(size_t)e * S + c];
+        }
+        hamiltonians<NF, Real>(hv, A, g, hn, hb);
+        Real tr_[2][S]; // traceless rho of the stage outputs (nu, nubar)
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            Real w0, w1, o[SS], tr;
+            psi_weights(v, s, e, &w0, &w1);
+            if constexpr (STEP == STEP_RK4) {
+                const Real kap = tb[smax + q];
+                const Real cy = (Real)((st == 2) ? h : 0.5 * h);
+                const Real cb = (Real)((st == 0 || st == 3) ? h / 6.0 : h / 3.0);
+                Real y[SS], k[SS], bb[SS];
+                if (st == 0) load_state<Real, SS>(v.cur, v.npad, s, p, y);
+                else load_state<Real, SS>(v.aux, v.npad, s, p, y);
+                rhs_psi<NF, Real>(s == 0 ? hn : hb, kap, y, k);
+                if (st == 0) {
+#pragma unroll
+                    for (int c = 0; c < SS; ++c) bb[c] = y[c] + cb * k[c];
+                } else {
+                    load_state<Real, SS>(v.nxt, v.npad, s, p, bb);
+#pragma unroll
+                    for (int c = 0; c < SS; ++c) bb[c] += cb * k[c];
+                }
+                store_state<Real, SS>(v.nxt, v.npad, s, p, bb);
+                if (st < 3) {
+                    Real rn[SS];
+                    if (st == 0) {
+#pragma unroll
+                        for (int c = 0; c < SS; ++c) rn[c] = y[c];
+                    } else {
+                        load_state<Real, SS>(v.cur, v.npad, s, p, rn);
+                    }
+#pragma unroll
+                    for (int c = 0; c < SS; ++c) o[c] = rn[c] + cy * k[c];
+                    store_state<Real, SS>(v.aux, v.npad, s, p, o);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < SS; ++c) o[c] = bb[c];
+                }
+            } else {
+                const StepLen<Real> dl = load_dl(tb, smax, q);
+                Real x[SS], u[SS];
+                load_state<Real, SS>(v.cur, v.npad, s, p, x);
+                prop_psi<NF, Real>(s == 0 ? hn : hb, dl, x, u);
+                if (st == 0) {
+#pragma unroll
+                    for (int c = 0; c < SS; ++c) o[c] = u[c];
+                    store_state<Real, SS>(v.aux, v.npad, s, p, o);
+                } else {
+                    Real pp[SS];
+                    load_state<Real, SS>(v.aux, v.npad, s, p, pp);
+#pragma unroll
+                    for (int c = 0; c < SS; ++c) o[c] = Real(0.5) * (pp[c] + u[c]);
+                    store_state<Real, SS>(v.nxt, v.npad, s, p, o);
+                }
+            }
+            psi_rho<NF, Real>(o, w0, w1, tr_[s], &tr);
+        }
+        accum<NF, Real, Real>(tr_[0], tr_[1], tb[2 * smax + q], tb[3 * smax + q], m);
+    }
+    cta_partial<NV, NT, Real>(m, sh, part_out);
+}
+
+// Prologue for one tile in the wavefunction form: moments of the input state.
+template <int NF, typename Real, int NT>
+__device__ __forceinline__ void psi_prologue_tile(const TileView<Real> v, int smax, const Real *tb, Shared &sh,
+                                                  double *part_out)
+{
+    constexpr int S = Comp<NF>::S, SS = PsiComp<NF>::SS, NV = 2 * S;
+    Real m[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) m[c] = Real(0);
+    for (int p = v.p0 + threadIdx.x; p < v.p1; p += NT) {
+        const int j = p / v.n_E, e = p - j * v.n_E, q = j - v.j_lo;
+        Real t[2][S];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            Real x[SS], w0, w1, tr;
+            load_state<Real, SS>(v.cur, v.npad, s, p, x);
+            psi_weights(v, s, e, &w0, &w1);
+            psi_rho<NF, Real>(x, w0, w1, t[s], &tr);
+        }
+        accum<NF, Real, Real>(t[0], t[1], tb[2 * smax + q], tb[3 * smax + q], m);
+    }
+    cta_partial<NV, NT, Real>(m, sh, part_out);
+}
+
 // Prologue for one tile: weighted sums of the input state.
 template <int NF, typename Real, int NT, int VAR, typename SH, int NMOM = 2>
 __device__ __forceinline__ void prologue_tile(const TileView<Real> v, int smax, const Real *tb, SH &sh,
@@ -654,6 +784,7 @@ __device__ __forceinline__ TileView<Real> make_view(const RunArgs &a, const Inst
     v.aux = base + in.off[2];
     v.hvac = base + in.hvac_off;
     v.ref = base + in.ref_off;
+    v.phi = (const double *)a.arena + in.phi_off;
     v.n_E = in.n_E;
     v.npad = in.npad;
     v.p0 = tl.p0;
@@ -713,8 +844,9 @@ __host__ __device__ constexpr int min_blocks(int nt, int real_bytes)
 // NFM: 2 or 3 (every instance has that many flavors) or 0 (mixed pack);
 // VAR: VAR_PLAIN, VAR_COMP or VAR_RENORM.
 // NMOM: 2 moments (the bulb model) or 4 (the extended bulb model, Eq. 3.18;
-// its problems may also have a single azimuth bin).
-template <int NFM, int STEP, typename Real, int NT, int VAR, int NMOM = 2>
+// its problems may also have a single azimuth bin).  FORM: FORM_RHO, or
+// FORM_PSI (wavefunctions; plain arithmetic, two moments).
+template <int NFM, int STEP, typename Real, int NT, int VAR, int NMOM = 2, int FORM = FORM_RHO>
 __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real))) xf_run_kernel(RunArgs a)
 {
     extern __shared__ double s_dyn[];
@@ -744,7 +876,13 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real))) xf_run_kerne
         if constexpr (NMOM == 4) build_azimuth_table(in, s_tab, smax, TabSlots<Real>::n, v.j_lo, span, r_in, r_in);
         __syncthreads();
         double *out = a.partials + (size_t)t * NVMAX;
-        if (nf == 2) {
+        if constexpr (FORM == FORM_PSI) {
+            if (nf == 2) {
+                if constexpr (NFM != 3) psi_prologue_tile<2, Real, NT>(v, smax, s_tab, sh, out);
+            } else {
+                if constexpr (NFM != 2) psi_prologue_tile<3, Real, NT>(v, smax, s_tab, sh, out);
+            }
+        } else if (nf == 2) {
             if constexpr (NFM != 3) prologue_tile<2, Real, NT, VAR, Shared, NMOM>(v, smax, s_tab, sh, out);
         } else {
             if constexpr (NFM != 2) prologue_tile<3, Real, NT, VAR, Shared, NMOM>(v, smax, s_tab, sh, out);
@@ -814,7 +952,13 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real))) xf_run_kerne
                     sh.A = matter_A(in, r_rhs);
                 }
                 __syncthreads();
-                if (nf == 2) {
+                if constexpr (FORM == FORM_PSI) {
+                    if (nf == 2) {
+                        if constexpr (NFM != 3) psi_stage_tile<2, STEP, Real, NT>(v, smax, st, s_tab, sh, out);
+                    } else {
+                        if constexpr (NFM != 2) psi_stage_tile<3, STEP, Real, NT>(v, smax, st, s_tab, sh, out);
+                    }
+                } else if (nf == 2) {
                     if constexpr (NFM != 3) stage_tile<2, STEP, Real, NT, VAR, NMOM>(v, smax, st, s_tab, sh, out);
                 } else {
                     if constexpr (NFM != 2) stage_tile<3, STEP, Real, NT, VAR, NMOM>(v, smax, st, s_tab, sh, out);

@@ -24,6 +24,7 @@ RK4, EXPH, EXPH_ADAPTIVE = 0, 1, 2
 BULB, MU_R4, SINGLE_ANGLE, CONST = 0, 1, 2, 3
 MATTER_NONE, MATTER_POWER, MATTER_EXP = 0, 1, 2
 FP64, FP32_M64, FP32_COMP, FP32_M64_RENORM = 0, 1, 2, 3
+FORM_RHO, FORM_PSI = 0, 1  # state: density matrices, or one wavefunction per initial flavor
 
 
 @dataclass
@@ -38,6 +39,7 @@ class Problem:
     geometry: int = BULB
     precision: int = FP64
     strict: int = 0                   # 1: refuse RK4 steps outside the stable region
+    form: int = FORM_RHO              # FORM_PSI: the wavefunction form (Eq. 3.9-3.11)
     R_nu: float = 10.0                # km, neutrinosphere radius
     mu0: float = 1.0e5                # km^-1
     E_min: float = 1.0                # MeV

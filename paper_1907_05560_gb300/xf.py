@@ -38,7 +38,7 @@ class XFParams(ctypes.Structure):
         ("size", ctypes.c_uint32), ("version", ctypes.c_uint32),
         ("stepper", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("geometry", ctypes.c_int32), ("hierarchy", ctypes.c_int32),
-        ("matter", ctypes.c_int32), ("n_phi", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("matter", ctypes.c_int32), ("n_phi", ctypes.c_int32), ("form", ctypes.c_int32),
         ("strict", ctypes.c_int32),
         ("R_nu_km", ctypes.c_double), ("mu0_per_km", ctypes.c_double),
         ("E_min_MeV", ctypes.c_double), ("E_max_MeV", ctypes.c_double),
@@ -117,6 +117,11 @@ SIGNATURES = {
                                        ctypes.POINTER(_P)]),
     "xf_batch_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "xf_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.c_size_t, ctypes.c_double]),
+    "xf_set_psi": (ctypes.c_int, [_P, _D, ctypes.c_size_t, ctypes.c_double]),
+    "xf_get_psi": (ctypes.c_int, [_P, _D, ctypes.c_size_t, _D, ctypes.POINTER(ctypes.c_int64)]),
+    "xf_batch_set_psi": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.c_size_t, ctypes.c_double]),
+    "xf_batch_get_psi": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.c_size_t, _D,
+                                        ctypes.POINTER(ctypes.c_int64)]),
     "xf_batch_init_state": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
     "xf_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.c_size_t, _D,
                                           ctypes.POINTER(ctypes.c_int64)]),
@@ -181,7 +186,7 @@ def params_from(p: I.Problem) -> XFParams:
     L.xf_params_default(ctypes.byref(x))
     x.stepper, x.precision, x.geometry = p.stepper, p.precision, p.geometry
     x.hierarchy, x.matter, x.strict = p.hierarchy, p.matter, p.strict
-    x.n_phi = p.n_phi
+    x.n_phi, x.form = p.n_phi, p.form
     x.R_nu_km, x.mu0_per_km, x.E_min_MeV, x.E_max_MeV = p.R_nu, p.mu0, p.E_min, p.E_max
     x.dm2_eV2[:] = list(p.dm2)
     x.theta[:] = list(p.theta)
@@ -285,6 +290,19 @@ class Context:
         n = ctypes.c_int64(0)
         self._check(self.L.xf_get_state(self.h, _dp(rho), rho.size, ctypes.byref(r), ctypes.byref(n)))
         return rho, r.value, n.value
+
+    def set_psi(self, psi: np.ndarray, r_km: float, i: int = 0):
+        """Wavefunction form: [s][u][phi][E][a][i] as (re, im) pairs."""
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        return self._check(self.L.xf_batch_set_psi(self.h, i, _dp(psi), psi.size, float(r_km)))
+
+    def get_psi(self, i: int = 0, out: np.ndarray | None = None):
+        p = getattr(self, "problems", [self.problem])[i]
+        psi = out if out is not None else np.empty(p.n_bins * 2 * p.n_f * p.n_f)
+        r = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        self._check(self.L.xf_batch_get_psi(self.h, i, _dp(psi), psi.size, ctypes.byref(r), ctypes.byref(n)))
+        return psi, r.value, n.value
 
     def moments(self):
         m = self.n_f * self.n_f
