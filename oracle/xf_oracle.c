@@ -1107,7 +1107,9 @@ static void propagate_psi(const orc_ctx *c, mom_t M, double mu, double A, const 
     (void)m;
 }
 
-/* d(psi)/dr = -i H psi dl/dr for every bin and flavor. */
+/* d(psi)/dr = -i H psi dl/dr for every bin and flavor, H taken traceless as
+ * in the propagator of Eq. 3.11 (its trace would only turn every wavefunction
+ * of the bin by one common phase, which rho = sum phi psi psi^+ never sees). */
 static int rhs_psi(const orc_ctx *c, scratch_t *w, cplx *rho_scr, double r, const cplx *psi, cplx *K)
 {
     int n = c->n, nE = c->nE, nt = c->nt;
@@ -1124,6 +1126,9 @@ static int rhs_psi(const orc_ctx *c, scratch_t *w, cplx *rho_scr, double r, cons
         cplx G[NFMAX * NFMAX], H[NFMAX * NFMAX];
         g_of(c, &w->g, t, mu, M, G);
         hamiltonian(c, s, e, G, A, H);
+        double trn = 0.0;
+        for (int i = 0; i < n; ++i) trn += creal(H[i * n + i]) / n;
+        for (int i = 0; i < n; ++i) H[i * n + i] -= trn;
         for (int a = 0; a < n; ++a) {
             const cplx *v = psi + ((size_t)b * n + a) * n;
             cplx *k = K + ((size_t)b * n + a) * n;
