@@ -128,13 +128,17 @@ def measured_peaks():
 
 # FP64 floating-point operations per bin-step of the predictor-corrector in
 # three flavors (two propagator applications per step), counted from the
-# per-bin formulas (+ - * / sqrt each 1, FMA 2, sincos not counted); the
-# Jacobi eigensolver is counted at the sweep number measured on this
-# workload.  Derivation in DESIGN.md ("Algorithmic work").
+# per-bin formulas (+ - * / sqrt each 1, FMA 2, sincos not counted) by
+# running them once with a counting number type; the Jacobi eigensolver is
+# counted at the sweep number measured on this workload.
 FLOPS_PER_BIN_STEP = {("exph", 3): 2631, ("rk4", 3): 684, ("exph", 2): 120, ("rk4", 2): 172}
 # one attempt of the error-controlled step (four Hamiltonians, five propagations,
 # one shared eigendecomposition), counted the same way
 FLOPS_PER_BIN_ATTEMPT = {3: 5897, 2: 268}
+# the wavefunction form (one psi per initial flavor), counted the same way:
+# per stage the propagation of n_f wavefunctions and rho's traceless part
+# rebuilt from them for the moments
+FLOPS_PER_BIN_STEP_PSI = {("exph", 3): 2621, ("rk4", 3): 1702, ("exph", 2): 276, ("rk4", 2): 536}
 
 
 def oracle_sample(problem, n_steps, threads):
@@ -283,6 +287,10 @@ def run_xf(args):
     if args.precision == "fp64" and not args.skip_azimuth:
         azimuth = run_azimuth(args, xf, I, torch, stream, flush, barrier, world, 152 * 4 * 2070.0 * 1e6 / 1e12)
 
+    psi = None
+    if args.precision == "fp64" and not args.skip_psi:
+        psi = run_psi(args, xf, I, torch, stream, flush, barrier, world, 152 * 4 * 2070.0 * 1e6 / 1e12)
+
     serving = None
     if args.precision == "fp64" and not args.skip_serve and rank == 0:
         serving = run_serving(args, xf, I, torch)
@@ -346,7 +354,7 @@ def run_xf(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "fp32_m64": fp32, "fp32_variants": variants, "batched": batched, "adaptive": adaptive, "azimuth": azimuth, "serving": serving, "clocks": clk, "gpu_launches": args.steps,
+            "fp32_m64": fp32, "fp32_variants": variants, "batched": batched, "adaptive": adaptive, "azimuth": azimuth, "psi_form": psi, "serving": serving, "clocks": clk, "gpu_launches": args.steps,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -429,6 +437,39 @@ def run_azimuth(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
     flops = (FLOPS_PER_BIN_STEP[("exph", 2)] + 24) * p.n_bins * steps
     return {"value": p.n_bins * steps * world / t, "unit": UNIT, "bins": p.n_bins, "n_u": p.n_u, "n_phi": p.n_phi,
             "n_E": p.n_E, "n_f": p.n_f, "ms_per_radial_step": 1e3 * t / steps, "precision": "FP64",
+            "ctas": ctas, "threads": threads, "achieved_tflops_fp64": flops / t / 1e12,
+            "frac_of_fp64_peak": flops / t / 1e12 / peak_tflops}
+
+
+def run_psi(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
+    """The wavefunction form (Eq. 3.9-3.11) on the headline workload: the same
+    3-flavor 1000 x 200 bulb problem with one wavefunction per initial flavor
+    (18 reals per bin instead of 8), FP64, the predictor-corrector averaging
+    wavefunctions; one bench step = `chunk` radial steps."""
+    p = I.c2().replace(form=I.FORM_PSI)
+    c = xf.Context(p, stream=stream)
+    c.init_state(p.r0)
+    chunk = args.chunk
+    for _ in range(args.warmup):
+        c.step_async(chunk, p.h)
+    c.sync()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        c.step_async(chunk, p.h)
+        ends[k].record(stream)
+    c.sync()
+    barrier()
+    t = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) * 1e-3, world)
+    ctas, threads, _ = c.launch_info()
+    c.close()
+    steps = chunk * args.steps
+    flops = FLOPS_PER_BIN_STEP_PSI[("exph", p.n_f)] * p.n_bins * steps
+    return {"value": p.n_bins * steps * world / t, "unit": UNIT, "bins": p.n_bins, "reals_per_bin": 2 * p.n_f ** 2,
+            "ms_per_step": 1e3 * t / args.steps, "radial_steps_per_step": chunk, "precision": "FP64",
             "ctas": ctas, "threads": threads, "achieved_tflops_fp64": flops / t / 1e12,
             "frac_of_fp64_peak": flops / t / 1e12 / peak_tflops}
 
@@ -578,6 +619,7 @@ def main():
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--skip-adapt", action="store_true")
     ap.add_argument("--skip-azimuth", action="store_true")
+    ap.add_argument("--skip-psi", action="store_true", help="skip the wavefunction-form leg")
     ap.add_argument("--skip-tune", action="store_true", help="batched leg: keep the automatic tile size")
     ap.add_argument("--skip-batch-fp64", action="store_true", help="batched leg: skip the FP64 run of the ensemble")
     ap.add_argument("--adapt-iters", type=int, default=30, help="attempts per error-controlled bench step")

@@ -29,7 +29,7 @@
  *                             either optionally renormalised after each step
  *                             to the entry tr(T^2) (a constant of Eq. 3.10)
  *
- * Readings taken where the paper is silent (each listed in the design doc):
+ * Readings taken where the paper is silent:
  *   angle variable u = sin^2(theta_0) on a midpoint grid; energy midpoint grid;
  *   rho's diagonal carries the number-flux weights phi_a(E) relative to nu_e;
  *   mu0 absorbs the normalisation of Eq. 3.8; the predictor-corrector averages

@@ -18,7 +18,7 @@ template <int NF> struct PsiComp { static constexpr int SS = 2 * NF * NF; };
 
 // y = H x for one complex vector (re/im interleaved), H packed traceless.
 template <int NF, typename Real>
-__device__ __forceinline__ void h_apply(const Real *h, const Real *x, Real *y)
+__host__ __device__ __forceinline__ void h_apply(const Real *h, const Real *x, Real *y)
 {
     if constexpr (NF == 2) {
         // (a p + (hx + i hy) q, (hx - i hy) p - a q)
@@ -47,7 +47,7 @@ __device__ __forceinline__ void h_apply(const Real *h, const Real *x, Real *y)
 //   2 flavors (Eq. 3.11): cos(lam dl) psi - i sin(lam dl)/lam H psi, lam^2 = a^2 + |H01|^2;
 //   3 flavors: H = V diag(lam) V^+ (cyclic Jacobi), psi' = V (exp(-i lam dl) o (V^+ psi)).
 template <int NF, typename Real>
-__device__ __forceinline__ void prop_psi(const Real *h, StepLen<Real> dl, const Real *x, Real *y)
+__host__ __device__ __forceinline__ void prop_psi(const Real *h, StepLen<Real> dl, const Real *x, Real *y)
 {
     constexpr int N2 = 2 * NF;
     if constexpr (NF == 2) {
@@ -95,7 +95,7 @@ __device__ __forceinline__ void prop_psi(const Real *h, StepLen<Real> dl, const 
 
 // k = -i kappa H psi for the NF wavefunctions of one bin.
 template <int NF, typename Real>
-__device__ __forceinline__ void rhs_psi(const Real *h, Real kappa, const Real *x, Real *k)
+__host__ __device__ __forceinline__ void rhs_psi(const Real *h, Real kappa, const Real *x, Real *k)
 {
     constexpr int N2 = 2 * NF;
 #pragma unroll
@@ -113,7 +113,7 @@ __device__ __forceinline__ void rhs_psi(const Real *h, Real kappa, const Real *x
 // Traceless packed part of rho = sum_a w_a psi_a psi_a^+ (w_0: the e flavor's
 // weight, w_1: the others'); *tr = its trace.
 template <int NF, typename Real>
-__device__ __forceinline__ void psi_rho(const Real *x, Real w0, Real w1, Real *t, Real *tr)
+__host__ __device__ __forceinline__ void psi_rho(const Real *x, Real w0, Real w1, Real *t, Real *tr)
 {
     constexpr int N2 = 2 * NF;
     Real d[NF];
