@@ -64,6 +64,7 @@ def lib():
                                  ctypes.POINTER(ctypes.c_int64)]
         L.orc_moments.argtypes = [P, dp, ctypes.c_double, dp, dp]
         L.orc_moments_ex.argtypes = [P, dp, ctypes.c_double, dp]
+        L.orc_cyl_pair.argtypes = [P, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp]
         L.orc_init_psi.argtypes = [P, dp]
         L.orc_psi_to_rho.argtypes = [P, dp, dp]
         L.orc_evolve_psi.argtypes = [P, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
@@ -207,6 +208,16 @@ def evolve_psi(p, psi: np.ndarray, r0: float, h: float, n_steps: int, n_threads:
     if rc < 0:
         raise ValueError(f"orc_evolve_psi: {rc}")
     return out, rc, done.value
+
+
+def cyl_pair(p, r: float, j: int, jp: int):
+    """Cylinder model (Eq. 3.20): (Phi' - Phi, w_jp (1 - cos(alpha_j - alpha_jp)))."""
+    o = params(p)
+    sh, w = np.zeros(1), np.zeros(1)
+    rc = lib().orc_cyl_pair(ctypes.byref(o), float(r), int(j), int(jp), _dp(sh), _dp(w))
+    if rc != 0:
+        raise ValueError(f"orc_cyl_pair: {rc}")
+    return float(sh[0]), float(w[0])
 
 
 def moments_ex(p, rho: np.ndarray, r: float) -> np.ndarray:

@@ -18,7 +18,8 @@
  *   - matter potential        Eq. 3.7, profiles Eq. 4.3 (power law) / Eq. 4.4
  *   - antineutrino rule       A -> -A, B -> -B, B_et -> -B_et*  (after Eq. 3.4)
  *   - nu-nu potential         Eq. 3.13 with the bulb geometry Eq. 3.14-3.15;
- *                             single-angle form Eq. 3.16-3.17
+ *                             single-angle form Eq. 3.16-3.17; the extended
+ *                             bulb Eq. 3.18; the cylinder/line model Eq. 3.20
  *   - trajectory length       Eq. 3.3 (l = r cos(theta))
  *   - spectra                 Eq. 4.1-4.2 (Fermi-Dirac, 1/(exp(E/T-eta)+1))
  *   - propagator              Eq. 3.10-3.12 (2 flavors); 3 flavors: spectral
@@ -51,14 +52,15 @@ typedef double complex cplx;
 
 /* ---- parameters (layout mirrored by oracle/oracle.py) ------------------- */
 enum { ORC_RK4 = 0, ORC_EXPH = 1 };
-enum { ORC_BULB = 0, ORC_MU_R4 = 1, ORC_SINGLE_ANGLE = 2, ORC_CONST = 3 };
+enum { ORC_BULB = 0, ORC_MU_R4 = 1, ORC_SINGLE_ANGLE = 2, ORC_CONST = 3, ORC_CYLINDER = 4 };
 enum { ORC_MATTER_NONE = 0, ORC_MATTER_POWER = 1, ORC_MATTER_EXP = 2 };
 
 typedef struct {
     int32_t n_E, n_u, n_f, stepper, geometry, hierarchy, matter, n_threads;
     int32_t renorm;   /* 1: after every step, scale each bin's traceless part back to
                          the tr(T^2) it had on entry (see renormalise()) */
-    int32_t n_phi;    /* azimuth bins of the extended bulb model (Eq. 3.18); 0 or 1: none */
+    int32_t n_phi;    /* azimuth bins of the extended bulb model (Eq. 3.18), or latitude
+                         bins of the cylinder model (Eq. 3.20); 0 or 1: none */
     double R_nu;      /* neutrinosphere radius, km */
     double mu0;       /* nu-nu coupling, km^-1 */
     double E_min, E_max; /* MeV */
@@ -305,6 +307,7 @@ typedef struct {
     int n, nE, nu, nphi, nt, nbins, m; /* m = n*n; nt = nu * nphi trajectories */
     double dE, du;
     double *E, *u, *phi; /* phi[a*nE + e], a = nu_e, nubar_e, nu_x, nubar_x */
+    double *th;          /* cylinder: emission angles theta_j in (-pi/2, pi/2) */
     cplx *Hvac;          /* [nE][n][n] */
 } orc_ctx;
 
@@ -318,7 +321,8 @@ static int ctx_init(orc_ctx *c, const orc_params *p)
     c->nE = p->n_E;
     c->nu = p->n_u;
     c->nphi = p->n_phi > 1 ? p->n_phi : 1;
-    if (c->nphi > 1 && p->geometry != ORC_BULB) return -1; /* azimuth bins extend the bulb model only */
+    if (c->nphi > 1 && p->geometry != ORC_BULB && p->geometry != ORC_CYLINDER)
+        return -1; /* azimuth (or latitude) bins belong to the bulb (or cylinder) model only */
     c->nt = c->nu * c->nphi;
     c->nbins = 2 * c->nt * p->n_E;
     c->dE = (p->E_max - p->E_min) / p->n_E;
@@ -327,9 +331,11 @@ static int ctx_init(orc_ctx *c, const orc_params *p)
     c->u = malloc(sizeof(double) * c->nu);
     c->phi = malloc(sizeof(double) * 4 * c->nE);
     c->Hvac = malloc(sizeof(cplx) * c->nE * c->m);
-    if (!c->E || !c->u || !c->phi || !c->Hvac) return -2;
+    c->th = malloc(sizeof(double) * c->nu);
+    if (!c->E || !c->u || !c->phi || !c->Hvac || !c->th) return -2;
     for (int e = 0; e < c->nE; ++e) c->E[e] = p->E_min + (e + 0.5) * c->dE;
     for (int j = 0; j < c->nu; ++j) c->u[j] = (j + 0.5) * c->du;
+    for (int j = 0; j < c->nu; ++j) c->th[j] = -0.5 * PI + (j + 0.5) * PI / c->nu;
 
     /* Eq. 4.1-4.2: f_a(E) = E^2 / (F2(eta) T^3 (exp(E/T - eta) + 1)), and the
      * number flux weight L_a/<E_a> relative to nu_e, <E> = T F3/F2. */
@@ -385,6 +391,7 @@ static void ctx_free(orc_ctx *c)
     free(c->u);
     free(c->phi);
     free(c->Hvac);
+    free(c->th);
 }
 
 /* Eq. 3.7 with the configured n_e(r) */
@@ -407,9 +414,22 @@ static double matter_A(const orc_ctx *c, double r)
  *       - sin(th) sin(th') (cos(ph) cos(ph') + sin(ph) sin(ph')), with
  *       sin(theta') = x sqrt(u) and azimuth midpoints ph_k = (k + 1/2) 2 pi / n_phi
  *       of weight 1/n_phi: four moments.  With one azimuth bin the model is the
- *       azimuthally symmetric bulb (M2 = M3 = 0). */
+ *       azimuthally symmetric bulb (M2 = M3 = 0).
+ * CYLINDER (Sec. 3.2.5, Eq. 3.20): an infinite cylinder of radius R emits
+ *       perpendicular to its axis; trajectory t = j n_phi + k leaves latitude
+ *       Phi_k = (k + 1/2) 2 pi / n_phi at angle theta_j (midpoints of
+ *       (-pi/2, pi/2), measured from the outward normal, positive clockwise).
+ *       At radius r it makes the angle alpha_j = asin(x sin(theta_j)) with
+ *       the radial direction, so dl/dr = 1/cos(alpha_j) and l = r cos(alpha_j).
+ *       G_t is not a sum of a few moments when n_phi > 1 (cyl_G below); the
+ *       moments M0..M2 here are the latitude averages with the weights
+ *       cos(theta') / cos(alpha') dtheta', times 1, cos(alpha'), sin(alpha'),
+ *       for which G = mu (M0 - cos(alpha) M1 - sin(alpha) M2) when the state is
+ *       the same at every latitude; mu_eff = mu0 x (a line source thins as 1/r). */
 typedef struct {
     double *w[4], *g1, *g2, *g3, *kap;
+    double *alpha, *wc;  /* cylinder: alpha_t and cos(theta)/cos(alpha) dtheta of trajectory t */
+    const cplx *S;       /* per-trajectory sums of the state the moments were taken from */
 } geom_t;
 
 static void geometry(const orc_ctx *c, double r, geom_t *g, double *mu_eff)
@@ -437,6 +457,19 @@ static void geometry(const orc_ctx *c, double r, geom_t *g, double *mu_eff)
             }
             break;
         }
+        case ORC_CYLINDER: {
+            double sa = x * sin(c->th[j]), ca = sqrt(1.0 - sa * sa);
+            double wc = cos(c->th[j]) / ca * (PI / c->nu);
+            g->alpha[t] = asin(sa);
+            g->wc[t] = wc;
+            g->w[0][t] = wc / c->nphi;
+            g->w[1][t] = wc * ca / c->nphi;
+            g->w[2][t] = wc * sa / c->nphi;
+            g->g1[t] = ca;
+            g->g2[t] = sa;
+            g->kap[t] = 1.0 / ca;
+            break;
+        }
         case ORC_MU_R4:
             g->w[0][t] = c->du;
             g->w[1][t] = c->du * cth;
@@ -452,6 +485,7 @@ static void geometry(const orc_ctx *c, double r, geom_t *g, double *mu_eff)
         }
     }
     if (p->geometry == ORC_MU_R4) *mu_eff = p->mu0 * x2 * x2;
+    else if (p->geometry == ORC_CYLINDER) *mu_eff = p->mu0 * x;
     else if (p->geometry == ORC_SINGLE_ANGLE) {
         double t = 1.0 - sqrt(1.0 - x2); /* Eq. 3.17 */
         *mu_eff = p->mu0 * 0.5 * t * t;
@@ -464,9 +498,13 @@ static void geometry(const orc_ctx *c, double r, geom_t *g, double *mu_eff)
  * on the zenith bin only. */
 static double path_length(const orc_ctx *c, int t, double r, double h)
 {
-    if (c->p.geometry != ORC_BULB && c->p.geometry != ORC_MU_R4) return h;
     const int j = t / c->nphi;
     double R = c->p.R_nu;
+    if (c->p.geometry == ORC_CYLINDER) { /* l = sqrt(r^2 - R^2 sin^2(theta_j)) */
+        double b2 = R * R * sin(c->th[j]) * sin(c->th[j]);
+        return h * (2.0 * r + h) / (sqrt(r * r - b2) + sqrt((r + h) * (r + h) - b2));
+    }
+    if (c->p.geometry != ORC_BULB && c->p.geometry != ORC_MU_R4) return h;
     double x0 = R / r, x1 = R / (r + h);
     double l0 = r * sqrt(1.0 - x0 * x0 * c->u[j]);
     double l1 = (r + h) * sqrt(1.0 - x1 * x1 * c->u[j]);
@@ -479,10 +517,11 @@ static double path_length(const orc_ctx *c, int t, double r, double h)
  * are zero without azimuth bins. */
 typedef cplx mom_t[4][NFMAX * NFMAX];
 
-static void moments(const orc_ctx *c, const cplx *rho, const geom_t *g, mom_t M, cplx *Sbuf)
+static void moments(const orc_ctx *c, const cplx *rho, geom_t *g, mom_t M, cplx *Sbuf)
 {
     int m = c->m, nE = c->nE, nt = c->nt;
-    const int nmom = c->nphi > 1 ? 4 : 2;
+    const int nmom = (c->nphi > 1 || c->p.geometry == ORC_CYLINDER) ? 4 : 2;
+    g->S = Sbuf;
 #pragma omp parallel for schedule(static)
     for (int t = 0; t < nt; ++t) {
         cplx S[NFMAX * NFMAX];
@@ -503,9 +542,39 @@ static void moments(const orc_ctx *c, const cplx *rho, const geom_t *g, mom_t M,
         for (int k = 0; k < m; ++k) M[q][k] *= c->dE;
 }
 
-/* G_t = mu (M0 - g1_t M1 - g2_t M2 - g3_t M3) */
+/* Cylinder model, Eq. 3.20, for trajectory t = (theta_j, Phi_k):
+ *   G_t = mu dE sum_j' w_j' [1 - cos(alpha_j - alpha_j')] S(Phi', theta_j'),
+ *   w_j' = cos(theta_j') / cos(alpha_j') dtheta,
+ *   Phi' = Phi_k + theta_j' - theta_j + alpha_j - alpha_j'  (the background
+ *          trajectory that crosses t's point at radius r left from latitude Phi'),
+ * S(Phi', .) by periodic linear interpolation between the two latitude bins
+ * around Phi' (the paper does not say how Phi' off the grid is read). */
+static void cyl_G(const orc_ctx *c, const geom_t *g, int t, double mu, cplx *G)
+{
+    const int m = c->m, nphi = c->nphi, j = t / nphi, k = t % nphi;
+    const double dphi = 2.0 * PI / nphi;
+    for (int q = 0; q < m; ++q) G[q] = 0;
+    for (int jp = 0; jp < c->nu; ++jp) {
+        double a = g->alpha[j * nphi], ap = g->alpha[jp * nphi];
+        double shift = c->th[jp] - c->th[j] + a - ap; /* Phi' - Phi_k */
+        double pos = k + shift / dphi;                /* Phi' in units of the latitude grid */
+        double fl = floor(pos), f = pos - fl;
+        int i0 = ((int)fl % nphi + nphi) % nphi, i1 = (i0 + 1) % nphi;
+        double K = g->wc[jp * nphi] * (1.0 - cos(a - ap));
+        const cplx *S0 = g->S + (size_t)(jp * nphi + i0) * m, *S1 = g->S + (size_t)(jp * nphi + i1) * m;
+        for (int q = 0; q < m; ++q) G[q] += K * ((1.0 - f) * S0[q] + f * S1[q]);
+    }
+    for (int q = 0; q < m; ++q) G[q] *= mu * c->dE;
+}
+
+/* G_t = mu (M0 - g1_t M1 - g2_t M2 - g3_t M3); the cylinder model with
+ * latitude bins from the state's per-trajectory sums (cyl_G). */
 static void g_of(const orc_ctx *c, const geom_t *g, int t, double mu, mom_t M, cplx *G)
 {
+    if (c->p.geometry == ORC_CYLINDER && c->nphi > 1) {
+        cyl_G(c, g, t, mu, G);
+        return;
+    }
     for (int k = 0; k < c->m; ++k)
         G[k] = mu * (M[0][k] - g->g1[t] * M[1][k] - g->g2[t] * M[2][k] - g->g3[t] * M[3][k]);
 }
@@ -549,8 +618,10 @@ static int scratch_alloc(const orc_ctx *c, scratch_t *w)
     w->g.g2 = malloc(sizeof(double) * c->nt);
     w->g.g3 = malloc(sizeof(double) * c->nt);
     w->g.kap = malloc(sizeof(double) * c->nt);
+    w->g.alpha = malloc(sizeof(double) * c->nt);
+    w->g.wc = malloc(sizeof(double) * c->nt);
     w->Sbuf = malloc(sizeof(cplx) * c->nt * c->m);
-    return w->g.w[3] && w->g.kap && w->Sbuf ? 0 : -2;
+    return w->g.w[3] && w->g.kap && w->g.alpha && w->g.wc && w->Sbuf ? 0 : -2;
 }
 
 static void scratch_free(scratch_t *w)
@@ -560,6 +631,8 @@ static void scratch_free(scratch_t *w)
     free(w->g.g2);
     free(w->g.g3);
     free(w->g.kap);
+    free(w->g.alpha);
+    free(w->g.wc);
     free(w->Sbuf);
 }
 
@@ -1288,6 +1361,29 @@ int orc_evolve_psi(const orc_params *p, double *psi_packed, double r0, double h,
     scratch_free(&w);
     ctx_free(&c);
     return status;
+}
+
+/* Cylinder model: the latitude shift Phi' - Phi of background angle bin jp
+ * seen from angle bin j at radius r, and its coupling weight
+ * w_jp (1 - cos(alpha_j - alpha_jp)) (Eq. 3.20); 0, or -1 for a bad index. */
+int orc_cyl_pair(const orc_params *p, double r, int j, int jp, double *shift, double *weight)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, p);
+    if (rc || p->geometry != ORC_CYLINDER || j < 0 || jp < 0 || j >= c.nu || jp >= c.nu) {
+        ctx_free(&c);
+        return rc ? rc : -1;
+    }
+    scratch_t w;
+    scratch_alloc(&c, &w);
+    double mu;
+    geometry(&c, r, &w.g, &mu);
+    double a = w.g.alpha[j * c.nphi], ap = w.g.alpha[jp * c.nphi];
+    *shift = c.th[jp] - c.th[j] + a - ap;
+    *weight = w.g.wc[jp * c.nphi] * (1.0 - cos(a - ap));
+    scratch_free(&w);
+    ctx_free(&c);
+    return 0;
 }
 
 /* Moments of a packed state at radius r (packed Hermitian n*n each). */

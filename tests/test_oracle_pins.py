@@ -791,3 +791,123 @@ def test_psi_norms_under_the_two_steppers(orc):
         r, _, _ = orc.evolve_psi(base.replace(stepper=I.RK4), psi, 50.0, 1.0 / n, n)
         drift.append(np.abs(_psi_norms(r, 2) - 1).max())
     assert 14.0 < drift[1] / drift[2] < drift[0] / drift[1] < 34.0
+
+
+# ------------------------------------------------------------ cylinder / line model (Sec. 3.2.5)
+
+def _cyl(**kw):
+    base = dict(n_E=6, n_u=8, n_phi=5, n_f=2, geometry=I.CYLINDER, stepper=I.EXPH, mu0=1e3, eps=1e-2,
+                r0=20.0, r1=21.0, n_steps=50, seed=17)
+    base.update(kw)
+    return I.Problem(**base)
+
+
+def _ray_point(R, r, lat, th):
+    """Where the ray that leaves the circle of radius R at latitude `lat`, at
+    angle `th` from the outward normal (positive clockwise), reaches radius r,
+    and its direction there (plane geometry, written from scratch)."""
+    e = R * np.array([np.cos(lat), np.sin(lat)])
+    d = np.array([np.cos(lat - th), np.sin(lat - th)])
+    s = -R * np.cos(th) + np.sqrt(r * r - (R * np.sin(th)) ** 2)
+    return e + s * d, d
+
+
+def test_cylinder_latitude_map_by_ray_tracing(orc):
+    """Eq. 3.20's Phi' = Phi + theta' - theta + asin(x sin theta) - asin(x sin theta')
+    is the latitude from which the background ray of angle theta' left to
+    cross the point that the ray (Phi, theta) reaches at radius r, with theta
+    measured clockwise from the outward normal; and 1 - cos(alpha - alpha') is
+    one minus the dot product of the two rays' directions there.  Both
+    checked against plane ray tracing."""
+    p = _cyl(n_u=12)
+    rng = np.random.default_rng(3)
+    th = -np.pi / 2 + (np.arange(p.n_u) + 0.5) * np.pi / p.n_u
+    for _ in range(40):
+        r = p.R_nu * (1.0 + 4.0 * rng.random())
+        j, jp = rng.integers(0, p.n_u, 2)
+        lat = 2 * np.pi * rng.random()
+        P, d = _ray_point(p.R_nu, r, lat, th[j])
+        # the background ray from latitude 0, rotated onto the point P
+        P0, d0 = _ray_point(p.R_nu, r, 0.0, th[jp])
+        rot = np.arctan2(P[1], P[0]) - np.arctan2(P0[1], P0[0])
+        dp = np.array([np.cos(rot) * d0[0] - np.sin(rot) * d0[1], np.sin(rot) * d0[0] + np.cos(rot) * d0[1]])
+        shift, weight = orc.cyl_pair(p, r, int(j), int(jp))
+        assert abs(np.angle(np.exp(1j * (rot - lat - shift)))) < 1e-12  # Phi' - Phi, mod 2 pi
+        x = p.R_nu / r
+        wc = np.cos(th[jp]) / np.sqrt(1 - (x * np.sin(th[jp])) ** 2) * np.pi / p.n_u
+        assert weight == pytest.approx(wc * (1.0 - d @ dp), rel=1e-12, abs=1e-15)
+
+
+def test_cylinder_weights_cover_the_visible_arc(orc):
+    """For a state equal on every trajectory the moments are closed forms:
+    sum_j cos(theta_j)/cos(alpha_j) dtheta -> int cos th / sqrt(1 - x^2 sin^2 th)
+    dth = (2/x) asin(x) (so mu0 x M0 / S is the arc 2 asin(x) the cylinder
+    fills in the sky of the point); the cos(alpha) moment -> int cos th dth = 2;
+    the sin(alpha) moment vanishes (theta -> -theta)."""
+    p = _cyl(n_u=4000, n_phi=1, n_E=1, eps=0.0)
+    rho = orc.init_state(p)
+    r = 15.0
+    x = p.R_nu / r
+    M = orc.moments_ex(p, rho, r).reshape(4, 4)
+    R = orc.unpack(rho, 2).reshape(2, p.n_u, 2, 2)
+    S = (R[0, 0] - np.conj(R[1, 0])) * (p.E_max - p.E_min)  # dE times the one energy bin, any trajectory
+    assert M[0, 0] == pytest.approx(S[0, 0].real * 2 * np.arcsin(x) / x, rel=1e-6)
+    assert M[1, 0] == pytest.approx(S[0, 0].real * 2.0, rel=1e-6)
+    assert abs(M[2, 0]) < 1e-12 * abs(M[0, 0])
+
+
+@pytest.mark.parametrize("stepper", [I.RK4, I.EXPH])
+def test_cylinder_uniform_latitudes_equal_one_latitude(orc, stepper):
+    """A state the same at every latitude stays so, and equals the model with
+    one latitude bin, where G = mu (M0 - cos(alpha) M1 - sin(alpha) M2) from
+    three moments: the interpolated pair sum and the moment sum agree."""
+    p = _cyl(stepper=stepper, n_steps=40)
+    one = p.replace(n_phi=1)
+    rho1 = orc.init_state(one)
+    rho = np.ascontiguousarray(np.broadcast_to(rho1.reshape(2, p.n_u, 1, p.n_E, 4),
+                                               (2, p.n_u, p.n_phi, p.n_E, 4))).reshape(-1)
+    a, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    b, st1, _ = orc.evolve(one, rho1, p.r0, p.h, p.n_steps)
+    assert st == 0 and st1 == 0
+    a = a.reshape(2, p.n_u, p.n_phi, p.n_E, 4)
+    assert np.abs(b - rho1).max() > 1e-4
+    for k in range(p.n_phi):
+        assert np.abs(a[:, :, k] - b.reshape(2, p.n_u, p.n_E, 4)).max() < 1e-12
+
+
+def test_cylinder_rotation_and_mirror(orc):
+    """The model is invariant under a rotation by one latitude bin and under
+    the mirror (Phi, theta) -> (-Phi, -theta): evolving the rotated or
+    mirrored state gives the rotated or mirrored result."""
+    p = _cyl(n_steps=30)
+    rho = orc.init_state(p).reshape(2, p.n_u, p.n_phi, p.n_E, 4)
+    out, st, _ = orc.evolve(p, rho.reshape(-1), p.r0, p.h, p.n_steps)
+    out = out.reshape(rho.shape)
+    rot, _, _ = orc.evolve(p, np.roll(rho, 1, axis=2).reshape(-1), p.r0, p.h, p.n_steps)
+    assert np.abs(rot.reshape(rho.shape) - np.roll(out, 1, axis=2)).max() < 1e-14
+    mir = rho[:, ::-1, ::-1]
+    m, _, _ = orc.evolve(p, np.ascontiguousarray(mir).reshape(-1), p.r0, p.h, p.n_steps)
+    assert np.abs(m.reshape(rho.shape) - out[:, ::-1, ::-1]).max() < 1e-12
+    assert np.abs(out - rho).max() > 1e-4
+
+
+@pytest.mark.parametrize("stepper,tol", [(I.RK4, 2e-8), (I.EXPH, 1e-11)])
+def test_cylinder_vacuum_survival(orc, stepper, tol):
+    """P1 on the cylinder's trajectories: mu = A = 0 gives P_ee = 1 -
+    sin^2(2 theta) sin^2(Delta L/2) with L = sqrt(r^2 - R^2 sin^2 th) between
+    r0 and r1 (the chord of a straight ray whose impact parameter is R sin th)."""
+    p = _cyl(n_E=12, n_u=7, n_phi=3, stepper=stepper, mu0=0.0, eps=0.0, theta=(0.3, 0, 0), hierarchy=-1,
+             E_min=1.0, E_max=13.0, r0=20.0, r1=30.0, n_steps=1000)
+    E, u, phi, Hv = orc.tables(p)
+    out, st, _ = orc.evolve(p, orc.init_state(p), p.r0, p.h, p.n_steps)
+    assert st == 0
+    M = orc.unpack(out, 2).reshape(2, p.n_u, p.n_phi, p.n_E, 2, 2)
+    th = -np.pi / 2 + (np.arange(p.n_u) + 0.5) * np.pi / p.n_u
+    b2 = (p.R_nu * np.sin(th)) ** 2
+    L = np.sqrt(p.r1 ** 2 - b2) - np.sqrt(p.r0 ** 2 - b2)
+    Delta = orc.vac_coeff() * p.hierarchy * p.dm2[0] / E
+    Pee = 1 - np.sin(2 * 0.3) ** 2 * np.sin(np.outer(L, Delta) / 2) ** 2
+    for s, (ie, ix) in enumerate([(0, 2), (1, 3)]):
+        want = phi[ix] + (phi[ie] - phi[ix]) * Pee
+        for k in range(p.n_phi):
+            assert np.abs(M[s, :, k, :, 0, 0].real - want).max() < tol * phi[0].max()
