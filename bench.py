@@ -291,6 +291,10 @@ def run_xf(args):
     if args.precision == "fp64" and not args.skip_psi:
         psi = run_psi(args, xf, I, torch, stream, flush, barrier, world, 152 * 4 * 2070.0 * 1e6 / 1e12)
 
+    cylinder = None
+    if args.precision == "fp64" and not args.skip_cylinder:
+        cylinder = run_cylinder(args, xf, I, torch, stream, flush, barrier, world, 152 * 4 * 2070.0 * 1e6 / 1e12)
+
     serving = None
     if args.precision == "fp64" and not args.skip_serve and rank == 0:
         serving = run_serving(args, xf, I, torch)
@@ -354,7 +358,7 @@ def run_xf(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "fp32_m64": fp32, "fp32_variants": variants, "batched": batched, "adaptive": adaptive, "azimuth": azimuth, "psi_form": psi, "serving": serving, "clocks": clk, "gpu_launches": args.steps,
+            "fp32_m64": fp32, "fp32_variants": variants, "batched": batched, "adaptive": adaptive, "azimuth": azimuth, "psi_form": psi, "cylinder": cylinder, "serving": serving, "clocks": clk, "gpu_launches": args.steps,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -472,6 +476,47 @@ def run_psi(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
             "ms_per_step": 1e3 * t / args.steps, "radial_steps_per_step": chunk, "precision": "FP64",
             "ctas": ctas, "threads": threads, "achieved_tflops_fp64": flops / t / 1e12,
             "frac_of_fp64_peak": flops / t / 1e12 / peak_tflops}
+
+
+def run_cylinder(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
+    """The cylinder/line model (Eq. 3.20): 512 emission angles x 128 latitudes
+    x 100 energies x nu/nubar (1.3e7 bins), two flavors, FP64, the
+    predictor-corrector from 20 km; one bench step = 10 radial steps.  Per
+    stage every trajectory sums over all 512 angle bins at their latitude
+    offsets (the angle-pair contraction), then updates its 200 bins."""
+    p = I.Problem(n_E=100, n_u=512, n_phi=128, n_f=2, geometry=I.CYLINDER, stepper=I.EXPH, mu0=1e3, eps=1e-6,
+                  r0=20.0, r1=30.0, n_steps=1000, seed=7)
+    c = xf.Context(p, stream=stream)
+    c.init_state(p.r0)
+    chunk = 10
+    for _ in range(args.warmup):
+        c.step_async(chunk, p.h)
+    c.sync()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        c.step_async(chunk, p.h)
+        ends[k].record(stream)
+    c.sync()
+    barrier()
+    t = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) * 1e-3, world)
+    ctas, threads, _ = c.launch_info()
+    c.close()
+    steps = chunk * args.steps
+    S = p.n_f ** 2 - 1
+    traj = p.n_u * p.n_phi
+    # per bin-step: the two-flavor predictor-corrector update with plain
+    # trajectory sums (105 flop); per trajectory and stage: 2 S FMA per angle bin
+    bin_flops = 105.0 * p.n_bins * steps
+    pair_flops = 2.0 * traj * p.n_u * 4 * S * steps
+    return {"value": p.n_bins * steps * world / t, "unit": UNIT, "bins": p.n_bins, "n_u": p.n_u, "n_phi": p.n_phi,
+            "n_E": p.n_E, "n_f": p.n_f, "ms_per_radial_step": 1e3 * t / steps, "precision": "FP64",
+            "ctas": ctas, "threads": threads, "angle_pair_flop_share": pair_flops / (pair_flops + bin_flops),
+            "achieved_tflops_fp64": (bin_flops + pair_flops) / t / 1e12,
+            "frac_of_fp64_peak": (bin_flops + pair_flops) / t / 1e12 / peak_tflops}
 
 
 def run_batched(args, xf, I, torch, stream, flush, barrier, world):
@@ -620,6 +665,7 @@ def main():
     ap.add_argument("--skip-adapt", action="store_true")
     ap.add_argument("--skip-azimuth", action="store_true")
     ap.add_argument("--skip-psi", action="store_true", help="skip the wavefunction-form leg")
+    ap.add_argument("--skip-cylinder", action="store_true", help="skip the cylinder-model leg")
     ap.add_argument("--skip-tune", action="store_true", help="batched leg: keep the automatic tile size")
     ap.add_argument("--skip-batch-fp64", action="store_true", help="batched leg: skip the FP64 run of the ensemble")
     ap.add_argument("--adapt-iters", type=int, default=30, help="attempts per error-controlled bench step")

@@ -92,7 +92,20 @@ enum xf_geometry {
     XF_GEOM_BULB = 0,         /* Eq. 3.13-3.15: w_u = x^2 du/(2 cos_u), x = R/r; dl/dr = 1/cos_u */
     XF_GEOM_MU_R4 = 1,        /* literal mu0 (R/r)^4 with r-independent weights du; dl/dr = 1/cos_u */
     XF_GEOM_SINGLE_ANGLE = 2, /* Eq. 3.16-3.17: G = mu0 D(r/R) dE sum(rho - conj rho_bar), dl = dr */
-    XF_GEOM_CONST = 3         /* isotropic, constant mu0: G = mu0 dE du sum(...), dl = dr */
+    XF_GEOM_CONST = 3,        /* isotropic, constant mu0: G = mu0 dE du sum(...), dl = dr */
+    XF_GEOM_CYLINDER = 4      /* Sec. 3.2.5, Eq. 3.20: an infinite cylinder of radius R_nu emitting
+                                 perpendicular to its axis.  n_u angle bins theta_j = -pi/2 +
+                                 (j + 1/2) pi/n_u from the outward normal (clockwise), n_phi
+                                 latitude bins Phi_k = (k + 1/2) 2 pi/n_phi; alpha_j =
+                                 asin((R/r) sin theta_j), dl/dr = 1/cos(alpha_j);
+                                 G_jk = mu0 (R/r) dE sum_j' w_j' (1 - cos(alpha_j - alpha_j'))
+                                 D(Phi', j'), w_j' = cos(theta_j')/cos(alpha_j') pi/n_u,
+                                 Phi' = Phi_k + theta_j' - theta_j + alpha_j - alpha_j', D the
+                                 per-trajectory sum over E of (rho_nu - conj rho_nubar), read at
+                                 Phi' by periodic linear interpolation.  Fixed steps, XF_FP64 or
+                                 XF_FP32_M64, density-matrix form, n_u <= 2048, one problem per
+                                 context, not strict.  The moments (xf_moments_ex) are the
+                                 latitude averages of w, w cos(alpha), w sin(alpha) */
 };
 enum xf_form {
     XF_FORM_RHO = 0, /* density matrices rho(u, E), Eq. 3.1-3.4 */
@@ -124,10 +137,12 @@ typedef struct xf_params {
     int32_t geometry;   /* enum xf_geometry */
     int32_t hierarchy;  /* +1 normal, -1 inverted: sign of dm2 (2 fl) / dm2_31 (3 fl) */
     int32_t matter;     /* enum xf_matter */
-    int32_t n_phi;      /* azimuth bins of the extended bulb model (Eq. 3.18) [Pbins]; 1 = the
-                           azimuthally symmetric bulb model (default).  > 1 needs XF_GEOM_BULB, a
-                           fixed-step stepper and XF_FP64 or XF_FP32_M64.  A problem then has
-                           2 n_u n_phi n_E bins, ordered [s][u][phi][E] in every host array */
+    int32_t n_phi;      /* azimuth bins of the extended bulb model (Eq. 3.18) [Pbins], or the
+                           latitude bins of XF_GEOM_CYLINDER; 1 = the
+                           azimuthally symmetric bulb model (default).  > 1 needs XF_GEOM_BULB
+                           or XF_GEOM_CYLINDER, a fixed-step stepper and XF_FP64 or XF_FP32_M64.
+                           A problem has 2 n_u n_phi n_E bins, ordered [s][u][phi][E] in every
+                           host array */
     int32_t form;       /* enum xf_form: what a bin's state is (default XF_FORM_RHO) */
     int32_t strict;     /* 1: xf_step / xf_batch_step with RK4 return XF_E_UNSTABLE, without
                            stepping, when for some angle u

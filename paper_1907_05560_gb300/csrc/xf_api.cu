@@ -18,6 +18,7 @@
 #include "xf_adapt.cuh"
 #include "xf_aux.cuh"
 #include "xf_kernels.h"
+#include "xf_cyl.cuh"
 #include "xf_pack.h"
 
 using namespace xf;
@@ -164,12 +165,21 @@ int validate(xf_ctx *c, const xf_params *p, int n_E, int n_u, int nf)
     }
     if (p->precision < XF_FP64 || p->precision > XF_FP32_M64_RENORM)
         return fail(c, XF_E_ARG, "bad precision %d", p->precision);
-    if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CONST) return fail(c, XF_E_ARG, "bad geometry %d", p->geometry);
+    if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CYLINDER)
+        return fail(c, XF_E_ARG, "bad geometry %d", p->geometry);
+    if (p->geometry == XF_GEOM_CYLINDER) {
+        if (p->stepper == XF_EXPH_ADAPTIVE || (p->precision != XF_FP64 && p->precision != XF_FP32_M64) ||
+            p->form != XF_FORM_RHO || p->strict)
+            return fail(c, XF_E_UNSUPPORTED,
+                        "the cylinder model runs fixed steps in FP64 or FP32_M64, density matrices, not strict");
+        if (n_u > xf::CYL_MAX_U) return fail(c, XF_E_UNSUPPORTED, "the cylinder model takes n_u <= %d", xf::CYL_MAX_U);
+    }
     if (p->geometry == XF_GEOM_SINGLE_ANGLE && n_u != 1) return fail(c, XF_E_ARG, "single-angle geometry needs n_u == 1");
     if (p->n_phi < 1) return fail(c, XF_E_ARG, "n_phi must be >= 1");
     if ((long long)n_E * n_u * p->n_phi > (long long)(INT_MAX / 16)) return fail(c, XF_E_ARG, "n_E * n_u * n_phi too large");
     if (p->n_phi > 1) {
-        if (p->geometry != XF_GEOM_BULB) return fail(c, XF_E_ARG, "azimuth bins extend the bulb geometry only");
+        if (p->geometry != XF_GEOM_BULB && p->geometry != XF_GEOM_CYLINDER)
+            return fail(c, XF_E_ARG, "azimuth (latitude) bins extend the bulb (cylinder) geometry only");
         if (p->stepper == XF_EXPH_ADAPTIVE || (p->precision != XF_FP64 && p->precision != XF_FP32_M64))
             return fail(c, XF_E_UNSUPPORTED, "azimuth bins run with fixed steps in FP64 or FP32_M64");
     }
@@ -284,8 +294,11 @@ double pair_cost(const InstHost &in) { return in.nf == 3 ? 10.0 : 1.0; }
 
 // Tile every instance into runs of at most TP pairs, then give
 // each CTA a contiguous run of tiles of about equal cost.
+int plan_launch_cyl(xf_ctx *c);
+
 int plan_launch(xf_ctx *c)
 {
+    if (c->cyl) return plan_launch_cyl(c);
     const int nt = c->kern.nt;
     int occ_free = 0;
     XF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_free, c->kern.fn, nt, 0), "occupancy");
@@ -384,6 +397,65 @@ int plan_launch(xf_ctx *c)
         c->max_tiles = T;
     }
     XF_CUDA(c, cudaMemcpy(c->tiles_d, c->tiles.data(), sizeof(Tile) * T, cudaMemcpyHostToDevice), "copy tiles");
+    XF_CUDA(c, cudaMemcpy(c->cta_tiles_d, ct.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice), "copy tiling");
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return XF_OK;
+}
+
+// Cylinder model: one problem; CTA c owns tile c, a run of whole trajectories
+// (about T / G each), and a table of 4 doubles per angle bin; the partials
+// buffer holds two slots of per-trajectory sums (8 doubles each).
+int plan_launch_cyl(xf_ctx *c)
+{
+    InstHost &in = c->in[0];
+    c->tiles.clear();
+    c->dirty = false;
+    if (!in.active) {
+        c->G = 0;
+        c->cta_tiles.assign(1, 0);
+        return XF_OK;
+    }
+    const int T = in.n_u * in.n_phi, nw = c->kern.nt / 32;
+    const size_t smem = (size_t)4 * in.n_u * sizeof(double);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(c->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, XF_E_UNSUPPORTED, "angle table needs %zu bytes of shared memory", smem);
+    }
+    int occ = 0;
+    XF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->kern.fn, c->kern.nt, smem), "occupancy");
+    if (occ < 1) return fail(c, XF_E_UNSUPPORTED, "kernel cannot be resident (smem %zu)", smem);
+    int G = std::min((T + nw - 1) / nw, occ * c->num_sms);
+    if (c->grid_request > 0) G = std::min(G, c->grid_request);
+    G = std::max(G, 1);
+    for (int g = 0; g < G; ++g) {
+        const int ta = (int)((long long)T * g / G), tb = (int)((long long)T * (g + 1) / G);
+        c->tiles.push_back({0, ta * in.n_E, (tb - ta) * in.n_E, 0});
+    }
+    in.tile_begin = 0;
+    in.tile_end = G;
+    std::vector<int> ct(G + 1);
+    for (int g = 0; g <= G; ++g) ct[g] = g;
+    c->G = G;
+    c->tile_pairs = 0;
+    c->span_max = in.n_u;
+    c->smem = smem;
+    c->cta_tiles = ct;
+    const size_t need = std::max((size_t)2 * G * NVMAX, (size_t)2 * T * xf::CYL_DS);
+    if (G > c->max_tiles || need > c->partials_doubles) {
+        if (c->partials) dev_free(c, c->partials);
+        c->partials = (double *)dev_alloc(c, sizeof(double) * need);
+        c->partials_doubles = c->partials ? need : 0;
+        c->tiles_d = (Tile *)dev_alloc(c, sizeof(Tile) * (size_t)G);
+        c->cta_tiles_d = (int *)dev_alloc(c, sizeof(int) * (size_t)(G + 1));
+        if (!c->partials || !c->tiles_d || !c->cta_tiles_d)
+            return fail(c, XF_E_NOMEM, "device allocation of the tile tables failed");
+        c->max_tiles = G;
+    }
+    XF_CUDA(c, cudaMemcpy(c->tiles_d, c->tiles.data(), sizeof(Tile) * G, cudaMemcpyHostToDevice), "copy tiles");
     XF_CUDA(c, cudaMemcpy(c->cta_tiles_d, ct.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice), "copy tiling");
     if (c->graph) {
         cudaGraphExecDestroy(c->graph);
@@ -532,8 +604,10 @@ int enqueue_run(xf_ctx *c, long long n, cudaStream_t stream)
     a.skip_cta = c->skip_cta;
     a.apos = c->apos_d;
     a.tstate = c->tstate_d;
+    a.first_bad = c->bar + 1;
     if (c->G == 0) return XF_OK;
     XF_CUDA(c, cudaMemsetAsync(c->bar, 0, sizeof(unsigned), stream), "reset barrier");
+    if (c->cyl) XF_CUDA(c, cudaMemsetAsync(c->bar + 1, 0xff, sizeof(unsigned), stream), "reset flag");
     void *args[] = {&a};
     cudaError_t e;
     if (c->G > 1)
@@ -816,7 +890,7 @@ int setup_problem(xf_ctx *c, int i, const xf_problem &prob)
 
 // A ctx with its control buffers and an arena of arena_bytes, no problem yet.
 int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, int nfm, const xf_allocator *alloc,
-               xf_ctx **out, int nmom = 2, int form = XF_FORM_RHO)
+               xf_ctx **out, int nmom = 2, int form = XF_FORM_RHO, bool cyl = false)
 {
     xf_ctx *c = new (std::nothrow) xf_ctx();
     if (!c) return fail(nullptr, XF_E_NOMEM, "host allocation failed");
@@ -840,7 +914,10 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
     const int st = (stepper == XF_RK4) ? STEP_RK4 : STEP_EXPH;
     c->nmom = nmom;
     c->form = form;
-    if (form == XF_FORM_PSI)
+    c->cyl = cyl;
+    if (cyl)
+        c->kern = run_kernel_cyl(nfm, st, c->real_bytes == 8);
+    else if (form == XF_FORM_PSI)
         c->kern = run_kernel_psi(nfm, st, c->real_bytes == 8);
     else if (stepper == XF_EXPH_ADAPTIVE)
         c->kern = run_kernel_adapt(nfm, c->real_bytes == 8);
@@ -897,9 +974,10 @@ int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ct
     *out = nullptr;
     if (n <= 0 || !probs) return fail(nullptr, XF_E_ARG, "need at least one problem");
     if (alloc && (!alloc->alloc || !alloc->free)) return fail(nullptr, XF_E_ARG, "allocator callbacks missing");
-    bool has2 = false, has3 = false, has_phi = false;
+    bool has2 = false, has3 = false, has_phi = false, has_cyl = false;
     for (int i = 0; i < n; ++i) {
         has_phi = has_phi || probs[i].params.n_phi > 1;
+        has_cyl = has_cyl || probs[i].params.geometry == XF_GEOM_CYLINDER;
         int rc = validate(nullptr, &probs[i].params, probs[i].n_E, probs[i].n_u, probs[i].n_flavor);
         if (rc) {
             if (n > 1) g_create_error = "problem " + std::to_string(i) + ": " + g_create_error;
@@ -910,13 +988,15 @@ int create_pack(int n, const xf_problem *probs, const xf_allocator *alloc, xf_ct
             return fail(nullptr, XF_E_ARG, "all problems of a pack need the same stepper, precision and form");
         (probs[i].n_flavor == 2 ? has2 : has3) = true;
     }
+    if (has_cyl && n > 1) return fail(nullptr, XF_E_UNSUPPORTED, "a cylinder-model problem runs alone in its context");
     long long bytes = 0;
     for (int i = 0; i < n; ++i)
         bytes += block_bytes(probs[i].n_E, probs[i].n_u * probs[i].params.n_phi, probs[i].n_flavor,
                              probs[0].params.precision, probs[0].params.form);
     xf_ctx *c = nullptr;
     int rc = create_ctx(n, bytes, probs[0].params.stepper, probs[0].params.precision,
-                        (has2 && has3) ? 0 : (has3 ? 3 : 2), alloc, &c, has_phi ? 4 : 2, probs[0].params.form);
+                        (has2 && has3) ? 0 : (has3 ? 3 : 2), alloc, &c, has_phi ? 4 : 2, probs[0].params.form,
+                        has_cyl);
     if (rc) return rc;
     for (int i = 0; i < n && !rc; ++i) rc = setup_problem(c, i, probs[i]);
     if (!rc) rc = plan_launch(c);
@@ -948,6 +1028,8 @@ int add_problem(xf_ctx *c, const xf_problem &prob, const double *rho, double r_k
         return fail(c, XF_E_ARG, "stepper, precision or form differs from the pack's");
     if (c->nfm && prob.n_flavor != c->nfm) return fail(c, XF_E_ARG, "flavor count differs from the pack's");
     if (prob.params.n_phi > 1 && c->nmom != 4) return fail(c, XF_E_UNSUPPORTED, "azimuth bins need a 4-moment pack");
+    if (prob.params.geometry == XF_GEOM_CYLINDER || c->cyl)
+        return fail(c, XF_E_UNSUPPORTED, "a cylinder-model problem runs alone in its context");
     if (!std::isfinite(dr_km) || dr_km <= 0) return fail(c, XF_E_ARG, "dr_km must be finite and > 0");
     int i = -1;
     for (int k = 0; k < (int)c->in.size(); ++k)
@@ -1634,6 +1716,7 @@ int xf_batch_run_moments(xf_ctx *c, int inst, double *M0, double *M1, size_t n_d
     if (!h) return c ? fail(c, XF_E_ARG, "bad instance index %d", inst) : XF_E_ARG;
     if (!M0 || !M1) return fail(c, XF_E_ARG, "M0/M1 NULL");
     if (n_doubles != (size_t)h->nf * h->nf) return fail(c, XF_E_ARG, "n_doubles must be n_f*n_f");
+    if (c->cyl) return fail(c, XF_E_UNSUPPORTED, "the cylinder model's G is not a sum of two moments");
     if (c->pending) {
         int rc = sync_status(c);
         if (rc) return rc;

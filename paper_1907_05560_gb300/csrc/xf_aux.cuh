@@ -184,12 +184,24 @@ struct MomArgs {
 
 // Weights of trajectory t = j n_phi + k for the moments M0..M3 at radius m.r
 // (Eq. 3.13-3.15 and, with azimuth bins, Eq. 3.18: each bin carries 1/n_phi
-// of its zenith bin's weight, M2 / M3 weighted by sin th' cos / sin ph').
+// of its zenith bin's weight, M2 / M3 weighted by sin th' cos / sin ph'; the
+// cylinder model's latitude-averaged moments, Eq. 3.20).
 __device__ __forceinline__ void mom_weights(const MomArgs &m, int t, double *w)
 {
     const int j = t / m.n_phi, k = t - j * m.n_phi;
     w[0] = m.du;
     w[1] = w[2] = w[3] = 0.0;
+    if (m.geometry == 4) { // cylinder (Eq. 3.20): latitude averages of w, w cos(alpha), w sin(alpha)
+        const double pi = 3.14159265358979323846;
+        double st, ct;
+        sincos(-0.5 * pi + (j + 0.5) * pi / m.n_u, &st, &ct);
+        const double sa = (m.R / m.r) * st, ca = sqrt(1.0 - sa * sa);
+        const double wc = ct / ca * (pi / m.n_u);
+        w[0] = wc / m.n_phi;
+        w[1] = wc * ca / m.n_phi;
+        w[2] = wc * sa / m.n_phi;
+        return;
+    }
     if (m.geometry == 0 || m.geometry == 1) {
         double x = m.R / m.r, x2 = x * x, u = (j + 0.5) * m.du;
         double c = sqrt(1.0 - x2 * u);

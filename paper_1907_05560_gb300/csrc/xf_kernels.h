@@ -1,5 +1,6 @@
 // xf_kernels.h -- host-visible handles of the persistent integrator kernels
-// (instantiated in xf_k64.cu, xf_k32*.cu and xf_ka.cu, compiled in parallel).
+// (instantiated in xf_k64.cu, xf_k32*.cu, xf_ka.cu, xf_kaz.cu, xf_kpsi.cu and
+// xf_kcyl.cu, compiled in parallel).
 #pragma once
 
 #include "xf_run.cuh"
@@ -22,5 +23,7 @@ RunKernel run_kernel_adapt(int nfm, bool fp64);
 RunKernel run_kernel_azimuth(int nfm, int stepper, bool fp64);
 // the wavefunction form, plain arithmetic, FP64 or FP32 bins
 RunKernel run_kernel_psi(int nfm, int stepper, bool fp64);
+// the cylinder/line model (one problem per launch), FP64 or FP32 bins
+RunKernel run_kernel_cyl(int nf, int stepper, bool fp64);
 
 } // namespace xf

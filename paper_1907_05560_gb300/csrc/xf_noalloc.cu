@@ -361,6 +361,8 @@ extern "C" int xf_step_noalloc(int n_E, int n_u, int n_flavor, const xf_params *
     if (p->n_phi != 1) return noalloc_fail(XF_E_UNSUPPORTED, "azimuth bins are not built for this entry point");
     if (p->form != XF_FORM_RHO)
         return noalloc_fail(XF_E_UNSUPPORTED, "the wavefunction form is not built for this entry point");
+    if (p->geometry == XF_GEOM_CYLINDER)
+        return noalloc_fail(XF_E_UNSUPPORTED, "the cylinder model is not built for this entry point");
     if (p->stepper != XF_RK4 && p->stepper != XF_EXPH) return noalloc_fail(XF_E_ARG, "bad stepper");
     if (p->precision < XF_FP64 || p->precision > XF_FP32_M64_RENORM) return noalloc_fail(XF_E_ARG, "bad precision");
     if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CONST) return noalloc_fail(XF_E_ARG, "bad geometry");

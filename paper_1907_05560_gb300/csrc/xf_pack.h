@@ -114,6 +114,7 @@ struct xf_ctx {
     int real_bytes = 8, precision = XF_FP64, stepper = XF_RK4, nfm = 2;
     int nmom = 2; // moments per stage: 2, or 4 when a problem has azimuth bins (extended bulb model)
     int form = XF_FORM_RHO; // what the state planes hold (one form per pack)
+    bool cyl = false;       // the cylinder model's kernel (one problem)
     cudaStream_t stream = nullptr;
     xf_allocator alloc{};
     bool has_alloc = false;
@@ -140,6 +141,7 @@ struct xf_ctx {
     xfp::AdaptPos *apos_d = nullptr, *tstate_d = nullptr; // error-controlled step only
     double *partials = nullptr, *mom_out = nullptr, *mom_part = nullptr, *mom_full = nullptr;
     int mom_part_slots = 0;
+    size_t partials_doubles = 0; // cylinder model: size of the partials buffer
     unsigned *bar = nullptr;
     int *err = nullptr, *bad = nullptr;
 

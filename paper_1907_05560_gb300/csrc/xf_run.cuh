@@ -31,7 +31,7 @@
 
 namespace xf {
 
-enum { GEOM_BULB = 0, GEOM_MU_R4 = 1, GEOM_SA = 2, GEOM_CONST = 3 };
+enum { GEOM_BULB = 0, GEOM_MU_R4 = 1, GEOM_SA = 2, GEOM_CONST = 3, GEOM_CYL = 4 };
 enum { MAT_NONE = 0, MAT_POWER = 1, MAT_EXP = 2 };
 enum { STEP_RK4 = 0, STEP_EXPH = 1, STEP_ADAPT = 2 };
 enum { ERR_NONFINITE = 1, ERR_BARRIER = 2 };
@@ -105,6 +105,8 @@ struct RunArgs {
     int skip_cta;           // test hook: this CTA leaves at its first barrier (-1: none)
     AdaptPos *apos;         // error-controlled step: [n_inst] progress (else unused)
     AdaptPos *tstate;       // error-controlled step: [n_tiles] per-tile copies of it
+    unsigned *first_bad;    // cylinder model: lowest barrier number after which a non-finite
+                            // trajectory sum is read (all ones at launch)
 };
 
 __device__ __forceinline__ unsigned long long gtimer()
@@ -174,6 +176,7 @@ __host__ __device__ __forceinline__ double mu_eff(const Inst &a, double r)
 {
     double x = a.R / r, x2 = x * x;
     if (a.geometry == GEOM_MU_R4) return a.mu0 * x2 * x2;
+    if (a.geometry == GEOM_CYL) return a.mu0 * x; // a line source thins as 1/r
     if (a.geometry == GEOM_SA) {
         double t = 1.0 - sqrt(1.0 - x2); // Eq. 3.17
         return a.mu0 * 0.5 * t * t;

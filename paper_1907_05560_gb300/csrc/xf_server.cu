@@ -217,6 +217,7 @@ int xf_submit(xf_server *s, const xf_job *job, uint64_t *job_id)
     if (validate(nullptr, &p.params, p.n_E, p.n_u, p.n_flavor)) return XF_E_ARG;
     if (p.params.n_phi != 1) return XF_E_UNSUPPORTED; // the server's packs run the bulb model's two moments
     if (p.params.form != XF_FORM_RHO) return XF_E_UNSUPPORTED; // the server's packs hold density matrices
+    if (p.params.geometry == XF_GEOM_CYLINDER) return XF_E_UNSUPPORTED; // runs alone in its context
     if (p.params.stepper != s->cfg.stepper || p.params.precision != s->cfg.precision) return XF_E_ARG;
     if (s->cfg.n_flavor && p.n_flavor != s->cfg.n_flavor) return XF_E_ARG;
     if (!std::isfinite(job->r0_km) || job->r0_km < p.params.R_nu_km || !std::isfinite(job->dr_km) ||
