@@ -289,8 +289,16 @@ int elementwise_grid(xf_ctx *c, const InstHost &in)
     return (int)std::max<long long>(1, std::min<long long>(g, (long long)c->num_sms * 16));
 }
 
-// Cost weight of a pair (relative work per stage): three flavors ~10x two.
-double pair_cost(const InstHost &in) { return in.nf == 3 ? 10.0 : 1.0; }
+// Cost weight of a pair (relative work per step): the per-bin operation
+// counts of the steppers, three flavors against two: 2631 / 120 ~ 22 for the
+// predictor-corrector (a 3x3 eigendecomposition against a Bloch rotation),
+// 684 / 172 ~ 4 for RK4 (commutators); the error-controlled attempt as the
+// predictor-corrector.
+double pair_cost(const xf_ctx *c, const InstHost &in)
+{
+    if (in.nf != 3) return 1.0;
+    return c->stepper == XF_RK4 ? 4.0 : 22.0;
+}
 
 // Tile every instance into runs of at most TP pairs, then give
 // each CTA a contiguous run of tiles of about equal cost.
@@ -309,7 +317,7 @@ int plan_launch(xf_ctx *c)
     for (const InstHost &in : c->in) {
         if (!in.active) continue;
         total_pairs += in.n_pairs;
-        total_cost += pair_cost(in) * in.n_pairs;
+        total_cost += pair_cost(c, in) * in.n_pairs;
         ++n_active;
     }
     // tile size: one problem -> one tile per co-resident CTA slot (every CTA
@@ -372,7 +380,7 @@ int plan_launch(xf_ctx *c)
     int cta = 1;
     for (int t = 0; t < T && cta < G; ++t) {
         const InstHost &in = c->in[c->tiles[t].inst];
-        acc += pair_cost(in) * c->tiles[t].np;
+        acc += pair_cost(c, in) * c->tiles[t].np;
         const bool must_cut = (T - (t + 1)) == (G - cta); // one tile left per remaining CTA
         if ((acc >= total_cost * cta / G || must_cut) && T - (t + 1) >= G - cta) ct[cta++] = t + 1;
     }

@@ -119,7 +119,8 @@ def test_moments_outputs_and_checkpoint(xf, orc):
     p = CASES["3f-rk4"]
     c = xf.Context(p)
     c.init_state(p.r0)
-    assert np.array_equal(c.get_state()[0], orc.init_state(p))
+    seeded = orc.init_state(p)
+    assert np.abs(c.get_state()[0] - seeded).max() < 1e-15 * np.abs(seeded).max()
     c.step(20, p.h)
     rho, r, _ = c.get_state()
     M = c.moments_ex()
