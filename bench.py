@@ -129,16 +129,17 @@ def measured_peaks():
 # FP64 floating-point operations per bin-step of the predictor-corrector in
 # three flavors (two propagator applications per step), counted from the
 # per-bin formulas (+ - * / sqrt each 1, FMA 2, sincos not counted) by
-# running them once with a counting number type; the Jacobi eigensolver is
-# counted at the sweep number measured on this workload.
-FLOPS_PER_BIN_STEP = {("exph", 3): 2631, ("rk4", 3): 684, ("exph", 2): 120, ("rk4", 2): 172}
+# running them once with a counting number type that drops operations on
+# structural zeros (a product with a literal zero, a sum with one); the
+# Jacobi eigensolver is counted at the sweep number measured on this workload.
+FLOPS_PER_BIN_STEP = {("exph", 3): 2089, ("rk4", 3): 684, ("exph", 2): 120, ("rk4", 2): 172}
 # one attempt of the error-controlled step (four Hamiltonians, five propagations,
 # one shared eigendecomposition), counted the same way
-FLOPS_PER_BIN_ATTEMPT = {3: 5897, 2: 268}
+FLOPS_PER_BIN_ATTEMPT = {3: 4741, 2: 268}
 # the wavefunction form (one psi per initial flavor), counted the same way:
 # per stage the propagation of n_f wavefunctions and rho's traceless part
 # rebuilt from them for the moments
-FLOPS_PER_BIN_STEP_PSI = {("exph", 3): 2621, ("rk4", 3): 1702, ("exph", 2): 276, ("rk4", 2): 536}
+FLOPS_PER_BIN_STEP_PSI = {("exph", 3): 2205, ("rk4", 3): 1666, ("exph", 2): 268, ("rk4", 2): 520}
 
 
 def oracle_sample(problem, n_steps, threads):

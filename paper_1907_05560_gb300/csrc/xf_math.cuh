@@ -207,13 +207,21 @@ __host__ __device__ constexpr int oidx(int a, int b) { return a == 0 ? b - 1 : 2
 // and A_PP -> A_PP - t |A_PQ|, A_QQ -> A_QQ + t |A_PQ|.  With rD = 1/D and
 // rc = 1/c from two reciprocal square roots, the rotation needs no division
 // and no square root.
-template <typename Real, int P, int Q>
-__host__ __device__ __forceinline__ void jacobi_rot(Real *dg, cx<Real> *o, cx<Real> (*V)[3])
+// ZR: which entry of the third row R is exactly zero on entry (the pivot the
+// previous rotation of a cyclic (0,1), (0,2), (1,2) sweep zeroed): 0 none,
+// 1 A_RP, 2 A_RQ; its terms are left out (x * 0 is not folded in IEEE
+// arithmetic).
+template <typename Real, int P, int Q, int ZR = 0>
+__host__ __device__ __forceinline__ bool jacobi_angles(Real *dg, cx<Real> *o, Real *c_out, cx<Real> *se_out)
 {
     constexpr int R = 3 - P - Q;
     cx<Real> g = o[oidx(P, Q)];
     Real ag2 = g.r * g.r + g.i * g.i;
-    if (!(ag2 > Real(0))) return;
+    if (!(ag2 > Real(0))) {
+        *c_out = Real(1);
+        *se_out = mk(Real(0), Real(0));
+        return false;
+    }
     const Real d = Real(0.5) * (dg[Q] - dg[P]);
     const Real rD = rsqrt_r(d * d + ag2);
     const Real u = Real(0.5) + Real(0.5) * fabs(d) * rD; // c^2, in [1/2, 1]
@@ -229,12 +237,34 @@ __host__ __device__ __forceinline__ void jacobi_rot(Real *dg, cx<Real> *o, cx<Re
     cx<Real> aRP = (R < P) ? o[oidx(R, P)] : cj(o[oidx(P, R)]);
     cx<Real> aRQ = (R < Q) ? o[oidx(R, Q)] : cj(o[oidx(Q, R)]);
     // (J^dagger A J)_RP = c A_RP - s e^{-i phi} A_RQ,  (.)_RQ = s e^{i phi} A_RP + c A_RQ
-    cx<Real> nRP = c * aRP - sec * aRQ;
-    cx<Real> nRQ = se * aRP + c * aRQ;
+    cx<Real> nRP, nRQ;
+    if constexpr (ZR == 1) {
+        const cx<Real> m = sec * aRQ;
+        nRP = mk(-m.r, -m.i);
+        nRQ = c * aRQ;
+    } else if constexpr (ZR == 2) {
+        nRP = c * aRP;
+        nRQ = se * aRP;
+    } else {
+        nRP = c * aRP - sec * aRQ;
+        nRQ = se * aRP + c * aRQ;
+    }
     if (R < P) o[oidx(R, P)] = nRP;
     else o[oidx(P, R)] = cj(nRP);
     if (R < Q) o[oidx(R, Q)] = nRQ;
     else o[oidx(Q, R)] = cj(nRQ);
+    *c_out = c;
+    *se_out = se;
+    return true;
+}
+
+template <typename Real, int P, int Q, int ZR = 0>
+__host__ __device__ __forceinline__ void jacobi_rot(Real *dg, cx<Real> *o, cx<Real> (*V)[3])
+{
+    Real c;
+    cx<Real> se;
+    if (!jacobi_angles<Real, P, Q, ZR>(dg, o, &c, &se)) return;
+    const cx<Real> sec = cj(se);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         cx<Real> vp = V[k][P], vq = V[k][Q];
@@ -279,14 +309,36 @@ __host__ __device__ __forceinline__ void eig3(const Real *h, Real *dg, cx<Real> 
         return !(off2 > JacobiTol<Real>::rel2 * scale2);
     };
     if (converged()) return;
-    jacobi_rot<Real, 0, 1>(dg, o, V);
-    jacobi_rot<Real, 0, 2>(dg, o, V);
-    jacobi_rot<Real, 1, 2>(dg, o, V);
+    {
+        // the first sweep from V = I, with its structural zeros and real
+        // entries written out (x * 0 is not folded in IEEE arithmetic)
+        Real c1, c2, c3;
+        cx<Real> s1, s2, s3;
+        jacobi_angles<Real, 0, 1>(dg, o, &c1, &s1); // V = [[c1, s1, 0], [-s1*, c1, 0], [0, 0, 1]]
+        jacobi_angles<Real, 0, 2, 1>(dg, o, &c2, &s2); // columns 0 and 2
+        const cx<Real> m1 = mk(-s1.r, s1.i); // -conj(s1)
+        const Real v00 = c2 * c1;
+        const cx<Real> v10 = c2 * m1, v02 = c1 * s2;
+        const cx<Real> v12 = m1 * s2, v20 = mk(-s2.r, s2.i);
+        // V = [[v00, s1, v02], [v10, c1, v12], [v20, 0, c2]]
+        jacobi_angles<Real, 1, 2, 2>(dg, o, &c3, &s3); // columns 1 and 2
+        const cx<Real> s3c = cj(s3);
+        V[0][0] = mk(v00, Real(0));
+        V[1][0] = v10;
+        V[2][0] = v20;
+        V[0][1] = c3 * s1 - s3c * v02;
+        V[0][2] = s3 * s1 + c3 * v02;
+        const cx<Real> w12 = s3c * v12;
+        V[1][1] = mk(c3 * c1 - w12.r, -w12.i);
+        V[1][2] = c1 * s3 + c3 * v12;
+        V[2][1] = mk(-(c2 * s3c.r), -(c2 * s3c.i));
+        V[2][2] = mk(c3 * c2, Real(0));
+    }
     for (int sweep = 1; sweep < JacobiTol<Real>::sweeps; ++sweep) {
         if (converged()) break;
-        jacobi_rot<Real, 0, 1>(dg, o, V);
-        jacobi_rot<Real, 0, 2>(dg, o, V);
-        jacobi_rot<Real, 1, 2>(dg, o, V);
+        jacobi_rot<Real, 0, 1, 2>(dg, o, V);
+        jacobi_rot<Real, 0, 2, 1>(dg, o, V);
+        jacobi_rot<Real, 1, 2, 2>(dg, o, V);
     }
 }
 
@@ -294,17 +346,20 @@ template <typename Real>
 __host__ __device__ __forceinline__ void apply3(const Real *dg, const cx<Real> (*V)[3], StepLen<Real> dl, const Real *t,
                                                 Real *out)
 {
-    // T as a full Hermitian matrix
-    const Real t3 = -(t[0] + t[1]);
-    const cx<Real> T[3][3] = {{mk(t[0], Real(0)), mk(t[2], t[3]), mk(t[4], t[5])},
-                              {mk(t[2], -t[3]), mk(t[1], Real(0)), mk(t[6], t[7])},
-                              {mk(t[4], -t[5]), mk(t[6], -t[7]), mk(t3, Real(0))}};
-    // W = T V
+    // T: real diagonal Td, off-diagonal To[a][b] (a != b; To[b][a] = conj To[a][b])
+    const Real Td[3] = {t[0], t[1], -(t[0] + t[1])};
+    const cx<Real> To[3][3] = {{mk(Real(0), Real(0)), mk(t[2], t[3]), mk(t[4], t[5])},
+                               {mk(t[2], -t[3]), mk(Real(0), Real(0)), mk(t[6], t[7])},
+                               {mk(t[4], -t[5]), mk(t[6], -t[7]), mk(Real(0), Real(0))}};
+    // W = T V, the diagonal term as real x complex
     cx<Real> W[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) W[a][k] = T[a][0] * V[0][k] + T[a][1] * V[1][k] + T[a][2] * V[2][k];
+        for (int k = 0; k < 3; ++k) {
+            const int b1 = a == 0 ? 1 : 0, b2 = a == 2 ? 1 : 2;
+            W[a][k] = Td[a] * V[a][k] + To[a][b1] * V[b1][k] + To[a][b2] * V[b2][k];
+        }
     // R = V^dagger W (Hermitian): diag real, upper entries
     Real Rd[3];
     cx<Real> Ro[3]; // (0,1), (0,2), (1,2)
@@ -325,15 +380,18 @@ __host__ __device__ __forceinline__ void apply3(const Real *dg, const cx<Real> (
         phase_sincos(dg[1] - dg[2], dl, &s, &c);
         Ro[2] = Ro[2] * mk(c, -s);
     }
-    const cx<Real> Rm[3][3] = {{mk(Rd[0], Real(0)), Ro[0], Ro[1]},
-                               {cj(Ro[0]), mk(Rd[1], Real(0)), Ro[2]},
-                               {cj(Ro[1]), cj(Ro[2]), mk(Rd[2], Real(0))}};
-    // Z = V R', T' = Z V^dagger
+    const cx<Real> Rm[3][3] = {{mk(Real(0), Real(0)), Ro[0], Ro[1]},
+                               {cj(Ro[0]), mk(Real(0), Real(0)), Ro[2]},
+                               {cj(Ro[1]), cj(Ro[2]), mk(Real(0), Real(0))}};
+    // Z = V R' (the diagonal of R' real), T' = Z V^dagger
     cx<Real> Z[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) Z[a][k] = V[a][0] * Rm[0][k] + V[a][1] * Rm[1][k] + V[a][2] * Rm[2][k];
+        for (int k = 0; k < 3; ++k) {
+            const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
+            Z[a][k] = Rd[k] * V[a][k] + V[a][j1] * Rm[j1][k] + V[a][j2] * Rm[j2][k];
+        }
     Real o00 = Z[0][0].r * V[0][0].r + Z[0][0].i * V[0][0].i + Z[0][1].r * V[0][1].r +
                Z[0][1].i * V[0][1].i + Z[0][2].r * V[0][2].r + Z[0][2].i * V[0][2].i;
     Real o11 = Z[1][0].r * V[1][0].r + Z[1][0].i * V[1][0].i + Z[1][1].r * V[1][1].r +

@@ -120,7 +120,7 @@ def test_moments_outputs_and_checkpoint(xf, orc):
     c = xf.Context(p)
     c.init_state(p.r0)
     seeded = orc.init_state(p)
-    assert np.abs(c.get_state()[0] - seeded).max() < 1e-15 * np.abs(seeded).max()
+    assert np.abs(c.get_state()[0] - seeded).max() < 1e-14 * np.abs(seeded).max()  # the traceless pack round trip
     c.step(20, p.h)
     rho, r, _ = c.get_state()
     M = c.moments_ex()
