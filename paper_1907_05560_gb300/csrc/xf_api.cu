@@ -289,16 +289,20 @@ int elementwise_grid(xf_ctx *c, const InstHost &in)
     return (int)std::max<long long>(1, std::min<long long>(g, (long long)c->num_sms * 16));
 }
 
-// Cost weight of a pair (relative work per step): the per-bin operation
-// counts of the steppers, three flavors against two: 2631 / 120 ~ 22 for the
-// predictor-corrector (a 3x3 eigendecomposition against a Bloch rotation),
-// 684 / 172 ~ 4 for RK4 (commutators); the error-controlled attempt as the
-// predictor-corrector.
-double pair_cost(const xf_ctx *c, const InstHost &in)
+// Cost weight of a three-flavor pair against a two-flavor one (relative work
+// per step).  FP64 bins are bound by the FP64 ALUs, so the per-bin operation
+// counts decide: 2089 / 120 ~ 17 for the predictor-corrector (a 3x3
+// eigendecomposition against a Bloch rotation; the error-controlled attempt
+// alike), 684 / 172 ~ 4 for RK4.  FP32 bins run at 64x the ALU rate, where
+// memory traffic and fixed per-pair work weigh more: 10 and 3.  xf_autotune
+// also tries half and twice the value on packs of mixed flavors.
+double default_cost3(int stepper, int precision)
 {
-    if (in.nf != 3) return 1.0;
-    return c->stepper == XF_RK4 ? 4.0 : 22.0;
+    const bool fp64 = precision == XF_FP64;
+    if (stepper == XF_RK4) return fp64 ? 4.0 : 3.0;
+    return fp64 ? 17.0 : 10.0;
 }
+double pair_cost(const xf_ctx *c, const InstHost &in) { return in.nf == 3 ? c->cost3 : 1.0; }
 
 // Tile every instance into runs of at most TP pairs, then give
 // each CTA a contiguous run of tiles of about equal cost.
@@ -909,6 +913,7 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
     c->real_bytes = (precision == XF_FP64) ? 8 : 4;
     c->precision = precision;
     c->stepper = stepper;
+    c->cost3 = default_cost3(stepper, precision);
     c->nfm = nfm;
     auto bail = [&](int code) {
         free_all(c);
@@ -1837,10 +1842,22 @@ int xf_autotune(xf_ctx *c, int64_t n_probe, double dr_km, const int *cand_in, in
     const int tile0 = c->tile_request;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = cuda_fail(c, cudaErrorUnknown, "event");
+    // cost weights of a three-flavor pair to try: the default, and on packs of
+    // mixed flavors also half and twice it
+    bool has2 = false, has3 = false;
+    for (const InstHost &h : c->in)
+        if (h.active) (h.nf == 3 ? has3 : has2) = true;
+    const double cost0 = c->cost3;
+    std::vector<double> costs = {cost0};
+    if (has2 && has3) costs = {cost0, 0.5 * cost0, 2.0 * cost0};
+    std::vector<std::pair<int, double>> trials;
+    for (double w : costs)
+        for (int t : cands) trials.push_back({t, w});
     int best = -1;
-    double best_t = 0.0;
-    for (size_t k = 0; k < cands.size() && !rc; ++k) {
-        c->tile_request = cands[k];
+    double best_t = 0.0, best_cost = cost0;
+    for (size_t k = 0; k < trials.size() && !rc; ++k) {
+        c->tile_request = trials[k].first;
+        c->cost3 = trials[k].second;
         rc = plan_launch(c);
         if (!rc) rc = upload_instances(c);
         for (int i = 0; i < ni && !rc; ++i)
@@ -1854,7 +1871,8 @@ int xf_autotune(xf_ctx *c, int64_t n_probe, double dr_km, const int *cand_in, in
         float ms = 0.0f;
         if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = cuda_fail(c, cudaErrorUnknown, "event");
         if (!rc && (best < 0 || ms < best_t)) {
-            best = cands[k];
+            best = trials[k].first;
+            best_cost = trials[k].second;
             best_t = ms;
         }
     }
@@ -1876,6 +1894,7 @@ int xf_autotune(xf_ctx *c, int64_t n_probe, double dr_km, const int *cand_in, in
     if (e1) cudaEventDestroy(e1);
     dev_free(c, snap);
     c->tile_request = rc ? tile0 : best;
+    c->cost3 = rc ? cost0 : best_cost;
     int rp = plan_launch(c);
     if (!rp) rp = upload_instances(c);
     if (rc) return rc;

@@ -162,6 +162,25 @@ template <typename Real> __host__ __device__ __forceinline__ cx<Real> mulc(cx<Re
 {
     return {a.r * b.r + a.i * b.i, a.i * b.r - a.r * b.i};
 }
+template <typename Real> __host__ __device__ __forceinline__ cx<Real> neg(cx<Real> a) { return {-a.r, -a.i}; }
+
+__host__ __device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
+__host__ __device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+// acc + a b, acc + a conj(b) and acc + s a (s real) with the products fused
+// into the sum: two FMA per component, where a complex product and then a
+// complex sum take a multiply, an FMA and an add per component.
+template <typename Real> __host__ __device__ __forceinline__ cx<Real> cfma(cx<Real> a, cx<Real> b, cx<Real> acc)
+{
+    return {fma_r(a.r, b.r, fma_r(-a.i, b.i, acc.r)), fma_r(a.r, b.i, fma_r(a.i, b.r, acc.i))};
+}
+template <typename Real> __host__ __device__ __forceinline__ cx<Real> cfmac(cx<Real> a, cx<Real> b, cx<Real> acc)
+{
+    return {fma_r(a.r, b.r, fma_r(a.i, b.i, acc.r)), fma_r(a.i, b.r, fma_r(-a.r, b.i, acc.i))};
+}
+template <typename Real> __host__ __device__ __forceinline__ cx<Real> rfma(Real s, cx<Real> a, cx<Real> acc)
+{
+    return {fma_r(s, a.r, acc.r), fma_r(s, a.i, acc.i)};
+}
 
 // -i[H, T] for traceless Hermitian 3x3 (comps layout above).  With X = H T:
 //   D_kk = 2 Im X_kk,   D_jk = -i (X_jk - conj(X_kj))  (j < k)
@@ -246,8 +265,8 @@ __host__ __device__ __forceinline__ bool jacobi_angles(Real *dg, cx<Real> *o, Re
         nRP = c * aRP;
         nRQ = se * aRP;
     } else {
-        nRP = c * aRP - sec * aRQ;
-        nRQ = se * aRP + c * aRQ;
+        nRP = cfma(neg(sec), aRQ, c * aRP);
+        nRQ = cfma(se, aRP, c * aRQ);
     }
     if (R < P) o[oidx(R, P)] = nRP;
     else o[oidx(P, R)] = cj(nRP);
@@ -268,8 +287,8 @@ __host__ __device__ __forceinline__ void jacobi_rot(Real *dg, cx<Real> *o, cx<Re
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         cx<Real> vp = V[k][P], vq = V[k][Q];
-        V[k][P] = c * vp - sec * vq;
-        V[k][Q] = se * vp + c * vq;
+        V[k][P] = cfma(neg(sec), vq, c * vp);
+        V[k][Q] = cfma(se, vp, c * vq);
     }
 }
 
@@ -326,11 +345,10 @@ __host__ __device__ __forceinline__ void eig3(const Real *h, Real *dg, cx<Real> 
         V[0][0] = mk(v00, Real(0));
         V[1][0] = v10;
         V[2][0] = v20;
-        V[0][1] = c3 * s1 - s3c * v02;
-        V[0][2] = s3 * s1 + c3 * v02;
-        const cx<Real> w12 = s3c * v12;
-        V[1][1] = mk(c3 * c1 - w12.r, -w12.i);
-        V[1][2] = c1 * s3 + c3 * v12;
+        V[0][1] = cfma(neg(s3c), v02, c3 * s1);
+        V[0][2] = cfma(s3, s1, c3 * v02);
+        V[1][1] = mk(fma_r(-s3c.r, v12.r, fma_r(s3c.i, v12.i, c3 * c1)), fma_r(-s3c.r, v12.i, -(s3c.i * v12.r)));
+        V[1][2] = rfma(c1, s3, c3 * v12);
         V[2][1] = mk(-(c2 * s3c.r), -(c2 * s3c.i));
         V[2][2] = mk(c3 * c2, Real(0));
     }
@@ -358,7 +376,7 @@ __host__ __device__ __forceinline__ void apply3(const Real *dg, const cx<Real> (
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int b1 = a == 0 ? 1 : 0, b2 = a == 2 ? 1 : 2;
-            W[a][k] = Td[a] * V[a][k] + To[a][b1] * V[b1][k] + To[a][b2] * V[b2][k];
+            W[a][k] = cfma(To[a][b2], V[b2][k], cfma(To[a][b1], V[b1][k], Td[a] * V[a][k]));
         }
     // R = V^dagger W (Hermitian): diag real, upper entries
     Real Rd[3];
@@ -367,9 +385,9 @@ __host__ __device__ __forceinline__ void apply3(const Real *dg, const cx<Real> (
     for (int j = 0; j < 3; ++j)
         Rd[j] = V[0][j].r * W[0][j].r + V[0][j].i * W[0][j].i + V[1][j].r * W[1][j].r +
                 V[1][j].i * W[1][j].i + V[2][j].r * W[2][j].r + V[2][j].i * W[2][j].i;
-    Ro[0] = mulc(W[0][1], V[0][0]) + mulc(W[1][1], V[1][0]) + mulc(W[2][1], V[2][0]);
-    Ro[1] = mulc(W[0][2], V[0][0]) + mulc(W[1][2], V[1][0]) + mulc(W[2][2], V[2][0]);
-    Ro[2] = mulc(W[0][2], V[0][1]) + mulc(W[1][2], V[1][1]) + mulc(W[2][2], V[2][1]);
+    Ro[0] = cfmac(W[2][1], V[2][0], cfmac(W[1][1], V[1][0], mulc(W[0][1], V[0][0])));
+    Ro[1] = cfmac(W[2][2], V[2][0], cfmac(W[1][2], V[1][0], mulc(W[0][2], V[0][0])));
+    Ro[2] = cfmac(W[2][2], V[2][1], cfmac(W[1][2], V[1][1], mulc(W[0][2], V[0][1])));
     // phases exp(-i (lam_j - lam_k) dl) on the upper entries
     {
         Real s, c;
@@ -390,15 +408,15 @@ __host__ __device__ __forceinline__ void apply3(const Real *dg, const cx<Real> (
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
-            Z[a][k] = Rd[k] * V[a][k] + V[a][j1] * Rm[j1][k] + V[a][j2] * Rm[j2][k];
+            Z[a][k] = cfma(V[a][j2], Rm[j2][k], cfma(V[a][j1], Rm[j1][k], Rd[k] * V[a][k]));
         }
     Real o00 = Z[0][0].r * V[0][0].r + Z[0][0].i * V[0][0].i + Z[0][1].r * V[0][1].r +
                Z[0][1].i * V[0][1].i + Z[0][2].r * V[0][2].r + Z[0][2].i * V[0][2].i;
     Real o11 = Z[1][0].r * V[1][0].r + Z[1][0].i * V[1][0].i + Z[1][1].r * V[1][1].r +
                Z[1][1].i * V[1][1].i + Z[1][2].r * V[1][2].r + Z[1][2].i * V[1][2].i;
-    cx<Real> o01 = mulc(Z[0][0], V[1][0]) + mulc(Z[0][1], V[1][1]) + mulc(Z[0][2], V[1][2]);
-    cx<Real> o02 = mulc(Z[0][0], V[2][0]) + mulc(Z[0][1], V[2][1]) + mulc(Z[0][2], V[2][2]);
-    cx<Real> o12 = mulc(Z[1][0], V[2][0]) + mulc(Z[1][1], V[2][1]) + mulc(Z[1][2], V[2][2]);
+    cx<Real> o01 = cfmac(Z[0][2], V[1][2], cfmac(Z[0][1], V[1][1], mulc(Z[0][0], V[1][0])));
+    cx<Real> o02 = cfmac(Z[0][2], V[2][2], cfmac(Z[0][1], V[2][1], mulc(Z[0][0], V[2][0])));
+    cx<Real> o12 = cfmac(Z[1][2], V[2][2], cfmac(Z[1][1], V[2][1], mulc(Z[1][0], V[2][0])));
     // keep the result exactly traceless in the packed form: t3 is implied
     out[0] = o00;
     out[1] = o11;

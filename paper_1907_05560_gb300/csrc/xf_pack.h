@@ -115,6 +115,7 @@ struct xf_ctx {
     int nmom = 2; // moments per stage: 2, or 4 when a problem has azimuth bins (extended bulb model)
     int form = XF_FORM_RHO; // what the state planes hold (one form per pack)
     bool cyl = false;       // the cylinder model's kernel (one problem)
+    double cost3 = 17.0;    // cost weight of a three-flavor pair against a two-flavor one
     cudaStream_t stream = nullptr;
     xf_allocator alloc{};
     bool has_alloc = false;

@@ -82,10 +82,10 @@ __host__ __device__ __forceinline__ void prop_psi(const Real *h, StepLen<Real> d
                            x2 = mk(x[a * N2 + 4], x[a * N2 + 5]);
             cx<Real> w[3];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) w[j] = e[j] * (mulc(x0, V[0][j]) + mulc(x1, V[1][j]) + mulc(x2, V[2][j]));
+            for (int j = 0; j < 3; ++j) w[j] = e[j] * cfmac(x2, V[2][j], cfmac(x1, V[1][j], mulc(x0, V[0][j])));
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const cx<Real> z = V[i][0] * w[0] + V[i][1] * w[1] + V[i][2] * w[2];
+                const cx<Real> z = cfma(V[i][2], w[2], cfma(V[i][1], w[1], V[i][0] * w[0]));
                 y[a * N2 + 2 * i] = z.r;
                 y[a * N2 + 2 * i + 1] = z.i;
             }
