@@ -418,8 +418,8 @@ int plan_launch(xf_ctx *c)
 }
 
 // Cylinder model: one problem; CTA c owns tile c, a run of whole trajectories
-// (about T / G each), and a table of 4 doubles per angle bin; the partials
-// buffer holds two slots of per-trajectory sums (8 doubles each).
+// (about T / G each), and tables of 8 doubles and 2 ints per angle bin; the
+// partials buffer holds two slots of per-trajectory sums (8 doubles each).
 int plan_launch_cyl(xf_ctx *c)
 {
     InstHost &in = c->in[0];
@@ -431,7 +431,7 @@ int plan_launch_cyl(xf_ctx *c)
         return XF_OK;
     }
     const int T = in.n_u * in.n_phi, nw = c->kern.nt / 32;
-    const size_t smem = (size_t)4 * in.n_u * sizeof(double);
+    const size_t smem = (size_t)(4 + 2 * xf::CYL_ROWS) * in.n_u * sizeof(double) + (size_t)xf::CYL_ROWS * in.n_u * sizeof(int);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(c->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();

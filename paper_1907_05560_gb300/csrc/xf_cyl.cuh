@@ -11,22 +11,31 @@
 // D(Phi', j') read by periodic linear interpolation between latitude bins.
 //
 // G is not a sum of a few moments: every trajectory couples to every angle
-// bin at its own latitude offset.  So a stage is: per trajectory, G from the
-// previous stage's per-trajectory sums D (FP64, L2-resident, read with
-// .cg loads), the per-bin update of its 2 n_E bins, and its new D; one grid
-// barrier per stage as in the bulb kernel.  A warp owns a trajectory: lanes
-// split the angle sum of G, then the energy bins; both warp sums run in a
-// fixed shuffle tree, so runs are bitwise reproducible.  One problem per
-// launch; CTA c owns the trajectories of tile c.
+// bin at its own latitude offset.  A stage runs, per chunk of up to 128 of the
+// CTA's trajectories:
+//   1. the coupling rows of the chunk's angle bins j (at most two distinct j
+//      when n_phi >= 64): per background bin j' the weights K (1 - f), K f and
+//      the latitude offset floor(x) of x = (Phi' - Phi) / dPhi, in shared
+//      memory (else each thread computes its own);
+//   2. G of every trajectory of the chunk, one thread each, from the previous
+//      stage's per-trajectory sums D (FP64, component-major [c][t] so that
+//      neighbouring latitudes read neighbouring words; L2-resident, read with
+//      .cg loads because other SMs wrote them);
+//   3. the chunk's bins, one warp per trajectory, lanes over the energies, the
+//      bulb kernel's per-bin update, and the trajectory's new D from a fixed
+//      shuffle tree (so runs are bitwise reproducible);
+// then one grid barrier, as in the bulb kernel.  One problem per launch; CTA c
+// owns the trajectories of tile c.
 #pragma once
 
 #include "xf_run.cuh"
 
 namespace xf {
 
-constexpr int CYL_MAX_U = 2048; // angle bins held in the shared-memory table (4 doubles each)
-constexpr int CYL_DS = 8;       // doubles per trajectory sum (S <= 8)
+constexpr int CYL_MAX_U = 2048; // angle bins held in the shared-memory tables (9 doubles each)
+constexpr int CYL_DS = 8;       // components of a trajectory sum slot (S <= 8); D[slot][c][T]
 constexpr int CYL_NT = 128;
+constexpr int CYL_ROWS = 2;     // coupling rows held per chunk
 
 // Angle bin j at radius r: beta = theta - alpha, the coupling weight
 // wc = cos(theta) / cos(alpha) dtheta, cos(alpha), sin(alpha).
@@ -51,6 +60,23 @@ __device__ __forceinline__ double cyl_path_length(const Inst &a, int j, double r
     const double pi = 3.14159265358979323846;
     const double b = a.R * sin(-0.5 * pi + (j + 0.5) * pi / a.n_u), b2 = b * b;
     return h * (2.0 * r + h) / (sqrt(r * r - b2) + sqrt((r + h) * (r + h) - b2));
+}
+
+// Coupling of angle bin j to background bin jp from the angle table: the
+// interpolation weights K (1 - f), K f and the latitude offset floor(x) mod
+// n_phi, x = (Phi' - Phi) / dPhi = ((theta' - alpha') - (theta - alpha)) / dPhi.
+__device__ __forceinline__ void cyl_coupling(const double *tb_beta, const double *tb_wc, const double *tb_ca,
+                                             const double *tb_sa, int nu, int nphi, double inv_dphi, int j, int jp,
+                                             double *K0, double *K1, int *off)
+{
+    const double x = (tb_beta[jp] - tb_beta[j]) * inv_dphi;
+    const double fl = floor(x), f = x - fl;
+    int o = (int)fl % nphi;
+    if (o < 0) o += nphi;
+    const double K = tb_wc[jp] * (1.0 - (tb_ca[j] * tb_ca[jp] + tb_sa[j] * tb_sa[jp]));
+    *K0 = K * (1.0 - f);
+    *K1 = K * f;
+    *off = o;
 }
 
 // Sum over the warp's lanes into every lane (fixed tree to lane 0, then broadcast).
@@ -128,13 +154,14 @@ __device__ __forceinline__ void cyl_pair_stage(const TileView<Real> &v, int st, 
 // Write trajectory t's sum (lane 0) and flag a non-finite one with the
 // barrier number after which it is read.
 template <int S>
-__device__ __forceinline__ void cyl_store_sum(const RunArgs &a, double *Dout, int t, const double *d, unsigned nb)
+__device__ __forceinline__ void cyl_store_sum(const RunArgs &a, double *Dout, int T, int t, const double *d,
+                                              unsigned nb)
 {
     if ((threadIdx.x & 31) == 0) {
         bool ok = true;
 #pragma unroll
         for (int c = 0; c < S; ++c) {
-            __stcg(Dout + (size_t)t * CYL_DS + c, d[c]);
+            __stcg(Dout + (size_t)c * T + t, d[c]);
             ok = ok && isfinite(d[c]);
         }
         if (!ok) atomicMin(a.first_bad, nb);
@@ -146,11 +173,16 @@ __global__ void __launch_bounds__(CYL_NT, min_blocks(128, sizeof(Real))) xf_cyl_
 {
     constexpr int S = Comp<NF>::S, NT = CYL_NT, NW = NT / 32;
     extern __shared__ double s_dyn[];
+    __shared__ double s_G[NT][S]; // G of the chunk's trajectories (mu dE applied)
     __shared__ int s_flag;
     const Inst &in = a.inst[0];
-    const int nu = in.n_u, nphi = in.n_phi;
+    const int nu = in.n_u, nphi = in.n_phi, T = nu * nphi;
+    // dynamic shared memory: the angle table (4 nu doubles), then the
+    // coupling rows (2 CYL_ROWS nu doubles, CYL_ROWS nu ints)
     double *const tb_beta = s_dyn, *const tb_wc = s_dyn + nu, *const tb_ca = s_dyn + 2 * nu,
                   *const tb_sa = s_dyn + 3 * nu;
+    double *const rK0 = s_dyn + 4 * nu, *const rK1 = s_dyn + (4 + CYL_ROWS) * nu;
+    int *const rOff = (int *)(s_dyn + (4 + 2 * CYL_ROWS) * nu);
     const Tile tl = a.tiles[blockIdx.x];
     const int t_a = tl.p0 / in.n_E, t_b = (tl.p0 + tl.np) / in.n_E;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -163,7 +195,7 @@ __global__ void __launch_bounds__(CYL_NT, min_blocks(128, sizeof(Real))) xf_cyl_
     const InstPos ps = a.pos[0];
     const long long n = launch_steps(a, ps);
     if (n <= 0) return; // every CTA sees the same n
-    double *const Dbuf[2] = {a.partials, a.partials + (size_t)nu * nphi * CYL_DS};
+    double *const Dbuf[2] = {a.partials, a.partials + (size_t)CYL_DS * T};
     const double inv_dphi = nphi / (2.0 * 3.14159265358979323846);
 
     // ---- prologue: per-trajectory sums of the input state
@@ -183,7 +215,7 @@ __global__ void __launch_bounds__(CYL_NT, min_blocks(128, sizeof(Real))) xf_cyl_
                 for (int c = 0; c < S; ++c) d[c] += (double)dd[c];
             }
             warp_sum_bcast<S>(d);
-            cyl_store_sum<S>(a, Dbuf[0], t, d, 1u);
+            cyl_store_sum<S>(a, Dbuf[0], T, t, d, 1u);
         }
     }
     if (!grid_barrier(a, ++nbar, &s_flag)) return;
@@ -208,56 +240,80 @@ __global__ void __launch_bounds__(CYL_NT, min_blocks(128, sizeof(Real))) xf_cyl_
             const Real A = (Real)matter_A(in, r_rhs);
             const Real cy = (Real)((st == 2) ? h : 0.5 * h);
             const Real cb = (Real)((st == 0 || st == 3) ? h / 6.0 : h / 3.0);
-            __syncthreads(); // the previous stage's readers of the table are done
+            __syncthreads(); // the previous stage's readers of the tables are done
             for (int j = threadIdx.x; j < nu; j += NT) cyl_angle(in, j, r_rhs, tb_beta + j, tb_wc + j, tb_ca + j, tb_sa + j);
             __syncthreads();
             const TileView<Real> v = make_view<Real>(a, in, ps, tl, k);
             const double *const Din = Dbuf[(nbar - 1) & 1];
             double *const Dout = Dbuf[nbar & 1];
-            for (int t = t_a + warp; t < t_b; t += NW) {
-                const int j = t / nphi, kl = t - j * nphi;
-                const double beta_j = tb_beta[j], ca_j = tb_ca[j], sa_j = tb_sa[j];
-                // G of the trajectory: lanes split the angle bins j'
-                double g[S];
+            for (int c0 = t_a; c0 < t_b; c0 += NT) {
+                const int c1 = min(c0 + NT, t_b);
+                const int j_lo = c0 / nphi, rows = (c1 - 1) / nphi - j_lo + 1;
+                const bool tab = rows <= CYL_ROWS;
+                // 1. the chunk's coupling rows
+                if (tab)
+                    for (int q = threadIdx.x; q < rows * nu; q += NT) {
+                        const int row = q / nu, jp = q - row * nu;
+                        cyl_coupling(tb_beta, tb_wc, tb_ca, tb_sa, nu, nphi, inv_dphi, j_lo + row, jp,
+                                     rK0 + row * nu + jp, rK1 + row * nu + jp, rOff + row * nu + jp);
+                    }
+                __syncthreads();
+                // 2. G, one thread per trajectory
+                const int t = c0 + (int)threadIdx.x;
+                if (t < c1) {
+                    const int j = t / nphi, kl = t - j * nphi, row = j - j_lo;
+                    double g[S];
 #pragma unroll
-                for (int c = 0; c < S; ++c) g[c] = 0.0;
-                for (int jp = lane; jp < nu; jp += 32) {
-                    const double pos = kl + (tb_beta[jp] - beta_j) * inv_dphi;
-                    const double fl = floor(pos), f = pos - fl;
-                    int i0 = (int)fl % nphi;
-                    if (i0 < 0) i0 += nphi;
-                    const int i1 = (i0 + 1 == nphi) ? 0 : i0 + 1;
-                    const double K = tb_wc[jp] * (1.0 - (ca_j * tb_ca[jp] + sa_j * tb_sa[jp]));
-                    const double K0 = K * (1.0 - f), K1 = K * f;
-                    const double *d0 = Din + (size_t)(jp * nphi + i0) * CYL_DS;
-                    const double *d1 = Din + (size_t)(jp * nphi + i1) * CYL_DS;
+                    for (int c = 0; c < S; ++c) g[c] = 0.0;
+                    for (int jp = 0; jp < nu; ++jp) {
+                        double K0, K1;
+                        int off;
+                        if (tab) {
+                            K0 = rK0[row * nu + jp];
+                            K1 = rK1[row * nu + jp];
+                            off = rOff[row * nu + jp];
+                        } else {
+                            cyl_coupling(tb_beta, tb_wc, tb_ca, tb_sa, nu, nphi, inv_dphi, j, jp, &K0, &K1, &off);
+                        }
+                        int i0 = kl + off;
+                        if (i0 >= nphi) i0 -= nphi;
+                        const int i1 = (i0 + 1 == nphi) ? 0 : i0 + 1;
+                        const double *const Dj = Din + (size_t)jp * nphi;
 #pragma unroll
-                    for (int c = 0; c < S; ++c) g[c] += K0 * __ldcg(d0 + c) + K1 * __ldcg(d1 + c);
+                        for (int c = 0; c < S; ++c)
+                            g[c] = fma(K0, __ldcg(Dj + (size_t)c * T + i0), fma(K1, __ldcg(Dj + (size_t)c * T + i1), g[c]));
+                    }
+#pragma unroll
+                    for (int c = 0; c < S; ++c) s_G[threadIdx.x][c] = mu * g[c];
                 }
-                warp_sum_bcast<S>(g);
-                Real gr[S];
+                __syncthreads();
+                // 3. the bins, one warp per trajectory
+                for (int tt = c0 + warp; tt < c1; tt += NW) {
+                    const int j = tt / nphi;
+                    Real gr[S];
 #pragma unroll
-                for (int c = 0; c < S; ++c) gr[c] = (Real)(mu * g[c]);
-                const Real kap = (Real)(1.0 / ca_j);
-                const StepLen<Real> dl = make_step_len(STEP == STEP_EXPH ? cyl_path_length(in, j, r, h) : 0.0,
-                                                       (Real *)nullptr);
-                // the trajectory's bins: lanes split the energies
-                double d[S];
+                    for (int c = 0; c < S; ++c) gr[c] = (Real)s_G[tt - c0][c];
+                    const Real kap = (Real)(1.0 / tb_ca[j]);
+                    const StepLen<Real> dl = make_step_len(STEP == STEP_EXPH ? cyl_path_length(in, j, r, h) : 0.0,
+                                                           (Real *)nullptr);
+                    double d[S];
 #pragma unroll
-                for (int c = 0; c < S; ++c) d[c] = 0.0;
-                for (int e = lane; e < in.n_E; e += 32) {
-                    const int p = t * in.n_E + e;
-                    Real hv[S], hn[S], hb[S], on[S], ob[S], dd[S];
+                    for (int c = 0; c < S; ++c) d[c] = 0.0;
+                    for (int e = lane; e < in.n_E; e += 32) {
+                        const int p = tt * in.n_E + e;
+                        Real hv[S], hn[S], hb[S], on[S], ob[S], dd[S];
 #pragma unroll
-                    for (int c = 0; c < S; ++c) hv[c] = v.hvac[(size_t)e * S + c];
-                    hamiltonians<NF, Real>(hv, A, gr, hn, hb);
-                    cyl_pair_stage<NF, STEP, Real>(v, st, p, hn, hb, kap, dl, cy, cb, on, ob);
-                    nu_minus_conj_nubar<NF, Real>(on, ob, dd);
+                        for (int c = 0; c < S; ++c) hv[c] = v.hvac[(size_t)e * S + c];
+                        hamiltonians<NF, Real>(hv, A, gr, hn, hb);
+                        cyl_pair_stage<NF, STEP, Real>(v, st, p, hn, hb, kap, dl, cy, cb, on, ob);
+                        nu_minus_conj_nubar<NF, Real>(on, ob, dd);
 #pragma unroll
-                    for (int c = 0; c < S; ++c) d[c] += (double)dd[c];
+                        for (int c = 0; c < S; ++c) d[c] += (double)dd[c];
+                    }
+                    warp_sum_bcast<S>(d);
+                    cyl_store_sum<S>(a, Dout, T, tt, d, nbar + 1);
                 }
-                warp_sum_bcast<S>(d);
-                cyl_store_sum<S>(a, Dout, t, d, nbar + 1);
+                __syncthreads(); // the chunk's G and rows are consumed
             }
             if (!grid_barrier(a, ++nbar, &s_flag)) return;
         }
