@@ -118,11 +118,13 @@ __host__ __device__ __forceinline__ void comm2(const Real *h, const Real *t, Rea
 template <typename Real>
 __host__ __device__ __forceinline__ void prop2(const Real *h, StepLen<Real> dl, const Real *t, Real *out)
 {
-    Real lam2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
-    Real lam = sqrt_r(lam2);
+    // lam and sin(lam dl)/lam from one reciprocal square root (no division)
+    const Real lam2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+    const Real rl = (lam2 > Real(0)) ? rsqrt_r(lam2) : Real(0);
+    const Real lam = lam2 * rl;
     Real sn, cs;
     phase_sincos(lam, dl, &sn, &cs);
-    Real sig = (lam > Real(0)) ? sn / lam : step_len_value(dl);
+    const Real sig = (lam2 > Real(0)) ? sn * rl : step_len_value(dl);
     Real w[3], q[3];
     w[0] = h[2] * t[1] - h[1] * t[2];
     w[1] = h[0] * t[2] - t[0] * h[2];
@@ -458,7 +460,9 @@ __host__ __device__ __forceinline__ void prop_pair(const Real *h, StepLen<Real> 
                                                    Real *out1, Real *out2)
 {
     if constexpr (NF == 2) {
-        Real lam = sqrt_r(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+        const Real lam2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+        const Real rl = (lam2 > Real(0)) ? rsqrt_r(lam2) : Real(0);
+        const Real lam = lam2 * rl;
         Real w[3], q[3];
         w[0] = h[2] * t[1] - h[1] * t[2];
         w[1] = h[0] * t[2] - t[0] * h[2];
@@ -471,7 +475,7 @@ __host__ __device__ __forceinline__ void prop_pair(const Real *h, StepLen<Real> 
             const StepLen<Real> dl = i ? dl2 : dl1;
             Real sn, cs;
             phase_sincos(lam, dl, &sn, &cs);
-            Real sig = (lam > Real(0)) ? sn / lam : step_len_value(dl);
+            Real sig = (lam2 > Real(0)) ? sn * rl : step_len_value(dl);
             Real c1 = Real(2) * sig * cs, c2 = Real(2) * sig * sig;
             Real *o = i ? out2 : out1;
 #pragma unroll
