@@ -390,15 +390,16 @@ __host__ __device__ __forceinline__ void apply3(const Real *dg, const cx<Real> (
     Ro[0] = cfmac(W[2][1], V[2][0], cfmac(W[1][1], V[1][0], mulc(W[0][1], V[0][0])));
     Ro[1] = cfmac(W[2][2], V[2][0], cfmac(W[1][2], V[1][0], mulc(W[0][2], V[0][0])));
     Ro[2] = cfmac(W[2][2], V[2][1], cfmac(W[1][2], V[1][1], mulc(W[0][2], V[0][1])));
-    // phases exp(-i (lam_j - lam_k) dl) on the upper entries
+    // phases exp(-i (lam_j - lam_k) dl) on the upper entries; the (0,2) phase
+    // is the product of the (0,1) and (1,2) ones (two sine-cosine pairs, not three)
     {
-        Real s, c;
-        phase_sincos(dg[0] - dg[1], dl, &s, &c);
-        Ro[0] = Ro[0] * mk(c, -s);
-        phase_sincos(dg[0] - dg[2], dl, &s, &c);
-        Ro[1] = Ro[1] * mk(c, -s);
-        phase_sincos(dg[1] - dg[2], dl, &s, &c);
-        Ro[2] = Ro[2] * mk(c, -s);
+        Real s01, c01, s12, c12;
+        phase_sincos(dg[0] - dg[1], dl, &s01, &c01);
+        phase_sincos(dg[1] - dg[2], dl, &s12, &c12);
+        const cx<Real> e01 = mk(c01, -s01), e12 = mk(c12, -s12);
+        Ro[0] = Ro[0] * e01;
+        Ro[1] = Ro[1] * (e01 * e12);
+        Ro[2] = Ro[2] * e12;
     }
     const cx<Real> Rm[3][3] = {{mk(Real(0), Real(0)), Ro[0], Ro[1]},
                                {cj(Ro[0]), mk(Real(0), Real(0)), Ro[2]},

@@ -72,12 +72,15 @@ __host__ __device__ __forceinline__ void prop_psi(const Real *h, StepLen<Real> d
         cx<Real> V[3][3];
         eig3<Real>(h, dg, V);
         cx<Real> e[3];
+        // exp(-i lam_j dl) for j = 0, 1; lam_2 = -(lam_0 + lam_1) (H traceless)
+        // gives the third as conj(e_0 e_1)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
+        for (int j = 0; j < 2; ++j) {
             Real sn, cs;
             phase_sincos(dg[j], dl, &sn, &cs);
             e[j] = mk(cs, -sn);
         }
+        e[2] = cj(e[0] * e[1]);
 #pragma unroll
         for (int a = 0; a < NF; ++a) {
             const cx<Real> x0 = mk(x[a * N2 + 0], x[a * N2 + 1]), x1 = mk(x[a * N2 + 2], x[a * N2 + 3]),
