@@ -358,3 +358,25 @@ def test_fp32_three_flavor_error_vs_fp64_oracle(xf, orc, make):
     err = rel_err(got, ref, 3)
     print(f"{make.__name__} FP32_M64 rel err after {n} steps: {err:.3e}")
     assert done == n and err < 1e-4
+
+
+@pytest.mark.parametrize("stepper", [I.RK4, I.EXPH])
+@pytest.mark.parametrize("n_f", [2, 3])
+def test_degenerate_cases(xf, orc, n_f, stepper):
+    """Zero steps leave the state bitwise; a vanishing Hamiltonian (no mass
+    splitting, no matter, no coupling: lambda = 0 in the rotation, a zero
+    matrix for the eigensolver) leaves every bin unchanged to rounding."""
+    kw = dict(THREE) if n_f == 3 else {}
+    p = small(n_u=5, n_E=9, stepper=stepper, **kw)
+    rho0 = orc.init_state(p)
+    c = xf.Context(p)
+    c.set_state(rho0, p.r0)
+    before = c.get_state()[0]
+    c.step(0, p.h)
+    after, r, n = c.get_state()
+    c.close()
+    assert n == 0 and r == p.r0 and np.array_equal(before, after)
+    q = p.replace(dm2=(0.0, 0.0), mu0=0.0, matter=I.MATTER_NONE)
+    got, r, n = gpu_run(xf, q, rho0, q.r0, q.h, 50)
+    assert n == 50
+    assert np.abs(got - rho0).max() <= 1e-14 * np.abs(rho0).max()  # the pack round trip
