@@ -51,12 +51,8 @@ __host__ __device__ __forceinline__ void prop_psi(const Real *h, StepLen<Real> d
 {
     constexpr int N2 = 2 * NF;
     if constexpr (NF == 2) {
-        const Real lam2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
-        const Real rl = (lam2 > Real(0)) ? rsqrt_r(lam2) : Real(0);
-        const Real lam = lam2 * rl;
-        Real sn, cs;
-        phase_sincos(lam, dl, &sn, &cs);
-        const Real sig = (lam2 > Real(0)) ? sn * rl : step_len_value(dl);
+        Real sn, cs, sig;
+        rotation_angle(h, dl, &sn, &cs, &sig);
 #pragma unroll
         for (int a = 0; a < NF; ++a) {
             Real hx[N2];
