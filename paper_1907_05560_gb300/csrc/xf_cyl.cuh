@@ -13,10 +13,11 @@
 // G is not a sum of a few moments: every trajectory couples to every angle
 // bin at its own latitude offset.  A stage runs, per chunk of up to 128 of the
 // CTA's trajectories:
-//   1. the coupling rows of the chunk's angle bins j (at most two distinct j
-//      when n_phi >= 64): per background bin j' the weights K (1 - f), K f and
-//      the latitude offset floor(x) of x = (Phi' - Phi) / dPhi, in shared
-//      memory (else each thread computes its own);
+//   1. when the chunk's trajectories have at most two distinct angle bins j
+//      (always when n_phi >= 127), their coupling rows: per background bin j'
+//      the weights K (1 - f), K f and the latitude offset floor(x) of
+//      x = (Phi' - Phi) / dPhi, in shared memory (else each thread computes
+//      its own);
 //   2. G of every trajectory of the chunk, one thread each, from the previous
 //      stage's per-trajectory sums D (FP64, component-major [c][t] so that
 //      neighbouring latitudes read neighbouring words; L2-resident, read with
