@@ -469,9 +469,9 @@ int xf_set_option(xf_ctx *ctx, int option, int64_t value);
  * takes 0, 128, 256, ..., 16384), time n_probe steps of size dr_km (<= 0:
  * each problem's current step size) after one untimed launch, and keep the
  * fastest, which stays set as XF_OPT_TILE_PAIRS.  On a batch mixing two-
- * and three-flavor problems each candidate also runs with half and twice the
- * default cost weight of a three-flavor pair in the split of tiles over CTAs,
- * and the fastest weight stays set.  Every problem's state,
+ * and three-flavor problems each candidate also runs with 0.7 and 1.4 times
+ * the default cost weight of a three-flavor pair in the split of tiles over
+ * CTAs, and the fastest weight stays set.  Every problem's state,
  * radius and step count are restored afterwards (device copies of the state
  * planes), so the search does not advance the problems.  Needs a valid
  * state in every problem.  *best_tile (may be NULL) receives the chosen

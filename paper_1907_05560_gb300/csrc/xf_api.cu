@@ -291,16 +291,18 @@ int elementwise_grid(xf_ctx *c, const InstHost &in)
 
 // Cost weight of a three-flavor pair against a two-flavor one (relative work
 // per step).  FP64 bins are bound by the FP64 ALUs, so the per-bin operation
-// counts decide: 2089 / 120 ~ 17 for the predictor-corrector (a 3x3
+// counts decide: 2097 / 122 ~ 17 for the predictor-corrector (a 3x3
 // eigendecomposition against a Bloch rotation; the error-controlled attempt
-// alike), 684 / 172 ~ 4 for RK4.  FP32 bins run at 64x the ALU rate, where
-// memory traffic and fixed per-pair work weigh more: 10 and 3.  xf_autotune
-// also tries half and twice the value on packs of mixed flavors.
+// alike), 684 / 172 ~ 4 for RK4.  FP32 bins run at 64x the ALU rate and a
+// pair costs about its state bytes (8 against 3 components): 3 measured best
+// on the 256-problem ensemble (1.33e10 bin-steps/s against 1.0e10 at 1 or 5
+// and 6.0e9 at 10).  xf_autotune also tries 0.7 and 1.4 times the value on
+// packs of mixed flavors.
 double default_cost3(int stepper, int precision)
 {
     const bool fp64 = precision == XF_FP64;
     if (stepper == XF_RK4) return fp64 ? 4.0 : 3.0;
-    return fp64 ? 17.0 : 10.0;
+    return fp64 ? 17.0 : 3.0;
 }
 double pair_cost(const xf_ctx *c, const InstHost &in) { return in.nf == 3 ? c->cost3 : 1.0; }
 
@@ -1843,13 +1845,13 @@ int xf_autotune(xf_ctx *c, int64_t n_probe, double dr_km, const int *cand_in, in
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = cuda_fail(c, cudaErrorUnknown, "event");
     // cost weights of a three-flavor pair to try: the default, and on packs of
-    // mixed flavors also half and twice it
+    // mixed flavors also 0.7 and 1.4 times it
     bool has2 = false, has3 = false;
     for (const InstHost &h : c->in)
         if (h.active) (h.nf == 3 ? has3 : has2) = true;
     const double cost0 = c->cost3;
     std::vector<double> costs = {cost0};
-    if (has2 && has3) costs = {cost0, 0.5 * cost0, 2.0 * cost0};
+    if (has2 && has3) costs = {cost0, 0.7 * cost0, 1.4 * cost0};
     std::vector<std::pair<int, double>> trials;
     for (double w : costs)
         for (int t : cands) trials.push_back({t, w});
