@@ -290,19 +290,21 @@ int elementwise_grid(xf_ctx *c, const InstHost &in)
 }
 
 // Cost weight of a three-flavor pair against a two-flavor one (relative work
-// per step).  FP64 bins are bound by the FP64 ALUs, so the per-bin operation
-// counts decide: 2097 / 122 ~ 17 for the predictor-corrector (a 3x3
+// per step).  FP64 bins are bound by the FP64 ALUs: the per-bin operation
+// counts give 2097 / 122 ~ 17 for the predictor-corrector (a 3x3
 // eigendecomposition against a Bloch rotation; the error-controlled attempt
-// alike), 684 / 172 ~ 4 for RK4.  FP32 bins run at 64x the ALU rate and a
-// pair costs about its state bytes (8 against 3 components): 3 measured best
-// on the 256-problem ensemble (1.33e10 bin-steps/s against 1.0e10 at 1 or 5
-// and 6.0e9 at 10).  xf_autotune also tries 0.7 and 1.4 times the value on
-// packs of mixed flavors.
+// alike), the 256-problem ensemble ran fastest at 12 (4.45e8 bin-steps/s
+// against 4.25e8 at 17 and 3.9e8 at 24), a two-flavor pair carrying some
+// fixed per-pair work; 684 / 172 ~ 4 for RK4.  FP32 bins run at 64x the ALU
+// rate and a pair costs about its state bytes (8 against 3 components): 3
+// measured best on the ensemble (1.33e10 bin-steps/s against 1.0e10 at 1 or
+// 5 and 6.0e9 at 10).  xf_autotune also tries 0.7 and 1.4 times the value
+// on packs of mixed flavors.
 double default_cost3(int stepper, int precision)
 {
     const bool fp64 = precision == XF_FP64;
     if (stepper == XF_RK4) return fp64 ? 4.0 : 3.0;
-    return fp64 ? 17.0 : 3.0;
+    return fp64 ? 12.0 : 3.0;
 }
 double pair_cost(const xf_ctx *c, const InstHost &in) { return in.nf == 3 ? c->cost3 : 1.0; }
 
