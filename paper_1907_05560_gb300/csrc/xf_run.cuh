@@ -835,13 +835,18 @@ __device__ __forceinline__ void finish_instance(const RunArgs &a, const Inst &in
 // Resident CTAs per SM the register allocation is fitted to (occupancy for
 // latency hiding; no kernel here is limited by shared memory):
 //   FP64, 128 threads (three flavors / mixed): 3 (168 registers, a few words
-//     spilled) instead of 2 at 252;
-//   FP32, 128 threads: 4 (128 registers, no spills) instead of 2 at ~200;
+//     spilled); 2 at 244-252 registers measured no faster (the FP64 pipe
+//     bounds it);
+//   FP32, 128 threads, three flavors: 4 (128 registers, no spills); 5 and 6
+//     ran the L2-resident 400,000-bin problem 16 % and 32 % slower;
+//   FP32, 128 threads, mixed packs (nfm 0): 6 (80 registers, 56 bytes
+//     spilled): their state streams from HBM and more warps hide it (the
+//     256-problem ensemble ran 14 % faster than at 4);
 //   FP64, 256 threads (two flavors): 2 (~120 registers, no spills);
 //   FP32, 256 threads: 4 (64 registers, no spills).
-__host__ __device__ constexpr int min_blocks(int nt, int real_bytes)
+__host__ __device__ constexpr int min_blocks(int nt, int real_bytes, int nfm = 3)
 {
-    return nt == 128 ? (real_bytes == 8 ? 3 : 4) : (real_bytes == 8 ? 2 : 4);
+    return nt == 128 ? (real_bytes == 8 ? 3 : (nfm == 0 ? 6 : 4)) : (real_bytes == 8 ? 2 : 4);
 }
 
 // NFM: 2 or 3 (every instance has that many flavors) or 0 (mixed pack);
@@ -850,7 +855,7 @@ __host__ __device__ constexpr int min_blocks(int nt, int real_bytes)
 // its problems may also have a single azimuth bin).  FORM: FORM_RHO, or
 // FORM_PSI (wavefunctions; plain arithmetic, two moments).
 template <int NFM, int STEP, typename Real, int NT, int VAR, int NMOM = 2, int FORM = FORM_RHO>
-__global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real))) xf_run_kernel(RunArgs a)
+__global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM)) xf_run_kernel(RunArgs a)
 {
     extern __shared__ double s_dyn[];
     Real *const s_tab = (Real *)s_dyn;
