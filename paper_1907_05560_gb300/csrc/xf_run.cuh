@@ -400,22 +400,33 @@ __device__ __forceinline__ void cta_partial(Acc *m, SH &sh, double *part)
     __syncthreads();
 }
 
-// Moments of an instance: the partials of its tiles [t0, t1) summed in tile
-// order (times dE), written to sh.M.
+// Moments of an instance: the partials of its tiles [t0, t1) summed (times
+// dE), written to sh.M.  Component c of tile g is read by thread
+// (g - t0) mod lg * nvp + c, nvp = nv rounded up to a power of two and
+// lg = NT / nvp, so that neighbouring threads read one tile's slot; each
+// thread keeps two running sums (alternate tiles) to have more loads in
+// flight, and the lg sums of a component are added in thread order: a fixed
+// order, so results are reproducible.
 template <int NT>
 __device__ __forceinline__ void instance_total(const double *part, int t0, int t1, int nv, double dE, Shared &sh)
 {
-    constexpr int LG = NT / NVMAX; // threads per component
-    const int t = threadIdx.x, c = t / LG, k = t % LG;
-    double acc = 0.0;
-    if (c < nv)
-        for (int g = t0 + k; g < t1; g += LG) acc += __ldcg(part + (size_t)g * NVMAX + c);
-    sh.scr[t] = acc;
+    const int nvp = nv <= 8 ? 8 : (nv <= 16 ? 16 : 32);
+    const int lg = NT / nvp;
+    const int t = threadIdx.x, c = t & (nvp - 1), k = t / nvp;
+    double a0 = 0.0, a1 = 0.0;
+    if (c < nv) {
+        int g = t0 + k;
+        for (; g + lg < t1; g += 2 * lg) {
+            a0 += __ldcg(part + (size_t)g * NVMAX + c);
+            a1 += __ldcg(part + (size_t)(g + lg) * NVMAX + c);
+        }
+        if (g < t1) a0 += __ldcg(part + (size_t)g * NVMAX + c);
+    }
+    sh.scr[t] = a0 + a1;
     __syncthreads();
     if (t < nv) {
         double s = 0.0;
-#pragma unroll
-        for (int q = 0; q < LG; ++q) s += sh.scr[t * LG + q];
+        for (int q = 0; q < lg; ++q) s += sh.scr[q * nvp + t];
         sh.M[t] = s * dE;
     }
     __syncthreads();
