@@ -134,8 +134,10 @@ def measured_peaks():
 # Jacobi eigensolver is counted at the sweep number measured on this workload.
 FLOPS_PER_BIN_STEP = {("exph", 3): 2097, ("rk4", 3): 684, ("exph", 2): 122, ("rk4", 2): 172}
 # one attempt of the error-controlled step (four Hamiltonians, five propagations,
-# one shared eigendecomposition), counted the same way
-FLOPS_PER_BIN_ATTEMPT = {3: 4761, 2: 272}
+# one shared eigendecomposition), counted the same way; three flavors at the
+# 2.31 mean Jacobi sweeps that this leg's Hamiltonians (250-260 km) take,
+# each sweep beyond two adding 280 flop per eigendecomposition (4761 at two)
+FLOPS_PER_BIN_ATTEMPT = {3: 5108, 2: 272}
 # the wavefunction form (one psi per initial flavor), counted the same way:
 # per stage the propagation of n_f wavefunctions and rho's traceless part
 # rebuilt from them for the moments
