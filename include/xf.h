@@ -451,6 +451,11 @@ int xf_server_destroy(xf_server *srv);
  *   XF_OPT_BARRIER_TIMEOUT_NS: time limit of one grid-barrier wait
  *     (default 2e9 ns).  On expiry every CTA leaves and the call returns
  *     XF_E_BARRIER_TIMEOUT.
+ *   XF_OPT_DYNAMIC_TILES: 1 = when a pack has more tiles than CTAs, every
+ *     stage's tiles are claimed from a device counter instead of each CTA
+ *     taking its own run of them (fixed-step steppers); 0 = own runs.  The
+ *     results do not depend on it (a tile's arithmetic is the same wherever
+ *     it runs, and the moments add in tile order).
  *   XF_OPT_TEST_SKIP_ARRIVAL: test hook; CTA `value` (>= 0) leaves the kernel
  *     at its first grid barrier without arriving, so the other CTAs' bounded
  *     wait runs out.  -1 (default) disables it.  Exercises the timeout path
@@ -460,7 +465,8 @@ enum xf_option {
     XF_OPT_BARRIER_TIMEOUT_NS = 2,
     XF_OPT_TEST_SKIP_ARRIVAL = 3,
     XF_OPT_TILE_PAIRS = 4,
-    XF_OPT_GRAPH = 5
+    XF_OPT_GRAPH = 5,
+    XF_OPT_DYNAMIC_TILES = 6
 };
 int xf_set_option(xf_ctx *ctx, int option, int64_t value);
 

@@ -621,8 +621,11 @@ int enqueue_run(xf_ctx *c, long long n, cudaStream_t stream)
     a.apos = c->apos_d;
     a.tstate = c->tstate_d;
     a.first_bad = c->bar + 1;
+    a.ticket = (unsigned long long *)(c->bar + 2);
+    a.dynamic = (!c->cyl && c->stepper != XF_EXPH_ADAPTIVE && c->dynamic_tiles && (int)c->tiles.size() > c->G) ? 1 : 0;
     if (c->G == 0) return XF_OK;
     XF_CUDA(c, cudaMemsetAsync(c->bar, 0, sizeof(unsigned), stream), "reset barrier");
+    if (a.dynamic) XF_CUDA(c, cudaMemsetAsync(c->bar + 2, 0, sizeof(unsigned long long), stream), "reset tickets");
     if (c->cyl) XF_CUDA(c, cudaMemsetAsync(c->bar + 1, 0xff, sizeof(unsigned), stream), "reset flag");
     void *args[] = {&a};
     cudaError_t e;
@@ -1943,6 +1946,18 @@ int xf_set_option(xf_ctx *c, int option, int64_t value)
     case XF_OPT_GRAPH:
         if (value != 0 && value != 1) return fail(c, XF_E_ARG, "graph option is 0 or 1");
         c->use_graph = (int)value;
+        return XF_OK;
+    case XF_OPT_DYNAMIC_TILES:
+        if (value != 0 && value != 1) return fail(c, XF_E_ARG, "dynamic-tile option is 0 or 1");
+        if (c->pending) {
+            int rc = sync_status(c);
+            if (rc) return rc;
+        }
+        c->dynamic_tiles = (int)value;
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
         return XF_OK;
     default: return fail(c, XF_E_ARG, "unknown option %d", option);
     }

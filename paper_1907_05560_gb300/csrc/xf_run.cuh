@@ -107,6 +107,8 @@ struct RunArgs {
     AdaptPos *tstate;       // error-controlled step: [n_tiles] per-tile copies of it
     unsigned *first_bad;    // cylinder model: lowest barrier number after which a non-finite
                             // trajectory sum is read (all ones at launch)
+    unsigned long long *ticket; // dynamic tile claiming: ticket counter (zero at launch)
+    int dynamic, pad2_;     // 1: CTAs claim a stage's tiles from the counter; 0: own runs
 };
 
 __device__ __forceinline__ unsigned long long gtimer()
@@ -329,6 +331,8 @@ struct Shared {
     double w[8][NVMAX];     // per-warp sums (NT <= 256)
     double A, mu;           // stage scalars of the current tile's instance
     int flag, m_inst;       // barrier flag; instance whose moments sit in M
+    long long ticket;       // the tile this CTA claimed (dynamic claiming)
+    InstPos ps;             // progress record of the current tile's instance
 };
 
 // Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
@@ -918,16 +922,22 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM)) xf_run_
             const double *part_in = a.partials + (size_t)((nbar - 1) & 1) * a.n_tiles * NVMAX;
             double *part_out = a.partials + (size_t)(nbar & 1) * a.n_tiles * NVMAX;
             if (threadIdx.x == 0) sh.m_inst = -1;
-            for (int t = t_begin; t < t_end; ++t) {
+            auto tile_stage = [&](const int t) {
                 const Tile tl = a.tiles[t];
                 const Inst &in = a.inst[tl.inst];
-                const InstPos ps = a.pos[tl.inst];
+                // one read of the progress record for the whole CTA: another
+                // CTA may advance it meanwhile (an instance that ends or stops),
+                // and every thread must take the same branches
+                __syncthreads();
+                if (threadIdx.x == 0) sh.ps = a.pos[tl.inst];
+                __syncthreads();
+                const InstPos ps = sh.ps;
                 const long long n_i = launch_steps(a, ps);
-                if (n_i <= 0 || k > n_i) continue;
+                if (n_i <= 0 || k > n_i) return;
                 const int nf = NFM ? NFM : in.nf, nv = NMOM * (nf * nf - 1);
                 if (k == n_i) { // the instance's last step of this launch just completed
                     if (st == 0 && t == in.tile_begin) finish_instance<NT>(a, in, tl.inst, n_i, part_in, nv, sh);
-                    continue;
+                    return;
                 }
                 double *out = part_out + (size_t)t * NVMAX;
                 // moments of the stage input of this tile's instance (once per instance)
@@ -947,7 +957,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM)) xf_run_
                         const long long done = (st == 0) ? (k > 0 ? k - 1 : 0) : k;
                         advance(a.pos + tl.inst, done, ERR_NONFINITE);
                     }
-                    continue;
+                    return;
                 }
                 const double kk = (double)(ps.k0 + k), h = in.h;
                 const double r = in.r0 + kk * h, r_half = in.r0 + (kk + 0.5) * h, r_next = in.r0 + (kk + 1.0) * h;
@@ -984,6 +994,23 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM)) xf_run_
                 } else {
                     if constexpr (NFM != 2) stage_tile<3, STEP, Real, NT, VAR, NMOM>(v, smax, st, s_tab, sh, out);
                 }
+            };
+            if (a.dynamic) {
+                // claim the stage's tiles from the counter; stage s owns the
+                // tickets [s (T + G), (s + 1) (T + G)): each CTA draws until one
+                // lands past the T tiles, so exactly G tickets beyond them go
+                const unsigned long long base =
+                    (unsigned long long)(k * NSTAGE + st) * (unsigned long long)(a.n_tiles + gridDim.x);
+                for (;;) {
+                    __syncthreads();
+                    if (threadIdx.x == 0) sh.ticket = (long long)(atomicAdd(a.ticket, 1ull) - base);
+                    __syncthreads();
+                    const long long t = sh.ticket;
+                    if (t >= a.n_tiles) break;
+                    tile_stage((int)t);
+                }
+            } else {
+                for (int t = t_begin; t < t_end; ++t) tile_stage(t);
             }
             if (!grid_barrier(a, ++nbar, &sh.flag)) return;
         }

@@ -399,7 +399,7 @@ class Context:
         return g.value, t.value, b.value
 
 
-OPT_GRID, OPT_BARRIER_TIMEOUT_NS, OPT_TEST_SKIP_ARRIVAL, OPT_TILE_PAIRS, OPT_GRAPH = 1, 2, 3, 4, 5
+OPT_GRID, OPT_BARRIER_TIMEOUT_NS, OPT_TEST_SKIP_ARRIVAL, OPT_TILE_PAIRS, OPT_GRAPH, OPT_DYNAMIC_TILES = 1, 2, 3, 4, 5, 6
 
 
 class Batch(Context):

@@ -194,3 +194,22 @@ def test_autotune_restores_state_and_keeps_the_chosen_tile(xf, orc):
     for i in range(len(probs)):
         assert np.array_equal(got[i], c.get_state_i(i)[0])
     c.close()
+
+
+def test_dynamic_tile_claiming_is_bitwise_the_static_split(xf, orc):
+    """Claiming a stage's tiles from a counter gives every problem bitwise the
+    result of the static split of tiles over CTAs (a tile's arithmetic and
+    the tile order of the moment sums do not depend on which CTA ran it)."""
+    probs = [p.replace(n_steps=20) for p in I.c4_instances(n_instances=12)]
+    outs = []
+    for dyn in (0, 1):
+        b = xf.Batch(probs)
+        b.set_option(xf.OPT_TILE_PAIRS, 256)
+        b.set_option(xf.OPT_GRID, 16)  # many more tiles than CTAs
+        b.set_option(xf.OPT_DYNAMIC_TILES, dyn)
+        b.init_state_i(-1, probs[0].r0)
+        b.step_all(20, [q.h for q in probs])
+        outs.append([b.get_state_i(i)[0] for i in range(len(probs))])
+        b.close()
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
