@@ -535,6 +535,7 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
     chunk = args.batch_chunk
     # measured tile-size search (state restored afterwards), outside the timed region
     tile, tile_ms = (None, None) if args.skip_tune else b.autotune(2, h)
+    dynamic = b.get_option(xf.OPT_DYNAMIC_TILES)  # the autotuner times tile claiming on and off
     for _ in range(args.warmup):
         b.step_all(chunk, h)
     s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -564,6 +565,7 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
         # the FP64 side gets its own (shorter) measured search of tile size and
         # three-flavor cost weight, outside the timed region
         tile64 = None if args.skip_tune else c.autotune(1, h, candidates=[0, 2048, 4096, 8192])[0]
+        dynamic64 = c.get_option(xf.OPT_DYNAMIC_TILES)
         c.step_all(chunk, h)  # warm-up
         n64 = max(1, min(args.steps, 2))
         s64 = torch.cuda.Event(enable_timing=True)
@@ -577,13 +579,15 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
         t64 = max_over_ranks(s64.elapsed_time(e64) * 1e-3, world)
         c.close()
         fp64 = {"value": bins * chunk * n64 * world / t64, "unit": UNIT, "ms_per_step": 1e3 * t64 / n64,
-                "precision": "FP64", "steps": n64, "tile_pairs": tile64 if tile64 is not None else "rule"}
+                "precision": "FP64", "steps": n64, "tile_pairs": tile64 if tile64 is not None else "rule",
+                "dynamic_tiles": dynamic64}
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     return {"value": bins * chunk * args.steps * world / t, "unit": UNIT, "problems": len(probs), "bins": bins,
             "radial_steps_per_step": chunk, "ms_per_step": 1e3 * avg, "problems_ok": ok,
             "precision": "FP32 bins, FP64 moments/radius/phase", "graph": True, "ctas": ctas, "threads": threads,
             "tile_pairs": tile if tile is not None else "rule", "autotune_ms_per_step": tile_ms,
+            "dynamic_tiles": dynamic,
             "fp64_plain_same_inputs": fp64,
             "speedup_vs_fp64_plain": (bins * chunk * args.steps * world / t / fp64["value"]) if fp64 else None,
             "achieved_gbs": state_bytes / avg / 1e9, "hbm_peak_gbs": hbm,

@@ -453,9 +453,12 @@ int xf_server_destroy(xf_server *srv);
  *     XF_E_BARRIER_TIMEOUT.
  *   XF_OPT_DYNAMIC_TILES: 1 = when a pack has more tiles than CTAs, every
  *     stage's tiles are claimed from a device counter instead of each CTA
- *     taking its own run of them (fixed-step steppers); 0 = own runs.  The
- *     results do not depend on it (a tile's arithmetic is the same wherever
- *     it runs, and the moments add in tile order).
+ *     taking its own run of them (fixed-step steppers); 0 (default) = own
+ *     runs.  The results do not depend on it (a tile's arithmetic is the
+ *     same wherever it runs, and the moments add in tile order).  Claiming
+ *     pays on packs of unequal problems whose cost the static split
+ *     misjudges, and costs two CTA barriers and an atomic per tile;
+ *     xf_autotune measures both.
  *   XF_OPT_TEST_SKIP_ARRIVAL: test hook; CTA `value` (>= 0) leaves the kernel
  *     at its first grid barrier without arriving, so the other CTAs' bounded
  *     wait runs out.  -1 (default) disables it.  Exercises the timeout path
@@ -469,6 +472,10 @@ enum xf_option {
     XF_OPT_DYNAMIC_TILES = 6
 };
 int xf_set_option(xf_ctx *ctx, int option, int64_t value);
+/* Current value of an option (for XF_OPT_GRID and XF_OPT_TILE_PAIRS the
+ * request, 0 = automatic; after xf_autotune the settings it chose).
+ * XF_E_ARG for an unknown option or a NULL pointer. */
+int xf_get_option(xf_ctx *ctx, int option, int64_t *value);
 
 /* Measured search of the tile size of a fixed-step context or batch: for
  * each candidate (pairs per tile; 0 = the automatic rule; candidates = NULL
@@ -477,7 +484,9 @@ int xf_set_option(xf_ctx *ctx, int option, int64_t value);
  * fastest, which stays set as XF_OPT_TILE_PAIRS.  On a batch mixing two-
  * and three-flavor problems each candidate also runs with 0.7 and 1.4 times
  * the default cost weight of a three-flavor pair in the split of tiles over
- * CTAs, and the fastest weight stays set.  Every problem's state,
+ * CTAs, and the fastest weight stays set.  Every plan with more tiles than
+ * CTAs also runs with XF_OPT_DYNAMIC_TILES on and off, and the faster
+ * setting stays.  Every problem's state,
  * radius and step count are restored afterwards (device copies of the state
  * planes), so the search does not advance the problems.  Needs a valid
  * state in every problem.  *best_tile (may be NULL) receives the chosen

@@ -1860,7 +1860,10 @@ int xf_autotune(xf_ctx *c, int64_t n_probe, double dr_km, const int *cand_in, in
     std::vector<std::pair<int, double>> trials;
     for (double w : costs)
         for (int t : cands) trials.push_back({t, w});
-    int best = -1;
+    // each plan runs with static runs of tiles and, where it has more tiles
+    // than CTAs, with dynamic claiming too
+    const int dyn0 = c->dynamic_tiles;
+    int best = -1, best_dyn = dyn0;
     double best_t = 0.0, best_cost = cost0;
     for (size_t k = 0; k < trials.size() && !rc; ++k) {
         c->tile_request = trials[k].first;
@@ -1870,17 +1873,26 @@ int xf_autotune(xf_ctx *c, int64_t n_probe, double dr_km, const int *cand_in, in
         for (int i = 0; i < ni && !rc; ++i)
             if (c->in[i].active && dr_km > 0) rc = set_step_size(c, i, dr_km);
         if (!rc) rc = upload_instances(c);
-        if (!rc) rc = enqueue_steps(c, n_probe, -1); // untimed
-        if (!rc && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = cuda_fail(c, cudaErrorUnknown, "event");
-        if (!rc) rc = enqueue_steps(c, n_probe, -1);
-        if (!rc && cudaEventRecord(e1, c->stream) != cudaSuccess) rc = cuda_fail(c, cudaErrorUnknown, "event");
-        if (!rc) rc = sync_status(c);
-        float ms = 0.0f;
-        if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = cuda_fail(c, cudaErrorUnknown, "event");
-        if (!rc && (best < 0 || ms < best_t)) {
-            best = trials[k].first;
-            best_cost = trials[k].second;
-            best_t = ms;
+        for (int dyn = 0; dyn < 2 && !rc; ++dyn) {
+            if (dyn && (int)c->tiles.size() <= c->G) break;
+            c->dynamic_tiles = dyn;
+            if (c->graph) { // a captured launch holds the previous setting
+                cudaGraphExecDestroy(c->graph);
+                c->graph = nullptr;
+            }
+            rc = enqueue_steps(c, n_probe, -1); // untimed
+            if (!rc && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = cuda_fail(c, cudaErrorUnknown, "event");
+            if (!rc) rc = enqueue_steps(c, n_probe, -1);
+            if (!rc && cudaEventRecord(e1, c->stream) != cudaSuccess) rc = cuda_fail(c, cudaErrorUnknown, "event");
+            if (!rc) rc = sync_status(c);
+            float ms = 0.0f;
+            if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = cuda_fail(c, cudaErrorUnknown, "event");
+            if (!rc && (best < 0 || ms < best_t)) {
+                best = trials[k].first;
+                best_cost = trials[k].second;
+                best_dyn = dyn;
+                best_t = ms;
+            }
         }
     }
     // restore states, progress and host views whatever happened
@@ -1902,6 +1914,7 @@ int xf_autotune(xf_ctx *c, int64_t n_probe, double dr_km, const int *cand_in, in
     dev_free(c, snap);
     c->tile_request = rc ? tile0 : best;
     c->cost3 = rc ? cost0 : best_cost;
+    c->dynamic_tiles = rc ? dyn0 : best_dyn;
     int rp = plan_launch(c);
     if (!rp) rp = upload_instances(c);
     if (rc) return rc;
@@ -1968,6 +1981,21 @@ int xf_tables(xf_ctx *c, double *E, double *phi)
     if (!c) return XF_E_ARG;
     if (E) std::memcpy(E, c->in[0].E.data(), sizeof(double) * c->in[0].E.size());
     if (phi) std::memcpy(phi, c->in[0].phi.data(), sizeof(double) * c->in[0].phi.size());
+    return XF_OK;
+}
+
+int xf_get_option(xf_ctx *c, int option, int64_t *value)
+{
+    if (!c || !value) return XF_E_ARG;
+    switch (option) {
+    case XF_OPT_GRID: *value = c->grid_request; break;
+    case XF_OPT_BARRIER_TIMEOUT_NS: *value = (int64_t)c->timeout_ns; break;
+    case XF_OPT_TEST_SKIP_ARRIVAL: *value = c->skip_cta; break;
+    case XF_OPT_TILE_PAIRS: *value = c->tile_request; break;
+    case XF_OPT_GRAPH: *value = c->use_graph; break;
+    case XF_OPT_DYNAMIC_TILES: *value = c->dynamic_tiles; break;
+    default: return fail(c, XF_E_ARG, "unknown option %d", option);
+    }
     return XF_OK;
 }
 

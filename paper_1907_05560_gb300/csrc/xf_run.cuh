@@ -331,7 +331,7 @@ struct Shared {
     double w[8][NVMAX];     // per-warp sums (NT <= 256)
     double A, mu;           // stage scalars of the current tile's instance
     int flag, m_inst;       // barrier flag; instance whose moments sit in M
-    long long ticket;       // the tile this CTA claimed (dynamic claiming)
+    int ticket, pad_;       // the tile this CTA claimed (-1: none left; dynamic claiming)
     InstPos ps;             // progress record of the current tile's instance
 };
 
@@ -925,13 +925,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM)) xf_run_
             auto tile_stage = [&](const int t) {
                 const Tile tl = a.tiles[t];
                 const Inst &in = a.inst[tl.inst];
-                // one read of the progress record for the whole CTA: another
-                // CTA may advance it meanwhile (an instance that ends or stops),
-                // and every thread must take the same branches
-                __syncthreads();
-                if (threadIdx.x == 0) sh.ps = a.pos[tl.inst];
-                __syncthreads();
-                const InstPos ps = sh.ps;
+                const InstPos &ps = sh.ps;
                 const long long n_i = launch_steps(a, ps);
                 if (n_i <= 0 || k > n_i) return;
                 const int nf = NFM ? NFM : in.nf, nv = NMOM * (nf * nf - 1);
@@ -995,22 +989,36 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM)) xf_run_
                     if constexpr (NFM != 2) stage_tile<3, STEP, Real, NT, VAR, NMOM>(v, smax, st, s_tab, sh, out);
                 }
             };
-            if (a.dynamic) {
-                // claim the stage's tiles from the counter; stage s owns the
-                // tickets [s (T + G), (s + 1) (T + G)): each CTA draws until one
-                // lands past the T tiles, so exactly G tickets beyond them go
-                const unsigned long long base =
-                    (unsigned long long)(k * NSTAGE + st) * (unsigned long long)(a.n_tiles + gridDim.x);
-                for (;;) {
-                    __syncthreads();
-                    if (threadIdx.x == 0) sh.ticket = (long long)(atomicAdd(a.ticket, 1ull) - base);
-                    __syncthreads();
-                    const long long t = sh.ticket;
-                    if (t >= a.n_tiles) break;
-                    tile_stage((int)t);
+            // Thread 0 takes the next tile (the next of the CTA's own run, or
+            // a ticket) and reads its instance's progress record; both reach
+            // the CTA through shared memory.  One call site of tile_stage
+            // serves both ways of taking tiles, so a tile runs the same
+            // instructions whichever CTA takes it.  Dynamic claiming: stage s
+            // owns the tickets [s (T + G), (s + 1) (T + G)); each CTA draws
+            // until one lands past the T tiles, so exactly G tickets beyond
+            // them go.  The progress record is read once per tile and CTA:
+            // another CTA may advance it meanwhile (an instance that ends or
+            // stops), and every thread must take the same branches.
+            int next = t_begin;
+            for (;;) {
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int t = -1;
+                    if (a.dynamic) {
+                        const unsigned long long base =
+                            (unsigned long long)(k * NSTAGE + st) * (unsigned long long)(a.n_tiles + gridDim.x);
+                        const long long d = (long long)(atomicAdd(a.ticket, 1ull) - base);
+                        if (d < a.n_tiles) t = (int)d;
+                    } else if (next < t_end) {
+                        t = next++;
+                    }
+                    sh.ticket = t;
+                    if (t >= 0) sh.ps = a.pos[a.tiles[t].inst];
                 }
-            } else {
-                for (int t = t_begin; t < t_end; ++t) tile_stage(t);
+                __syncthreads();
+                const int t = sh.ticket;
+                if (t < 0) break;
+                tile_stage(t);
             }
             if (!grid_barrier(a, ++nbar, &sh.flag)) return;
         }

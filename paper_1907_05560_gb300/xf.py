@@ -113,6 +113,7 @@ SIGNATURES = {
     "xf_launch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
     "xf_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
+    "xf_get_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     "xf_create_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(XFProblem), ctypes.POINTER(XFAllocator),
                                        ctypes.POINTER(_P)]),
     "xf_batch_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
@@ -392,6 +393,11 @@ class Context:
 
     def set_option(self, option: int, value: int):
         return self._check(self.L.xf_set_option(self.h, int(option), int(value)))
+
+    def get_option(self, option: int) -> int:
+        v = ctypes.c_int64(0)
+        self._check(self.L.xf_get_option(self.h, int(option), ctypes.byref(v)))
+        return v.value
 
     def launch_info(self):
         g, t, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

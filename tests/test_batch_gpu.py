@@ -182,6 +182,10 @@ def test_autotune_restores_state_and_keeps_the_chosen_tile(xf, orc):
     before = [b.get_state_i(i) for i in range(len(probs))]
     tile, ms = b.autotune(4, h, [64, 256, 1024])
     assert tile in (64, 256, 1024) and ms > 0
+    assert b.get_option(xf.OPT_TILE_PAIRS) == tile and b.get_option(xf.OPT_DYNAMIC_TILES) in (0, 1)
+    with pytest.raises(xf.XFError) as ei:
+        b.get_option(99)
+    assert ei.value.name == "XF_E_ARG"
     for i, (x, r, n) in enumerate(before):
         y, r2, n2 = b.get_state_i(i)
         assert np.array_equal(x, y) and r == r2 and n == n2
@@ -196,17 +200,19 @@ def test_autotune_restores_state_and_keeps_the_chosen_tile(xf, orc):
     c.close()
 
 
-def test_dynamic_tile_claiming_is_bitwise_the_static_split(xf, orc):
+@pytest.mark.parametrize("precision", [I.FP32_M64, I.FP64])
+def test_dynamic_tile_claiming_is_bitwise_the_static_split(xf, orc, precision):
     """Claiming a stage's tiles from a counter gives every problem bitwise the
     result of the static split of tiles over CTAs (a tile's arithmetic and
     the tile order of the moment sums do not depend on which CTA ran it)."""
-    probs = [p.replace(n_steps=20) for p in I.c4_instances(n_instances=12)]
+    probs = [p.replace(n_steps=20, precision=precision) for p in I.c4_instances(n_instances=12)]
     outs = []
     for dyn in (0, 1):
         b = xf.Batch(probs)
         b.set_option(xf.OPT_TILE_PAIRS, 256)
         b.set_option(xf.OPT_GRID, 16)  # many more tiles than CTAs
         b.set_option(xf.OPT_DYNAMIC_TILES, dyn)
+        assert b.get_option(xf.OPT_DYNAMIC_TILES) == dyn and b.get_option(xf.OPT_TILE_PAIRS) == 256
         b.init_state_i(-1, probs[0].r0)
         b.step_all(20, [q.h for q in probs])
         outs.append([b.get_state_i(i)[0] for i in range(len(probs))])
