@@ -534,7 +534,10 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
     h = probs[0].h
     chunk = args.batch_chunk
     # measured tile-size search (state restored afterwards), outside the timed region
-    tile, tile_ms = (None, None) if args.skip_tune else b.autotune(2, h)
+    if args.skip_tune:  # a fixed launch shape (profiling)
+        b.set_option(xf.OPT_TILE_PAIRS, args.batch_tile)
+        b.set_option(xf.OPT_DYNAMIC_TILES, args.batch_dynamic)
+    tile, tile_ms = ((args.batch_tile or None), None) if args.skip_tune else b.autotune(2, h)
     dynamic = b.get_option(xf.OPT_DYNAMIC_TILES)  # the autotuner times tile claiming on and off
     for _ in range(args.warmup):
         b.step_all(chunk, h)
@@ -678,6 +681,9 @@ def main():
     ap.add_argument("--skip-cylinder", action="store_true", help="skip the cylinder-model leg")
     ap.add_argument("--skip-tune", action="store_true", help="batched leg: keep the automatic tile size")
     ap.add_argument("--skip-batch-fp64", action="store_true", help="batched leg: skip the FP64 run of the ensemble")
+    ap.add_argument("--batch-tile", type=int, default=0, help="batched leg with --skip-tune: pairs per tile (0: rule)")
+    ap.add_argument("--batch-dynamic", type=int, default=0, choices=[0, 1],
+                    help="batched leg with --skip-tune: dynamic tile claiming")
     ap.add_argument("--adapt-iters", type=int, default=30, help="attempts per error-controlled bench step")
     ap.add_argument("--serve-rate", type=float, default=10.0, help="sustained arrival rate, jobs/s")
     ap.add_argument("--serve-window", type=float, default=5.0, help="arrival window at the sustained rate, s")
