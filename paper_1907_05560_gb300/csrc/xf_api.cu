@@ -339,13 +339,24 @@ int plan_launch(xf_ctx *c)
     }
     tp = std::min<long long>(std::max<long long>((tp + 31) / 32 * 32, 32), 1 << 20);
     const int TP = (int)tp;
+    // problems in descending order of the cost of a pair (three-flavor ones
+    // first, stable otherwise): CTAs working at the same time then mostly
+    // run one flavor's code, which keeps the instruction cache warm on packs
+    // of mixed flavors, and dynamic claiming hands out the dearer tiles
+    // first.  Each problem's tiles stay contiguous and in order, so its
+    // moment sums do not change.
+    std::vector<int> order(c->in.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return pair_cost(c, c->in[x]) > pair_cost(c, c->in[y]);
+    });
     c->tiles.clear();
-    for (size_t i = 0; i < c->in.size(); ++i) {
+    for (const int i : order) {
         InstHost &in = c->in[i];
         in.tile_begin = (int)c->tiles.size();
         if (in.active)
             for (int p0 = 0; p0 < in.n_pairs; p0 += TP)
-                c->tiles.push_back({(int)i, p0, std::min(TP, in.n_pairs - p0), 0});
+                c->tiles.push_back({i, p0, std::min(TP, in.n_pairs - p0), 0});
         in.tile_end = (int)c->tiles.size();
     }
     const int T = (int)c->tiles.size();
