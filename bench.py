@@ -331,7 +331,7 @@ def run_xf(args):
     # DRAM bytes (read + write) per radial step of this kernel on this workload, from
     # one ncu capture of a 5-step launch (dram__bytes_read.sum + dram__bytes_write.sum
     # = 147.6 MB), scaled to the bench's launch; null for other precisions
-    traffic = 28.20e6 * chunk if args.precision == "fp64" else None
+    traffic = 28.67e6 * chunk if args.precision == "fp64" else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_nom, "unit": "TFLOP/s",
                 "frac": achieved / peak_nom, "traffic": traffic,
                 "traffic_note": "bytes per launch from ncu DRAM counters (5-step capture, scaled to %d steps); "
