@@ -378,10 +378,11 @@ int plan_launch(xf_ctx *c)
     const size_t per_angle = ad ? (c->real_bytes == 8 ? xf::ASlots<double>::n * sizeof(double)
                                                       : xf::ASlots<float>::n * sizeof(float))
                                 : (size_t)((c->real_bytes == 8 ? 5 : 6) + (c->nmom == 4 ? 4 : 0)) * c->real_bytes;
-    size_t smem = per_angle * (size_t)span;
-    smem = (smem + 15) & ~size_t(15);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(c->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    int stage_off = 0;
+    size_t smem = ad ? ((per_angle * (size_t)span + 15) & ~size_t(15))
+                     : xf::run_smem(per_angle * (size_t)span, c->real_bytes, c->stepper == XF_EXPH, c->nmom, c->form,
+                                    c->nfm, nt, &stage_off);
+    if (!allow_dynamic_smem(c->kern.fn, smem)) { // static plus dynamic shared memory may pass 48 KB
         cudaGetLastError();
         return fail(c, XF_E_UNSUPPORTED, "angle table needs %zu bytes of shared memory", smem);
     }
@@ -408,6 +409,7 @@ int plan_launch(xf_ctx *c)
     c->tile_pairs = TP;
     c->span_max = span;
     c->smem = smem;
+    c->stage_off = stage_off;
     c->cta_tiles = ct;
     // device copies (the tile buffers are sized for the most tiles seen)
     if (T > c->max_tiles) {
@@ -447,8 +449,7 @@ int plan_launch_cyl(xf_ctx *c)
     }
     const int T = in.n_u * in.n_phi, nw = c->kern.nt / 32;
     const size_t smem = (size_t)(4 + 2 * xf::CYL_ROWS) * in.n_u * sizeof(double) + (size_t)xf::CYL_ROWS * in.n_u * sizeof(int);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(c->kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    if (!allow_dynamic_smem(c->kern.fn, smem)) { // static plus dynamic shared memory may pass 48 KB
         cudaGetLastError();
         return fail(c, XF_E_UNSUPPORTED, "angle table needs %zu bytes of shared memory", smem);
     }
@@ -595,6 +596,10 @@ int sync_status(xf_ctx *c)
         }
     }
     c->pending = 0;
+    if (err == ERR_LAUNCH) { // the kernel left before touching anything
+        XF_CUDA(c, cudaMemset(c->err, 0, sizeof(int)), "reset error word");
+        return fail(c, XF_E_CUDA, "integrator launched without its shared-memory staging area");
+    }
     if (err) {
         XF_CUDA(c, cudaMemset(c->err, 0, sizeof(int)), "reset error word");
         for (InstHost &h : c->in) h.state_valid = false;
@@ -634,6 +639,7 @@ int enqueue_run(xf_ctx *c, long long n, cudaStream_t stream)
     a.first_bad = c->bar + 1;
     a.ticket = (unsigned long long *)(c->bar + 2);
     a.dynamic = (!c->cyl && c->stepper != XF_EXPH_ADAPTIVE && c->dynamic_tiles && (int)c->tiles.size() > c->G) ? 1 : 0;
+    a.stage_off = c->stage_off;
     if (c->G == 0) return XF_OK;
     XF_CUDA(c, cudaMemsetAsync(c->bar, 0, sizeof(unsigned), stream), "reset barrier");
     if (a.dynamic) XF_CUDA(c, cudaMemsetAsync(c->bar + 2, 0, sizeof(unsigned long long), stream), "reset tickets");

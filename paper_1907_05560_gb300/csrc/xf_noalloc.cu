@@ -166,10 +166,10 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
         1 << 20, std::max<long long>(32, ((n_pairs + slots - 1) / slots + 31) / 32 * 32));
     const int T = (n_pairs + TP - 1) / TP;
     const int span = std::min(n_u, (TP + n_E - 1) / n_E + 1);
-    size_t smem = (sizeof(Real) == 8 ? 5 * sizeof(double) : 6 * sizeof(float)) * (size_t)std::max(span, 1);
-    smem = (smem + 15) & ~size_t(15);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kern.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    int stage_off = 0;
+    const size_t smem = run_smem((sizeof(Real) == 8 ? 5 * sizeof(double) : 6 * sizeof(float)) * (size_t)std::max(span, 1),
+                                 (int)sizeof(Real), st == STEP_EXPH, 2, FORM_RHO, NF, kern.nt, &stage_off);
+    if (!allow_dynamic_smem(kern.fn, smem)) { // static plus dynamic shared memory may pass 48 KB
         cudaGetLastError();
         return noalloc_fail(XF_E_UNSUPPORTED, "angle table too large for shared memory");
     }
@@ -317,6 +317,7 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
         a.err = err;
         a.timeout_ns = 2000000000ull;
         a.skip_cta = -1;
+        a.stage_off = stage_off;
         NA_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), stream), "clear barrier");
         void *args[] = {&a};
         cudaError_t e = (G > 1) ? cudaLaunchCooperativeKernel(kern.fn, dim3(G), dim3(kern.nt), args, smem, stream)
@@ -332,6 +333,7 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
     NA_CUDA(cudaMemcpyAsync(&h_pos, pos, sizeof(InstPos), cudaMemcpyDeviceToHost, stream), "read progress");
     NA_CUDA(cudaStreamSynchronize(stream), "stream synchronize");
     if (h_bad) return noalloc_fail(XF_E_STATE, "input state contains non-finite values");
+    if (h_err & ERR_LAUNCH) return noalloc_fail(XF_E_CUDA, "integrator launched without its staging area");
     if (h_err & ERR_BARRIER) return noalloc_fail(XF_E_BARRIER_TIMEOUT, "grid barrier timed out; output not written");
 
     // working buffers -> caller's packed state (the buffer of the last step taken)

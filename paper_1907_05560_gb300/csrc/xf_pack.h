@@ -148,6 +148,7 @@ struct xf_ctx {
 
     // options
     int grid_request = 0, tile_request = 0, skip_cta = -1, use_graph = 0;
+    int stage_off = 0; // byte offset of the run kernel's staging columns in dynamic shared memory
     int dynamic_tiles = 0; // CTAs claim tiles per stage from a counter (when tiles outnumber CTAs)
     unsigned long long timeout_ns = 2000000000ull;
 

@@ -34,7 +34,7 @@ namespace xf {
 enum { GEOM_BULB = 0, GEOM_MU_R4 = 1, GEOM_SA = 2, GEOM_CONST = 3, GEOM_CYL = 4 };
 enum { MAT_NONE = 0, MAT_POWER = 1, MAT_EXP = 2 };
 enum { STEP_RK4 = 0, STEP_EXPH = 1, STEP_ADAPT = 2 };
-enum { ERR_NONFINITE = 1, ERR_BARRIER = 2 };
+enum { ERR_NONFINITE = 1, ERR_BARRIER = 2, ERR_LAUNCH = 4 };
 // variants of the per-bin arithmetic: plain; moments summed in compensated
 // FP32 (TwoSum) up to the warp; plain with the per-step restoration of each
 // bin's tr(rho0^2) (|P|^2 / 2 in two flavors) to its initial value
@@ -108,7 +108,9 @@ struct RunArgs {
     unsigned *first_bad;    // cylinder model: lowest barrier number after which a non-finite
                             // trajectory sum is read (all ones at launch)
     unsigned long long *ticket; // dynamic tile claiming: ticket counter (zero at launch)
-    int dynamic, pad2_;     // 1: CTAs claim a stage's tiles from the counter; 0: own runs
+    int dynamic;            // 1: CTAs claim a stage's tiles from the counter; 0: own runs
+    int stage_off;          // byte offset of the state staging columns in dynamic shared
+                            // memory (FP32 predictor-corrector kernels; 0: none)
 };
 
 __device__ __forceinline__ unsigned long long gtimer()
@@ -325,10 +327,13 @@ __device__ inline void build_azimuth_table(const Inst &a, Real *tb, int smax, in
 }
 
 // Shared per-CTA scratch of the kernel.
+template <int NT>
 struct Shared {
     double M[NVMAX];        // moments (dE applied) of the current tile's instance
-    double scr[256];        // reduction scratch (>= NT)
-    double w[8][NVMAX];     // per-warp sums (NT <= 256)
+    union {                 // never live at once: a barrier separates their uses
+        double scr[NT];     // instance totals' scratch
+        double w[NT / 32][NVMAX]; // per-warp sums of a tile's partial
+    };
     double A, mu;           // stage scalars of the current tile's instance
     int flag, m_inst;       // barrier flag; instance whose moments sit in M
     int ticket, pad_;       // the tile this CTA claimed (-1: none left; dynamic claiming)
@@ -412,7 +417,7 @@ __device__ __forceinline__ void cta_partial(Acc *m, SH &sh, double *part)
 // flight, and the lg sums of a component are added in thread order: a fixed
 // order, so results are reproducible.
 template <int NT>
-__device__ __forceinline__ void instance_total(const double *part, int t0, int t1, int nv, double dE, Shared &sh)
+__device__ __forceinline__ void instance_total(const double *part, int t0, int t1, int nv, double dE, Shared<NT> &sh)
 {
     const int nvp = nv <= 8 ? 8 : (nv <= 16 ? 16 : 32);
     const int lg = NT / nvp;
@@ -510,11 +515,79 @@ struct TileView {
     double h;
 };
 
-// One stage of one tile: update every pair, accumulate and reduce the sums.
-template <int NF, int STEP, typename Real, int NT, int VAR, int NMOM>
-__device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int st, const Real *tb, Shared &sh,
-                                           double *part_out)
+// Asynchronous 4-byte copies global -> shared (cp.async, completion tracked
+// per thread in commit groups).
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// State staging of the FP32 predictor-corrector: while a thread updates one
+// pair, the planes of its next pair (rho_n, and in the corrector the
+// predictor's output) are already on their way into shared memory.  Each
+// thread copies and reads only its own column, two buffers of
+// stage_planes(NF) words ([plane][thread], stride NT), so no CTA barrier
+// is involved.
+// Kernels of one flavor count only: in the kernel for mixed packs, which
+// issues on most cycles, the extra copy and shared-load instructions cost
+// more than the hidden latency gives (C4: 1.73e10 against 1.77e10
+// bin-steps/s), while the one-flavor kernels gain 2-3 %.
+template <int NFM, int STEP, typename Real, int NMOM>
+struct Staging { static constexpr bool on = NFM != 0 && STEP == STEP_EXPH && sizeof(Real) == 4 && NMOM == 2; };
+__host__ __device__ constexpr int stage_planes(int nf) { return 4 * (nf == 2 ? 3 : 8); }
+// Bytes of staging columns of a kernel of nfm (2 or 3) flavors.
+__host__ __device__ constexpr size_t stage_bytes(int nfm, int nt) { return (size_t)2 * stage_planes(nfm) * nt * 4; }
+// Dynamic shared memory of a fixed-step run kernel: the per-angle tables
+// (table_bytes), then, for the kernels that stage (FP32 predictor-corrector,
+// density-matrix form, two moments), the staging columns at *stage_off
+// (0 for the others).
+inline size_t run_smem(size_t table_bytes, int real_bytes, bool exph, int nmom, int form, int nfm, int nt,
+                       int *stage_off)
+{
+    size_t smem = (table_bytes + 15) & ~(size_t)15;
+    *stage_off = 0;
+    if (nfm != 0 && real_bytes == 4 && exph && nmom == 2 && form == FORM_RHO) {
+        *stage_off = (int)smem;
+        smem += stage_bytes(nfm, nt);
+    }
+    return smem;
+}
+// Let a kernel launch with `bytes` of dynamic shared memory.  The limit is a
+// property of the kernel shared by every context of the process, so it only
+// ever grows.  Returns false when the device cannot grant it.
+inline bool allow_dynamic_smem(const void *fn, size_t bytes)
+{
+    cudaFuncAttributes at;
+    if (cudaFuncGetAttributes(&at, fn) != cudaSuccess) return false;
+    if ((size_t)at.maxDynamicSharedSizeBytes >= bytes) return true;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+}
+__device__ __forceinline__ unsigned dynamic_smem_bytes()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
+template <int S, typename Real, int NT>
+__device__ __forceinline__ void stage_issue(Real *col, const TileView<Real> &v, int p, bool with_aux)
+{
+#pragma unroll
+    for (int k = 0; k < 2 * S; ++k) cp_async4(col + k * NT, v.cur + (size_t)k * v.npad + p);
+    if (with_aux)
+#pragma unroll
+        for (int k = 0; k < 2 * S; ++k) cp_async4(col + (2 * S + k) * NT, v.aux + (size_t)k * v.npad + p);
+}
+
+// One stage of one tile: update every pair, accumulate and reduce the sums.
+template <int NF, int STEP, typename Real, int NT, int VAR, int NMOM, bool PF>
+__device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int st, const Real *tb, Shared<NT> &sh,
+                                           double *part_out, Real *stg)
+{
+    constexpr int NPL = stage_planes(NF);
     static_assert(NMOM == 2 || (NMOM == 4 && VAR == VAR_PLAIN), "azimuth moments: plain arithmetic only");
     constexpr int S = Comp<NF>::S, NV = NMOM * S, AB = TabSlots<Real>::n;
     using Acc = Real; // warp-level accumulation precision
@@ -535,7 +608,19 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
 #pragma unroll
     for (int c = 0; c < NV; ++c) m[c] = Acc(0);
 
-    for (int p = v.p0 + threadIdx.x; p < v.p1; p += NT) {
+    Real *const col0 = PF ? stg + threadIdx.x : nullptr;
+    if constexpr (PF) {
+        if (v.p0 + (int)threadIdx.x < v.p1) stage_issue<S, Real, NT>(col0, v, v.p0 + threadIdx.x, st == 1);
+        cp_async_commit();
+    }
+    int buf = 0;
+    for (int p = v.p0 + threadIdx.x; p < v.p1; p += NT, buf ^= 1) {
+        Real *const col = PF ? col0 + buf * NPL * NT : nullptr;
+        if constexpr (PF) {
+            if (p + NT < v.p1) stage_issue<S, Real, NT>(col0 + (buf ^ 1) * NPL * NT, v, p + NT, st == 1);
+            cp_async_commit();
+            cp_async_wait<1>(); // this pair's copies have landed
+        }
         const int j = p / v.n_E, e = p - j * v.n_E, q = j - v.j_lo;
         const Real gam = tb[q];
         Real g[S], hv[S], hn[S], hb[S];
@@ -594,7 +679,12 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 Real rn[S], pr[S];
-                load_state<Real, S>(v.cur, v.npad, s, p, rn);
+                if constexpr (PF) {
+#pragma unroll
+                    for (int c = 0; c < S; ++c) rn[c] = col[(c * 2 + s) * NT];
+                } else {
+                    load_state<Real, S>(v.cur, v.npad, s, p, rn);
+                }
                 prop<NF, Real>(s == 0 ? hn : hb, dl, rn, pr);
                 Real *o = (s == 0) ? on : ob;
                 if (st == 0) {
@@ -603,7 +693,12 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
                     store_state<Real, S>(v.aux, v.npad, s, p, o);
                 } else {
                     Real pp[S];
-                    load_state<Real, S>(v.aux, v.npad, s, p, pp);
+                    if constexpr (PF) {
+#pragma unroll
+                        for (int c = 0; c < S; ++c) pp[c] = col[(2 * S + c * 2 + s) * NT];
+                    } else {
+                        load_state<Real, S>(v.aux, v.npad, s, p, pp);
+                    }
 #pragma unroll
                     for (int c = 0; c < S; ++c) o[c] = Real(0.5) * (pp[c] + pr[c]);
                     if (VAR == VAR_RENORM && last_stage) renormalise<NF, Real>(o, v.ref[(size_t)s * v.npad + p]);
@@ -618,6 +713,7 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
             accum_comp<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], m, mc);
         else accum<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], m);
     }
+    if constexpr (PF) cp_async_wait<0>();
     if constexpr (VAR == VAR_COMP) cta_partial_comp<NV, NT, Acc>(m, mc, sh, part_out);
     else cta_partial<NV, NT, Acc>(m, sh, part_out);
 }
@@ -634,7 +730,7 @@ __device__ __forceinline__ void psi_weights(const TileView<Real> &v, int s, int 
 // stage_tile (RK4 on d(psi)/dr = -i H psi dl/dr, or the predictor-corrector
 // averaging wavefunctions), moments of rho = sum_a phi_a psi_a psi_a^+.
 template <int NF, int STEP, typename Real, int NT>
-__device__ __forceinline__ void psi_stage_tile(const TileView<Real> v, int smax, int st, const Real *tb, Shared &sh,
+__device__ __forceinline__ void psi_stage_tile(const TileView<Real> v, int smax, int st, const Real *tb, Shared<NT> &sh,
                                                double *part_out)
 {
     constexpr int S = Comp<NF>::S, SS = PsiComp<NF>::SS, NV = 2 * S;
@@ -723,7 +819,7 @@ __device__ __forceinline__ void psi_stage_tile(const TileView<Real> v, int smax,
 
 // Prologue for one tile in the wavefunction form: moments of the input state.
 template <int NF, typename Real, int NT>
-__device__ __forceinline__ void psi_prologue_tile(const TileView<Real> v, int smax, const Real *tb, Shared &sh,
+__device__ __forceinline__ void psi_prologue_tile(const TileView<Real> v, int smax, const Real *tb, Shared<NT> &sh,
                                                   double *part_out)
 {
     constexpr int S = Comp<NF>::S, SS = PsiComp<NF>::SS, NV = 2 * S;
@@ -830,7 +926,7 @@ __device__ __forceinline__ void advance(InstPos *pp, long long done, int err)
 
 template <int NT>
 __device__ __forceinline__ void finish_instance(const RunArgs &a, const Inst &in, int inst, long long n,
-                                                const double *part_in, int nv, Shared &sh)
+                                                const double *part_in, int nv, Shared<NT> &sh)
 {
     __syncthreads();
     instance_total<NT>(part_in, in.tile_begin, in.tile_end, nv, in.dE, sh);
@@ -876,7 +972,8 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM)) xf_run_
 {
     extern __shared__ double s_dyn[];
     Real *const s_tab = (Real *)s_dyn;
-    __shared__ Shared sh;
+    Real *const s_stg = (Real *)((char *)s_dyn + a.stage_off);
+    __shared__ Shared<NT> sh;
     const int t_begin = a.cta_tiles[blockIdx.x], t_end = a.cta_tiles[blockIdx.x + 1];
     const int smax = a.span_max;
     unsigned nbar = 0;
@@ -885,6 +982,15 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM)) xf_run_
     if (threadIdx.x == 0) sh.flag = *(volatile int *)a.err;
     __syncthreads();
     if (sh.flag) return;
+    constexpr bool STG = FORM == FORM_RHO && Staging<NFM, STEP, Real, NMOM>::on;
+    if constexpr (STG) {
+        // a launch without room for the staging columns leaves at once, with
+        // every CTA, before any barrier
+        if (a.stage_off <= 0 || dynamic_smem_bytes() < (unsigned)a.stage_off + stage_bytes(NFM, NT)) {
+            if (threadIdx.x == 0) atomicOr(a.err, ERR_LAUNCH);
+            return;
+        }
+    }
 
     // ---- prologue: weighted sums of every tile's input state at its start radius
     for (int t = t_begin; t < t_end; ++t) {
@@ -908,9 +1014,9 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM)) xf_run_
                 if constexpr (NFM != 2) psi_prologue_tile<3, Real, NT>(v, smax, s_tab, sh, out);
             }
         } else if (nf == 2) {
-            if constexpr (NFM != 3) prologue_tile<2, Real, NT, VAR, Shared, NMOM>(v, smax, s_tab, sh, out);
+            if constexpr (NFM != 3) prologue_tile<2, Real, NT, VAR, Shared<NT>, NMOM>(v, smax, s_tab, sh, out);
         } else {
-            if constexpr (NFM != 2) prologue_tile<3, Real, NT, VAR, Shared, NMOM>(v, smax, s_tab, sh, out);
+            if constexpr (NFM != 2) prologue_tile<3, Real, NT, VAR, Shared<NT>, NMOM>(v, smax, s_tab, sh, out);
         }
     }
     if (!grid_barrier(a, ++nbar, &sh.flag)) return;
@@ -984,9 +1090,9 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM)) xf_run_
                         if constexpr (NFM != 2) psi_stage_tile<3, STEP, Real, NT>(v, smax, st, s_tab, sh, out);
                     }
                 } else if (nf == 2) {
-                    if constexpr (NFM != 3) stage_tile<2, STEP, Real, NT, VAR, NMOM>(v, smax, st, s_tab, sh, out);
+                    if constexpr (NFM != 3) stage_tile<2, STEP, Real, NT, VAR, NMOM, STG>(v, smax, st, s_tab, sh, out, s_stg);
                 } else {
-                    if constexpr (NFM != 2) stage_tile<3, STEP, Real, NT, VAR, NMOM>(v, smax, st, s_tab, sh, out);
+                    if constexpr (NFM != 2) stage_tile<3, STEP, Real, NT, VAR, NMOM, STG>(v, smax, st, s_tab, sh, out, s_stg);
                 }
             };
             // Thread 0 takes the next tile (the next of the CTA's own run, or
