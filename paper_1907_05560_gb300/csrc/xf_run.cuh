@@ -23,6 +23,8 @@
 // SM's FP64 pipe for 16 cycles on this GPU).
 #pragma once
 
+#include <mutex>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -560,6 +562,8 @@ inline size_t run_smem(size_t table_bytes, int real_bytes, bool exph, int nmom, 
 // ever grows.  Returns false when the device cannot grant it.
 inline bool allow_dynamic_smem(const void *fn, size_t bytes)
 {
+    static std::mutex mu; // read-and-raise is one step for the whole process
+    std::lock_guard<std::mutex> lock(mu);
     cudaFuncAttributes at;
     if (cudaFuncGetAttributes(&at, fn) != cudaSuccess) return false;
     if ((size_t)at.maxDynamicSharedSizeBytes >= bytes) return true;
