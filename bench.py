@@ -163,7 +163,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_1907_05560_gb300 import inputs as I
-    p = I.c2()
+    p = I.bulb3f_1000x200()
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
         oracle_sample(p, 1, threads)
@@ -206,7 +206,7 @@ def run_xf(args):
 
     stream = torch.cuda.current_stream()
     chunk = args.chunk
-    p = I.c2().replace(seed=2 + rank)
+    p = I.bulb3f_1000x200().replace(seed=2 + rank)
     if args.precision == "fp32":
         p = p.replace(precision=I.FP32_M64)
 
@@ -344,7 +344,7 @@ def run_xf(args):
     cpu = None
     if rank == 0 and not args.skip_cpu:
         threads_cpu = os.cpu_count() or 1
-        v, dt = oracle_sample(I.c2(), args.cpu_steps, threads_cpu)
+        v, dt = oracle_sample(I.bulb3f_1000x200(), args.cpu_steps, threads_cpu)
         cpu = {"value": v, "unit": UNIT, "cores": threads_cpu, "kind": "oracle",
                "sample": f"{args.cpu_steps} radial steps of the full 400,000-bin problem from 10 km ({dt:.1f} s)"}
 
@@ -374,7 +374,7 @@ def run_adaptive(args, xf, I, torch, stream, flush, barrier, world, peak_tflops)
     """The paper's error-controlled step on the three-flavor 400,000-bin
     workload from 250 km (eps0 = 1e-6, dr_max = 0.05 km), FP64: one bench step
     = a fixed budget of attempts (xf_evolve toward 1000 km stops on the budget)."""
-    p = I.c2().replace(stepper=I.EXPH_ADAPTIVE, r0=250.0, eps0=1e-6, dr_max=0.05)
+    p = I.bulb3f_1000x200().replace(stepper=I.EXPH_ADAPTIVE, r0=250.0, eps0=1e-6, dr_max=0.05)
     c = xf.Context(p, stream=stream)
     c.init_state(p.r0)
     iters = args.adapt_iters
@@ -453,7 +453,7 @@ def run_psi(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
     3-flavor 1000 x 200 bulb problem with one wavefunction per initial flavor
     (18 reals per bin instead of 8), FP64, the predictor-corrector averaging
     wavefunctions; one bench step = `chunk` radial steps."""
-    p = I.c2().replace(form=I.FORM_PSI)
+    p = I.bulb3f_1000x200().replace(form=I.FORM_PSI)
     c = xf.Context(p, stream=stream)
     c.init_state(p.r0)
     chunk = args.chunk
@@ -527,7 +527,7 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
     2 or 3 flavors, mu0 1e3-1e6, either hierarchy), FP32 bins with FP64
     moments, the predictor-corrector, replayed from a captured CUDA graph;
     one bench step = `batch_chunk` radial steps of every problem."""
-    probs = I.c4_instances()
+    probs = I.ensemble_problems()
     b = xf.Batch(probs, stream=stream)
     b.set_option(xf.OPT_GRAPH, 1)
     b.init_state_i(-1, probs[0].r0)
@@ -610,7 +610,7 @@ def run_serving(args, xf, I, torch):
     budget = int(min(150e9, 0.5 * free))
     out = {}
     for label, rate, window in (("sustained", args.serve_rate, args.serve_window), ("rate_200", 200.0, 1.0)):
-        arrivals = I.c5_arrivals(rate_per_s=rate, window_s=window, seed=5)
+        arrivals = I.job_arrivals(rate_per_s=rate, window_s=window, seed=5)
         srv = xf.Server(max_jobs=256, mem_budget_bytes=budget, chunk_steps=args.serve_chunk)
         ids, t_sub = [], []
         t0 = time.perf_counter()
@@ -642,7 +642,7 @@ def run_serving(args, xf, I, torch):
                       "gpu_busy_value": st["bin_steps"] / max(st["busy_s"], 1e-9),
                       "max_resident": st["max_resident"], "epochs": st["epochs"]}
     # the same kind of jobs, each alone in FP64 (sample of 3)
-    sample = [p for _, p in I.c5_arrivals(rate_per_s=200.0, window_s=1.0, seed=6)][:3]
+    sample = [p for _, p in I.job_arrivals(rate_per_s=200.0, window_s=1.0, seed=6)][:3]
     work, t = 0.0, 0.0
     for p in sample:
         q = p.replace(precision=I.FP64)

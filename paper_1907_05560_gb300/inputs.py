@@ -80,20 +80,20 @@ class Problem:
 
 # ---- the measured run shapes --------------------------------------------
 
-def c1() -> Problem:
+def bulb2f_16x32() -> Problem:
     """Two flavors, 16 angles x 32 energies (1-60 MeV), inverted hierarchy,
     mu0 = 1e5 km^-1, no matter, 2000 steps from 10 to 200 km."""
     return Problem(n_E=32, n_u=16, n_f=2, stepper=EXPH, mu0=1.0e5, r0=10.0, r1=200.0,
                    n_steps=2000, seed=1)
 
 
-def c1a() -> Problem:
-    """C1 physics from 50 to 250 km in 20000 steps (h = 0.01 km), where
+def bulb2f_16x32_from_50km() -> Problem:
+    """The two-flavor 16 x 32 physics from 50 to 250 km in 20000 steps (h = 0.01 km), where
     explicit RK4 is stable."""
-    return c1().replace(stepper=RK4, r0=50.0, r1=250.0, n_steps=20000)
+    return bulb2f_16x32().replace(stepper=RK4, r0=50.0, r1=250.0, n_steps=20000)
 
 
-def c2() -> Problem:
+def bulb3f_1000x200() -> Problem:
     """Three flavors, 1000 angles x 200 energies (400,000 3x3 bins),
     dm21 = 7.5e-5, dm31 = 2.4e-3 eV^2 (normal), angles 0.59/0.15/0.72,
     n_e = 1e33 (10 km / r)^3 cm^-3, 20000 steps from 10 to 1000 km."""
@@ -103,20 +103,20 @@ def c2() -> Problem:
                    r0=10.0, r1=1000.0, n_steps=20000, seed=2)
 
 
-def c2a() -> Problem:
-    """C2 physics from 250 to 1000 km in 20000 steps, stable for RK4."""
-    return c2().replace(stepper=RK4, r0=250.0, r1=1000.0, n_steps=20000)
+def bulb3f_1000x200_from_250km() -> Problem:
+    """The three-flavor 1000 x 200 physics from 250 to 1000 km in 20000 steps, stable for RK4."""
+    return bulb3f_1000x200().replace(stepper=RK4, r0=250.0, r1=1000.0, n_steps=20000)
 
 
-def c3(precision: int = FP32_M64) -> Problem:
-    """C1 physics from 10 km with h = 0.1 km (precision study; checkpoints at
+def bulb2f_16x32_coarse(precision: int = FP32_M64) -> Problem:
+    """The two-flavor 16 x 32 physics from 10 km with h = 0.1 km (precision study; checkpoints at
     100, 300 and 1000 km)."""
-    return c1().replace(stepper=EXPH, precision=precision, r0=10.0, r1=1000.0, n_steps=9900)
+    return bulb2f_16x32().replace(stepper=EXPH, precision=precision, r0=10.0, r1=1000.0, n_steps=9900)
 
 
-def c3a(precision: int = FP32_M64, stepper: int = RK4) -> Problem:
-    """C3 physics from 50 km with h = 0.01 km."""
-    return c1().replace(stepper=stepper, precision=precision, r0=50.0, r1=1000.0, n_steps=95000)
+def bulb2f_16x32_fine(precision: int = FP32_M64, stepper: int = RK4) -> Problem:
+    """The precision-study physics (two flavors, 16 x 32) from 50 km with h = 0.01 km."""
+    return bulb2f_16x32().replace(stepper=stepper, precision=precision, r0=50.0, r1=1000.0, n_steps=95000)
 
 
 # ---- seeded generators ----------------------------------------------------
@@ -145,10 +145,10 @@ class SplitMix64:
         return lo + min(int(self.uniform() * (hi - lo + 1)), hi - lo)
 
 
-def c4_instances(n_instances: int = 256, seed: int = 4, n_steps: int = 1000) -> List[Problem]:
+def ensemble_problems(n_instances: int = 256, seed: int = 4, n_steps: int = 1000) -> List[Problem]:
     """Batched ensemble: n_u ~ U{64..1024}, n_E ~ U{32..256}, 2 or 3 flavors,
     mu0 log-uniform in [1e3, 1e6] km^-1, either hierarchy, theta_v ~ U[0.01, 0.6]
-    (2 flavors; 3 flavors use the C2 angles), r 50 -> 250 km."""
+    (2 flavors; 3 flavors use the 1000-angle problem's), r 50 -> 250 km."""
     g = SplitMix64(seed)
     out = []
     for i in range(n_instances):
@@ -167,10 +167,10 @@ def c4_instances(n_instances: int = 256, seed: int = 4, n_steps: int = 1000) -> 
     return out
 
 
-def c5_arrivals(rate_per_s: float = 200.0, window_s: float = 60.0, seed: int = 5,
+def job_arrivals(rate_per_s: float = 200.0, window_s: float = 60.0, seed: int = 5,
                 size_scale: float = 1.0) -> List[Tuple[float, Problem]]:
     """Served job stream: Poisson arrivals at `rate_per_s` over `window_s`;
-    two-flavor jobs with the C4 size distribution (scaled by size_scale),
+    two-flavor jobs with the batched ensemble's size distribution (scaled by size_scale),
     1000-20000 steps of h = 0.01 km from 50 km, FP32 with FP64 moments."""
     g = SplitMix64(seed)
     t = 0.0

@@ -143,7 +143,7 @@ def test_full_c4_batch_sampled_against_oracle(xf, orc):
     moments), a few steps in the bench's launch configuration; a sample of
     problems is checked against the FP64 oracle on every bin."""
     import torch
-    probs = I.c4_instances()
+    probs = I.ensemble_problems()
     b = xf.Batch(probs)
     b.init_state_i(-1, probs[0].r0)
     n = 3
@@ -205,7 +205,7 @@ def test_dynamic_tile_claiming_is_bitwise_the_static_split(xf, orc, precision):
     """Claiming a stage's tiles from a counter gives every problem bitwise the
     result of the static split of tiles over CTAs (a tile's arithmetic and
     the tile order of the moment sums do not depend on which CTA ran it)."""
-    probs = [p.replace(n_steps=20, precision=precision) for p in I.c4_instances(n_instances=12)]
+    probs = [p.replace(n_steps=20, precision=precision) for p in I.ensemble_problems(n_instances=12)]
     outs = []
     for dyn in (0, 1):
         b = xf.Batch(probs)

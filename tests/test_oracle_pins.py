@@ -454,7 +454,7 @@ def test_initial_state_structure(orc):
 def test_literal_rk4_config_reports_nonfinite(orc):
     """Explicit RK4 at h = 0.095 km from 10 km (mu0 = 1e5) is far outside its
     stability region; the oracle reports it and keeps the last finite state."""
-    p = I.c1().replace(stepper=I.RK4)
+    p = I.bulb2f_16x32().replace(stepper=I.RK4)
     rho = orc.init_state(p)
     out, st, done = orc.evolve(p, rho, p.r0, p.h, 400)
     assert st == 1 and done < 400

@@ -144,7 +144,7 @@ def test_parity_many_ctas_ragged(xf, orc, n_f, stepper):
 
 def test_parity_c1a_full_run_rk4(xf, orc):
     """Two flavors, 16 x 32 bins, RK4, 20000 steps from 50 to 250 km."""
-    p = I.c1a()
+    p = I.bulb2f_16x32_from_50km()
     rho0 = orc.init_state(p)
     ref, st, _ = orc.evolve(p, rho0, p.r0, p.h, p.n_steps, n_threads=THREADS)
     got, r, n = gpu_run(xf, p, rho0, p.r0, p.h, p.n_steps)
@@ -155,7 +155,7 @@ def test_parity_c1a_full_run_rk4(xf, orc):
 def test_parity_c1_full_run_exph(xf, orc):
     """The literal two-flavor run (10 -> 200 km, 2000 steps) with the paper's
     predictor-corrector and exact propagator."""
-    p = I.c1()
+    p = I.bulb2f_16x32()
     rho0 = orc.init_state(p)
     ref, st, _ = orc.evolve(p, rho0, p.r0, p.h, p.n_steps, n_threads=THREADS)
     got, r, n = gpu_run(xf, p, rho0, p.r0, p.h, p.n_steps)
@@ -163,7 +163,7 @@ def test_parity_c1_full_run_exph(xf, orc):
     assert rel_err(got, ref, 2) < TOL64
 
 
-@pytest.mark.parametrize("make", [I.c2, I.c2a])
+@pytest.mark.parametrize("make", [I.bulb3f_1000x200, I.bulb3f_1000x200_from_250km])
 def test_parity_three_flavor_full_size(xf, orc, make):
     """400,000 3x3 bins (1000 angles x 200 energies) in the launch shape the
     bench uses: a few steps against the oracle on every bin."""
@@ -181,7 +181,7 @@ def test_parity_three_flavor_full_size(xf, orc, make):
 def test_literal_rk4_reports_nonfinite_like_oracle(xf, orc):
     """Explicit RK4 from 10 km at h = 0.095 km diverges; both sides stop and
     keep the last finite state."""
-    p = I.c1().replace(stepper=I.RK4)
+    p = I.bulb2f_16x32().replace(stepper=I.RK4)
     rho0 = orc.init_state(p)
     ref, st, done_o = orc.evolve(p, rho0, p.r0, p.h, 400, n_threads=THREADS)
     assert st == 1
@@ -201,7 +201,7 @@ def test_strict_rk4_refuses_unstable_step_sizes(xf, orc):
     """Strict mode: the literal 10 km RK4 step (h = 0.095 km, mu0 = 1e5) is
     refused before any step is taken; the stable 50 km companion
     (h = 0.01 km) runs and matches the oracle."""
-    p = I.c1().replace(stepper=I.RK4, strict=1)
+    p = I.bulb2f_16x32().replace(stepper=I.RK4, strict=1)
     rho0 = orc.init_state(p)
     c = xf.Context(p)
     c.set_state(rho0, p.r0)
@@ -212,7 +212,7 @@ def test_strict_rk4_refuses_unstable_step_sizes(xf, orc):
     # untouched: only the packing round trip (trace split in FP64) differs
     assert done == 0 and r == p.r0 and np.abs(got - rho0).max() <= 1e-15 * np.abs(rho0).max()
     c.close()
-    q = I.c1a().replace(strict=1, n_steps=200, r1=52.0)
+    q = I.bulb2f_16x32_from_50km().replace(strict=1, n_steps=200, r1=52.0)
     rho0 = orc.init_state(q)
     c = xf.Context(q)
     c.set_state(rho0, q.r0)
@@ -277,7 +277,7 @@ def test_fp32_m64_error_vs_fp64_oracle(xf, orc):
     """FP32 per-bin arithmetic with FP64 moments: survival-probability error
     against the FP64 oracle on the stable two-flavor run (50 km on, h = 0.01),
     over bins whose spectra are distinguishable (|phi_e - phi_x| >= 1e-2 max)."""
-    p = I.c1a().replace(n_steps=5000, r1=100.0)
+    p = I.bulb2f_16x32_from_50km().replace(n_steps=5000, r1=100.0)
     rho0 = orc.init_state(p)
     ref, st, _ = orc.evolve(p, rho0, p.r0, p.h, p.n_steps, n_threads=THREADS)
     q = p.replace(precision=I.FP32_M64)
@@ -345,7 +345,7 @@ def test_barrier_wait_times_out_with_status(xf, orc):
     assert rel_err(c.get_state()[0], ref, 2) < TOL64
 
 
-@pytest.mark.parametrize("make", [I.c2, I.c2a])
+@pytest.mark.parametrize("make", [I.bulb3f_1000x200, I.bulb3f_1000x200_from_250km])
 def test_fp32_three_flavor_error_vs_fp64_oracle(xf, orc, make):
     """FP32 bins with FP64 moments on the full three-flavor workload, 20 steps
     against the FP64 oracle on every bin: the error stays at FP32 rounding

@@ -78,7 +78,7 @@ def purity_drift(c, q0):
 @pytest.mark.parametrize("n_f,stepper", [(2, I.RK4), (2, I.EXPH), (3, I.RK4), (3, I.EXPH)])
 def test_renormalised_variant_holds_purity(xf, orc, n_f, stepper):
     kw = dict(dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.72), hierarchy=+1) if n_f == 3 else {}
-    p = I.c1().replace(n_f=n_f, stepper=stepper, r0=50.0, r1=70.0, n_steps=2000, **kw)
+    p = I.bulb2f_16x32().replace(n_f=n_f, stepper=stepper, r0=50.0, r1=70.0, n_steps=2000, **kw)
     drift = {}
     for name in ("fp32_m64", "fp32_m64_renorm"):
         c = xf.Context(p.replace(precision=VARIANTS[name]))
@@ -97,7 +97,7 @@ def test_renormalised_variant_holds_purity(xf, orc, n_f, stepper):
 
 def test_renormalised_variant_through_init_state_and_no_alloc(xf, orc):
     import torch
-    p = I.c1().replace(stepper=I.EXPH, precision=I.FP32_M64_RENORM, r0=50.0, r1=60.0, n_steps=1000)
+    p = I.bulb2f_16x32().replace(stepper=I.EXPH, precision=I.FP32_M64_RENORM, r0=50.0, r1=60.0, n_steps=1000)
     c = xf.Context(p)
     c.init_state(p.r0)
     q0 = c.outputs()[2]
@@ -122,9 +122,9 @@ def test_renormalised_variant_through_init_state_and_no_alloc(xf, orc):
 
 CHECK_R = (100.0, 300.0, 1000.0)
 CASES = {
-    "c3_exph_h0.1": lambda prec: I.c3(prec),
-    "c3a_rk4_h0.01": lambda prec: I.c3a(prec, I.RK4),
-    "c3a_exph_h0.01": lambda prec: I.c3a(prec, I.EXPH),
+    "c3_exph_h0.1": lambda prec: I.bulb2f_16x32_coarse(prec),
+    "c3a_rk4_h0.01": lambda prec: I.bulb2f_16x32_fine(prec, I.RK4),
+    "c3a_exph_h0.01": lambda prec: I.bulb2f_16x32_fine(prec, I.EXPH),
 }
 _oracle_cache = {}
 

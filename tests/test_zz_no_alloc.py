@@ -84,7 +84,7 @@ def test_noalloc_matches_regular_entry_points_on_two_calls(env, p):
 
 def test_noalloc_refuses_problem_larger_than_its_array(env):
     torch, xf, L = env
-    p = I.c2()  # 400,000 3x3 bins: about 150 MB of FP64 working memory
+    p = I.bulb3f_1000x200()  # 400,000 3x3 bins: about 150 MB of FP64 working memory
     prm = xf.params_from(p)
     dev = torch.zeros(1, dtype=torch.float64, device="cuda")  # never touched
     rc = L.xf_step_noalloc(p.n_E, p.n_u, p.n_f, ctypes.byref(prm), ctypes.c_void_p(dev.data_ptr()),
