@@ -535,8 +535,8 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 // is involved.
 // Kernels of one flavor count only: in the kernel for mixed packs, which
 // issues on most cycles, the extra copy and shared-load instructions cost
-// more than the hidden latency gives (C4: 1.73e10 against 1.77e10
-// bin-steps/s), while the one-flavor kernels gain 2-3 %.
+// more than the hidden latency gives (the 256-problem ensemble: 1.73e10
+// against 1.77e10 bin-steps/s), while the one-flavor kernels gain 2-3 %.
 template <int NFM, int STEP, typename Real, int NMOM>
 struct Staging { static constexpr bool on = NFM != 0 && STEP == STEP_EXPH && sizeof(Real) == 4 && NMOM == 2; };
 __host__ __device__ constexpr int stage_planes(int nf) { return 4 * (nf == 2 ? 3 : 8); }
