@@ -380,3 +380,34 @@ def test_degenerate_cases(xf, orc, n_f, stepper):
     got, r, n = gpu_run(xf, q, rho0, q.r0, q.h, 50)
     assert n == 50
     assert np.abs(got - rho0).max() <= 1e-14 * np.abs(rho0).max()  # the pack round trip
+
+
+def _lepton_invariants(orc, p, rho):
+    """tr(Pi_k F) with F = sum_{u,e} (rho_nu - conj rho_nubar) / n_u and Pi_k
+    the vacuum mass-basis projectors (the oracle's unpacking and tables)."""
+    n = p.n_f
+    M = orc.unpack(rho, n).reshape(2, p.n_u, p.n_E, n, n)
+    F = (M[0] - M[1].conj()).sum(axis=(0, 1)) / p.n_u
+    _, _, _, Hv = orc.tables(p)
+    _, V = np.linalg.eigh(orc.unpack(Hv[:1].reshape(-1), n)[0])
+    return np.array([(V[:, k].conj() @ F @ V[:, k]).real for k in range(n)]), np.abs(F).max()
+
+
+@pytest.mark.parametrize("n_f", [2, 3])
+def test_lepton_number_moment_conserved(xf, orc, n_f):
+    """Without matter the nu-nu terms cancel in d/dr tr(Pi_k F) (Eq. 3.13-3.15:
+    sum_u (du/c_u)[M0 - c_u M1, S_u] = [M0, M0] - [M1, M1] = 0); the GPU's RK4
+    keeps this linear invariant to rounding while the bins move at O(1)."""
+    kw = dict(dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.72)) if n_f == 3 else {}
+    p = I.Problem(n_E=24, n_u=40, n_f=n_f, stepper=I.RK4, mu0=3e4, r0=20.0, r1=22.0, n_steps=400, eps=1e-2,
+                  seed=17, **kw)
+    rho = orc.init_state(p)
+    c = xf.Context(p)
+    c.set_state(rho, p.r0)
+    c.step(p.n_steps, p.h)
+    out = c.get_state()[0]
+    c.close()
+    I0, scale = _lepton_invariants(orc, p, rho)
+    I1, _ = _lepton_invariants(orc, p, out)
+    assert np.abs(orc.unpack(out, n_f) - orc.unpack(rho, n_f)).max() > 1e-4
+    assert np.abs(I1 - I0).max() < 1e-12 * scale
