@@ -479,7 +479,8 @@ int xf_get_option(xf_ctx *ctx, int option, int64_t *value);
 
 /* Measured search of the tile size of a fixed-step context or batch: for
  * each candidate (pairs per tile; 0 = the automatic rule; candidates = NULL
- * takes 0, 128, 256, ..., 16384), time n_probe steps of size dr_km (<= 0:
+ * takes 0, 128, 256, 512, 1024, 2048, 3072, 4096, 5120, 6144, 8192, 12288
+ * and 16384), time n_probe steps of size dr_km (<= 0:
  * each problem's current step size) after one untimed launch, and keep the
  * fastest, which stays set as XF_OPT_TILE_PAIRS.  On a batch mixing two-
  * and three-flavor problems each candidate also runs with 0.7 and 1.4 times

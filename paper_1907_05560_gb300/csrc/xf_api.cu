@@ -1831,8 +1831,9 @@ int xf_autotune(xf_ctx *c, int64_t n_probe, double dr_km, const int *cand_in, in
             cands.push_back(cand_in[k]);
         }
     } else {
-        cands.push_back(0);
-        for (int t = 128; t <= 16384; t *= 2) cands.push_back(t);
+        // 0, powers of two from 128 to 16384, and 1.25x / 1.5x steps above 2048
+        // (the batched ensemble's optimum lies between 4096 and 8192)
+        for (int t : {0, 128, 256, 512, 1024, 2048, 3072, 4096, 5120, 6144, 8192, 12288, 16384}) cands.push_back(t);
     }
     // snapshot: the state planes of every active problem, the progress
     // records and the host views
