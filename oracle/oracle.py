@@ -20,6 +20,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "xf_oracle.c")
 _LIB = os.path.join(_HERE, "liborc.so")
+# A prebuilt oracle library to load instead (tests/test_oracle_mutations.py
+# points this at deliberately broken copies to show that the pins catch them).
+_LIB_OVERRIDE = os.environ.get("XF_ORACLE_LIB")
 
 _lib = None
 
@@ -41,21 +44,28 @@ class OrcParams(ctypes.Structure):
     ]
 
 
+CFLAGS = ["-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def compile_to(src: str, out: str) -> None:
+    """gcc the oracle source `src` into the shared library `out`."""
+    subprocess.check_call(["gcc", *CFLAGS, src, "-o", out + ".tmp", "-lm"])
+    os.replace(out + ".tmp", out)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/liborc.so with gcc (no CUDA)."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp", "-lm"]
-        subprocess.check_call(cmd)
-        os.replace(_LIB + ".tmp", _LIB)
+        compile_to(_SRC, _LIB)
     return _LIB
 
 
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB)
+        L = ctypes.CDLL(build())
         P = ctypes.POINTER(OrcParams)
         dp = ctypes.POINTER(ctypes.c_double)
         L.orc_tables.argtypes = [P, dp, dp, dp, dp]

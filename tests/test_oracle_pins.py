@@ -183,6 +183,212 @@ def test_constant_matter_msw(orc, stepper, tol):
         assert np.abs(M[s, :, 0, 0].real - want).max() < tol * phi[0].max()
 
 
+@pytest.mark.parametrize("hierarchy", [+1, -1])
+def test_constant_matter_three_flavor(orc, hierarchy):
+    """P3 with matter: three flavors in constant matter (Eq. 3.4-3.7 with the
+    three-flavor vacuum term, delta_CP = 0) is a constant Hamiltonian, so
+    rho(L) = exp(-iHL) rho(0) exp(iHL) with the library exponential
+    (scipy.linalg.expm).  H_nu = U diag(0, dm21, +-dm31) U^T / 2E + A diag(1, 0, 0),
+    H_nubar the same with -A; U the textbook PMNS matrix.  The predictor-
+    corrector is exact for a constant H; the density spans the resonances."""
+    from scipy.linalg import expm
+    p = _small(n_f=3, n_E=6, n_u=1, geometry=I.CONST, stepper=I.EXPH, eps=1e-2, dm2=(7.5e-5, 2.4e-3),
+               theta=(0.59, 0.15, 0.72), hierarchy=hierarchy, E_min=2.0, E_max=40.0,
+               matter=I.MATTER_POWER, ne_ref=5e26, ne_power=0.0, r0=20.0, r1=24.0, n_steps=200)
+    E, u, phi, Hv = orc.tables(p)
+    A = 5e26 * orc.matter_coeff()
+    K = orc.vac_coeff()
+    assert K * 2.4e-3 / E.max() < A < K * 2.4e-3 / E.min()
+    s12, c12 = math.sin(0.59), math.cos(0.59)
+    s13, c13 = math.sin(0.15), math.cos(0.15)
+    s23, c23 = math.sin(0.72), math.cos(0.72)
+    U = np.array([[c12 * c13, s12 * c13, s13],
+                  [-s12 * c23 - c12 * s23 * s13, c12 * c23 - s12 * s23 * s13, s23 * c13],
+                  [s12 * s23 - c12 * c23 * s13, -c12 * s23 - s12 * c23 * s13, c23 * c13]])
+    m2 = np.array([0.0, 7.5e-5, hierarchy * 2.4e-3])
+    rho = orc.init_state(p)
+    out, st, _ = orc.evolve(p, rho, p.r0, p.h, p.n_steps)
+    assert st == 0
+    R0 = orc.unpack(rho, 3).reshape(2, p.n_E, 3, 3)
+    R1 = orc.unpack(out, 3).reshape(2, p.n_E, 3, 3)
+    L = p.r1 - p.r0
+    for s, sgn in ((0, 1.0), (1, -1.0)):
+        for e in range(p.n_E):
+            H = K * U @ np.diag(m2) @ U.T / E[e] + sgn * A * np.diag([1.0, 0.0, 0.0])
+            V = expm(-1j * H * L)
+            want = V @ R0[s, e] @ V.conj().T
+            assert np.abs(R1[s, e] - want).max() < 1e-11 * np.trace(R0[s, e]).real
+
+
+# ---------------------------------------------------------------- matter profiles (Eq. 3.7, 4.3, 4.4)
+#
+# The matter potential A(r) = sqrt(2) G_F Y_e n_b(r) enters only through the
+# flavor evolution it drives.  These pins check that evolution against closed
+# forms of the two-flavor MSW problem (mu = 0, one radial trajectory), whose
+# inputs are the profile's stated shape: n_e = n_ref (r_ref / r)^p (Eq. 4.3,
+# p = 3) and n_b' = n_b0 exp(-(r - R) / h_NS) with n_e = Y_e n_b (Eq. 3.7, 4.4).
+
+def _msw(matter, th, n_E, E=(5.0, 45.0), **kw):
+    return _small(n_E=n_E, n_u=1, geometry=I.CONST, stepper=I.EXPH, mu0=0.0, eps=0.0,
+                  theta=(th, 0, 0), dm2=(2.4e-3, 0), hierarchy=+1, E_min=E[0], E_max=E[1],
+                  matter=matter, R_nu=10.0, **kw)
+
+
+def _pure_nu_e(orc, p):
+    """Every neutrino and antineutrino bin in its electron flavor."""
+    rho = np.zeros(orc.state_size(p)).reshape(2, p.n_E, 4)
+    rho[:, :, 0] = 1.0
+    return rho.reshape(-1)
+
+
+def _populations(orc, rho, p, vecs):
+    """<v|rho|v> for each bin, v = vecs[s][e] (a unit 2-vector)."""
+    M = orc.unpack(rho, 2).reshape(2, p.n_E, 2, 2)
+    return np.einsum("sei,seij,sej->se", vecs.conj(), M, vecs).real
+
+
+def _mass_basis_nu1(p):
+    """The lighter vacuum mass state (cos t, -sin t) of H_vac = (Delta/2)
+    [[-cos 2t, sin 2t], [sin 2t, cos 2t]] (Eq. 3.5), normal ordering."""
+    th = p.theta[0]
+    v = np.array([math.cos(th), -math.sin(th)])
+    return np.broadcast_to(v, (2, p.n_E, 2))
+
+
+def test_exponential_profile_hop_probability_is_exact(orc):
+    """Eq. 3.7 with the exponential profile of Eq. 4.4: an electron neutrino
+    that starts far above resonance (A >> Delta) and leaves into vacuum ends in
+    the lighter mass state with the probability of the exactly solvable
+    exponential-density problem (Petcov 1988; Kuo & Pantaleone 1989, the
+    double-exponential formula with F = 1 - tan^2 t):
+        P_c = (exp(-2 pi Delta h sin^2 t) - exp(-2 pi Delta h)) / (1 - exp(-2 pi Delta h)),
+    Delta = dm^2 / 2E, h the scale height h_NS.  Antineutrinos see -A (after
+    Eq. 3.4) and cross no resonance; they are the same problem with sin^2 t ->
+    cos^2 t, and leave in the lighter state with probability 1 - P_c(cos^2 t).
+    The mixing angle is large, so the check is exact, not the Landau-Zener
+    limit.  Any error in the sign of the exponent or in the scale height moves
+    these numbers; the density normalisation (Y_e n_b0, the offset R) does not
+    enter P_c and is pinned by the adiabatic-track test below."""
+    th, h_ns, Ye = 0.3, 3.0, 0.5
+    p = _msw(I.MATTER_EXP, th, 8, h_ns=h_ns, Ye=Ye)
+    E, u, phi, Hv = orc.tables(p)
+    Delta = orc.vac_coeff() * p.dm2[0] / E
+    A0 = 1e4 * Delta.max()                     # at r = R: far above every resonance
+    p = p.replace(nb0=A0 / (orc.matter_coeff() * Ye))
+    r0 = p.R_nu
+    r1 = r0 + h_ns * math.log(A0 / (1e-5 * Delta.min()))   # A(r1) << Delta sin 2t
+    out, st, _ = orc.evolve(p, _pure_nu_e(orc, p), r0, (r1 - r0) / 4000, 4000)
+    assert st == 0
+    P1 = _populations(orc, out, p, _mass_basis_nu1(p))
+    x = 2 * math.pi * Delta * h_ns
+
+    def pc(s2):
+        return (np.exp(-x * s2) - np.exp(-x)) / (1 - np.exp(-x))
+
+    assert 0.2 < P1[0].min() and P1[0].max() < 0.8           # the hop is neither 0 nor 1
+    assert np.abs(P1[0] - pc(math.sin(th) ** 2)).max() < 5e-5
+    assert np.abs(P1[1] - (1 - pc(math.cos(th) ** 2))).max() < 5e-5
+
+
+def test_power_law_profile_landau_zener(orc):
+    """Eq. 3.7 with the r^-3 profile of Eq. 4.3 (the three-flavor workload's
+    matter): at small mixing the hop probability across the resonance is the
+    Landau-Zener value exp(-pi gamma / 2), gamma = Delta sin^2 2t / (cos 2t
+    |d ln A / dr|) = Delta sin^2 2t r_res / (3 cos 2t), with r_res where
+    A(r_res) = Delta cos 2t.  For a power-law profile the exact result differs
+    from this limit by a relative O(tan^2 t) in the exponent (Kuo &
+    Pantaleone 1989), about 2e-3 here, which bounds the tolerance.  The
+    energies span gamma = 0.56 ... 1.8, so the profile's direction, exponent
+    and normalisation each shift the answer by far more than that."""
+    th = 0.03
+    p = _msw(I.MATTER_POWER, th, 8, r_ref=10.0, ne_power=3.0)
+    E, u, phi, Hv = orc.tables(p)
+    Delta = orc.vac_coeff() * p.dm2[0] / E
+    C = orc.matter_coeff()
+    s2, c2 = math.sin(2 * th), math.cos(2 * th)
+    Dmid = math.sqrt(Delta.max() * Delta.min())
+    rres_mid = 3 * c2 / (Dmid * s2 * s2)        # gamma = 1 at the middle energy
+    ne_ref = Dmid * c2 / C * (rres_mid / p.r_ref) ** 3
+    p = p.replace(ne_ref=ne_ref)
+
+    def radius(A):                              # where C ne_ref (r_ref / r)^3 = A
+        return p.r_ref * (C * ne_ref / A) ** (1 / 3)
+
+    rres = radius(Delta * c2)
+    gamma = Delta * s2 * s2 * rres / (3 * c2)
+    rho = _pure_nu_e(orc, p)
+    # from A = 100 Delta_max to A = 1e-4 Delta_min, steps growing with r
+    rs = np.geomspace(radius(100 * Delta.max()), radius(1e-4 * Delta.min()), 21)
+    for a, b in zip(rs[:-1], rs[1:]):
+        rho, st, _ = orc.evolve(p, rho, a, (b - a) / 1000, 1000)
+        assert st == 0
+    P1 = _populations(orc, rho, p, _mass_basis_nu1(p))
+    lz = np.exp(-math.pi / 2 * gamma)
+    assert 0.5 < gamma.min() and gamma.max() < 2
+    assert np.abs(P1[0] - lz).max() < 1.5e-3
+    # no resonance for antineutrinos (-A): they stay in the lighter state
+    assert np.abs(P1[1] - 1).max() < 1e-4
+
+
+@pytest.mark.parametrize("profile", ["exp", "power"])
+def test_matter_profile_adiabatic_track(orc, profile):
+    """Adiabatic MSW (Mikheyev-Smirnov): with a slowly varying profile
+    (gamma ~ 130 at resonance) the state keeps its population in each local
+    matter eigenstate of H = H_vac + A diag(1, 0) (Eq. 3.5, 3.7), neutrino
+    and antineutrino (-A) alike, to O(1/gamma^2).  The eigenstates are taken
+    at the density the paper's profile gives at three radii around the
+    resonance (A = 3, 1, 1/3 Delta cos 2t at the middle energy).  A wrong
+    density there (a dropped Y_e, a missing offset R in Eq. 4.4, a wrong
+    n_ref or exponent in Eq. 4.3) turns the basis by up to the full mixing
+    and moves the population by far more than the tolerance."""
+    th = 0.3
+    c2 = math.cos(2 * th)
+    p = _msw(I.MATTER_NONE, th, 4, E=(10.0, 30.0))
+    E, u, phi, Hv = orc.tables(p)
+    Delta = orc.vac_coeff() * p.dm2[0] / E
+    Dmid = math.sqrt(Delta.max() * Delta.min())
+    C = orc.matter_coeff()
+    if profile == "exp":
+        Ye, h_ns = 0.5, 1000.0
+        nb0 = Dmid * c2 / (C * Ye) * math.exp(5.0)      # resonance at R + 5 h_NS
+        p = p.replace(matter=I.MATTER_EXP, Ye=Ye, nb0=nb0, h_ns=h_ns)
+
+        def A(r):
+            return C * Ye * nb0 * math.exp(-(r - p.R_nu) / h_ns)
+        rres = p.R_nu + 5 * h_ns
+        radii = [rres - h_ns * math.log(k) for k in (30.0, 3.0, 1.0, 1 / 3)]
+    else:
+        rres = 3000.0
+        ne_ref = Dmid * c2 / C * (rres / 10.0) ** 3
+        p = p.replace(matter=I.MATTER_POWER, ne_ref=ne_ref, r_ref=10.0, ne_power=3.0)
+
+        def A(r):
+            return C * ne_ref * (10.0 / r) ** 3
+        radii = [rres / k ** (1 / 3) for k in (30.0, 3.0, 1.0, 1 / 3)]
+
+    def local_states(r):
+        v = np.zeros((2, p.n_E, 2))
+        for s, sgn in ((0, 1.0), (1, -1.0)):
+            for e in range(p.n_E):
+                H = Delta[e] / 2 * np.array([[-c2, math.sin(2 * th)], [math.sin(2 * th), c2]])
+                H[0, 0] += sgn * A(r)
+                w, V = np.linalg.eigh(H)
+                v[s, e] = V[:, 1] if sgn > 0 else V[:, 0]   # where nu_e / nubar_e start
+        return v
+
+    rho = _pure_nu_e(orc, p)
+    start = _populations(orc, rho, p, local_states(radii[0]))
+    assert start.min() > 0.999
+    for a, b in zip(radii[:-1], radii[1:]):
+        rho, st, _ = orc.evolve(p, rho, a, (b - a) / 5000, 5000)
+        assert st == 0
+        pop = _populations(orc, rho, p, local_states(b))
+        assert np.abs(pop - start).max() < 5e-4
+    # the neutrinos did cross the resonance: their electron content changed
+    Pee = orc.unpack(rho, 2).reshape(2, p.n_E, 2, 2)[0, :, 0, 0].real
+    assert Pee.max() < 0.7
+
+
 @pytest.mark.parametrize("stepper,tol", [(I.RK4, 5e-8), (I.EXPH, 1e-11)])
 def test_vacuum_three_flavor(orc, stepper, tol):
     """P3: three-flavor vacuum oscillation (textbook, delta_CP = 0):
@@ -233,6 +439,90 @@ def test_bulb_moments_isotropic_closed_form(orc):
         assert np.allclose(M1, dE * S * x * x / 2, rtol=1e-9)
         D = 0.5 * (1 - math.sqrt(1 - x * x)) ** 2
         assert f0 - x * x / 2 == pytest.approx(D, rel=1e-12)
+
+
+# ---------------------------------------------------------------- nu-nu coupling's radial dependence
+
+def _precession(orc, geometry, stepper, n_chunks=40, steps_per_chunk=50, mu0=400.0, r0=20.0, r1=24.0):
+    """One trajectory (n_u = 1, u = 1/2), three energies, no vacuum or matter
+    term, antineutrinos empty: S = sum_E rho_nu is conserved and every bin
+    precesses about it.  Returns the accumulated rotation angle of each bin's
+    Bloch vector about S (chunks short enough to unwrap), the drift of S, and
+    the quantities the closed forms need."""
+    p = _small(n_E=3, n_u=1, geometry=geometry, stepper=stepper, mu0=mu0, eps=0.0,
+               dm2=(0.0, 0.0), hierarchy=+1, E_min=10.0, E_max=13.0, R_nu=10.0)
+    rng = np.random.default_rng(3)
+    rho = np.zeros((2, p.n_E, 4))
+    for e in range(p.n_E):
+        v = rng.normal(size=3)
+        v *= 0.4 / np.linalg.norm(v)
+        rho[0, e] = [0.5 + v[2] / 2, 0.5 - v[2] / 2, v[0] / 2, -v[1] / 2]
+    rho = rho.reshape(-1)
+
+    def bloch(x):
+        M = orc.unpack(x, 2).reshape(2, p.n_E, 2, 2)[0]
+        return np.stack([2 * M[:, 0, 1].real, -2 * M[:, 0, 1].imag, (M[:, 0, 0] - M[:, 1, 1]).real], 1)
+
+    P = bloch(rho)
+    S0 = P.sum(0)
+    n = S0 / np.linalg.norm(S0)
+    total = np.zeros(p.n_E)
+    h = (r1 - r0) / (n_chunks * steps_per_chunk)
+    r = r0
+    for _ in range(n_chunks):
+        rho, st, _ = orc.evolve(p, rho, r, h, steps_per_chunk)
+        assert st == 0
+        r += h * steps_per_chunk
+        Q = bloch(rho)
+        for e in range(p.n_E):
+            a = P[e] - (P[e] @ n) * n
+            b = Q[e] - (Q[e] @ n) * n
+            total[e] += math.atan2(np.cross(a, b) @ n, a @ b)
+        P = Q
+    dE = (p.E_max - p.E_min) / p.n_E
+    return total, np.linalg.norm(P.sum(0) - S0), dict(mu0=mu0, dE=dE, sig=np.linalg.norm(S0), u=0.5,
+                                                      R=p.R_nu, y0=p.R_nu / r0, y1=p.R_nu / r1)
+
+
+@pytest.mark.parametrize("stepper,tol", [(I.RK4, 1e-6), (I.EXPH, 1e-3)])
+def test_literal_mu_r4_coupling_precession_closed_form(orc, stepper, tol):
+    """The literal coupling mode (r-independent weights du, du cos, and
+    mu = mu0 (R/r)^4): with one trajectory G = mu0 x^4 dE (1 - cos^2) S and
+    1 - cos^2 = x^2 u (Eq. 3.14), so the Bloch vectors turn about S at
+    mu0 dE |S| u x^6 / cos per unit radius (dl/dr = 1/cos, Eq. 3.3).  With
+    y = R/r and y = sin(t)/sqrt(u):
+        angle = mu0 dE |S| u R u^(-5/2) [3t/8 - sin 2t/4 + sin 4t/32] between
+    the end points.  A wrong power of x in the coupling changes the angle
+    several-fold."""
+    ang, dS, q = _precession(orc, I.MU_R4, stepper)
+
+    def F(y):
+        t = math.asin(math.sqrt(q["u"]) * y)
+        return (3 * t / 8 - math.sin(2 * t) / 4 + math.sin(4 * t) / 32) * q["u"] ** -2.5
+
+    want = q["mu0"] * q["dE"] * q["sig"] * q["u"] * q["R"] * (F(q["y0"]) - F(q["y1"]))
+    assert 3 < abs(want) < 30
+    assert dS < 1e-12
+    assert np.abs(np.abs(ang) - want).max() < tol * want
+
+
+@pytest.mark.parametrize("stepper,tol", [(I.RK4, 1e-6), (I.EXPH, 1e-3)])
+def test_bulb_coupling_precession_closed_form(orc, stepper, tol):
+    """The bulb geometry (Eq. 3.13-3.15) on one trajectory: the weights
+    x^2 du / (2 cos), x^2 du / 2 give G = mu0 dE (x^2 u / (2 cos)) (1 - cos^2) S
+    and, with dl/dr = 1/cos, a precession rate mu0 dE |S| u x^4 / (2 (1 - u x^2));
+    with y = R/r the angle is mu0 dE |S| u R / 2 [(atanh(sqrt(u) y)/sqrt(u) - y)/u]
+    between the end points."""
+    ang, dS, q = _precession(orc, I.BULB, stepper)
+
+    def G(y):
+        su = math.sqrt(q["u"])
+        return (math.atanh(su * y) / su - y) / q["u"]
+
+    want = q["mu0"] * q["dE"] * q["sig"] * q["u"] / 2 * q["R"] * (G(q["y0"]) - G(q["y1"]))
+    assert 3 < abs(want) < 30
+    assert dS < 1e-12
+    assert np.abs(np.abs(ang) - want).max() < tol * want
 
 
 # ---------------------------------------------------------------- invariants
