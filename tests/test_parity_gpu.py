@@ -97,8 +97,10 @@ CASES = [
     (1, 1, I.CONST, False),
     (3, 7, I.BULB, False),
     (16, 32, I.BULB, False),
-    (5, 33, I.BULB, True),
+    (5, 33, I.BULB, "power"),
+    (6, 21, I.BULB, "exp"),
     (4, 9, I.MU_R4, False),
+    (4, 9, I.MU_R4, "exp"),
     (1, 13, I.SINGLE_ANGLE, False),
 ]
 
@@ -109,9 +111,12 @@ CASES = [
 def test_parity_small(xf, orc, n_u, n_E, geometry, matter, n_f, stepper):
     kw = dict(THREE) if n_f == 3 else {}
     mu0 = 50.0 if geometry == I.CONST else 1e5
-    if matter:
+    if matter == "power":
         # A(50 km) ~ 51 km^-1: A h ~ 0.5 keeps explicit RK4 stable
         kw.update(matter=I.MATTER_POWER, ne_ref=1e31, r_ref=10.0, ne_power=3.0)
+    elif matter == "exp":
+        # Eq. 4.4 with Y_e: A(50 km) ~ 50 km^-1, scale height 20 km
+        kw.update(matter=I.MATTER_EXP, nb0=1.15e30, Ye=0.5, h_ns=20.0)
     p = small(n_u=n_u, n_E=n_E, geometry=geometry, stepper=stepper, mu0=mu0, **kw)
     rho0 = orc.init_state(p)
     ref, st, done = orc.evolve(p, rho0, p.r0, p.h, p.n_steps, n_threads=THREADS)
@@ -166,14 +171,57 @@ def test_parity_c1_full_run_exph(xf, orc):
 @pytest.mark.parametrize("make", [I.bulb3f_1000x200, I.bulb3f_1000x200_from_250km])
 def test_parity_three_flavor_full_size(xf, orc, make):
     """400,000 3x3 bins (1000 angles x 200 energies) in the launch shape the
-    bench uses: a few steps against the oracle on every bin."""
+    bench uses (persistent launches of 100 radial steps): 200 steps against
+    the oracle on every bin (10 -> 19.9 km for the predictor-corrector run,
+    the start of the bench's own range; 250 -> 257.5 km for RK4)."""
     p = make()
     rho0 = orc.init_state(p)
-    n = 2
+    n, chunk = 200, 100
     ref, st, _ = orc.evolve(p, rho0, p.r0, p.h, n, n_threads=THREADS)
-    got, r, done = gpu_run(xf, p, rho0, p.r0, p.h, n)
-    assert done == n
-    assert rel_err(got, ref, 3) < TOL64
+    assert st == 0
+    c = xf.Context(p)
+    c.set_state(rho0, p.r0)
+    for _ in range(n // chunk):
+        c.step_async(chunk, p.h)
+    c.sync()
+    got, r, done = c.get_state()
+    c.close()
+    assert done == n and r == pytest.approx(p.r0 + n * p.h, rel=1e-13)
+    assert np.abs(ref - rho0).max() > 1e-6 * np.abs(rho0).max()
+    err = rel_err(got, ref, 3)
+    print(f"{make.__name__}: max |d rho| / tr rho after {n} steps = {err:.3e}")
+    assert err < TOL64
+
+
+@pytest.mark.skipif(not os.environ.get("XF_FULL_RUN"), reason="set XF_FULL_RUN=1: about 25 min of oracle time")
+def test_parity_three_flavor_full_run(xf, orc):
+    """The whole three-flavor bulb run (1000 angles x 200 energies, matter
+    r^-3, 20000 predictor-corrector steps from 10 to 1000 km) against the
+    oracle, both in chunks of 2000 steps, the error printed at every chunk.
+    The device's sine-cosine differs from the host library's by ulps and the
+    nonlinear flow amplifies such differences, so the gate applies where the
+    flow has not amplified them (max error printed for every radius)."""
+    p = I.bulb3f_1000x200()
+    rho0 = orc.init_state(p)
+    c = xf.Context(p)
+    c.set_state(rho0, p.r0)
+    ref = rho0
+    errs = []
+    k = 0
+    while k < p.n_steps:
+        m = min(2000, p.n_steps - k)
+        ref, st, _ = orc.evolve(p, ref, p.r0 + k * p.h, p.h, m, n_threads=THREADS)
+        assert st == 0
+        for _ in range(m // 100):
+            c.step_async(100, p.h)
+        c.sync()
+        k += m
+        got, r, done = c.get_state()
+        assert done == k
+        errs.append((r, rel_err(got, ref, 3)))
+        print(f"r = {r:8.3f} km  steps {k:6d}  max |d rho| / tr rho = {errs[-1][1]:.3e}", flush=True)
+    c.close()
+    assert max(e for _, e in errs) < TOL64
 
 
 # ------------------------------------------------------------------ status paths
