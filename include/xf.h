@@ -499,8 +499,12 @@ int xf_autotune(xf_ctx *ctx, int64_t n_probe, double dr_km, const int *candidate
 /* Measured ALU peaks of the current device, for roofline denominators:
  * XF_PEAK_FP64_FMA / XF_PEAK_FP32_FMA write the FMA throughput in FLOP/s
  * (an FMA counts 2) of a register-resident FMA loop over 8 CTAs per SM,
- * best of 5 timed launches (CUDA events).  Not part of the integration. */
-enum xf_peak_kind { XF_PEAK_FP64_FMA = 0, XF_PEAK_FP32_FMA = 1 };
+ * best of 5 timed launches (CUDA events).  XF_PEAK_FP64_RSQRT and
+ * XF_PEAK_FP64_SINCOS write calls per second of the FP64 reciprocal square
+ * root and sine-cosine pair in the same kind of loop (each call with one FMA
+ * that feeds the next), the two functions the 3x3 propagator (Eq. 3.11)
+ * calls besides its counted arithmetic.  Not part of the integration. */
+enum xf_peak_kind { XF_PEAK_FP64_FMA = 0, XF_PEAK_FP32_FMA = 1, XF_PEAK_FP64_RSQRT = 2, XF_PEAK_FP64_SINCOS = 3 };
 int xf_peak(int which, double *value);
 
 /* ---- stepping without allocation -----------------------------------------
@@ -520,20 +524,30 @@ int xf_peak(int which, double *value);
  * CTA partial moments, the barrier, error and step words) lives in one
  * file-scope device array of XF_NOALLOC_SCRATCH_BYTES that every GPU loading
  * libxf.so holds until the process exits.  The call makes no cudaMalloc,
- * cudaFree or other allocating call.  Precisions XF_FP64 and XF_FP32_M64.
+ * cudaFree or other allocating call.  Steppers XF_RK4 and XF_EXPH, every
+ * precision (XF_FP64, XF_FP32_M64, XF_FP32_COMP, XF_FP32_M64_RENORM),
+ * geometries bulb, literal mu0 (R/r)^4, single-angle and constant, no azimuth
+ * bins, the rho form (other choices: XF_E_UNSUPPORTED).
  *
+ *   - n_steps == 0 returns XF_OK at once and leaves rho_dev untouched.
+ *   - XF_E_STATE: rho_dev holds a non-finite value; refused before any step
+ *     is taken, rho_dev untouched.
  *   - XF_E_TOO_BIG: the problem's working set (about 2(n_f^2-1) x 3 x
  *     sizeof(Real) + 16 bytes per (angle, energy) pair, plus small tables)
  *     exceeds XF_NOALLOC_SCRATCH_BYTES; nothing was run.
  *   - The call is synchronous on `stream` (a cudaStream_t; NULL = legacy
- *     default stream).
+ *     default stream): it synchronises the stream and reads status words back
+ *     to the host, so it must never be called while `stream` is being
+ *     captured into a CUDA graph.
+ *   - Every failure's message is left where xf_last_error(NULL) reads it (per
+ *     host thread, the same slot as a failed xf_create); a successful call
+ *     clears it.
  *   - Every call shares the array and it keeps the previous call's contents;
  *     each call clears the words that must start at zero and rewrites the
  *     state buffers from rho_dev.  Calls whose GPU work overlaps (several
  *     host threads or streams at once) race on the array: serialise them.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture. */
+ *     (cudaGetSymbolAddress) with that device current. */
 #define XF_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int xf_step_noalloc(int n_E, int n_u, int n_flavor, const xf_params *p, double *rho_dev, double r_km,
                     int64_t n_steps, double dr_km, void *stream);
@@ -541,7 +555,8 @@ int xf_step_noalloc(int n_E, int n_u, int n_flavor, const xf_params *p, double *
 /* Human-readable name of a status code (static storage). */
 const char *xf_status_str(int status);
 /* Message of the last failure on ctx (static per-ctx storage; "" if none).
- * With ctx == NULL: the last failure of xf_create in this thread. */
+ * With ctx == NULL: the last failure of xf_create (or of the create calls of
+ * batches and servers) or of xf_step_noalloc in this thread. */
 const char *xf_last_error(const xf_ctx *ctx);
 
 #ifdef __cplusplus

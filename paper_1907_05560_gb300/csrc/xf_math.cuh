@@ -547,18 +547,23 @@ __host__ __device__ __forceinline__ void hamiltonians(const Real *hv, Real A, co
 {
     constexpr int S = Comp<NF>::S;
 #pragma unroll
-    for (int k = 0; k < S; ++k) {
-        hn[k] = hv[k] + g[k];
-        hb[k] = hv[k] - g[k];
-    }
+    for (int k = 0; k < S; ++k) hn[k] = hv[k] + g[k];
+    // conj(G) flips the imaginary parts: those of hb take +g
     if constexpr (NF == 2) {
+        hb[0] = hv[0] - g[0];
+        hb[1] = hv[1] - g[1];
         hb[2] = hv[2] + g[2];
-        hn[0] += Real(0.5) * A;
-        hb[0] -= Real(0.5) * A;
+        const Real a = Real(0.5) * A;
+        hn[0] += a;
+        hb[0] -= a;
     } else {
-        hb[3] = hv[3] + g[3];
-        hb[5] = hv[5] + g[5];
-        hb[7] = hv[7] + g[7];
+        hb[0] = hv[0] - g[0];
+        hb[1] = hv[1] - g[1];
+#pragma unroll
+        for (int k = 2; k < S; k += 2) {
+            hb[k] = hv[k] - g[k];
+            hb[k + 1] = hv[k + 1] + g[k + 1];
+        }
         const Real a1 = A * Real(2) / Real(3), a2 = A / Real(3);
         hn[0] += a1;
         hn[1] -= a2;

@@ -19,8 +19,14 @@
 //     of each call, the state buffers are fully rewritten from the input, and
 //     two calls whose work overlaps on the GPU (different streams or host
 //     threads) race on the array;
-//   - the first call on a device looks up the device address of the array
-//     (cudaGetSymbolAddress); make that first call outside any stream capture.
+//   - the call synchronises on its stream and reads status words back to the
+//     host, so it must never be called while that stream is being captured;
+//     the first call on a device also looks up the device address of the
+//     array (cudaGetSymbolAddress);
+//   - n_steps == 0 returns at once and leaves the caller's buffer untouched;
+//     a non-finite input is refused (XF_E_STATE) before any step is taken;
+//   - every failure leaves its message where xf_last_error(NULL) reads it
+//     (per host thread, shared with xf_create).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,6 +39,7 @@
 #include "../../include/xf.h"
 #include "xf_aux.cuh"
 #include "xf_kernels.h"
+#include "xf_pack.h"
 
 using namespace xf;
 
@@ -43,11 +50,11 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void *g_scratch_ptr[kMaxDevices] = {};
-// Failures are reported by status code only (the message documents the cause).
+// Failures return their status code and leave `why` in this host thread's
+// last-error message (xf_last_error(NULL)), as a failed xf_create does.
 int noalloc_fail(int code, const char *why)
 {
-    (void)why;
-    return code;
+    return xfp::fail(nullptr, code, "xf_step_noalloc: %s", why);
 }
 
 // Device address of the scratch array for the current device, looked up once
@@ -295,6 +302,11 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
     const int egrid = (int)std::min<long long>((2ll * n_pairs + 255) / 256, (long long)sms * 16);
     pack_to_state_kernel<NF, Real><<<egrid, 256, 0, stream>>>(la, rho_dev, rho0, trace, ref);
     NA_CUDA(cudaGetLastError(), "layout kernel");
+    // refuse a non-finite input before spending any step on it
+    int h_bad = 0;
+    NA_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, stream), "read flag");
+    NA_CUDA(cudaStreamSynchronize(stream), "stream synchronize");
+    if (h_bad) return noalloc_fail(XF_E_STATE, "input state contains non-finite values; nothing was run");
 
     // the persistent integrator, in launches of at most 65536 steps
     const long long kChunk = 1ll << 16;
@@ -326,13 +338,11 @@ int run_noalloc(int n_E, int n_u, const xf_params *p, double *rho_dev, double r_
         done += m;
     }
 
-    int h_err = 0, h_bad = 0;
+    int h_err = 0;
     InstPos h_pos;
     NA_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, stream), "read error word");
-    NA_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, stream), "read flag");
     NA_CUDA(cudaMemcpyAsync(&h_pos, pos, sizeof(InstPos), cudaMemcpyDeviceToHost, stream), "read progress");
     NA_CUDA(cudaStreamSynchronize(stream), "stream synchronize");
-    if (h_bad) return noalloc_fail(XF_E_STATE, "input state contains non-finite values");
     if (h_err & ERR_LAUNCH) return noalloc_fail(XF_E_CUDA, "integrator launched without its staging area");
     if (h_err & ERR_BARRIER) return noalloc_fail(XF_E_BARRIER_TIMEOUT, "grid barrier timed out; output not written");
 
@@ -378,6 +388,8 @@ extern "C" int xf_step_noalloc(int n_E, int n_u, int n_flavor, const xf_params *
     if (!std::isfinite(r_km) || r_km < p->R_nu_km) return noalloc_fail(XF_E_ARG, "r_km must be finite and >= R_nu");
     if (n_steps < 0) return noalloc_fail(XF_E_ARG, "n_steps must be >= 0");
     if (!std::isfinite(dr_km) || dr_km <= 0) return noalloc_fail(XF_E_ARG, "dr_km must be finite and > 0");
+    xfp::fail(nullptr, XF_OK, "%s", ""); // no failure so far in this call
+    if (n_steps == 0) return XF_OK;     // nothing to do: rho_dev is left as it is
     void *scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc) return rc;
