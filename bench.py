@@ -126,22 +126,45 @@ def measured_peaks():
 
 # ---------------------------------------------------------------- algorithmic work
 
-# FP64 floating-point operations per bin-step of the predictor-corrector in
-# three flavors (two propagator applications per step), counted from the
-# per-bin formulas (+ - * / sqrt each 1, FMA 2, sincos not counted) by
-# running them once with a counting number type that drops operations on
-# structural zeros (a product with a literal zero, a sum with one); the
-# Jacobi eigensolver is counted at the sweep number measured on this workload.
-FLOPS_PER_BIN_STEP = {("exph", 3): 2097, ("rk4", 3): 684, ("exph", 2): 122, ("rk4", 2): 172}
-# one attempt of the error-controlled step (four Hamiltonians, five propagations,
-# one shared eigendecomposition), counted the same way; three flavors at the
-# 2.31 mean Jacobi sweeps that this leg's Hamiltonians (250-260 km) take,
-# each sweep beyond two adding 280 flop per eigendecomposition (4761 at two)
-FLOPS_PER_BIN_ATTEMPT = {3: 5108, 2: 272}
-# the wavefunction form (one psi per initial flavor), counted the same way:
-# per stage the propagation of n_f wavefunctions and rho's traceless part
-# rebuilt from them for the moments
+# Floating-point operations per bin-step of the per-bin formulas (+ - * / sqrt
+# and reciprocal square root 1 each, FMA 2, sine-cosine pairs not counted,
+# operations on structural zeros dropped), as tests/xf_flopcount.cpp counts
+# them by running the kernels' own per-bin templates on a counting number
+# type; tests/test_flop_counts.py checks every figure here against it.  The
+# three-flavor figures are at two Jacobi sweeps per eigendecomposition, the
+# sweep count of every Hamiltonian of the headline workload over the timed
+# range (checked there too).
+FLOPS_PER_BIN_STEP = {("exph", 3): 2097, ("rk4", 3): 662, ("exph", 2): 122, ("rk4", 2): 162}
+# one attempt of the error-controlled step (four Hamiltonians, five
+# propagations, one shared eigendecomposition) at two sweeps; each sweep
+# beyond two adds FLOPS_PER_EXTRA_SWEEP to each of the four
+# eigendecompositions per bin-attempt.  ADAPT_MEAN_SWEEPS: the mean sweep
+# count of the three-flavor workload's Hamiltonians at the start and end of
+# the leg's range (250 and 258 km, seeded state).
+FLOPS_PER_BIN_ATTEMPT_2SWEEPS = {3: 4756, 2: 270}
+FLOPS_PER_EXTRA_SWEEP = 281
+ADAPT_MEAN_SWEEPS = 2.3186
+
+
+def flops_per_bin_attempt(n_f):
+    extra = 4 * (ADAPT_MEAN_SWEEPS - 2.0) * FLOPS_PER_EXTRA_SWEEP if n_f == 3 else 0.0
+    return FLOPS_PER_BIN_ATTEMPT_2SWEEPS[n_f] + extra
+
+
+# the wavefunction form (one psi per initial flavor): per stage the
+# propagation of n_f wavefunctions and rho's traceless part rebuilt from them
 FLOPS_PER_BIN_STEP_PSI = {("exph", 3): 2215, ("rk4", 3): 1666, ("exph", 2): 270, ("rk4", 2): 520}
+# the extended bulb model (four moments) and the cylinder model's per-bin
+# update (its angle-pair sum is counted per trajectory), two flavors
+FLOPS_PER_BIN_STEP_AZIMUTH_2F = 146
+FLOPS_PER_BIN_STEP_CYLINDER_2F = 107
+# one 3x3 propagation: its counted flop, and the work the count leaves out or
+# prices at one flop (its two sine-cosine pairs, its reciprocal square roots)
+PROP3_UNCOUNTED = {"sincos_pairs": 2, "rsqrt": 12, "flop": 1001}
+# DRAM bytes per radial step of the headline kernel on the headline workload,
+# from the ncu capture summarised in TRAFFIC_PROFILE
+TRAFFIC_PER_RADIAL_STEP_C2_FP64 = 28.67e6
+TRAFFIC_PROFILE = "profiles/xf_run_kernel_exph3_fp64_c2.md"
 
 
 def oracle_sample(problem, n_steps, threads):
@@ -240,6 +263,14 @@ def run_xf(args):
     barrier()
     clk = clocks.stop()
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms per chunk (one launch)
+    # FP64 ALU peak, one figure for every leg: derived from the unit counts
+    # (SMs x 2 DFMA per clock x 2 flop) at the largest SM clock seen during
+    # the timed region; the library's measured FMA loop is reported beside it
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak64 = {"derived_tflops": sms * 2 * 2 * sm_max * 1e6 / 1e12,
+              "measured_fma_tflops": xf.peak(xf.PEAK_FP64_FMA) / 1e12,
+              "source": "derived: %d SMs x 2 DFMA/clk x 2 flop x %.0f MHz; measured: xf_peak FMA loop" % (sms, sm_max)}
     t_sum = max_over_ranks(sum(per) * 1e-3, world)
     bin_steps = p.n_bins * chunk * args.steps
     value = whole_job_rate(bin_steps, world, t_sum)
@@ -283,20 +314,19 @@ def run_xf(args):
 
     adaptive = None
     if args.precision == "fp64" and not args.skip_adapt:
-        sm_max0 = 2070.0
-        adaptive = run_adaptive(args, xf, I, torch, stream, flush, barrier, world, 152 * 4 * sm_max0 * 1e6 / 1e12)
+        adaptive = run_adaptive(args, xf, I, torch, stream, flush, barrier, world, peak64)
 
     azimuth = None
     if args.precision == "fp64" and not args.skip_azimuth:
-        azimuth = run_azimuth(args, xf, I, torch, stream, flush, barrier, world, 152 * 4 * 2070.0 * 1e6 / 1e12)
+        azimuth = run_azimuth(args, xf, I, torch, stream, flush, barrier, world, peak64)
 
     psi = None
     if args.precision == "fp64" and not args.skip_psi:
-        psi = run_psi(args, xf, I, torch, stream, flush, barrier, world, 152 * 4 * 2070.0 * 1e6 / 1e12)
+        psi = run_psi(args, xf, I, torch, stream, flush, barrier, world, peak64)
 
     cylinder = None
     if args.precision == "fp64" and not args.skip_cylinder:
-        cylinder = run_cylinder(args, xf, I, torch, stream, flush, barrier, world, 152 * 4 * 2070.0 * 1e6 / 1e12)
+        cylinder = run_cylinder(args, xf, I, torch, stream, flush, barrier, world, peak64)
 
     serving = None
     if args.precision == "fp64" and not args.skip_serve and rank == 0:
@@ -324,21 +354,39 @@ def run_xf(args):
     flops = FLOPS_PER_BIN_STEP[kind] * p.n_bins * chunk
     achieved = flops / avg_launch_s / 1e12
     peak_meas = xf.peak(xf.PEAK_FP64_FMA if args.precision == "fp64" else xf.PEAK_FP32_FMA) / 1e12
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    # derived ALU peak: 152 SMs x (FP64: 2 FMA, FP32: 128 FMA) per clock x 2 flop x max clock
+    # derived ALU peak: SMs x (FP64: 2 FMA, FP32: 128 FMA) per clock x 2 flop x max clock
     per_clk = 2 if args.precision == "fp64" else 128
-    peak_nom = 152 * per_clk * 2 * sm_max * 1e6 / 1e12
+    peak_nom = sms * per_clk * 2 * sm_max * 1e6 / 1e12
     # DRAM bytes (read + write) per radial step of this kernel on this workload, from
-    # one ncu capture of a 5-step launch (dram__bytes_read.sum + dram__bytes_write.sum
-    # = 147.6 MB), scaled to the bench's launch; null for other precisions
-    traffic = 28.67e6 * chunk if args.precision == "fp64" else None
+    # one ncu capture of a 5-step launch (dram__bytes_read.sum + dram__bytes_write.sum),
+    # scaled to the bench's launch; null for other precisions
+    traffic = TRAFFIC_PER_RADIAL_STEP_C2_FP64 * chunk if args.precision == "fp64" else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_nom, "unit": "TFLOP/s",
                 "frac": achieved / peak_nom, "traffic": traffic,
-                "traffic_note": "bytes per launch from ncu DRAM counters (5-step capture, scaled to %d steps); "
-                                "the state planes are L2-resident" % chunk,
+                "traffic_note": "scaled, not measured in this run: ncu DRAM bytes (read + write) of a 5-step "
+                                "launch (%s) x %d/5; the state planes are L2-resident" % (TRAFFIC_PROFILE, chunk),
                 "kernel": "xf_run_kernel<3,EXPH,%s>" % ("double" if args.precision == "fp64" else "float"),
-                "peak_source": "derived: 152 SMs x %d FMA/clk x 2 x %.0f MHz (recipe FP64 1.25 TFLOP/s)" % (per_clk, sm_max),
-                "peak_measured_fma": peak_meas}
+                "peak_source": "derived: %d SMs x %d FMA/clk x 2 x %.0f MHz (recipe FP64 1.25 TFLOP/s)" % (sms, per_clk, sm_max),
+                "peak_measured_fma": peak_meas, "frac_of_measured_fma": achieved / peak_meas,
+                "flop_per_bin_step": FLOPS_PER_BIN_STEP[kind],
+                "flop_source": "tests/xf_flopcount.cpp (checked by tests/test_flop_counts.py)"}
+    if p.n_f == 3 and p.stepper == I.EXPH and args.precision == "fp64":
+        # work per 3x3 propagation that the count leaves out (sine-cosine pairs)
+        # or prices at one flop (reciprocal square roots), priced in FP64 FMA
+        # issue slots by the library's microbenchmarks; two propagations per bin-step
+        fma_slots = peak_meas * 1e12 / 2.0
+        pp = dict(PROP3_UNCOUNTED)
+        pp["achieved_fma_slots_per_propagation"] = fma_slots * avg_launch_s / (2.0 * p.n_bins * chunk)
+        try:
+            c_rsqrt = fma_slots / xf.peak(xf.PEAK_FP64_RSQRT)
+            c_sincos = fma_slots / xf.peak(xf.PEAK_FP64_SINCOS)
+            pp.update(rsqrt_fma_slots=c_rsqrt, sincos_fma_slots=c_sincos,
+                      uncounted_fma_slots=pp["rsqrt"] * (c_rsqrt - 0.5) + pp["sincos_pairs"] * c_sincos,
+                      note="rsqrt counted as 1 flop (half an FMA slot) in flop; each microbenchmark call "
+                           "carries one FMA of its own")
+        except (AttributeError, xf.XFError):
+            pass  # a library without these microbenchmarks
+        roofline["per_propagation"] = pp
 
     # CPU baseline: the oracle on the host cores, bounded sample
     cpu = None
@@ -347,6 +395,12 @@ def run_xf(args):
         v, dt = oracle_sample(I.bulb3f_1000x200(), args.cpu_steps, threads_cpu)
         cpu = {"value": v, "unit": UNIT, "cores": threads_cpu, "kind": "oracle",
                "sample": f"{args.cpu_steps} radial steps of the full 400,000-bin problem from 10 km ({dt:.1f} s)"}
+        if batched is not None and batched.get("_finals"):
+            cpu["batched_sample"] = oracle_batched_sample(I, batched["_finals"], threads_cpu)
+            batched["p_surv_err_vs_oracle"] = cpu["batched_sample"]["p_surv_err_vs_oracle"]
+            batched["p_surv_err_sample"] = cpu["batched_sample"]["sample"]
+    if batched is not None:
+        batched.pop("_finals", None)
 
     if rank == 0:
         line = {
@@ -370,7 +424,13 @@ def run_xf(args):
     return 0
 
 
-def run_adaptive(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
+def fp64_fracs(tflops, peak64):
+    """Fractions of the derived FP64 ALU peak and of the measured FMA loop."""
+    return {"achieved_tflops_fp64": tflops, "frac_of_fp64_peak": tflops / peak64["derived_tflops"],
+            "frac_of_measured_fma": tflops / peak64["measured_fma_tflops"]}
+
+
+def run_adaptive(args, xf, I, torch, stream, flush, barrier, world, peak64):
     """The paper's error-controlled step on the three-flavor 400,000-bin
     workload from 250 km (eps0 = 1e-6, dr_max = 0.05 km), FP64: one bench step
     = a fixed budget of attempts (xf_evolve toward 1000 km stops on the budget)."""
@@ -405,15 +465,15 @@ def run_adaptive(args, xf, I, torch, stream, flush, barrier, world, peak_tflops)
     st = c.adapt_status()
     c.close()
     attempts = iters * args.steps
-    flops = FLOPS_PER_BIN_ATTEMPT[p.n_f] * p.n_bins * attempts
+    flops = flops_per_bin_attempt(p.n_f) * p.n_bins * attempts
     return {"value": p.n_bins * acc * world / t, "unit": UNIT + " (accepted)",
             "bin_attempts_per_s": p.n_bins * attempts * world / t, "attempts": attempts, "accepted": acc,
             "rejected": rej, "ms_per_attempt": 1e3 * t / attempts, "r_km": st["r"], "h_next_km": st["h_next"],
             "eps0": p.eps0, "dr_max_km": p.dr_max, "precision": "FP64",
-            "achieved_tflops_fp64": flops / t / 1e12, "frac_of_fp64_peak": flops / t / 1e12 / peak_tflops}
+            "flop_per_bin_attempt": flops_per_bin_attempt(p.n_f), **fp64_fracs(flops / t / 1e12, peak64)}
 
 
-def run_azimuth(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
+def run_azimuth(args, xf, I, torch, stream, flush, barrier, world, peak64):
     """The extended bulb model (Eq. 3.18) at the size the paper quotes for it:
     1000 zenith x 100 azimuth x 100 energy bins (2 x 10^7 bins), two flavors,
     FP64, the predictor-corrector from 50 km; one bench step = 10 radial steps."""
@@ -439,16 +499,14 @@ def run_azimuth(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
     ctas, threads, _ = c.launch_info()
     c.close()
     steps = chunk * args.steps
-    # the two-moment count plus, per bin and stage, the two extra moments in G
-    # (2 x 3 FMA) and in the sums (2 x 3 FMA): +24 flop per bin-step
-    flops = (FLOPS_PER_BIN_STEP[("exph", 2)] + 24) * p.n_bins * steps
+    # the two-moment count plus the two extra moments in G and in the sums
+    flops = FLOPS_PER_BIN_STEP_AZIMUTH_2F * p.n_bins * steps
     return {"value": p.n_bins * steps * world / t, "unit": UNIT, "bins": p.n_bins, "n_u": p.n_u, "n_phi": p.n_phi,
             "n_E": p.n_E, "n_f": p.n_f, "ms_per_radial_step": 1e3 * t / steps, "precision": "FP64",
-            "ctas": ctas, "threads": threads, "achieved_tflops_fp64": flops / t / 1e12,
-            "frac_of_fp64_peak": flops / t / 1e12 / peak_tflops}
+            "ctas": ctas, "threads": threads, **fp64_fracs(flops / t / 1e12, peak64)}
 
 
-def run_psi(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
+def run_psi(args, xf, I, torch, stream, flush, barrier, world, peak64):
     """The wavefunction form (Eq. 3.9-3.11) on the headline workload: the same
     3-flavor 1000 x 200 bulb problem with one wavefunction per initial flavor
     (18 reals per bin instead of 8), FP64, the predictor-corrector averaging
@@ -477,11 +535,10 @@ def run_psi(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
     flops = FLOPS_PER_BIN_STEP_PSI[("exph", p.n_f)] * p.n_bins * steps
     return {"value": p.n_bins * steps * world / t, "unit": UNIT, "bins": p.n_bins, "reals_per_bin": 2 * p.n_f ** 2,
             "ms_per_step": 1e3 * t / args.steps, "radial_steps_per_step": chunk, "precision": "FP64",
-            "ctas": ctas, "threads": threads, "achieved_tflops_fp64": flops / t / 1e12,
-            "frac_of_fp64_peak": flops / t / 1e12 / peak_tflops}
+            "ctas": ctas, "threads": threads, **fp64_fracs(flops / t / 1e12, peak64)}
 
 
-def run_cylinder(args, xf, I, torch, stream, flush, barrier, world, peak_tflops):
+def run_cylinder(args, xf, I, torch, stream, flush, barrier, world, peak64):
     """The cylinder/line model (Eq. 3.20): 512 emission angles x 128 latitudes
     x 100 energies x nu/nubar (1.3e7 bins), two flavors, FP64, the
     predictor-corrector from 20 km; one bench step = 10 radial steps.  Per
@@ -512,14 +569,13 @@ def run_cylinder(args, xf, I, torch, stream, flush, barrier, world, peak_tflops)
     S = p.n_f ** 2 - 1
     traj = p.n_u * p.n_phi
     # per bin-step: the two-flavor predictor-corrector update with plain
-    # trajectory sums (107 flop); per trajectory and stage: 2 S FMA per angle bin
-    bin_flops = 107.0 * p.n_bins * steps
+    # trajectory sums; per trajectory and stage: 2 S FMA per angle bin
+    bin_flops = float(FLOPS_PER_BIN_STEP_CYLINDER_2F) * p.n_bins * steps
     pair_flops = 2.0 * traj * p.n_u * 4 * S * steps
     return {"value": p.n_bins * steps * world / t, "unit": UNIT, "bins": p.n_bins, "n_u": p.n_u, "n_phi": p.n_phi,
             "n_E": p.n_E, "n_f": p.n_f, "ms_per_radial_step": 1e3 * t / steps, "precision": "FP64",
             "ctas": ctas, "threads": threads, "angle_pair_flop_share": pair_flops / (pair_flops + bin_flops),
-            "achieved_tflops_fp64": (bin_flops + pair_flops) / t / 1e12,
-            "frac_of_fp64_peak": (bin_flops + pair_flops) / t / 1e12 / peak_tflops}
+            **fp64_fracs((bin_flops + pair_flops) / t / 1e12, peak64)}
 
 
 def run_batched(args, xf, I, torch, stream, flush, barrier, world):
@@ -558,6 +614,18 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
     avg = t / args.steps
     ok = sum(1 for i in range(len(probs)) if b.status_i(i)[0] == "XF_OK")
     ctas, threads, _ = b.launch_info()
+    # the whole run (every problem's n_steps from its seeded state, same launch
+    # configuration), whose final states the CPU-baseline leg checks against
+    # the oracle on a sample of problems
+    finals = {}
+    if args.batch_check and not args.skip_cpu and dist_env()[0] == 0:
+        b.init_state_i(-1, probs[0].r0)
+        n_all = probs[0].n_steps
+        for _ in range(n_all // chunk):
+            b.step_all(chunk, h)
+        for i in batch_sample(probs, args.batch_check):
+            st = b.status_i(i)
+            finals[i] = (b.get_state_i(i)[0], st[0], st[1])
     b.close()
     # the plain FP64 path on the same inputs (same ensemble, seeds and steps)
     fp64 = None
@@ -595,7 +663,115 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
             "speedup_vs_fp64_plain": (bins * chunk * args.steps * world / t / fp64["value"]) if fp64 else None,
             "achieved_gbs": state_bytes / avg / 1e9, "hbm_peak_gbs": hbm,
             "hbm_frac": (state_bytes / avg / 1e9 / hbm) if hbm else None,
-            "achieved_tflops_fp32": flops / avg / 1e12}
+            "achieved_tflops_fp32": flops / avg / 1e12, "_finals": finals}
+
+
+def batch_sample(probs, k):
+    """The k smallest problems of the ensemble (by bins; ties by index)."""
+    return sorted(sorted(range(len(probs)), key=lambda i: (probs[i].n_bins, i))[:k])
+
+
+def p_surv_error(got, ref, rho0, n_f):
+    """max |P_surv(got) - P_surv(ref)|, P_surv = (rho_ee - phi_x)/(phi_e - phi_x)
+    with phi from the initial diagonal, over bins whose spectra are
+    distinguishable (|phi_e - phi_x| >= 1e-2 of the species' largest)."""
+    import numpy as np
+    m = n_f * n_f
+    g, r, x0 = got.reshape(2, -1, m), ref.reshape(2, -1, m), rho0.reshape(2, -1, m)
+    worst = 0.0
+    for s in range(2):
+        sep = x0[s, :, 0] - x0[s, :, 1]
+        mask = np.abs(sep) >= 1e-2 * np.abs(sep).max()
+        worst = max(worst, float(np.abs((g[s, mask, 0] - r[s, mask, 0]) / sep[mask]).max()))
+    return worst
+
+
+def oracle_batched_sample(I, finals, threads):
+    """CPU baseline of the batched leg: the oracle (as it stands) on the
+    sampled problems of the ensemble for their whole run, timed; and the FP32
+    batched results' survival-probability error against it."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    O.build()
+    probs = I.ensemble_problems()
+    work, t, err, bad = 0.0, 0.0, 0.0, 0
+    for i, (got, status, done) in sorted(finals.items()):
+        q = probs[i]
+        rho0 = O.init_state(q)
+        t0 = time.perf_counter()
+        ref, st, k = O.evolve(q, rho0, q.r0, q.h, q.n_steps, n_threads=threads)
+        t += time.perf_counter() - t0
+        work += q.n_bins * q.n_steps
+        if st != 0 or status != "XF_OK" or done != q.n_steps:
+            bad += 1
+            continue
+        err = max(err, p_surv_error(got, ref, rho0, q.n_f))
+    return {"value": work / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"the {len(finals)} smallest of the 256 ensemble problems, their whole 1000-step runs "
+                      f"({sum(probs[i].n_bins for i in finals)} bins, {t:.1f} s)",
+            "p_surv_err_vs_oracle": err, "problems_not_comparable": bad}
+
+
+def serve_window(xf, I, torch, rate, window, budget, chunk, drain_s):
+    """Poisson arrivals at `rate` jobs/s for `window` s into a fresh server;
+    then at most `drain_s` more seconds for the jobs to finish.  A job still
+    unfinished at that cut-off counts with its waiting time so far (a lower
+    bound on its latency: the percentiles are then lower bounds too)."""
+    import threading
+    arrivals = I.job_arrivals(rate_per_s=rate, window_s=window, seed=5)
+    srv = xf.Server(max_jobs=256, mem_budget_bytes=budget, chunk_steps=chunk)
+    ids, t_sub = [], []
+    t0 = time.perf_counter()
+
+    def feeder():
+        for t_arr, p in arrivals:
+            d = t0 + t_arr - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            ids.append(srv.submit(p))
+            t_sub.append(time.perf_counter())
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    t_cut = t0 + window + drain_s
+    lat, pending = {}, list(ids)
+    while pending and time.perf_counter() < t_cut:
+        still = []
+        for j in pending:
+            r = srv.poll(j)
+            if r is None:
+                still.append(j)
+            else:  # the library's own submit and finish times
+                lat[j] = r[0]["t_done"] - r[0]["t_submit"]
+        pending = still
+        time.sleep(0.1)
+    t_end = time.perf_counter()
+    st = srv.stats()
+    srv.close()  # abandons what is still queued or resident
+    work = sum(p.n_bins * p.n_steps for j, (_, p) in zip(ids, arrivals) if j in lat)
+    all_lat = [lat[j] if j in lat else t_end - ts for j, ts in zip(ids, t_sub)]
+    censored = len(ids) - len(lat)
+
+    def pct(xs, f):
+        xs = sorted(xs)
+        return xs[min(len(xs) - 1, int(f * len(xs)))] if xs else None
+
+    half = [t_arr < window / 2 for t_arr, _ in arrivals[:len(ids)]]
+    first = [x for x, h in zip(all_lat, half) if h]
+    second = [x for x, h in zip(all_lat, half) if not h]
+    p99_1, p99_2 = pct(first, 0.99), pct(second, 0.99)
+    # sustainable: every job finished within the drain allowance, and the tail
+    # latency of the window's second half is no worse than its first half's
+    stable = censored == 0 and p99_1 is not None and p99_2 is not None and p99_2 <= 1.5 * p99_1 + 0.25
+    return {"rate_jobs_per_s": rate, "window_s": window, "drain_limit_s": drain_s, "jobs": len(ids),
+            "finished": len(lat), "unfinished_at_cutoff": censored,
+            "p50_s": pct(all_lat, 0.50), "p99_s": pct(all_lat, 0.99),
+            "percentiles_are_lower_bounds": censored > 0,
+            "p99_first_half_s": p99_1, "p99_second_half_s": p99_2, "stable": stable,
+            "value": work / (t_end - t0), "unit": UNIT,
+            "gpu_busy_value": st["bin_steps"] / max(st["busy_s"], 1e-9),
+            "max_resident": st["max_resident"], "epochs": st["epochs"]}
 
 
 def run_serving(args, xf, I, torch):
@@ -603,59 +779,40 @@ def run_serving(args, xf, I, torch):
     batched ensemble's size distribution (n_u 64-1024, n_E 32-256), 1000-20000
     steps of h = 0.01 km from 50 km, FP32 bins with FP64 moments; continuous
     batching in a server with up to 256 resident jobs and a memory budget of
-    up to 150 GB.  Latency = finish - arrival.  Reported at a rate the GPU
-    sustains and, briefly, at the overloaded rate of 200 jobs/s."""
-    import threading
+    up to 150 GB.  Latency = finish - arrival.  Reported at the highest rate
+    the GPU sustains (--serve-rate, from the --serve-search sweep) and at the
+    stream's nominal 200 jobs/s, each over the same window; --serve-search
+    also sweeps --serve-rates."""
     free, _ = torch.cuda.mem_get_info()
     budget = int(min(150e9, 0.5 * free))
-    out = {}
-    for label, rate, window in (("sustained", args.serve_rate, args.serve_window), ("rate_200", 200.0, 1.0)):
-        arrivals = I.job_arrivals(rate_per_s=rate, window_s=window, seed=5)
-        srv = xf.Server(max_jobs=256, mem_budget_bytes=budget, chunk_steps=args.serve_chunk)
-        ids, t_sub = [], []
-        t0 = time.perf_counter()
-
-        def feeder():
-            for t_arr, p in arrivals:
-                d = t0 + t_arr - time.perf_counter()
-                if d > 0:
-                    time.sleep(d)
-                ids.append(srv.submit(p))
-                t_sub.append(time.perf_counter())
-
-        th = threading.Thread(target=feeder)
-        th.start()
-        th.join()
-        srv.drain(timeout_s=600.0)
-        t_end = time.perf_counter()
-        lat, work = [], 0.0
-        for j, (t_arr, p) in zip(ids, arrivals):
-            meta, _ = srv.poll(j)
-            lat.append(meta["t_done"] - meta["t_submit"])
-            work += p.n_bins * p.n_steps
-        st = srv.stats()
-        srv.close()
-        lat.sort()
-        q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
-        out[label] = {"rate_jobs_per_s": rate, "window_s": window, "jobs": len(ids), "p50_s": q(0.50),
-                      "p99_s": q(0.99), "value": work / (t_end - t0), "unit": UNIT,
-                      "gpu_busy_value": st["bin_steps"] / max(st["busy_s"], 1e-9),
-                      "max_resident": st["max_resident"], "epochs": st["epochs"]}
-    # the same kind of jobs, each alone in FP64 (sample of 3)
-    sample = [p for _, p in I.job_arrivals(rate_per_s=200.0, window_s=1.0, seed=6)][:3]
+    out = {"budget_bytes": budget}
+    if args.serve_search:
+        rates = [float(x) for x in args.serve_rates.split(",")]
+        out["search"] = [serve_window(xf, I, torch, r, args.serve_window, budget, args.serve_chunk, args.serve_drain)
+                         for r in rates]
+        ok = [w["rate_jobs_per_s"] for w in out["search"] if w["stable"]]
+        out["highest_stable_rate"] = max(ok) if ok else None
+    out["sustained"] = serve_window(xf, I, torch, args.serve_rate, args.serve_window, budget, args.serve_chunk,
+                                    args.serve_drain)
+    out["rate_200"] = serve_window(xf, I, torch, 200.0, args.serve_window, budget, args.serve_chunk,
+                                   args.serve_overload_drain)
+    # the same kind of jobs, each alone in FP64 (first --alone-jobs jobs of a
+    # second stream, at most --alone-steps steps each: a per-step rate)
+    sample = [p for _, p in I.job_arrivals(rate_per_s=200.0, window_s=10.0, seed=6)][:args.alone_jobs]
     work, t = 0.0, 0.0
     for p in sample:
         q = p.replace(precision=I.FP64)
+        n = min(q.n_steps, args.alone_steps)
         c = xf.Context(q)
         c.init_state(q.r0)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        c.step(q.n_steps, q.h)
+        c.step(n, q.h)
         t += time.perf_counter() - t1
-        work += q.n_bins * q.n_steps
+        work += q.n_bins * n
         c.close()
-    out["alone_fp64"] = {"value": work / t, "unit": UNIT, "jobs": len(sample)}
-    out["budget_bytes"] = budget
+    out["alone_fp64"] = {"value": work / t, "unit": UNIT, "jobs": len(sample),
+                         "steps_per_job": f"min(job's steps, {args.alone_steps})"}
     return out
 
 
@@ -681,13 +838,25 @@ def main():
     ap.add_argument("--skip-cylinder", action="store_true", help="skip the cylinder-model leg")
     ap.add_argument("--skip-tune", action="store_true", help="batched leg: keep the automatic tile size")
     ap.add_argument("--skip-batch-fp64", action="store_true", help="batched leg: skip the FP64 run of the ensemble")
+    ap.add_argument("--batch-check", type=int, default=16,
+                    help="batched leg: problems (the smallest) whose whole run the CPU-baseline leg checks "
+                         "against the oracle (0: none)")
     ap.add_argument("--batch-tile", type=int, default=0, help="batched leg with --skip-tune: pairs per tile (0: rule)")
     ap.add_argument("--batch-dynamic", type=int, default=0, choices=[0, 1],
                     help="batched leg with --skip-tune: dynamic tile claiming")
     ap.add_argument("--adapt-iters", type=int, default=30, help="attempts per error-controlled bench step")
-    ap.add_argument("--serve-rate", type=float, default=10.0, help="sustained arrival rate, jobs/s")
-    ap.add_argument("--serve-window", type=float, default=5.0, help="arrival window at the sustained rate, s")
+    ap.add_argument("--serve-rate", type=float, default=10.0,
+                    help="sustained arrival rate, jobs/s (the highest stable rate of the --serve-search sweep)")
+    ap.add_argument("--serve-window", type=float, default=30.0, help="arrival window of each serving run, s")
+    ap.add_argument("--serve-drain", type=float, default=30.0,
+                    help="seconds after the window for a sustained run's jobs to finish")
+    ap.add_argument("--serve-overload-drain", type=float, default=5.0,
+                    help="seconds after the window before the 200 jobs/s run is cut off")
     ap.add_argument("--serve-chunk", type=int, default=200, help="radial steps per serving epoch")
+    ap.add_argument("--serve-search", action="store_true", help="also sweep the arrival rates of --serve-rates")
+    ap.add_argument("--serve-rates", default="8,10,12,14,16,18,20", help="rates for --serve-search, jobs/s")
+    ap.add_argument("--alone-jobs", type=int, default=20, help="jobs timed alone in FP64")
+    ap.add_argument("--alone-steps", type=int, default=2000, help="steps per job timed alone in FP64")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")

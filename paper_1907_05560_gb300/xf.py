@@ -481,11 +481,12 @@ class Batch(Context):
         return STATUS.get(st.value, st.value), n.value, r.value
 
 
-PEAK_FP64_FMA, PEAK_FP32_FMA = 0, 1
+PEAK_FP64_FMA, PEAK_FP32_FMA, PEAK_FP64_RSQRT, PEAK_FP64_SINCOS = 0, 1, 2, 3
 
 
 def peak(which: int) -> float:
-    """Measured FMA throughput (FLOP/s) of the current device."""
+    """Measured FMA throughput (FLOP/s), or calls/s of the FP64 reciprocal
+    square root or sine-cosine pair, on the current device."""
     v = ctypes.c_double(0.0)
     rc = load().xf_peak(int(which), ctypes.byref(v))
     if rc != XF_OK:
