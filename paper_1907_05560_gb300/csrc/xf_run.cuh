@@ -618,6 +618,10 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
         cp_async_commit();
     }
     int buf = 0;
+    // the pair's angle and energy, (j, e) = divmod(p, n_E), advanced by the
+    // stride NT = dj n_E + de without a division per pair
+    const int dj = NT / v.n_E, de = NT - dj * v.n_E;
+    int j = (v.p0 + (int)threadIdx.x) / v.n_E, e = v.p0 + (int)threadIdx.x - j * v.n_E;
     for (int p = v.p0 + threadIdx.x; p < v.p1; p += NT, buf ^= 1) {
         Real *const col = PF ? col0 + buf * NPL * NT : nullptr;
         if constexpr (PF) {
@@ -625,7 +629,7 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
             cp_async_commit();
             cp_async_wait<1>(); // this pair's copies have landed
         }
-        const int j = p / v.n_E, e = p - j * v.n_E, q = j - v.j_lo;
+        const int q = j - v.j_lo;
         const Real gam = tb[q];
         Real g[S], hv[S], hn[S], hb[S];
 #pragma unroll
@@ -716,6 +720,12 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
         else if constexpr (VAR == VAR_COMP)
             accum_comp<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], m, mc);
         else accum<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], m);
+        e += de;
+        j += dj;
+        if (e >= v.n_E) {
+            e -= v.n_E;
+            ++j;
+        }
     }
     if constexpr (PF) cp_async_wait<0>();
     if constexpr (VAR == VAR_COMP) cta_partial_comp<NV, NT, Acc>(m, mc, sh, part_out);
