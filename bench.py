@@ -397,16 +397,21 @@ def run_xf(args):
                "sample": f"{args.cpu_steps} radial steps of the full 400,000-bin problem from 10 km ({dt:.1f} s)"}
         if batched is not None and batched.get("_finals"):
             cpu["batched_sample"] = oracle_batched_sample(I, batched["_finals"], threads_cpu,
-                                                          batched.get("_finals64"))
+                                                          batched.get("_finals64"), batched.get("_finals_ff"))
             bs = cpu["batched_sample"]
             batched["p_surv_err_vs_oracle"] = bs["p_surv_err_vs_oracle"]
             batched["p_surv_err_within_target"] = bs["within_target"]
             batched["p_surv_err_over_target"] = bs["over_target"]
             batched["fp64_p_surv_err_vs_oracle"] = bs["fp64_p_surv_err_vs_oracle"]
+            if batched.get("fp32x2_same_inputs"):
+                batched["fp32x2_same_inputs"]["p_surv_err_vs_oracle"] = bs["fp32x2_p_surv_err_vs_oracle"]
+            if batched.get("target_guarded"):
+                batched["target_guarded"]["p_surv_err_vs_oracle"] = bs["guarded_p_surv_err_vs_oracle"]
             batched["p_surv_err_sample"] = bs["sample"]
     if batched is not None:
         batched.pop("_finals", None)
         batched.pop("_finals64", None)
+        batched.pop("_finals_ff", None)
 
     if rank == 0:
         line = {
@@ -648,6 +653,15 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
             st = c.status_i(k)
             finals64[i] = (c.get_state_i(k)[0], st[0], st[1])
         c.close()
+    # float-float bins (XF_FP32X2) on the same inputs, and the split that keeps
+    # every problem within the target: FP32 bins where the measured domain of
+    # the FP32 target holds (mu0 <= FP32_TARGET_MU0), float-float bins beyond
+    ff = guarded = None
+    finals_ff = {}
+    if not args.skip_batch_ff:
+        ff, finals_ff = run_batched_ff(args, xf, I, torch, stream, barrier, world, probs, h, chunk,
+                                       sorted(finals) if finals else [])
+        guarded = run_batched_guarded(args, xf, I, torch, stream, barrier, world, probs, h, chunk)
     # the plain FP64 path on the same inputs (same ensemble, seeds and steps)
     fp64 = None
     if not args.skip_batch_fp64:
@@ -680,11 +694,96 @@ def run_batched(args, xf, I, torch, stream, flush, barrier, world):
             "precision": "FP32 bins, FP64 moments/radius/phase", "graph": True, "ctas": ctas, "threads": threads,
             "tile_pairs": tile if tile is not None else "rule", "autotune_ms_per_step": tile_ms,
             "dynamic_tiles": dynamic,
-            "fp64_plain_same_inputs": fp64,
+            "fp64_plain_same_inputs": fp64, "fp32x2_same_inputs": ff, "target_guarded": guarded,
             "speedup_vs_fp64_plain": (bins * chunk * args.steps * world / t / fp64["value"]) if fp64 else None,
             "achieved_gbs": state_bytes / avg / 1e9, "hbm_peak_gbs": hbm,
             "hbm_frac": (state_bytes / avg / 1e9 / hbm) if hbm else None,
-            "achieved_tflops_fp32": flops / avg / 1e12, "_finals": finals, "_finals64": finals64}
+            "achieved_tflops_fp32": flops / avg / 1e12, "_finals": finals, "_finals64": finals64,
+            "_finals_ff": finals_ff}
+
+
+# mu0 bound of the FP32 bins' measured target domain: the ensemble's sampled
+# problems with mu0 <= 1e5 (three flavors) and <= 1.8e5 (two flavors) kept
+# FP32 within 1e-3 in P_surv, with 7.9e-4 at mu0 = 7e4 (three flavors); the
+# split takes a margin below both
+FP32_TARGET_MU0 = 5e4
+
+
+def _timed_steps(torch, stream, barrier, world, fn, n):
+    s_ev = torch.cuda.Event(enable_timing=True)
+    e_ev = torch.cuda.Event(enable_timing=True)
+    barrier()
+    s_ev.record(stream)
+    for _ in range(n):
+        fn()
+    e_ev.record(stream)
+    barrier()
+    return max_over_ranks(s_ev.elapsed_time(e_ev) * 1e-3, world)
+
+
+def run_batched_ff(args, xf, I, torch, stream, barrier, world, probs, h, chunk, sample):
+    """The ensemble with float-float bins: FP64 state and sums, the
+    propagator in float-float on the FP32 pipes.  Returns the timing and the
+    sampled problems' whole runs (checked against the oracle with the FP32
+    ones)."""
+    pf = [q.replace(precision=I.FP32X2) for q in probs]
+    b = xf.Batch(pf, stream=stream)
+    b.set_option(xf.OPT_GRAPH, 1)
+    b.init_state_i(-1, pf[0].r0)
+    tile = None if args.skip_tune else b.autotune(1, h, candidates=[0, 2048, 4096, 8192])[0]
+    dynamic = b.get_option(xf.OPT_DYNAMIC_TILES)
+    b.step_all(chunk, h)  # warm-up
+    n = max(1, min(args.steps, 2))
+    t = _timed_steps(torch, stream, barrier, world, lambda: b.step_all(chunk, h), n)
+    bins = sum(q.n_bins for q in pf)
+    ok = sum(1 for i in range(len(pf)) if b.status_i(i)[0] == "XF_OK")
+    b.close()
+    finals = {}
+    if sample:
+        ps = [pf[i] for i in sample]
+        c = xf.Batch(ps, stream=stream)
+        c.init_state_i(-1, ps[0].r0)
+        for _ in range(ps[0].n_steps // chunk):
+            c.step_all(chunk, h)
+        for k, i in enumerate(sample):
+            st = c.status_i(k)
+            finals[i] = (c.get_state_i(k)[0], st[0], st[1])
+        c.close()
+    return ({"value": bins * chunk * n * world / t, "unit": UNIT, "ms_per_step": 1e3 * t / n, "steps": n,
+             "precision": "FP32X2: FP64 state and sums, float-float propagator", "problems_ok": ok,
+             "tile_pairs": tile if tile is not None else "rule", "dynamic_tiles": dynamic}, finals)
+
+
+def run_batched_guarded(args, xf, I, torch, stream, barrier, world, probs, h, chunk):
+    """The ensemble split by the FP32 target's measured domain: problems with
+    mu0 <= FP32_TARGET_MU0 in FP32 bins, the rest in float-float bins, two
+    launches per step on one stream."""
+    lo = [q for q in probs if q.mu0 <= FP32_TARGET_MU0]
+    hi = [q.replace(precision=I.FP32X2) for q in probs if q.mu0 > FP32_TARGET_MU0]
+    packs = []
+    for ps in (lo, hi):
+        if not ps:
+            continue
+        b = xf.Batch(ps, stream=stream)
+        b.set_option(xf.OPT_GRAPH, 1)
+        b.init_state_i(-1, ps[0].r0)
+        if not args.skip_tune:
+            b.autotune(1, h, candidates=[0, 2048, 4096, 5120, 8192])
+        packs.append(b)
+
+    def step():
+        for b in packs:
+            b.step_all(chunk, h)
+    step()  # warm-up
+    n = max(1, min(args.steps, 2))
+    t = _timed_steps(torch, stream, barrier, world, step, n)
+    for b in packs:
+        b.close()
+    bins = sum(q.n_bins for q in probs)
+    return {"value": bins * chunk * n * world / t, "unit": UNIT, "ms_per_step": 1e3 * t / n, "steps": n,
+            "rule": f"FP32_M64 bins for mu0 <= {FP32_TARGET_MU0:g} km^-1, FP32X2 bins above",
+            "fp32_problems": len(lo), "fp32x2_problems": len(hi),
+            "fp32x2_bins": sum(q.n_bins for q in hi), "bins": bins}
 
 
 def batch_sample(probs, k):
@@ -710,7 +809,7 @@ def p_surv_error(got, ref, rho0, n_f):
     return worst
 
 
-def oracle_batched_sample(I, finals, threads, finals64=None):
+def oracle_batched_sample(I, finals, threads, finals64=None, finals_ff=None):
     """CPU baseline of the batched leg: the oracle (as it stands) on the
     sampled problems of the ensemble for their whole run, timed; and the FP32
     batched results' survival-probability error against it, per problem,
@@ -719,7 +818,7 @@ def oracle_batched_sample(I, finals, threads, finals64=None):
     import oracle as O
     O.build()
     probs = I.ensemble_problems()
-    work, t, err, err64, bad = 0.0, 0.0, 0.0, 0.0, 0
+    work, t, err, err64, err_ff, err_guard, bad = 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0
     over = []
     for i, (got, status, done) in sorted(finals.items()):
         q = probs[i]
@@ -738,12 +837,23 @@ def oracle_batched_sample(I, finals, threads, finals64=None):
                          "hierarchy": q.hierarchy, "p_surv_err": e})
         if finals64 and i in finals64 and finals64[i][1] == "XF_OK":
             err64 = max(err64, p_surv_error(finals64[i][0], ref, rho0, q.n_f))
+        e_ff = None
+        if finals_ff and i in finals_ff and finals_ff[i][1] == "XF_OK":
+            e_ff = p_surv_error(finals_ff[i][0], ref, rho0, q.n_f)
+            err_ff = max(err_ff, e_ff)
+        # the target-guarded split takes FP32 bins below the mu0 bound
+        if q.mu0 <= FP32_TARGET_MU0:
+            err_guard = max(err_guard, e)
+        elif e_ff is not None:
+            err_guard = max(err_guard, e_ff)
     n_ok = len(finals) - bad - len(over)
     return {"value": work / t, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"the {len(finals)} smallest of the 256 ensemble problems, their whole 1000-step runs "
                       f"({sum(probs[i].n_bins for i in finals)} bins, {t:.1f} s)",
             "p_surv_err_vs_oracle": err, "within_target": f"{n_ok} of {len(finals) - bad}",
             "over_target": over, "fp64_p_surv_err_vs_oracle": err64 if finals64 else None,
+            "fp32x2_p_surv_err_vs_oracle": err_ff if finals_ff else None,
+            "guarded_p_surv_err_vs_oracle": err_guard if finals_ff else None,
             "problems_not_comparable": bad}
 
 
@@ -873,6 +983,8 @@ def main():
     ap.add_argument("--skip-cylinder", action="store_true", help="skip the cylinder-model leg")
     ap.add_argument("--skip-tune", action="store_true", help="batched leg: keep the automatic tile size")
     ap.add_argument("--skip-batch-fp64", action="store_true", help="batched leg: skip the FP64 run of the ensemble")
+    ap.add_argument("--skip-batch-ff", action="store_true",
+                    help="batched leg: skip the float-float (FP32X2) and target-guarded runs of the ensemble")
     ap.add_argument("--batch-check", type=int, default=16,
                     help="batched leg: problems (the smallest) whose whole run the CPU-baseline leg checks "
                          "against the oracle (0: none)")

@@ -86,7 +86,14 @@ enum xf_precision {
     XF_FP32_M64_RENORM = 3 /* FP32_M64 plus, after every step, each bin's traceless part scaled
                               back to its initial tr(T^2) (|P| in 2 flavors, tr rho^2 in 3; both
                               are constants of the exact flow, Eq. 3.10).  The trace is exact in
-                              every variant (kept per bin in FP64, never updated) */
+                              every variant (kept per bin in FP64, never updated) */,
+    XF_FP32X2 = 4 /* FP64 state, tables, moments, radius and phase; the predictor-corrector's
+                     propagator (Eq. 3.10-3.12: the eigendecomposition and U T U^dagger) in
+                     float-float arithmetic (hi + lo of two floats, about 48 bits; Dekker's
+                     products and Knuth's sums) on the FP32 pipes.  XF_EXPH only; fixed steps,
+                     density matrices, bulb-type geometries, one azimuth bin; batches and the
+                     server accept it.  Error per propagation about 1e-14 of |T| (FP32 bins:
+                     1.5e-7), so it meets the FP32 target where FP32 rounding is amplified */
 };
 enum xf_geometry {
     XF_GEOM_BULB = 0,         /* Eq. 3.13-3.15: w_u = x^2 du/(2 cos_u), x = R/r; dl/dr = 1/cos_u */

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxf.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["xf_api.cu", "xf_server.cu", "xf_k64.cu", "xf_k32.cu", "xf_k32c.cu", "xf_k32r.cu", "xf_ka.cu", "xf_kaz.cu", "xf_kpsi.cu", "xf_kcyl.cu", "xf_peaks.cu", "xf_noalloc.cu", "xf_ckpt.cu"]
+SOURCES = ["xf_api.cu", "xf_server.cu", "xf_k64.cu", "xf_kff.cu", "xf_k32.cu", "xf_k32c.cu", "xf_k32r.cu", "xf_ka.cu", "xf_kaz.cu", "xf_kpsi.cu", "xf_kcyl.cu", "xf_peaks.cu", "xf_noalloc.cu", "xf_ckpt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include")]

@@ -163,8 +163,10 @@ int validate(xf_ctx *c, const xf_params *p, int n_E, int n_u, int nf)
         if (!(p->ksi > 0) || !(p->ksi <= 1)) return fail(c, XF_E_ARG, "ksi must be in (0, 1]");
         if (!(p->dr_max_km > 0) || !std::isfinite(p->dr_max_km)) return fail(c, XF_E_ARG, "dr_max must be finite and > 0");
     }
-    if (p->precision < XF_FP64 || p->precision > XF_FP32_M64_RENORM)
+    if (p->precision < XF_FP64 || p->precision > XF_FP32X2)
         return fail(c, XF_E_ARG, "bad precision %d", p->precision);
+    if (p->precision == XF_FP32X2 && p->stepper != XF_EXPH)
+        return fail(c, XF_E_UNSUPPORTED, "XF_FP32X2 runs the predictor-corrector (XF_EXPH) only");
     if (p->geometry < XF_GEOM_BULB || p->geometry > XF_GEOM_CYLINDER)
         return fail(c, XF_E_ARG, "bad geometry %d", p->geometry);
     if (p->geometry == XF_GEOM_CYLINDER) {
@@ -302,7 +304,7 @@ int elementwise_grid(xf_ctx *c, const InstHost &in)
 // on packs of mixed flavors.
 double default_cost3(int stepper, int precision)
 {
-    const bool fp64 = precision == XF_FP64;
+    const bool fp64 = precision == XF_FP64 || precision == XF_FP32X2;
     if (stepper == XF_RK4) return fp64 ? 4.0 : 3.0;
     return fp64 ? 12.0 : 3.0;
 }
@@ -858,7 +860,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // weights, and for the renormalising variant the initial tr(T^2) per bin.
 long long block_bytes(int n_E, int n_u, int nf, int precision, int form)
 {
-    const long long rb = precision == XF_FP64 ? 8 : 4;
+    const long long rb = (precision == XF_FP64 || precision == XF_FP32X2) ? 8 : 4;
     const long long S = nf * nf - 1, n_pairs = (long long)n_E * n_u, npad = (n_pairs + 63) & ~63ll;
     const long long SS = form == XF_FORM_PSI ? 2 * nf * nf : S;
     const long long ref = precision == XF_FP32_M64_RENORM ? (long long)align256(2 * npad * rb) : 0;
@@ -934,7 +936,7 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
         c->alloc = *alloc;
         c->has_alloc = true;
     }
-    c->real_bytes = (precision == XF_FP64) ? 8 : 4;
+    c->real_bytes = (precision == XF_FP64 || precision == XF_FP32X2) ? 8 : 4;
     c->precision = precision;
     c->stepper = stepper;
     c->cost3 = default_cost3(stepper, precision);
@@ -961,7 +963,8 @@ int create_ctx(int n_slots, long long arena_bytes, int stepper, int precision, i
     else if (nmom == 4)
         c->kern = run_kernel_azimuth(nfm, st, c->real_bytes == 8);
     else
-        c->kern = (c->real_bytes == 8) ? run_kernel_fp64(nfm, st)
+        c->kern = precision == XF_FP32X2 ? run_kernel_ff(nfm, st)
+                  : (c->real_bytes == 8) ? run_kernel_fp64(nfm, st)
                   : precision == XF_FP32_COMP ? run_kernel_fp32(nfm, st, VAR_COMP)
                   : precision == XF_FP32_M64_RENORM ? run_kernel_fp32(nfm, st, VAR_RENORM)
                                                      : run_kernel_fp32(nfm, st, VAR_PLAIN);

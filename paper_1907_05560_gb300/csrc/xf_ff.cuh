@@ -1,0 +1,152 @@
+// xf_ff.cuh -- float-float numbers for the per-bin arithmetic of the
+// XF_FP32X2 precision.
+//
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2
+// (about 48 significant bits, unit roundoff near 2^-47).  The operations
+// follow the double-float arithmetic of Dekker (1971): Knuth's TwoSum for
+// the exact error of a sum, the fused multiply-add for the exact error of a
+// product, and a final renormalisation (Dekker's Fast2Sum).  On GB300 a warp
+// issues 64 float operations per FP64 one, so a float-float operation of
+// 5-15 float instructions costs a fraction of an FP64 operation while keeping
+// most of its precision.
+//
+// The device code uses the *_rn intrinsics for every rounding step that must
+// stay a separate operation: the compiler never fuses them into an FMA,
+// which would break the error-free transformations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <math.h>
+
+namespace xf {
+
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ float ff_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float ff_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ff_mul(float a, float b) { return __fmul_rn(a, b); }
+#else
+inline float ff_add(float a, float b) { return a + b; }
+inline float ff_sub(float a, float b) { return a - b; }
+inline float ff_mul(float a, float b) { return a * b; }
+#endif
+
+struct ff {
+    float hi, lo;
+    ff() = default;
+    __host__ __device__ constexpr ff(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ ff(float f) : hi(f), lo(0.0f) {}
+    __host__ __device__ ff(int i) : hi((float)i), lo(0.0f) {}
+    // the double rounded to float, and the rest rounded to float
+    __host__ __device__ ff(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+};
+
+__host__ __device__ __forceinline__ double to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// s + e == a + b exactly, s = fl(a + b) (Knuth's TwoSum)
+__host__ __device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e)
+{
+    s = ff_add(a, b);
+    const float bb = ff_sub(s, a);
+    e = ff_add(ff_sub(a, ff_sub(s, bb)), ff_sub(b, bb));
+}
+// the same when |a| >= |b| (Dekker's Fast2Sum): the renormalisation step
+__host__ __device__ __forceinline__ ff fast_two_sum_f(float a, float b)
+{
+    const float s = ff_add(a, b);
+    return ff(s, ff_sub(b, ff_sub(s, a)));
+}
+
+__host__ __device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ ff operator+(ff a, ff b)
+{
+    float s, e;
+    two_sum_f(a.hi, b.hi, s, e);
+    e = ff_add(e, ff_add(a.lo, b.lo));
+    return fast_two_sum_f(s, e);
+}
+__host__ __device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+__host__ __device__ __forceinline__ ff operator*(ff a, ff b)
+{
+    const float p = ff_mul(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p); // the product's rounding error, exact
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum_f(p, e);
+}
+__host__ __device__ __forceinline__ ff &operator+=(ff &a, ff b) { return a = a + b; }
+__host__ __device__ __forceinline__ ff &operator-=(ff &a, ff b) { return a = a - b; }
+__host__ __device__ __forceinline__ ff &operator*=(ff &a, ff b) { return a = a * b; }
+
+// a b + c with one renormalisation
+__host__ __device__ __forceinline__ ff fma_r(ff a, ff b, ff c)
+{
+    const float p = ff_mul(a.hi, b.hi);
+    const float pe = fmaf(a.hi, b.hi, -p);
+    float s, se;
+    two_sum_f(p, c.hi, s, se);
+    const float t = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, c.lo));
+    return fast_two_sum_f(s, ff_add(ff_add(pe, se), t));
+}
+
+__host__ __device__ __forceinline__ bool operator>(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__host__ __device__ __forceinline__ bool operator<(ff a, ff b) { return b > a; }
+__host__ __device__ __forceinline__ bool operator>=(ff a, ff b) { return !(b > a); }
+__host__ __device__ __forceinline__ bool operator<=(ff a, ff b) { return !(a > b); }
+__host__ __device__ __forceinline__ ff abs_r(ff a) { return a.hi < 0.0f ? -a : a; }
+
+// 1/sqrt(x) for x > 0 in the normal float range: the float reciprocal square
+// root y (two ulps), then one third-order correction in float-float:
+// with e = 1 - x y^2, 1/sqrt(x) = y (1 - e)^(-1/2) = y (1 + e/2 + 3e^2/8 + O(e^3)),
+// and |e| < 2^-21 leaves O(e^3) below 2^-60.
+__host__ __device__ __forceinline__ ff rsqrt_r(ff x)
+{
+#ifdef __CUDA_ARCH__
+    const float y = rsqrtf(x.hi);
+#else
+    const float y = 1.0f / sqrtf(x.hi);
+#endif
+    // t = x y^2 in float-float (a float times a float-float, twice)
+    auto mulf = [](ff a, float b) {
+        const float p = ff_mul(a.hi, b);
+        float e = fmaf(a.hi, b, -p);
+        e = fmaf(a.lo, b, e);
+        return fast_two_sum_f(p, e);
+    };
+    const ff t = mulf(mulf(x, y), y);
+    const float e = ff_sub(ff_sub(1.0f, t.hi), t.lo); // 1 - t.hi is exact (t.hi near 1)
+    const float c = e * fmaf(0.375f, e, 0.5f);
+    const float p = ff_mul(y, c);
+    const float pe = fmaf(y, c, -p);
+    return fast_two_sum_f(y, ff_add(p, pe));
+}
+
+// The step's path length: a double (the phase is formed in FP64).
+template <typename Real> struct StepLen;
+template <> struct StepLen<ff> {
+    double v;
+};
+__host__ __device__ __forceinline__ StepLen<ff> make_step_len(double dl, ff *) { return {dl}; }
+__host__ __device__ __forceinline__ ff step_len_value(StepLen<ff> d) { return ff(d.v); }
+
+// (sin, cos) of lam * dl: the float-float eigenvalue difference times the
+// path length in FP64, then the FP64 library sine-cosine (four calls per
+// three-flavor bin-step, a small share of the FP64 pipe beside the
+// float-float work on the FP32 pipes).
+__host__ __device__ __forceinline__ void phase_sincos(ff lam, StepLen<ff> d, ff *s, ff *c)
+{
+    double sd, cd;
+    sincos(to_double(lam) * d.v, &sd, &cd);
+    *s = ff(sd);
+    *c = ff(cd);
+}
+
+template <typename Real> struct JacobiTol;
+// Sweeps stop at an off-diagonal norm of 1e-13 of the matrix's: a few units
+// of the float-float rounding, past which a sweep only chases rounding.
+template <> struct JacobiTol<ff> {
+    static constexpr float rel2 = 1e-26f;
+    static constexpr int sweeps = 8;
+};
+
+} // namespace xf

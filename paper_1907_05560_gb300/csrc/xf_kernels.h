@@ -1,5 +1,5 @@
 // xf_kernels.h -- host-visible handles of the persistent integrator kernels
-// (instantiated in xf_k64.cu, xf_k32*.cu, xf_ka.cu, xf_kaz.cu, xf_kpsi.cu and
+// (instantiated in xf_k64.cu, xf_kff.cu, xf_k32*.cu, xf_ka.cu, xf_kaz.cu, xf_kpsi.cu and
 // xf_kcyl.cu, compiled in parallel).
 #pragma once
 
@@ -17,6 +17,8 @@ struct RunKernel {
 // VAR_RENORM (FP32 only; mixed packs plain only).  fn == nullptr if not built.
 RunKernel run_kernel_fp64(int nfm, int stepper);
 RunKernel run_kernel_fp32(int nfm, int stepper, int var);
+// XF_FP32X2: FP64 storage and sums, float-float propagator (predictor-corrector only)
+RunKernel run_kernel_ff(int nfm, int stepper);
 // the error-controlled step (xf_adapt_kernel), FP64 or FP32 bins
 RunKernel run_kernel_adapt(int nfm, bool fp64);
 // the extended bulb model (four moments), plain arithmetic, FP64 or FP32 bins

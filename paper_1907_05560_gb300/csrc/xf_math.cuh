@@ -28,6 +28,8 @@ template <> struct Comp<3> { static constexpr int S = 8; };
 // ---------------------------------------------------------------- helpers
 __host__ __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
 __host__ __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
+__host__ __device__ __forceinline__ double abs_r(double x) { return fabs(x); }
+__host__ __device__ __forceinline__ float abs_r(float x) { return fabsf(x); }
 __host__ __device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
 __host__ __device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
 // 1/sqrt(x): the device's reciprocal square root (1 ulp in FP64, 2 in FP32);
@@ -305,7 +307,7 @@ __host__ __device__ __forceinline__ bool jacobi_angles(Real *dg, cx<Real> *o, Re
     }
     const Real d = Real(0.5) * (dg[Q] - dg[P]);
     const Real rD = rsqrt_r(d * d + ag2);
-    const Real u = Real(0.5) + Real(0.5) * fabs(d) * rD; // c^2, in [1/2, 1]
+    const Real u = Real(0.5) + Real(0.5) * abs_r(d) * rD; // c^2, in [1/2, 1]
     const Real rc = rsqrt_r(u);
     const Real c = u * rc;
     const Real h = (d >= Real(0) ? Real(0.5) : Real(-0.5)) * rD * rc; // sgn(d) / (2 D c)
@@ -640,3 +642,6 @@ __host__ __device__ __forceinline__ void renormalise(Real *t, Real ref)
 }
 
 } // namespace xf
+
+// float-float numbers (the XF_FP32X2 per-bin arithmetic) for the templates above
+#include "xf_ff.cuh"

@@ -40,7 +40,8 @@ enum { ERR_NONFINITE = 1, ERR_BARRIER = 2, ERR_LAUNCH = 4 };
 // variants of the per-bin arithmetic: plain; moments summed in compensated
 // FP32 (TwoSum) up to the warp; plain with the per-step restoration of each
 // bin's tr(rho0^2) (|P|^2 / 2 in two flavors) to its initial value
-enum { VAR_PLAIN = 0, VAR_COMP = 1, VAR_RENORM = 2 };
+enum { VAR_PLAIN = 0, VAR_COMP = 1, VAR_RENORM = 2, VAR_FF = 3 };
+
 // what the state planes hold: traceless density matrices, or one wavefunction
 // per initial flavor (2 n_f^2 reals per bin)
 enum { FORM_RHO = 0, FORM_PSI = 1 };
@@ -586,6 +587,31 @@ __device__ __forceinline__ void stage_issue(Real *col, const TileView<Real> &v, 
         for (int k = 0; k < 2 * S; ++k) cp_async4(col + (2 * S + k) * NT, v.aux + (size_t)k * v.npad + p);
 }
 
+// One bin's propagation T' = U T U^dagger of the predictor-corrector.  With
+// VAR_FF the state, Hamiltonian, tables and sums stay FP64 and only the
+// propagator (the eigendecomposition and U T U^dagger, nearly all of a
+// bin-step's arithmetic) runs in float-float on the FP32 pipes; its inputs
+// are rounded to float-float and its output read back as a double.
+template <int NF, typename Real, int VAR>
+__device__ __forceinline__ void propagate(const Real *h, StepLen<Real> dl, const Real *t, Real *out)
+{
+    if constexpr (VAR == VAR_FF) {
+        static_assert(sizeof(Real) == 8, "float-float propagation of FP64 state");
+        constexpr int S = Comp<NF>::S;
+        ff hf[S], tf[S], of[S];
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            hf[c] = ff(h[c]);
+            tf[c] = ff(t[c]);
+        }
+        prop<NF, ff>(hf, make_step_len(step_len_value(dl), (ff *)nullptr), tf, of);
+#pragma unroll
+        for (int c = 0; c < S; ++c) out[c] = to_double(of[c]);
+    } else {
+        prop<NF, Real>(h, dl, t, out);
+    }
+}
+
 // One stage of one tile: update every pair, accumulate and reduce the sums.
 template <int NF, int STEP, typename Real, int NT, int VAR, int NMOM, bool PF>
 __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int st, const Real *tb, Shared<NT> &sh,
@@ -682,6 +708,40 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
                     for (int c = 0; c < S; ++c) o[c] = bb[c];
                 }
             }
+        } else if constexpr (VAR == VAR_FF) {
+            // one copy of the float-float propagator in the code, run once per
+            // species (unrolled, the two copies overflow the instruction cache:
+            // the three-flavor workload ran 15 % and the ensemble 35 % slower)
+            const StepLen<Real> dl = load_dl(tb, smax, q);
+            const Acc wa = tb[2 * smax + q], wb = tb[3 * smax + q];
+#pragma unroll 1
+            for (int s = 0; s < 2; ++s) {
+                Real hs[S], rn[S], pr[S], o[S];
+#pragma unroll
+                for (int c = 0; c < S; ++c) hs[c] = s == 0 ? hn[c] : hb[c];
+                load_state<Real, S>(v.cur, v.npad, s, p, rn);
+                propagate<NF, Real, VAR>(hs, dl, rn, pr);
+                if (st == 0) {
+#pragma unroll
+                    for (int c = 0; c < S; ++c) o[c] = pr[c];
+                    store_state<Real, S>(v.aux, v.npad, s, p, o);
+                } else {
+                    Real pp[S];
+                    load_state<Real, S>(v.aux, v.npad, s, p, pp);
+#pragma unroll
+                    for (int c = 0; c < S; ++c) o[c] = Real(0.5) * (pp[c] + pr[c]);
+                    store_state<Real, S>(v.nxt, v.npad, s, p, o);
+                }
+                // this species' share of the weighted sums of rho_nu - conj(rho_nubar):
+                // the antineutrino enters with its diagonal and real parts negated
+                const Acc wa_s = s == 0 ? wa : -wa, wb_s = s == 0 ? wb : -wb;
+#pragma unroll
+                for (int c = 0; c < S; ++c) {
+                    const bool flip = NF == 2 ? c < 2 : (c < 2 || (c & 1) == 0);
+                    m[c] += (flip ? wa_s : wa) * (Acc)o[c];
+                    m[S + c] += (flip ? wb_s : wb) * (Acc)o[c];
+                }
+            }
         } else {
             const StepLen<Real> dl = load_dl(tb, smax, q);
 #pragma unroll
@@ -693,7 +753,7 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
                 } else {
                     load_state<Real, S>(v.cur, v.npad, s, p, rn);
                 }
-                prop<NF, Real>(s == 0 ? hn : hb, dl, rn, pr);
+                propagate<NF, Real, VAR>(s == 0 ? hn : hb, dl, rn, pr);
                 Real *o = (s == 0) ? on : ob;
                 if (st == 0) {
 #pragma unroll
@@ -714,7 +774,9 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
                 }
             }
         }
-        if constexpr (NMOM == 4)
+        if constexpr (VAR == VAR_FF && STEP == STEP_EXPH) {
+            // accumulated per species above
+        } else if constexpr (NMOM == 4)
             accum4<NF, Real, Acc>(on, ob, tb[2 * smax + q], tb[3 * smax + q], tb[(AB + 2) * smax + q],
                                   tb[(AB + 3) * smax + q], m);
         else if constexpr (VAR == VAR_COMP)
@@ -971,9 +1033,13 @@ __device__ __forceinline__ void finish_instance(const RunArgs &a, const Inst &in
 //   FP32, 256 threads (two flavors): 6 (40 registers, 68 bytes spilled): a
 //     stream of served jobs finished 11 % sooner than at 4 (64 registers),
 //     a 150-job pack ran 4 % faster.
-__host__ __device__ constexpr int min_blocks(int nt, int real_bytes, int nfm = 3)
+__host__ __device__ constexpr int min_blocks(int nt, int real_bytes, int nfm = 3, int var = 0)
 {
-    return nt == 128 ? (real_bytes == 8 ? 3 : (nfm == 0 ? 6 : 4)) : (real_bytes == 8 ? 2 : 6);
+    // float-float: 3 CTAs of 128 threads for one flavor count (the three-flavor
+    // workload ran 14 % faster than at 2), 2 for mixed packs (no spills; the
+    // ensemble ran 18 % faster than at 3)
+    return var == VAR_FF ? (nt == 128 ? (nfm == 0 ? 2 : 3) : 2)
+                         : nt == 128 ? (real_bytes == 8 ? 3 : (nfm == 0 ? 6 : 4)) : (real_bytes == 8 ? 2 : 6);
 }
 
 // NFM: 2 or 3 (every instance has that many flavors) or 0 (mixed pack);
@@ -982,7 +1048,7 @@ __host__ __device__ constexpr int min_blocks(int nt, int real_bytes, int nfm = 3
 // its problems may also have a single azimuth bin).  FORM: FORM_RHO, or
 // FORM_PSI (wavefunctions; plain arithmetic, two moments).
 template <int NFM, int STEP, typename Real, int NT, int VAR, int NMOM = 2, int FORM = FORM_RHO>
-__global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM)) xf_run_kernel(RunArgs a)
+__global__ void __launch_bounds__(NT, min_blocks(NT, sizeof(Real), NFM, VAR)) xf_run_kernel(RunArgs a)
 {
     extern __shared__ double s_dyn[];
     Real *const s_tab = (Real *)s_dyn;

@@ -184,7 +184,7 @@ int xf_server_create(const xf_server_cfg *cfg, xf_server **out)
         return XF_E_ARG;
     if (cfg->stepper == XF_EXPH_ADAPTIVE) return XF_E_UNSUPPORTED; // jobs advance in fixed chunks of steps
     if (cfg->stepper != XF_RK4 && cfg->stepper != XF_EXPH) return XF_E_ARG;
-    if (cfg->precision < XF_FP64 || cfg->precision > XF_FP32_M64_RENORM) return XF_E_ARG;
+    if (cfg->precision < XF_FP64 || cfg->precision > XF_FP32X2) return XF_E_ARG;
     if (cfg->n_flavor != 0 && cfg->n_flavor != 2 && cfg->n_flavor != 3) return XF_E_ARG;
     if (cfg->tile_pairs < 0) return XF_E_ARG;
     xf_server *s = new (std::nothrow) xf_server();

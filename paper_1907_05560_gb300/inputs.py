@@ -23,7 +23,7 @@ from typing import List, Tuple
 RK4, EXPH, EXPH_ADAPTIVE = 0, 1, 2
 BULB, MU_R4, SINGLE_ANGLE, CONST, CYLINDER = 0, 1, 2, 3, 4
 MATTER_NONE, MATTER_POWER, MATTER_EXP = 0, 1, 2
-FP64, FP32_M64, FP32_COMP, FP32_M64_RENORM = 0, 1, 2, 3
+FP64, FP32_M64, FP32_COMP, FP32_M64_RENORM, FP32X2 = 0, 1, 2, 3, 4
 FORM_RHO, FORM_PSI = 0, 1  # state: density matrices, or one wavefunction per initial flavor
 
 

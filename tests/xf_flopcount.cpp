@@ -84,6 +84,7 @@ static inline bool operator<(Cnt a, Cnt b) { return a.v < b.v; }
 static inline bool operator>=(Cnt a, Cnt b) { return a.v >= b.v; }
 static inline bool operator<=(Cnt a, Cnt b) { return a.v <= b.v; }
 static inline Cnt fabs(Cnt a) { return a.z ? a : val(std::fabs(a.v)); }
+static inline Cnt abs_r(Cnt a) { return fabs(a); }
 static inline Cnt fmax(Cnt a, Cnt b) { return val(std::fmax(a.v, b.v)); }
 
 #include "xf_math.cuh"
