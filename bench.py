@@ -232,6 +232,8 @@ def run_xf(args):
     p = I.bulb3f_1000x200().replace(seed=2 + rank)
     if args.precision == "fp32":
         p = p.replace(precision=I.FP32_M64)
+    elif args.precision == "fp32x2":
+        p = p.replace(precision=I.FP32X2)
 
     ctx = xf.Context(p, stream=stream)
     ctx.init_state(p.r0)
@@ -306,6 +308,11 @@ def run_xf(args):
         variants = {"fp32_comp": time_precision(I.FP32_COMP), "fp32_m64_renorm": time_precision(I.FP32_M64_RENORM)}
         variants["fp32_comp"]["precision"] = "FP32 bins, compensated FP32 moment sums to the warp"
         variants["fp32_m64_renorm"]["precision"] = "FP32_M64 plus per-step restoration of tr(T^2)"
+        variants["fp32x2"] = time_precision(I.FP32X2)
+        variants["fp32x2"]["precision"] = "FP64 state and sums, float-float propagator"
+        # the same counted work per bin-step as the FP64 kernel, against the FP64 peak
+        variants["fp32x2"]["fp64_class_tflops"] = FLOPS_PER_BIN_STEP[("exph", 3)] * variants["fp32x2"]["value"] / 1e12
+        variants["fp32x2"]["frac_of_fp64_peak"] = variants["fp32x2"]["fp64_class_tflops"] / peak64["derived_tflops"]
 
     # batched ensemble: 256 seeded problems (~40 M bins) in one persistent launch per call
     batched = None
@@ -353,9 +360,10 @@ def run_xf(args):
     kind = ("exph" if p.stepper == I.EXPH else "rk4", p.n_f)
     flops = FLOPS_PER_BIN_STEP[kind] * p.n_bins * chunk
     achieved = flops / avg_launch_s / 1e12
-    peak_meas = xf.peak(xf.PEAK_FP64_FMA if args.precision == "fp64" else xf.PEAK_FP32_FMA) / 1e12
+    fp64_class = args.precision in ("fp64", "fp32x2")  # FP32X2 is priced against the FP64 peak
+    peak_meas = xf.peak(xf.PEAK_FP64_FMA if fp64_class else xf.PEAK_FP32_FMA) / 1e12
     # derived ALU peak: SMs x (FP64: 2 FMA, FP32: 128 FMA) per clock x 2 flop x max clock
-    per_clk = 2 if args.precision == "fp64" else 128
+    per_clk = 2 if fp64_class else 128
     peak_nom = sms * per_clk * 2 * sm_max * 1e6 / 1e12
     # DRAM bytes (read + write) per radial step of this kernel on this workload, from
     # one ncu capture of a 5-step launch (dram__bytes_read.sum + dram__bytes_write.sum),
@@ -365,7 +373,8 @@ def run_xf(args):
                 "frac": achieved / peak_nom, "traffic": traffic,
                 "traffic_note": "scaled, not measured in this run: ncu DRAM bytes (read + write) of a 5-step "
                                 "launch (%s) x %d/5; the state planes are L2-resident" % (TRAFFIC_PROFILE, chunk),
-                "kernel": "xf_run_kernel<3,EXPH,%s>" % ("double" if args.precision == "fp64" else "float"),
+                "kernel": {"fp64": "xf_run_kernel<3,EXPH,double>", "fp32": "xf_run_kernel<3,EXPH,float>",
+                           "fp32x2": "xf_run_kernel<3,EXPH,double,VAR_FF>"}[args.precision],
                 "peak_source": "derived: %d SMs x %d FMA/clk x 2 x %.0f MHz (recipe FP64 1.25 TFLOP/s)" % (sms, per_clk, sm_max),
                 "peak_measured_fma": peak_meas, "frac_of_measured_fma": achieved / peak_meas,
                 "flop_per_bin_step": FLOPS_PER_BIN_STEP[kind],
@@ -418,7 +427,7 @@ def run_xf(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_sum / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32",
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp32x2": "f32x2"}[args.precision],
             "data": "synthetic (seeded initial state, paper's spectra)",
             "config": {"workload": WORKLOAD, "bins": p.n_bins, "n_u": p.n_u, "n_E": p.n_E, "n_f": p.n_f,
                        "radial_steps_per_step": chunk, "h_km": p.h, "ctas": ctas, "threads": threads,
@@ -968,7 +977,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="xf", choices=["xf", "reference"])
     ap.add_argument("--chunk", type=int, default=100, help="radial steps per bench step")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32x2"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-steps", type=int, default=250)
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")

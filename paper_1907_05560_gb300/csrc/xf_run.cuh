@@ -711,9 +711,8 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
         } else if constexpr (VAR == VAR_FF) {
             // one copy of the float-float propagator in the code, run once per
             // species (unrolled, the two copies overflow the instruction cache:
-            // the three-flavor workload ran 15 % and the ensemble 35 % slower)
+            // the three-flavor workload ran 18 % and the ensemble 53 % slower)
             const StepLen<Real> dl = load_dl(tb, smax, q);
-            const Acc wa = tb[2 * smax + q], wb = tb[3 * smax + q];
 #pragma unroll 1
             for (int s = 0; s < 2; ++s) {
                 Real hs[S], rn[S], pr[S], o[S];
@@ -732,14 +731,13 @@ __device__ __forceinline__ void stage_tile(const TileView<Real> v, int smax, int
                     for (int c = 0; c < S; ++c) o[c] = Real(0.5) * (pp[c] + pr[c]);
                     store_state<Real, S>(v.nxt, v.npad, s, p, o);
                 }
-                // this species' share of the weighted sums of rho_nu - conj(rho_nubar):
-                // the antineutrino enters with its diagonal and real parts negated
-                const Acc wa_s = s == 0 ? wa : -wa, wb_s = s == 0 ? wb : -wb;
+                // the weighted sums of the stage output, as the prologue forms them
+                // from stored states (so that chunked launches equal one launch)
+                if (s == 0) {
 #pragma unroll
-                for (int c = 0; c < S; ++c) {
-                    const bool flip = NF == 2 ? c < 2 : (c < 2 || (c & 1) == 0);
-                    m[c] += (flip ? wa_s : wa) * (Acc)o[c];
-                    m[S + c] += (flip ? wb_s : wb) * (Acc)o[c];
+                    for (int c = 0; c < S; ++c) on[c] = o[c];
+                } else {
+                    accum<NF, Real, Acc>(on, o, tb[2 * smax + q], tb[3 * smax + q], m);
                 }
             }
         } else {

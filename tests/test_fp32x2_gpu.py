@@ -10,7 +10,7 @@ Against the FP64 oracle of the same method:
 * the ensemble problems on which FP32 bins miss the 1e-3 survival-probability
   target (large mu0, two and three flavors), whole 1000-step runs in one
   batch, gated at 1e-3 like the FP32 target (and printed);
-and the pack rules: a batch equals each problem alone bitwise, and the
+and the pack rules: a batch and a server equal each problem alone bitwise, and the
 steppers the precision does not run are refused.
 """
 import os
@@ -173,3 +173,52 @@ def test_other_steppers_are_refused(xf, stepper):
     with pytest.raises(xf.XFError) as e:
         xf.Context(p)
     assert "XF_E_UNSUPPORTED" in str(e.value)
+
+
+def test_served_jobs_equal_alone(xf, orc):
+    """A server in FP32X2: jobs queued behind each other share launches and
+    each result is bitwise that of the job alone (same tile size)."""
+    g = I.SplitMix64(77)
+    ps = []
+    for k in range(4):
+        steps = g.randint(30, 90)
+        ps.append(I.Problem(n_E=g.randint(8, 40), n_u=g.randint(8, 60), n_f=2, mu0=10 ** (4 + 2 * g.uniform()),
+                            hierarchy=1 if k % 2 else -1, theta=(0.1 + 0.4 * g.uniform(), 0, 0), stepper=I.EXPH,
+                            precision=I.FP32X2, r0=50.0, r1=50.0 + 0.01 * steps, n_steps=steps, eps=1e-3,
+                            seed=700 + k))
+    rho0s = [orc.init_state(p) for p in ps]
+    tile = 512
+    srv = xf.Server(max_jobs=2, mem_budget_bytes=1 << 30, chunk_steps=20, stepper=I.EXPH,
+                    precision=I.FP32X2, tile_pairs=tile)
+    ids = [srv.submit(p, rho0=r, keep_state=True) for p, r in zip(ps, rho0s)]
+    srv.drain(timeout_s=120.0)
+    for j, p, r in zip(ids, ps, rho0s):
+        meta, got = srv.poll(j, want_state=True)
+        assert meta["status"] == "XF_OK" and meta["steps"] == p.n_steps
+        c = xf.Context(p)
+        c.set_option(xf.OPT_TILE_PAIRS, tile)
+        c.set_state(r, p.r0)
+        c.step(p.n_steps, p.h)
+        assert np.array_equal(got, c.get_state()[0])
+        c.close()
+    assert srv.stats()["max_resident"] == 2
+    srv.close()
+
+
+def test_chunked_launches_equal_one_launch(xf, orc):
+    """The moments a launch's prologue forms from the stored state equal those
+    the previous launch formed from its last stage's output, bit for bit, so
+    a run split into launches is the run in one launch."""
+    for kw in ({}, THREE):
+        p = small(n_E=23, n_u=31, n_steps=60, r1=50.6, seed=31, **kw)
+        rho0 = orc.init_state(p)
+        out = []
+        for chunks in ([60], [20, 20, 20], [7, 53]):
+            c = xf.Context(p)
+            c.set_option(xf.OPT_TILE_PAIRS, 512)
+            c.set_state(rho0, p.r0)
+            for n in chunks:
+                c.step(n, p.h)
+            out.append(c.get_state()[0])
+            c.close()
+        assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
