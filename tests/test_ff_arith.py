@@ -9,7 +9,9 @@ double-float unit roundoff is 2^-47 = 7.1e-15 for a correctly rounded
 operation; these sloppy forms stay within a few units), the reciprocal
 square root within 3e-14; one propagation within 1e-10 of the double
 result for |T| <= 1 and phases up to 3e3 rad (a relative eigenvalue error
-of a few 1e-15 times the phase)."""
+of a few 1e-15 times the phase); the phase sine-cosine (Cody-Waite reduction
+by pi/2 and Taylor polynomials in float-float) within four units of the
+float-float rounding of the phase itself."""
 import os
 import shutil
 import subprocess
@@ -45,3 +47,4 @@ def test_float_float_arithmetic_and_propagators(tmp_path):
     assert r["add_rel"] < 3e-14 and r["mul_rel"] < 3e-14 and r["fma_rel"] < 3e-14, out
     assert r["rsqrt_rel"] < 3e-14, out
     assert r["prop3_abs"] < 1e-10 and r["prop2_abs"] < 1e-10, out
+    assert r["phase_over"] < 4.0, out

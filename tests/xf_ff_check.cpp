@@ -7,7 +7,9 @@
 //   rsqrt_rel: relative error of rsqrt_r over 2^-60 .. 2^60;
 //   prop3_abs, prop2_abs: max |T'_ff - T'_double| over the packed components
 //     for |T| <= 1, Hamiltonians with eigenvalue spreads 1e-3 .. 1e4 and
-//     path lengths 0.01 .. 0.3 (phases up to 3e3 rad).
+//     path lengths 0.01 .. 0.3 (phases up to 3e3 rad);
+//   phase_over: the phase sine-cosine's largest error in units of the
+//     float-float rounding of the phase itself (|phase| 2^-47 + 1e-15).
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -75,7 +77,20 @@ int main()
         prop2<double>(hd, make_step_len(dl, (double *)nullptr), td, od);
         for (int k = 0; k < 3; ++k) prop2_abs = std::fmax(prop2_abs, std::fabs(to_double(of[k]) - od[k]));
     }
-    std::printf("add_rel %.3e\nmul_rel %.3e\nfma_rel %.3e\nrsqrt_rel %.3e\nprop3_abs %.3e\nprop2_abs %.3e\n", add_rel,
-                mul_rel, fma_rel, rsqrt_rel, prop3_abs, prop2_abs);
+    // the phase sine-cosine: error relative to the float-float rounding of
+    // the phase itself (|phase| 2^-47, plus 1e-15), phases 1e-6 .. 2e4 rad
+    double phase_over = 0;
+    for (int i = 0; i < 1000000; ++i) {
+        const double dl = 0.001 + 0.3 * uniform01();
+        const double mag = std::ldexp(1.0, -20 + (int)(34 * uniform01())) * (1.0 + uniform01());
+        const ff lam((uniform01() < 0.5 ? -mag : mag) / dl);
+        ff s, c;
+        phase_sincos(lam, make_step_len(dl, (ff *)nullptr), &s, &c);
+        const long double ph = exact(lam) * (long double)dl;
+        const long double e = std::fmax(std::fabs(std::sin(ph) - exact(s)), std::fabs(std::cos(ph) - exact(c)));
+        phase_over = std::fmax(phase_over, (double)(e / (std::fabs(ph) * 7.1e-15L + 1e-15L)));
+    }
+    std::printf("add_rel %.3e\nmul_rel %.3e\nfma_rel %.3e\nrsqrt_rel %.3e\nprop3_abs %.3e\nprop2_abs %.3e\n"
+                "phase_over %.3f\n", add_rel, mul_rel, fma_rel, rsqrt_rel, prop3_abs, prop2_abs, phase_over);
     return 0;
 }
