@@ -1033,9 +1033,10 @@ __device__ __forceinline__ void finish_instance(const RunArgs &a, const Inst &in
 //     a 150-job pack ran 4 % faster.
 __host__ __device__ constexpr int min_blocks(int nt, int real_bytes, int nfm = 3, int var = 0)
 {
-    // float-float: 3 CTAs of 128 threads (the three-flavor workload ran 14 %
-    // and the ensemble 2 % faster than at 2)
-    return var == VAR_FF ? (nt == 128 ? 3 : 2)
+    // float-float: 4 CTAs of 128 threads (128 registers; despite the spills the
+    // three-flavor workload ran 4 % and the ensemble 1 % faster than at 3, and
+    // 3 ran 14 % and 2 % faster than 2: the kernel wants warps)
+    return var == VAR_FF ? (nt == 128 ? 4 : 2)
                          : nt == 128 ? (real_bytes == 8 ? 3 : (nfm == 0 ? 6 : 4)) : (real_bytes == 8 ? 2 : 6);
 }
 
