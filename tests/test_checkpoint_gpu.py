@@ -32,6 +32,8 @@ CASES = {
                              eps=1e-3, seed=5),
     "3f-exph-renorm": I.Problem(n_E=20, n_u=17, stepper=I.EXPH, precision=I.FP32_M64_RENORM, r0=60.0, r1=60.8,
                                 n_steps=80, eps=1e-3, seed=6, mu0=1e4, **THREE),
+    "3f-exph-fp32x2": I.Problem(n_E=20, n_u=17, stepper=I.EXPH, precision=I.FP32X2, r0=60.0, r1=60.8,
+                                n_steps=80, eps=1e-3, seed=7, mu0=1e4, **THREE),
 }
 
 
