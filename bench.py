@@ -915,16 +915,23 @@ def serve_window(xf, I, torch, rate, window, budget, chunk, drain_s):
     first = [x for x, h in zip(all_lat, half) if h]
     second = [x for x, h in zip(all_lat, half) if not h]
     p99_1, p99_2 = pct(first, 0.99), pct(second, 0.99)
-    # sustainable: every job finished within the drain allowance, and the tail
-    # latency of the window's second half is no worse than its first half's
-    stable = censored == 0 and p99_1 is not None and p99_2 is not None and p99_2 <= 1.5 * p99_1 + 0.25
+    # the arrivals' work per second of window against what the server got
+    # through per second while busy: above 1 a backlog builds
+    offered = sum(p.n_bins * p.n_steps for _, p in arrivals[:len(ids)]) / window
+    busy = st["bin_steps"] / max(st["busy_s"], 1e-9)
+    # sustainable: every job finished within the drain allowance, the tail
+    # latency of the window's second half is no worse than its first half's,
+    # and the offered work exceeds the busy throughput by under 5 % (a backlog
+    # growing by less than 1.5 s of work over a 30 s window)
+    stable = (censored == 0 and p99_1 is not None and p99_2 is not None and p99_2 <= 1.5 * p99_1 + 0.25
+              and offered <= 1.05 * busy)
     return {"rate_jobs_per_s": rate, "window_s": window, "drain_limit_s": drain_s, "jobs": len(ids),
             "finished": len(lat), "unfinished_at_cutoff": censored,
             "p50_s": pct(all_lat, 0.50), "p99_s": pct(all_lat, 0.99),
             "percentiles_are_lower_bounds": censored > 0,
             "p99_first_half_s": p99_1, "p99_second_half_s": p99_2, "stable": stable,
             "value": work / (t_end - t0), "unit": UNIT,
-            "gpu_busy_value": st["bin_steps"] / max(st["busy_s"], 1e-9),
+            "gpu_busy_value": busy, "offered_bin_steps_per_s": offered, "offered_over_busy": offered / busy,
             "max_resident": st["max_resident"], "epochs": st["epochs"]}
 
 
@@ -1001,7 +1008,7 @@ def main():
     ap.add_argument("--batch-dynamic", type=int, default=0, choices=[0, 1],
                     help="batched leg with --skip-tune: dynamic tile claiming")
     ap.add_argument("--adapt-iters", type=int, default=30, help="attempts per error-controlled bench step")
-    ap.add_argument("--serve-rate", type=float, default=10.0,
+    ap.add_argument("--serve-rate", type=float, default=16.0,
                     help="sustained arrival rate, jobs/s (the highest stable rate of the --serve-search sweep)")
     ap.add_argument("--serve-window", type=float, default=30.0, help="arrival window of each serving run, s")
     ap.add_argument("--serve-drain", type=float, default=30.0,
@@ -1010,7 +1017,7 @@ def main():
                     help="seconds after the window before the 200 jobs/s run is cut off")
     ap.add_argument("--serve-chunk", type=int, default=200, help="radial steps per serving epoch")
     ap.add_argument("--serve-search", action="store_true", help="also sweep the arrival rates of --serve-rates")
-    ap.add_argument("--serve-rates", default="20,24,28,32,40,48", help="rates for --serve-search, jobs/s")
+    ap.add_argument("--serve-rates", default="8,12,16,18,20,24,28,40", help="rates for --serve-search, jobs/s")
     ap.add_argument("--alone-jobs", type=int, default=20, help="jobs timed alone in FP64")
     ap.add_argument("--alone-steps", type=int, default=2000, help="steps per job timed alone in FP64")
     args = ap.parse_args()
