@@ -93,7 +93,10 @@ enum xf_precision {
                      products and Knuth's sums) on the FP32 pipes.  XF_EXPH only; fixed steps,
                      density matrices, bulb-type geometries, one azimuth bin; batches and the
                      server accept it.  Error per propagation about 1e-14 of |T| (FP32 bins:
-                     1.5e-7), so it meets the FP32 target where FP32 rounding is amplified */
+                     1.5e-7), so it meets the FP32 target where FP32 rounding is amplified.
+                     Float-float numbers keep float's exponent range: Hamiltonian entries
+                     and their squares must stay within 1e-38 .. 3e38 (km^-1), else the run
+                     stops with XF_E_NONFINITE */
 };
 enum xf_geometry {
     XF_GEOM_BULB = 0,         /* Eq. 3.13-3.15: w_u = x^2 du/(2 cos_u), x = R/r; dl/dr = 1/cos_u */

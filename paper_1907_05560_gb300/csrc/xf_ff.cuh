@@ -42,7 +42,7 @@ struct ff {
     ff() = default;
     __host__ __device__ constexpr ff(float h, float l) : hi(h), lo(l) {}
     __host__ __device__ ff(float f) : hi(f), lo(0.0f) {}
-    __host__ __device__ ff(int i) : hi((float)i), lo(0.0f) {}
+    __host__ __device__ ff(int i) : hi((float)i), lo(0.0f) {} // the small literals of the templates
     // the double rounded to float, and the rest rounded to float
     __host__ __device__ ff(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
 };
