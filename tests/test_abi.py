@@ -94,3 +94,26 @@ def test_null_handles_are_errors_not_crashes(lib):
     assert lib.xf_angle_average(None, 0, None, 0) == E
     assert lib.xf_evolve(None, 1.0, 1, 0.1) == E
     assert lib.xf_autotune(None, 1, 0.0, None, 0, None, None) == E
+
+
+@pytest.mark.parametrize("mutate,want", [
+    (lambda p: setattr(p, "precision", 5), "XF_E_ARG"),
+    (lambda p: (setattr(p, "precision", 4), setattr(p, "stepper", 0)), "XF_E_UNSUPPORTED"),  # RK4
+    (lambda p: (setattr(p, "precision", 4), setattr(p, "stepper", 2)), "XF_E_UNSUPPORTED"),  # error-controlled
+    (lambda p: (setattr(p, "precision", 4), setattr(p, "stepper", 1), setattr(p, "n_phi", 4)), "XF_E_UNSUPPORTED"),
+    (lambda p: (setattr(p, "precision", 4), setattr(p, "stepper", 1), setattr(p, "form", 1)), "XF_E_UNSUPPORTED"),
+    (lambda p: (setattr(p, "precision", 4), setattr(p, "stepper", 1), setattr(p, "geometry", 4)),
+     "XF_E_UNSUPPORTED"),
+])
+def test_float_float_precision_refusals_without_gpu(lib, mutate, want):
+    """XF_FP32X2 runs the predictor-corrector on density matrices of the
+    bulb-type geometries with one azimuth bin; the rest is refused before
+    any device call."""
+    from paper_1907_05560_gb300 import xf
+    p = xf.XFParams()
+    lib.xf_params_default(ctypes.byref(p))
+    mutate(p)
+    h = ctypes.c_void_p(123)
+    rc = lib.xf_create(32, 16, 2, ctypes.byref(p), ctypes.byref(h))
+    assert rc == xf.STATUS_CODE[want], lib.xf_last_error(None).decode()
+    assert h.value is None
